@@ -1,0 +1,179 @@
+"""Closed forms and master-equation solutions that pin the oracle to the mathematics.
+
+TEST INFRASTRUCTURE ONLY.  Nothing here calls the C oracle: the rate functions are written out
+again from the model definitions so that a mistake in the oracle's propensities cannot hide
+behind a shared formula.
+
+  * 1-D birth-death chains: stationary law by detailed balance and the mean first-passage time
+    T(a -> b) = sum_{k=a}^{b-1} (sum_{j<=k} pi_j) / (lambda_k pi_k) (standard result for a chain
+    reflected at 0), used for Eq. "mfpt" checks and for the Schloegl MFPT the paper quotes as
+    about 5e4 s (Sec. III.B.3);
+  * the immigration-death process 0 -> X (kb), X -> 0 (kd x): X(t) = Binomial(x0, e^{-kd t})
+    + Poisson(kb/kd (1 - e^{-kd t})), independent, which tends to Poisson(kb/kd);
+  * truncated chemical master equations (CME) solved with a matrix exponential (1-D transients,
+    the Schloegl P(X >= 700, t=5) = 1.148e-9 of Sec. III.B.3) or a sparse linear solve (2-D
+    mean first-passage times of the toggle switch);
+  * the maximum-likelihood transition time of brute-force runs (Eq. "mld", Sec. II.C).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy import sparse
+from scipy.linalg import expm
+from scipy.sparse.linalg import expm_multiply, spsolve
+from scipy.special import gammaln, logsumexp
+
+
+# ----------------------------------------------------------------------------------------------
+# model rate functions, written out from the paper's reaction schemes
+# ----------------------------------------------------------------------------------------------
+def birth_death_rates(kb=10.0, kd=0.1):
+    return (lambda x: np.full(np.shape(x), kb, dtype=np.float64),
+            lambda x: kd * np.asarray(x, dtype=np.float64))
+
+
+def schlogl_rates(c1=3e-7, c2=1e-4, c3=1e-3, c4=3.5, A=1e5, B=2e5):
+    """Schloegl model (Sec. III.B.1) with combinatorial mass action: A+2X->3X at c1 A X(X-1)/2,
+    3X->A+2X at c2 X(X-1)(X-2)/6, B->X at c3 B, X->B at c4 X."""
+    def birth(x):
+        x = np.asarray(x, dtype=np.float64)
+        return c1 * A * x * (x - 1) / 2.0 + c3 * B
+
+    def death(x):
+        x = np.asarray(x, dtype=np.float64)
+        return c2 * x * (x - 1) * (x - 2) / 6.0 + c4 * x
+    return birth, death
+
+
+# ----------------------------------------------------------------------------------------------
+# 1-D birth-death chains
+# ----------------------------------------------------------------------------------------------
+def bd_log_stationary(birth, death, N: int) -> np.ndarray:
+    """log of the unnormalised stationary measure on {0..N}: pi_{x+1}/pi_x = birth(x)/death(x+1)."""
+    x = np.arange(N)
+    steps = np.log(birth(x)) - np.log(death(x + 1))
+    return np.concatenate([[0.0], np.cumsum(steps)])
+
+
+def bd_stationary(birth, death, N: int) -> np.ndarray:
+    lp = bd_log_stationary(birth, death, N)
+    return np.exp(lp - logsumexp(lp))
+
+
+def bd_modes(birth, death, N: int):
+    """Local maxima and minima (interior) of the stationary law."""
+    lp = bd_log_stationary(birth, death, N)
+    maxima = [x for x in range(1, N) if lp[x] >= lp[x - 1] and lp[x] >= lp[x + 1]]
+    minima = [x for x in range(1, N) if lp[x] <= lp[x - 1] and lp[x] <= lp[x + 1]]
+    return maxima, minima
+
+
+def bd_mfpt(a: int, b: int, birth, death) -> float:
+    """Mean first-passage time from a up to b > a of a chain on {0,1,...} reflected at 0."""
+    assert b > a >= 0
+    lp = bd_log_stationary(birth, death, b)
+    total = 0.0
+    for k in range(a, b):
+        # expected time to go from k to k+1
+        total += np.exp(logsumexp(lp[:k + 1]) - lp[k] - np.log(birth(np.array([k]))[0]))
+    return float(total)
+
+
+def bd_generator(birth, death, N: int) -> sparse.csr_matrix:
+    """Generator Q (rows = from) of the chain truncated to {0..N} (no birth out of N)."""
+    x = np.arange(N + 1)
+    up = birth(x).astype(np.float64)
+    up[-1] = 0.0
+    down = death(x).astype(np.float64)
+    down[0] = 0.0
+    Q = sparse.diags([-(up + down), up[:-1], down[1:]], [0, 1, -1], shape=(N + 1, N + 1), format="csr")
+    return Q
+
+
+def bd_transient(birth, death, x0: int, t: float, N: int) -> np.ndarray:
+    """P(X(t) = x | X(0) = x0) on {0..N} by the matrix exponential of the truncated CME."""
+    p0 = np.zeros(N + 1)
+    p0[x0] = 1.0
+    Q = bd_generator(birth, death, N)
+    return expm_multiply((Q.T * t).tocsr(), p0)
+
+
+# ----------------------------------------------------------------------------------------------
+# immigration-death closed form
+# ----------------------------------------------------------------------------------------------
+def log_poisson_pmf(x, mean: float) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float64)
+    return x * np.log(mean) - mean - gammaln(x + 1)
+
+
+def immigration_death_pmf(x0: int, kb: float, kd: float, t: float, N: int) -> np.ndarray:
+    """Law of X(t) on {0..N}: Binomial(x0, e^{-kd t}) convolved with Poisson(kb/kd (1-e^{-kd t}))."""
+    p = np.exp(-kd * t)
+    k = np.arange(x0 + 1)
+    lb = (gammaln(x0 + 1) - gammaln(k + 1) - gammaln(x0 - k + 1) + k * np.log(p)
+          + (x0 - k) * np.log1p(-p)) if 0 < p < 1 else np.where(k == x0, 0.0, -np.inf)
+    mean = kb / kd * (1 - p)
+    x = np.arange(N + 1)
+    lpo = log_poisson_pmf(x, mean)
+    out = np.full(N + 1, -np.inf)
+    for xi in range(N + 1):
+        kk = k[k <= xi]
+        out[xi] = logsumexp(lb[kk] + lpo[xi - kk])
+    return np.exp(out)
+
+
+# ----------------------------------------------------------------------------------------------
+# 2-D truncated CME: toggle switch mean first-passage time
+# ----------------------------------------------------------------------------------------------
+def toggle_mfpt(a_u: float, a_v: float, start, in_target, d=1.0, K=1.0, n=2, b0=0.0,
+                Umax: int = 200, Vmax: int = 200) -> float:
+    """MFPT from ``start`` into the set ``in_target(u, v)`` for the two-gene toggle
+    0->U at a_u/(1+(V/K)^n), 0->V at a_v/(1+(U/K)^n), U->0 and V->0 at d per molecule, plus basal
+    production b0.  Solves sum_y Q(x,y) T(y) = -1 off the target with T = 0 on it, on the grid
+    truncated to [0,Umax] x [0,Vmax] (no production out of the box)."""
+    nu, nv = Umax + 1, Vmax + 1
+    idx = lambda u, v: u * nv + v
+    rows, cols, vals = [], [], []
+    rhs = np.zeros(nu * nv)
+    for u in range(nu):
+        for v in range(nv):
+            i = idx(u, v)
+            if in_target(u, v):
+                rows.append(i); cols.append(i); vals.append(1.0)
+                continue
+            rhs[i] = -1.0
+            out = 0.0
+            moves = []
+            if u < Umax:
+                moves.append((idx(u + 1, v), a_u / (1.0 + (v / K) ** n) + b0))
+            if v < Vmax:
+                moves.append((idx(u, v + 1), a_v / (1.0 + (u / K) ** n) + b0))
+            if u > 0:
+                moves.append((idx(u - 1, v), d * u))
+            if v > 0:
+                moves.append((idx(u, v - 1), d * v))
+            for j, r in moves:
+                if r > 0:
+                    rows.append(i); cols.append(j); vals.append(r)
+                    out += r
+            rows.append(i); cols.append(i); vals.append(-out)
+    A = sparse.csr_matrix((vals, (rows, cols)), shape=(nu * nv, nu * nv))
+    T = spsolve(A.tocsc(), rhs)
+    return float(T[idx(*start)])
+
+
+# ----------------------------------------------------------------------------------------------
+# brute-force estimator of a transition time (Eq. "mld", Sec. II.C)
+# ----------------------------------------------------------------------------------------------
+def mle_transition_time(T: float, N: int, times) -> tuple:
+    """mu = (1 - n/N) T + (1/n) sum t_i and sigma = mu / sqrt(n), for n transitions seen at times
+    t_i among N runs of length T."""
+    times = np.asarray(times, dtype=np.float64)
+    n = len(times)
+    mu = (1.0 - n / N) * T + times.sum() / n
+    return mu, mu / np.sqrt(n)
+
+
+def small_generator_expm(Q: np.ndarray, p0: np.ndarray, t: float) -> np.ndarray:
+    """Dense matrix exponential for tiny state spaces (reference for brute-force checks)."""
+    return p0 @ expm(Q * t)

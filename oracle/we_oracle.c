@@ -1,0 +1,495 @@
+/*
+ * we_oracle.c -- plain CPU oracle for the weighted-ensemble Gillespie-SSA hot path of
+ * arXiv:1303.5986.  TEST INFRASTRUCTURE ONLY: the product library never links or calls it.
+ *
+ * Written to be read against the paper, not to be fast: propensities are recomputed in full
+ * after every event, the canonical propensity tree is rebuilt from the leaves every time it is
+ * needed, and every bin is searched linearly.  Floating point is IEEE double throughout; build
+ * with -ffp-contract=off so that no multiply-add is fused (the rounding of every operation is
+ * part of the definition below).
+ */
+#include "we_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------------------------
+ * Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+ * SC'11).  One round multiplies counter words 0 and 2 by the two Philox multipliers, keeps
+ * the 64-bit products' halves, and mixes the high halves with the other two counter words and
+ * the key; the key is bumped by the two Weyl constants between rounds.  Ten rounds.
+ * ------------------------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t mul0 = 0xD2511F53u, mul1 = 0xCD9E8D57u;
+  const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)mul0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)mul1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += weyl0;
+    k1 += weyl1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double orc_u01(uint32_t hi, uint32_t lo) {
+  uint64_t m = ((uint64_t)hi << 20) | (uint64_t)(lo >> 12);   /* 52 random bits */
+  return (double)(2u * m + 1u) * 0x1p-53;                      /* exact, in (0, 1) */
+}
+
+/* Key of a run: word 0 = low half of the seed, word 1 = high half plus the run id (mod 2^32). */
+static void run_key(uint64_t seed, uint32_t run_id, uint32_t key[2]) {
+  key[0] = (uint32_t)seed;
+  key[1] = (uint32_t)(seed >> 32) + run_id;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Network.  Mass action with combinatorial factors: a reactant taken m times contributes
+ * C(x, m) = x(x-1).../m!; this is the convention under which the Schloegl model (Sec. III.B.1,
+ * Eq. "schlogl") has its stable states at X=82 and X=563 and barrier at X=256 (Sec. III.B.3).
+ * Species held constant (A and B in the Schloegl model) are folded into the rate constant.
+ * Hill repression (Sec. III.C.1): a = c / (1 + (y/K)^n), written as c K^n / (K^n + y^n).
+ * ------------------------------------------------------------------------------------------ */
+struct orc_net {
+  int32_t S, M;
+  int32_t *n_reac;      /* dynamic reactant entries per reaction (<= 3) */
+  int32_t *reac_sp;     /* M x 3 */
+  int32_t *reac_m;      /* M x 3 */
+  double *keff;         /* mass action: folded rate constant; Hill: c * K^n (folded) */
+  int32_t *law;
+  int32_t *hill_sp;
+  int32_t *hill_n;
+  double *hill_Kn;      /* K^n */
+  int32_t *d_ptr, *d_sp, *d_val;   /* net change of dynamic species per reaction */
+};
+
+static int64_t binom_small(int64_t x, int32_t m) {
+  if (m == 1) return x;
+  if (m == 2) return x * (x - 1) / 2;
+  return x * (x - 1) * (x - 2) / 6;
+}
+
+void orc_net_destroy(orc_net *n) {
+  if (!n) return;
+  free(n->n_reac); free(n->reac_sp); free(n->reac_m); free(n->keff); free(n->law);
+  free(n->hill_sp); free(n->hill_n); free(n->hill_Kn); free(n->d_ptr); free(n->d_sp); free(n->d_val);
+  free(n);
+}
+
+int orc_net_create(const orc_network_in *in, orc_net **out) {
+  *out = NULL;
+  if (!in || in->n_species < 1 || in->n_reactions < 1) return ORC_EINVAL;
+  const int32_t S = in->n_species, M = in->n_reactions;
+  if (!in->reac_ptr || !in->prod_ptr || !in->rate) return ORC_EINVAL;
+  orc_net *n = (orc_net *)calloc(1, sizeof(orc_net));
+  if (!n) return ORC_ENOMEM;
+  n->S = S; n->M = M;
+  n->n_reac = calloc(M, sizeof(int32_t)); n->reac_sp = calloc(3 * (size_t)M, sizeof(int32_t));
+  n->reac_m = calloc(3 * (size_t)M, sizeof(int32_t)); n->keff = calloc(M, sizeof(double));
+  n->law = calloc(M, sizeof(int32_t)); n->hill_sp = calloc(M, sizeof(int32_t));
+  n->hill_n = calloc(M, sizeof(int32_t)); n->hill_Kn = calloc(M, sizeof(double));
+  n->d_ptr = calloc((size_t)M + 1, sizeof(int32_t));
+  n->d_sp = calloc((size_t)M * S, sizeof(int32_t)); n->d_val = calloc((size_t)M * S, sizeof(int32_t));
+  int64_t *reac_mult = calloc(S, sizeof(int64_t)), *net = calloc(S, sizeof(int64_t));
+  if (!n->n_reac || !n->reac_sp || !n->reac_m || !n->keff || !n->law || !n->hill_sp || !n->hill_n ||
+      !n->hill_Kn || !n->d_ptr || !n->d_sp || !n->d_val || !reac_mult || !net) {
+    free(reac_mult); free(net); orc_net_destroy(n); return ORC_ENOMEM;
+  }
+  int rc = ORC_OK;
+  int32_t nd = 0;
+  for (int32_t j = 0; j < M && rc == ORC_OK; ++j) {
+    memset(reac_mult, 0, sizeof(int64_t) * S);
+    memset(net, 0, sizeof(int64_t) * S);
+    int32_t order = 0;
+    for (int32_t e = in->reac_ptr[j]; e < in->reac_ptr[j + 1]; ++e) {
+      int32_t s = in->reac_species[e], m = in->reac_mult[e];
+      if (s < 0 || s >= S || m < 1 || m > 3) { rc = ORC_EINVAL; break; }
+      reac_mult[s] += m; net[s] -= m; order += m;
+    }
+    for (int32_t e = in->prod_ptr[j]; e < in->prod_ptr[j + 1] && rc == ORC_OK; ++e) {
+      int32_t s = in->prod_species[e], m = in->prod_mult[e];
+      if (s < 0 || s >= S || m < 0) { rc = ORC_EINVAL; break; }
+      net[s] += m;
+    }
+    if (rc != ORC_OK) break;
+    if (order > 3) { rc = ORC_EINVAL; break; }
+    double c = in->rate[j];
+    if (!(c >= 0.0) || isinf(c)) { rc = ORC_EINVAL; break; }
+    int32_t law = in->rate_law ? in->rate_law[j] : ORC_MASS_ACTION;
+    if (law != ORC_MASS_ACTION && law != ORC_HILL_REPRESSION) { rc = ORC_EINVAL; break; }
+    /* fold held-constant reactants, ascending species order */
+    double k = c;
+    int32_t nr = 0;
+    for (int32_t s = 0; s < S; ++s) {
+      if (reac_mult[s] == 0) continue;
+      int32_t fixed = in->fixed_count ? in->fixed_count[s] : -1;
+      if (fixed >= 0) {
+        k = k * (double)binom_small(fixed, (int32_t)reac_mult[s]);
+      } else {
+        n->reac_sp[3 * j + nr] = s;
+        n->reac_m[3 * j + nr] = (int32_t)reac_mult[s];
+        ++nr;
+      }
+    }
+    n->n_reac[j] = nr;
+    n->law[j] = law;
+    if (law == ORC_HILL_REPRESSION) {
+      if (!in->hill_species || !in->hill_K || !in->hill_n || nr != 0) { rc = ORC_EINVAL; break; }
+      int32_t hs = in->hill_species[j], hn = in->hill_n[j];
+      double K = in->hill_K[j];
+      if (hs < 0 || hs >= S || hn < 1 || hn > 3 || !(K > 0.0) || isinf(K)) { rc = ORC_EINVAL; break; }
+      double Kn = K;
+      for (int32_t p = 1; p < hn; ++p) Kn = Kn * K;
+      n->hill_sp[j] = hs; n->hill_n[j] = hn; n->hill_Kn[j] = Kn;
+      n->keff[j] = k * Kn;
+    } else {
+      n->keff[j] = k;
+    }
+    n->d_ptr[j] = nd;
+    for (int32_t s = 0; s < S; ++s) {
+      int32_t fixed = in->fixed_count ? in->fixed_count[s] : -1;
+      if (fixed >= 0 || net[s] == 0) continue;
+      n->d_sp[nd] = s; n->d_val[nd] = (int32_t)net[s]; ++nd;
+    }
+  }
+  n->d_ptr[M] = nd;
+  free(reac_mult); free(net);
+  if (rc != ORC_OK) { orc_net_destroy(n); return rc; }
+  *out = n;
+  return ORC_OK;
+}
+
+int32_t orc_net_n_species(const orc_net *n) { return n->S; }
+int32_t orc_net_n_reactions(const orc_net *n) { return n->M; }
+double orc_net_keff(const orc_net *n, int32_t j) { return n->keff[j]; }
+
+void orc_propensities(const orc_net *n, const int32_t *x, double *a) {
+  for (int32_t j = 0; j < n->M; ++j) {
+    if (n->law[j] == ORC_HILL_REPRESSION) {
+      int64_t y = x[n->hill_sp[j]];
+      int64_t yn = y;
+      for (int32_t p = 1; p < n->hill_n[j]; ++p) yn *= y;
+      double den = n->hill_Kn[j] + (double)yn;
+      a[j] = n->keff[j] / den;
+    } else {
+      int64_t h = 1;
+      for (int32_t r = 0; r < n->n_reac[j]; ++r)
+        h *= binom_small(x[n->reac_sp[3 * j + r]], n->reac_m[3 * j + r]);
+      a[j] = n->keff[j] * (double)h;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Canonical total propensity a0 = sum_j a_j (Sec. II.A: the waiting time is exponential with
+ * rate a0 and reaction j is chosen with probability a_j/a0).  The sum is fixed to one shape so
+ * that every implementation reaches the same double: a complete binary tree over the leaves,
+ * padded with +0.0 to a power of two, each node the rounded sum of its two children.
+ * ------------------------------------------------------------------------------------------ */
+static int32_t pow2_at_least(int32_t n) { int32_t p = 1; while (p < n) p <<= 1; return p; }
+
+static double *build_heap(int32_t n, const double *a, int32_t *P_out) {
+  int32_t P = pow2_at_least(n);
+  double *node = (double *)calloc(2 * (size_t)P, sizeof(double));
+  if (!node) return NULL;
+  for (int32_t j = 0; j < n; ++j) node[P + j] = a[j];
+  for (int32_t k = P - 1; k >= 1; --k) node[k] = node[2 * k] + node[2 * k + 1];
+  *P_out = P;
+  return node;
+}
+
+double orc_tree_total(int32_t n, const double *a) {
+  int32_t P;
+  double *node = build_heap(n, a, &P);
+  if (!node) return NAN;
+  double t = node[1];
+  free(node);
+  return t;
+}
+
+/* Descend from the root: go left while the target lies below the left sum; otherwise subtract
+ * the left sum and go right -- unless the right subtree sums to zero, in which case stay left
+ * (so a reaction with zero propensity is never chosen, whatever the rounding of the target). */
+int32_t orc_tree_select(int32_t n, const double *a, double target) {
+  int32_t P;
+  double *node = build_heap(n, a, &P);
+  if (!node) return -1;
+  int32_t k = 1;
+  while (k < P) {
+    double L = node[2 * k], R = node[2 * k + 1];
+    if (R == 0.0) {
+      k = 2 * k;
+    } else if (target < L) {
+      k = 2 * k;
+    } else {
+      target = target - L;
+      k = 2 * k + 1;
+    }
+  }
+  free(node);
+  return k - P;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Target set B for steady-state recycling (Sec. II.B.2): the conjunction of the clauses.
+ * ------------------------------------------------------------------------------------------ */
+static int in_target(const orc_we_config *cfg, const int32_t *x) {
+  if (cfg->n_clauses < 1) return 0;
+  for (int32_t c = 0; c < cfg->n_clauses; ++c) {
+    int32_t v = x[cfg->tgt_species[c]];
+    if (cfg->tgt_op[c] == ORC_OP_GE) { if (!(v >= cfg->tgt_threshold[c])) return 0; }
+    else { if (!(v <= cfg->tgt_threshold[c])) return 0; }
+  }
+  return 1;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Gillespie's direct SSA (Sec. II.A) for one WE interval of length tau (the "propagate dynamics"
+ * step of the WE algorithm, Sec. II.B).  Draw d of walker slot w in iteration i uses Philox
+ * counter (d, i, w, 0): words 0-1 give u1 (waiting time), words 2-3 give u2 (which reaction).
+ * A waiting time that would carry the clock past tau ends the interval; the unused remainder
+ * is discarded, which leaves the process exact because the exponential clock is memoryless.
+ * With feedback on, a walker that enters B is put back in the recycle state at once and keeps
+ * running for the rest of the interval (first passage is detected at the event that crosses).
+ * ------------------------------------------------------------------------------------------ */
+int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int32_t slot,
+                  int32_t *x, int64_t *n_ev, int32_t *n_rec) {
+  const int32_t S = n->S, M = n->M;
+  double *a = (double *)malloc(sizeof(double) * M);
+  int32_t *xn = (int32_t *)malloc(sizeof(int32_t) * S);
+  if (!a || !xn) { free(a); free(xn); return ORC_ENOMEM; }
+  uint32_t key[2];
+  run_key(cfg->seed, cfg->run_id, key);
+  double t = 0.0;
+  uint32_t draw = 0;
+  int64_t ev = 0;
+  int32_t rec = 0;
+  int status = ORC_OK;
+  orc_propensities(n, x, a);
+  for (;;) {
+    double a0 = orc_tree_total(M, a);
+    if (!(a0 > 0.0)) break;                     /* nothing can fire: idle to the end of tau */
+    uint32_t ctr[4] = {draw, (uint32_t)iter, (uint32_t)slot, 0u}, r[4];
+    ++draw;
+    orc_philox4x32_10(ctr, key, r);
+    double u1 = orc_u01(r[0], r[1]);
+    double u2 = orc_u01(r[2], r[3]);
+    double e = -log(u1);
+    double dt = e / a0;
+    double tn = t + dt;
+    if (tn > cfg->tau) break;
+    if (cfg->max_steps > 0 && ev >= cfg->max_steps) { status = ORC_ESTEPCAP; break; }
+    double target = u2 * a0;
+    int32_t j = orc_tree_select(M, a, target);
+    memcpy(xn, x, sizeof(int32_t) * S);
+    int over = 0;
+    for (int32_t e2 = n->d_ptr[j]; e2 < n->d_ptr[j + 1]; ++e2) {
+      int64_t v = (int64_t)xn[n->d_sp[e2]] + n->d_val[e2];
+      if (v > ORC_MAX_COUNT) over = 1;
+      xn[n->d_sp[e2]] = (int32_t)v;
+    }
+    if (over) { status = ORC_EOVERFLOW; break; }
+    memcpy(x, xn, sizeof(int32_t) * S);
+    ++ev;
+    t = tn;
+    if (cfg->feedback && in_target(cfg, x)) {
+      ++rec;
+      memcpy(x, cfg->recycle_state, sizeof(int32_t) * S);
+    }
+    orc_propensities(n, x, a);
+  }
+  free(a); free(xn);
+  *n_ev = ev;
+  *n_rec = rec;
+  return status;
+}
+
+/* Grid bins (Sec. II.B: non-overlapping bins on a regular 1-D or 2-D grid).  Bin k of a
+ * dimension is [edge_k, edge_{k+1}); values below the first edge go to bin 0, values at or above
+ * the last edge to the last bin (an overflow bin is a last edge at +infinity).  The flat index is
+ * row-major with the last dimension fastest. */
+int32_t orc_bin_of(const orc_we_config *cfg, const int32_t *x) {
+  int32_t flat = 0;
+  const double *edges = cfg->bin_edges;
+  for (int32_t d = 0; d < cfg->bin_ndim; ++d) {
+    int32_t nb = cfg->bin_nbins[d];
+    double v = (double)x[cfg->bin_species[d]];
+    int32_t idx = 0;
+    for (int32_t k = 0; k < nb; ++k)
+      if (edges[k] <= v) idx = k;
+    flat = flat * nb + idx;
+    edges += nb + 1;
+  }
+  return flat;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Split and merge inside each bin (Sec. II.B and its WE algorithm listing).  Bins are taken in
+ * ascending order and a bin's walkers in ascending slot order.
+ *  - More than M_targ: repeatedly merge the two lowest weights (Sec. II.B); ties go to the
+ *    earlier position.  Of the pair (earlier p, later q) p survives with probability
+ *    w_p/(w_p+w_q), decided by u < w_p/(w_p+w_q) with u from Philox counter (k, i, bin, 1) where
+ *    k counts the merges done in this bin this iteration.  The survivor keeps its position and
+ *    takes the pair's summed weight.
+ *  - Fewer than M_targ (and at least one): replicate until the bin holds M_targ.  Each walker
+ *    starts with one copy; the next copy goes to the walker whose per-copy weight w_i/c_i is
+ *    largest (ties to the earlier one).  Every copy carries w_i/c_i, which for a lone walker is
+ *    the paper's w/M_targ.  Copies follow their parent.
+ * The output is the concatenation over bins; parent[] holds the input slot of each output.
+ * ------------------------------------------------------------------------------------------ */
+int32_t orc_resample(int32_t n, int32_t S, const int32_t *states, const double *weights,
+                     const int32_t *bins, int32_t n_bins, int32_t m_targ, int32_t iter,
+                     uint64_t seed, uint32_t run_id, int32_t capacity,
+                     int32_t *out_states, double *out_weights, int32_t *out_parent) {
+  if (m_targ < 1 || n < 0 || n_bins < 1) return ORC_EINVAL;
+  uint32_t key[2];
+  run_key(seed, run_id, key);
+  int32_t *ls = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+  double *lw = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  int32_t *cp = (int32_t *)malloc(sizeof(int32_t) * (m_targ + 1));
+  if (!ls || !lw || !cp) { free(ls); free(lw); free(cp); return ORC_ENOMEM; }
+  int32_t out = 0;
+  int32_t status = 0;
+  for (int32_t b = 0; b < n_bins && status == 0; ++b) {
+    int32_t cnt = 0;
+    for (int32_t w = 0; w < n; ++w)
+      if (bins[w] == b) { ls[cnt] = w; lw[cnt] = weights[w]; ++cnt; }
+    if (cnt == 0) continue;
+    if (cnt > m_targ) {
+      uint32_t k = 0;
+      while (cnt > m_targ) {
+        int32_t ia = 0;
+        for (int32_t i = 1; i < cnt; ++i) if (lw[i] < lw[ia]) ia = i;
+        int32_t ib = (ia == 0) ? 1 : 0;
+        for (int32_t i = 0; i < cnt; ++i) if (i != ia && lw[i] < lw[ib]) ib = i;
+        int32_t p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
+        uint32_t ctr[4] = {k, (uint32_t)iter, (uint32_t)b, 1u}, r[4];
+        ++k;
+        orc_philox4x32_10(ctr, key, r);
+        double u = orc_u01(r[0], r[1]);
+        double wsum = lw[p] + lw[q];
+        double prob = lw[p] / wsum;
+        int32_t gone;
+        if (u < prob) { lw[p] = wsum; gone = q; }
+        else { lw[q] = wsum; gone = p; }
+        for (int32_t i = gone; i + 1 < cnt; ++i) { ls[i] = ls[i + 1]; lw[i] = lw[i + 1]; }
+        --cnt;
+      }
+      for (int32_t i = 0; i < cnt; ++i) {
+        if (out >= capacity) { status = ORC_EOVERFLOW; break; }
+        memcpy(out_states + (size_t)out * S, states + (size_t)ls[i] * S, sizeof(int32_t) * S);
+        out_weights[out] = lw[i]; out_parent[out] = ls[i]; ++out;
+      }
+    } else {
+      for (int32_t i = 0; i < cnt; ++i) cp[i] = 1;
+      for (int32_t extra = cnt; extra < m_targ; ++extra) {
+        int32_t best = 0;
+        double bw = lw[0] / (double)cp[0];
+        for (int32_t i = 1; i < cnt; ++i) {
+          double v = lw[i] / (double)cp[i];
+          if (v > bw) { bw = v; best = i; }
+        }
+        cp[best] += 1;
+      }
+      for (int32_t i = 0; i < cnt && status == 0; ++i) {
+        double wc = lw[i] / (double)cp[i];
+        for (int32_t c = 0; c < cp[i]; ++c) {
+          if (out >= capacity) { status = ORC_EOVERFLOW; break; }
+          memcpy(out_states + (size_t)out * S, states + (size_t)ls[i] * S, sizeof(int32_t) * S);
+          out_weights[out] = wc; out_parent[out] = ls[i]; ++out;
+        }
+      }
+    }
+  }
+  free(ls); free(lw); free(cp);
+  return status ? status : out;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * The WE procedure (Sec. II.B, algorithm listing): for each iteration, propagate every walker for
+ * tau, record the observables, then split/merge per bin.  Observables per iteration: the
+ * recycled weight (its ratio to tau is the flux whose inverse is the MFPT, Eq. "mfpt"), the
+ * number of events, a weighted histogram of one species taken after propagation and before
+ * resampling (the estimate of P(x, t) of Sec. II.B.1), and the total weight and walker count
+ * after resampling.
+ * ------------------------------------------------------------------------------------------ */
+int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
+  const int32_t S = n->S;
+  const int32_t cap = cfg->capacity;
+  if (cfg->n_init < 1 || cfg->n_init > cap || cfg->m_targ < 1 || !(cfg->tau > 0.0) ||
+      cfg->n_iters < 0 || cfg->bin_ndim < 1 || cfg->bin_ndim > 4)
+    return out->status = ORC_EINVAL;
+  int32_t n_bins = 1;
+  for (int32_t d = 0; d < cfg->bin_ndim; ++d) n_bins *= cfg->bin_nbins[d];
+  int32_t *st = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap * S);
+  int32_t *st2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap * S);
+  double *w = (double *)malloc(sizeof(double) * cap);
+  double *w2 = (double *)malloc(sizeof(double) * cap);
+  int32_t *par = (int32_t *)malloc(sizeof(int32_t) * cap);
+  int32_t *bins = (int32_t *)malloc(sizeof(int32_t) * cap);
+  int32_t *nrec = (int32_t *)malloc(sizeof(int32_t) * cap);
+  if (!st || !st2 || !w || !w2 || !par || !bins || !nrec) {
+    free(st); free(st2); free(w); free(w2); free(par); free(bins); free(nrec);
+    return out->status = ORC_ENOMEM;
+  }
+  int32_t nw = cfg->n_init;
+  memcpy(st, cfg->init_states, sizeof(int32_t) * (size_t)nw * S);
+  memcpy(w, cfg->init_weights, sizeof(double) * nw);
+  for (int32_t i = 0; i < nw; ++i) par[i] = -1;
+  int status = ORC_OK;
+  for (int32_t li = 0; li < cfg->n_iters && status == ORC_OK; ++li) {
+    int32_t iter = cfg->first_iter + li;
+    int64_t events = 0;
+    for (int32_t s = 0; s < nw; ++s) {
+      int64_t ev = 0;
+      int32_t rc = orc_propagate(n, cfg, iter, s, st + (size_t)s * S, &ev, &nrec[s]);
+      events += ev;
+      if (rc != ORC_OK && status == ORC_OK) status = rc;
+    }
+    double flux = 0.0;
+    for (int32_t s = 0; s < nw; ++s) flux = flux + (double)nrec[s] * w[s];
+    out->flux_weight[li] = flux;
+    out->events[li] = events;
+    if (out->hist && cfg->hist_len > 0) {
+      double *h = out->hist + (size_t)li * cfg->hist_len;
+      for (int32_t k = 0; k < cfg->hist_len; ++k) h[k] = 0.0;
+      for (int32_t s = 0; s < nw; ++s) {
+        int32_t v = st[(size_t)s * S + cfg->hist_species];
+        int32_t idx = v < cfg->hist_len - 1 ? v : cfg->hist_len - 1;
+        h[idx] = h[idx] + w[s];
+      }
+    }
+    if (status != ORC_OK) break;
+    if (cfg->resample) {
+      for (int32_t s = 0; s < nw; ++s) bins[s] = orc_bin_of(cfg, st + (size_t)s * S);
+      int32_t m = orc_resample(nw, S, st, w, bins, n_bins, cfg->m_targ, iter, cfg->seed,
+                               cfg->run_id, cap, st2, w2, par);
+      if (m < 0) { status = m; break; }
+      nw = m;
+      int32_t *ts = st; st = st2; st2 = ts;
+      double *tw = w; w = w2; w2 = tw;
+    } else {
+      for (int32_t s = 0; s < nw; ++s) par[s] = s;
+    }
+    double tot = 0.0;
+    for (int32_t s = 0; s < nw; ++s) tot = tot + w[s];
+    out->total_weight[li] = tot;
+    out->n_walkers[li] = nw;
+  }
+  memcpy(out->states, st, sizeof(int32_t) * (size_t)nw * S);
+  memcpy(out->weights, w, sizeof(double) * nw);
+  memcpy(out->parent, par, sizeof(int32_t) * nw);
+  out->n_final = nw;
+  out->status = status;
+  free(st); free(st2); free(w); free(w2); free(par); free(bins); free(nrec);
+  return status;
+}

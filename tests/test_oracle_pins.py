@@ -1,0 +1,395 @@
+"""Pins of the CPU oracle to things other than itself (closed forms, a library generator, the
+paper's printed numbers, brute force, invariants).  CPU only."""
+import ctypes
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import workloads as W
+from oracle import exact as E
+from oracle import oracle as O
+
+
+# ---------------------------------------------------------------- Philox-4x32-10 ---------------
+def _curand():
+    for p in ["/usr/local/cuda/lib64/libcurand.so", "libcurand.so", "libcurand.so.10"]:
+        try:
+            return ctypes.CDLL(p)
+        except OSError:
+            continue
+    return None
+
+
+@pytest.mark.parametrize("seed", [0, 1, 0x123456789ABCDEF0, 2**64 - 1])
+def test_philox_matches_curand_host_generator(seed):
+    """CURAND's host Philox4_32_10 generator (run, not read) emits block k of its stream as
+    Philox(counter=(0,0,k,0), key=(seed_lo, seed_hi)); the oracle must reproduce it."""
+    cur = _curand()
+    if cur is None:
+        pytest.skip("libcurand not available")
+    gen = ctypes.c_void_p()
+    if cur.curandCreateGeneratorHost(ctypes.byref(gen), 161) != 0:   # CURAND_RNG_PSEUDO_PHILOX4_32_10
+        pytest.skip("curand host generator unavailable")
+    try:
+        assert cur.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        n = 4 * 2048
+        buf = (ctypes.c_uint32 * n)()
+        assert cur.curandGenerate(gen, buf, ctypes.c_size_t(n)) == 0
+        ref = np.frombuffer(buf, dtype=np.uint32).reshape(-1, 4)
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        for k in list(range(0, 64)) + list(range(1900, 2048)):
+            assert np.array_equal(O.philox((0, 0, k, 0), key), ref[k]), k
+    finally:
+        cur.curandDestroyGenerator(gen)
+
+
+def test_philox_uniformity_and_counter_sensitivity():
+    """Every counter word and key word changes the output; words are uniform (chi-square)."""
+    base = O.philox((1, 2, 3, 4), (5, 6))
+    for i in range(4):
+        c = [1, 2, 3, 4]
+        c[i] ^= 1
+        assert not np.array_equal(O.philox(c, (5, 6)), base)
+    for i in range(2):
+        k = [5, 6]
+        k[i] ^= 1
+        assert not np.array_equal(O.philox((1, 2, 3, 4), k), base)
+    words = np.concatenate([O.philox((s, 7, 0, 1), (11, 13)) for s in range(4000)])
+    counts = np.bincount((words >> 28).astype(np.int64), minlength=16)
+    assert stats.chisquare(counts).pvalue > 1e-4
+
+
+def test_u01_exact_values():
+    assert O.u01(0, 0) == 2.0 ** -53
+    assert O.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert O.u01(0, 1 << 12) == 3.0 * 2.0 ** -53
+    assert O.u01(1, 0) == (2.0 ** 21 + 1) * 2.0 ** -53
+    assert O.u01(0x80000000, 0) == 0.5 + 2.0 ** -53
+    # low 12 bits of the second word are dropped
+    assert O.u01(123, 0xFFF) == O.u01(123, 0)
+
+
+# ---------------------------------------------------------------- propensities -----------------
+def test_schlogl_modes_pin_combinatorial_convention():
+    """With combinatorial mass action, the stationary law of the oracle's own Schloegl
+    propensities peaks at X=82 and X=563 with the barrier at X=256 (Sec. III.B.3)."""
+    net = O.Network(W.schlogl())
+    N = 1500
+    a = np.array([net.propensities([x, 100000, 200000]) for x in range(N + 1)])
+    birth = a[:, 0] + a[:, 2]
+    death = a[:, 1] + a[:, 3]
+    lp = np.concatenate([[0.0], np.cumsum(np.log(birth[:-1]) - np.log(death[1:]))])
+    maxima = [x for x in range(1, N) if lp[x] >= lp[x - 1] and lp[x] >= lp[x + 1]]
+    minima = [x for x in range(1, N) if lp[x] <= lp[x - 1] and lp[x] <= lp[x + 1]]
+    assert maxima == [82, 563]
+    assert minima == [256]
+
+
+def test_propensity_hand_values():
+    net = O.Network(W.schlogl())
+    # folded constants: c1*A and c3*B
+    assert net.keff(0) == 3e-7 * 100000.0 and net.keff(2) == 1e-3 * 200000.0
+    a = net.propensities([5, 100000, 200000])
+    # C(5,2)=10, C(5,3)=10
+    assert a[0] == net.keff(0) * 10.0 and a[1] == 1e-4 * 10.0 and a[2] == 200.0 and a[3] == 3.5 * 5.0
+    for x in (0, 1, 2):
+        a = net.propensities([x, 100000, 200000])
+        assert a[1] == 0.0 and (x >= 2 or a[0] == 0.0)
+    fut = O.Network(W.futile_cycle())
+    a = fut.propensities([50, 50, 1, 1, 0, 0])
+    assert list(a) == [50.0, 0.0, 0.0, 50.0, 0.0, 0.0]
+    tog = O.Network(W.toggle_switch(40.0, 30.0))
+    a = tog.propensities([7, 3])
+    assert a[0] == 40.0 / 10.0 and a[1] == 30.0 / 50.0 and a[2] == 7.0 and a[3] == 3.0
+    epi = O.Network(W.epigenetic_switch())
+    a = epi.propensities([4, 2])
+    assert a[0] == 156.0 / 9.0 and a[2] == 30.0 / 5.0
+
+
+def test_network_validation():
+    bad = W.NetworkSpec(species=["X"], reactants=[[(0, 4)]], products=[[]], rate=[[1.0]])
+    with pytest.raises(ValueError):
+        O.Network(bad)
+    bad = W.NetworkSpec(species=["X"], reactants=[[(1, 1)]], products=[[]], rate=[[1.0]])
+    with pytest.raises(ValueError):
+        O.Network(bad)
+    bad = W.NetworkSpec(species=["X"], reactants=[[]], products=[[(0, 1)]], rate=[[-1.0]])
+    with pytest.raises(ValueError):
+        O.Network(bad)
+
+
+# ---------------------------------------------------------------- canonical tree ---------------
+def test_tree_total_is_a_correct_sum():
+    rng = np.random.default_rng(1)
+    for n in [1, 2, 3, 4, 5, 7, 8, 9, 100, 3680]:
+        a = rng.exponential(size=n) * (rng.random(n) < 0.8)
+        t = O.tree_total(a)
+        exact = math.fsum(a)
+        depth = max(1, math.ceil(math.log2(n)))
+        assert abs(t - exact) <= depth * 2.0 ** -52 * exact + 1e-300
+    assert O.tree_total([3.0]) == 3.0
+    assert O.tree_total([0.0, 0.0, 0.0]) == 0.0
+    # pairwise shape: ((a+b)+(c+d)) differs from the left fold for these values
+    v = [1.0, 0.0, 2.0 ** -53, 2.0 ** -53]
+    assert O.tree_total(v) == 1.0 + 2.0 ** -52       # a left-to-right fold would give 1.0
+
+
+def test_tree_select_boundaries_and_zeros():
+    a = [1.0, 2.0, 3.0, 4.0]
+    cases = {0.0: 0, 0.999: 0, 1.0: 1, 2.999: 1, 3.0: 2, 5.999: 2, 6.0: 3, 9.999: 3}
+    for tgt, j in cases.items():
+        assert O.tree_select(a, tgt) == j
+    z = [0.0, 1.0, 0.0, 0.0, 2.0, 0.0, 0.0]
+    for tgt in np.linspace(0.0, 3.0, 61):
+        assert z[O.tree_select(z, tgt)] > 0.0
+    assert O.tree_select(z, 1e300) == 4      # a target rounded past the total stays on a live leaf
+
+
+def test_tree_select_frequencies():
+    rng = np.random.default_rng(2)
+    a = np.array([0.5, 0.0, 3.0, 1.5, 0.0, 2.0])
+    tot = O.tree_total(a)
+    n = 30000
+    picks = np.bincount([O.tree_select(a, u * tot) for u in rng.random(n)], minlength=len(a))
+    assert picks[1] == 0 and picks[4] == 0
+    expected = a / a.sum() * n
+    live = a > 0
+    assert stats.chisquare(picks[live], expected[live]).pvalue > 1e-4
+
+
+# ---------------------------------------------------------------- SSA dynamics -----------------
+def _brute_force(cfg, n_walkers, n_iters, seed=5):
+    S = cfg.network.n_species
+    init = np.repeat(cfg.x0[:1], n_walkers, axis=0)
+    cfg.seed = seed
+    return O.we_run(cfg, 0, n_iters=n_iters, resample=False, init_states=init,
+                    init_weights=np.full(n_walkers, 1.0 / n_walkers))
+
+
+def test_ssa_immigration_death_matches_closed_form():
+    """Brute-force SSA (no resampling) of 0->X, X->0 against Binomial * Poisson at t=2."""
+    cfg = W.birth_death_we()
+    out = _brute_force(cfg, 20000, 20)
+    x = out["states"][:, 0]
+    p = E.immigration_death_pmf(100, 10.0, 0.1, 2.0, 400)
+    obs = np.bincount(x, minlength=401)[:401]
+    exp = p * len(x)
+    keep = exp > 20
+    chi = ((obs[keep] - exp[keep]) ** 2 / exp[keep]).sum()
+    dof = keep.sum() - 1
+    assert stats.chi2.sf(chi, dof) > 1e-4
+    assert abs(x.mean() - (p * np.arange(401)).sum()) < 5 * x.std() / np.sqrt(len(x))
+
+
+def test_ssa_schlogl_matches_cme():
+    """Brute-force SSA of the Schloegl model from X=82 against the truncated CME at t=0.5."""
+    cfg = W.schlogl_mfpt_we()
+    cfg.target = None
+    cfg.x0[:, 0] = 82
+    cfg.recycle_state[:, 0] = 82
+    out = _brute_force(cfg, 8000, 10)
+    x = out["states"][:, 0]
+    b, d = E.schlogl_rates()
+    p = E.bd_transient(b, d, 82, 0.5, 1500)
+    obs = np.bincount(x, minlength=1501)[:1501]
+    exp = p * len(x)
+    # pool into blocks of 4 states for power
+    ob = obs[:1500].reshape(-1, 4).sum(1)
+    ex = exp[:1500].reshape(-1, 4).sum(1)
+    keep = ex > 20
+    chi = ((ob[keep] - ex[keep]) ** 2 / ex[keep]).sum()
+    assert stats.chi2.sf(chi, keep.sum() - 1) > 1e-4
+
+
+def test_recycling_rate_is_inverse_mfpt():
+    """With recycling and no resampling, each walker is a renewal process whose rate of hits is
+    1/MFPT(A -> B) (Eq. "mfpt"); MFPT(100 -> 115) of the birth-death chain is a closed form."""
+    cfg = W.birth_death_we(target=115)
+    n_w, n_it = 2000, 1500
+    out = _brute_force(cfg, n_w, n_it, seed=9)
+    hits = out["flux_weight"] * n_w            # every walker carries weight 1/n_w
+    bb, dd = E.birth_death_rates()
+    mfpt = E.bd_mfpt(100, 115, bb, dd)
+    rate = hits[200:].sum() / (n_w * (n_it - 200) * cfg.tau)
+    se = np.sqrt(hits[200:].sum()) / (n_w * (n_it - 200) * cfg.tau)
+    assert abs(rate - 1.0 / mfpt) < 4 * se + 0.02 / mfpt
+
+
+def test_step_cap_and_overflow_statuses():
+    cfg = W.birth_death_we()
+    x, ev, rec, rc = O.propagate_one(cfg, [100], 0, 0, max_steps=1)
+    assert rc == -5 and ev == 1
+    grow = W.NetworkSpec(species=["X"], reactants=[[]], products=[[(0, 1)]], rate=[[1e9]])
+    cfg2 = W.WEConfig(network=grow, bins=W.GridBins([0], [W.uniform_edges(0, 1, 1)]), tau=1.0,
+                      m_targ=1, n_iters=1, x0=[O.MAX_COUNT - 2])
+    x, ev, rec, rc = O.propagate_one(cfg2, [O.MAX_COUNT - 2], 0, 0)
+    assert rc == -4 and x[0] == O.MAX_COUNT and ev == 2
+
+
+def test_zero_propensity_walker_idles():
+    dead = W.NetworkSpec(species=["X"], reactants=[[(0, 1)]], products=[[]], rate=[[1.0]])
+    cfg = W.WEConfig(network=dead, bins=W.GridBins([0], [W.uniform_edges(0, 1, 1)]), tau=1.0,
+                     m_targ=1, n_iters=1, x0=[0])
+    x, ev, rec, rc = O.propagate_one(cfg, [0], 0, 0)
+    assert rc == 0 and ev == 0 and x[0] == 0
+
+
+# ---------------------------------------------------------------- split / merge -----------------
+def test_resample_invariants_random():
+    rng = np.random.default_rng(3)
+    for trial in range(40):
+        n = int(rng.integers(1, 300))
+        nb = int(rng.integers(1, 12))
+        M = int(rng.integers(1, 15))
+        st = rng.integers(0, 1000, size=(n, 2)).astype(np.int32)
+        w = rng.exponential(size=n) * 10.0 ** rng.uniform(-40, 0, size=n)
+        b = rng.integers(0, nb, size=n).astype(np.int32)
+        s2, w2, p2 = O.resample(st, w, b, nb, M, trial, 77)
+        occ = np.unique(b)
+        assert len(w2) == M * len(occ)
+        assert abs(w2.sum() - math.fsum(w)) <= 1e-14 * math.fsum(w)
+        for bin_ in occ:
+            assert abs(math.fsum(w2[b[p2] == bin_]) - math.fsum(w[b == bin_])) <= 1e-14 * math.fsum(w[b == bin_])
+        assert np.array_equal(s2, st[p2])
+        assert np.all(np.diff(b[p2]) >= 0)          # concatenation over ascending bins
+
+
+def test_lone_walker_split_gives_paper_weights():
+    s2, w2, p2 = O.resample([[5]], [0.3], [0], 1, 10, 0, 1)
+    assert len(w2) == 10 and np.all(w2 == 0.3 / 10) and np.all(p2 == 0)
+
+
+def test_split_allocation_greedy():
+    # weights 0.6, 0.2 with M=4: copies go to the largest per-copy weight: 0.6 -> 0.3 -> 0.2 tie
+    s2, w2, p2 = O.resample([[1], [2]], [0.6, 0.2], [0, 0], 1, 4, 0, 1)
+    assert list(p2) == [0, 0, 0, 1] and list(w2) == [0.6 / 3, 0.6 / 3, 0.6 / 3, 0.2]
+
+
+def test_merge_survivor_probability_and_unbiasedness():
+    """Merging keeps the expected weight of every walker (Sec. II.B; Huber & Kim): over many
+    draws the earlier of the two lightest walkers survives with probability w_p/(w_p+w_q)."""
+    w = np.array([0.1, 0.3, 0.2, 0.4])
+    b = np.zeros(4, dtype=np.int32)
+    st = np.arange(4, dtype=np.int32)[:, None]
+    n = 20000
+    acc = np.zeros(4)
+    first_merge_p = 0
+    for it in range(n):
+        s2, w2, p2 = O.resample(st, w, b, 1, 3, it, 1234)
+        for slot, ww in zip(p2, w2):
+            acc[slot] += ww
+        first_merge_p += int(0 in p2)
+    mean = acc / n
+    # walker 0 (0.1) merges with walker 2 (0.2): survives with prob 1/3
+    p = 1.0 / 3.0
+    assert abs(first_merge_p / n - p) < 4 * np.sqrt(p * (1 - p) / n)
+    sd = np.array([0.3 * np.sqrt(p * (1 - p)), 0, 0.3 * np.sqrt(p * (1 - p)), 0]) / np.sqrt(n)
+    assert np.all(np.abs(mean - w) <= 4 * sd + 1e-12)
+
+
+def test_merge_ties_take_earliest():
+    w = np.array([0.25, 0.25, 0.25, 0.25])
+    s2, w2, p2 = O.resample(np.arange(4)[:, None], w, np.zeros(4, dtype=np.int32), 1, 3, 0, 5)
+    # the pair is (slot 0, slot 1); exactly one of them survives with weight 0.5
+    assert sorted(w2.tolist()) == [0.25, 0.25, 0.5]
+    assert set(p2.tolist()) in ({0, 2, 3}, {1, 2, 3})
+
+
+# ---------------------------------------------------------------- whole WE runs ------------------
+def _replicas(cfg, R, **kw):
+    outs = []
+    for r in range(R):
+        cfg.run_ids = np.array([r], dtype=np.uint32)
+        outs.append(O.we_run(cfg, 0, **kw))
+    return outs
+
+
+def test_we_schlogl_tail_matches_cme():
+    """WE estimate of P(X >= x, t = 1) for the Schloegl model from X=82 (unit-width bins as in
+    Sec. III.B.2, 10 walkers per bin) against the truncated CME, within 4 standard errors over
+    independent replicas (the protocol of Sec. III.B.3).  Transient WE tail estimates are
+    unbiased but skewed, so the check stays where 16 replicas resolve them."""
+    cfg = W.schlogl_pdf_we(n_iters=20, m_targ=10, n_unit_bins=400)
+    outs = _replicas(cfg, 16)
+    b, d = E.schlogl_rates()
+    p = E.bd_transient(b, d, 82, 1.0, 1500)
+    for thr in (120, 150):
+        est = np.array([o["hist"][-1, thr:].sum() for o in outs])
+        exact = p[thr:].sum()
+        se = est.std(ddof=1) / np.sqrt(len(est))
+        assert abs(est.mean() - exact) < 4 * se + 0.1 * exact, (thr, est.mean(), exact, se)
+    for o in outs:
+        assert np.all(np.abs(o["total_weight"] - 1.0) < 1e-12)
+
+
+def test_we_birth_death_stationary_tails_match_poisson():
+    """Stationary WE of the birth-death process (kb=10, kd=0.1; 61 bins, 10 walkers per bin):
+    the time-averaged weighted histogram reproduces the Poisson(100) law in both tails
+    (P(X >= 150) ~ 1.9e-6, P(X <= 50) ~ 2.4e-8), within 4 standard errors over replicas."""
+    cfg = W.birth_death_we(n_iters=1500)
+    outs = _replicas(cfg, 16)
+    x = np.arange(401)
+    pois = np.exp(E.log_poisson_pmf(x, 100.0))
+    H = np.array([o["hist"][375:].mean(0) for o in outs])
+    for sel in (slice(150, None), slice(None, 51)):
+        est = H[:, sel].sum(1)
+        exact = pois[sel].sum()
+        se = est.std(ddof=1) / np.sqrt(len(est))
+        assert abs(est.mean() - exact) < 4 * se + 0.1 * exact, (sel, est.mean(), exact, se)
+
+
+def test_we_mfpt_matches_closed_form():
+    """Steady-state WE with recycling: MFPT = 1/flux (Eq. "mfpt") for the rare passage
+    100 -> 140 of the birth-death chain (closed form ~9.8e3), 4 standard errors."""
+    cfg = W.birth_death_we(n_iters=400, target=140)
+    outs = _replicas(cfg, 8)
+    bb, dd = E.birth_death_rates()
+    exact = 1.0 / E.bd_mfpt(100, 140, bb, dd)
+    est = np.array([o["flux_weight"][150:].mean() / cfg.tau for o in outs])
+    se = est.std(ddof=1) / np.sqrt(len(est))
+    assert abs(est.mean() - exact) < 4 * se + 0.05 * exact, (est.mean(), exact, se)
+    for o in outs:
+        assert np.all(np.abs(o["total_weight"] - 1.0) < 1e-12)
+
+
+def test_toggle_recycling_rate_matches_master_equation():
+    """Hill-repression dynamics (Sec. III.C.1 form, n=2): the renewal rate of first passages of
+    a toggle switch with a_U = a_V = 8 into {V >= 4, U <= 2} equals 1/MFPT from an exact sparse
+    solve of the 2-D master equation (~39.6)."""
+    a = 8.0
+    net = W.toggle_switch([a], [a])
+    tgt = W.Target(species=[1, 0], op=[W.configs.OP_GE, W.configs.OP_LE],
+                   threshold=np.array([[4, 2]], dtype=np.int32))
+    e = W.uniform_edges(0, 4, 29, overflow=True)
+    cfg = W.WEConfig(network=net, bins=W.GridBins([0, 1], [e, e]), tau=0.1, m_targ=8,
+                     n_iters=1, x0=[8, 0], target=tgt)
+    n_w, n_it = 2000, 1200
+    out = _brute_force(cfg, n_w, n_it, seed=21)
+    hits = out["flux_weight"] * n_w
+    mfpt = E.toggle_mfpt(a, a, (8, 0), lambda u, v: v >= 4 and u <= 2, Umax=60, Vmax=60)
+    span = n_w * (n_it - 300) * cfg.tau
+    rate = hits[300:].sum() / span
+    se = np.sqrt(hits[300:].sum()) / span
+    assert abs(rate - 1.0 / mfpt) < 4 * se + 0.02 / mfpt, (rate, 1.0 / mfpt, se)
+
+
+def test_synthetic_network_homodimer_and_conservation():
+    spec = W.synthetic_large()
+    assert spec.n_species == 354 and spec.n_reactions == 3680
+    net = O.Network(spec)
+    x = np.arange(354, dtype=np.int32) % 200
+    a = net.propensities(x)
+    seen_dimer = seen_bi = False
+    for j, (reac, prod) in enumerate(zip(spec.reactants, spec.products)):
+        assert sum(m for _, m in reac) == sum(m for _, m in prod)     # molecules conserved
+        if len(reac) == 1 and reac[0][1] == 2:
+            v = int(x[reac[0][0]])
+            assert a[j] == spec.rate[0, j] * float(v * (v - 1) // 2)
+            seen_dimer = True
+        if len(reac) == 2:
+            assert a[j] == spec.rate[0, j] * float(int(x[reac[0][0]]) * int(x[reac[1][0]]))
+            seen_bi = True
+    assert seen_dimer and seen_bi
