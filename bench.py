@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the weighted-ensemble Gillespie-SSA path on GB300.
+
+Workload (one "step" = one whole WE run of the batch, every row of the hot path): the Schloegl
+model of Sec. III.B.1 in steady-state (MFPT) mode -- 80 bins of width 10 on X, 20 walkers per
+bin, tau = 0.05, 1000 iterations, walkers recycled to X0 = 85 on reaching X >= 550 -- with
+`--replicas` independent replicas per GPU (10 by default, the replicate count of Sec. III.B.3).
+Each step uses fresh seeds, so every step is a new batch of synthetic trajectories.
+
+Prints one JSON line: SSA events/s (whole job), WE iterations/s, the MFPT estimate and its
+relative error against the closed form, the SSA kernel's roofline position, the CPU oracle
+timed on this host, and an end-to-end figure through the one-call C ABI with host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+ITERS = 1000
+DISCARD = 300              # iterations before the flux average (steady state, Sec. III.C.3 protocol)
+# FP64 operations the direct method needs per Schloegl event with dependency-graph updates:
+# 3 propensities (x keff), 3 tree additions, target u2*a0, 2 descent subtractions, log, divide,
+# clock addition.  Peak: 152 SMs x 2 FP64 lanes/clock x 2.07 GHz (1.25 TFLOP/s counting an FMA
+# as two operations).
+FLOPS_PER_EVENT = 12
+FP64_PEAK_GOPS = 152 * 2 * 2.07
+KERNELS_PER_ITER = 6       # SSA, bin scan, placement, split/merge, gather, finalize
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--replicas", type=int, default=10)
+    ap.add_argument("--iters", type=int, default=ITERS)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def exact_mfpt():
+    with open(os.path.join(ROOT, "tests", "golden", "exact_values.json")) as f:
+        return json.load(f)["schlogl_mfpt_85_to_550_s"]
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle leg (the only place besides --impl reference where bench.py runs oracle/)
+# ------------------------------------------------------------------------------------------
+def _oracle_sample(args):
+    replica, n_iters, seed = args
+    import numpy as np  # noqa: F401
+    import workloads as W
+    from oracle import oracle as O
+    cfg = W.schlogl_mfpt_we(n_iters=n_iters, n_runs=1, seed=seed)
+    cfg.run_ids = np.array([replica], dtype=np.uint32)
+    t0 = time.perf_counter()
+    o = O.we_run(cfg, 0)
+    return int(o["events"].sum()), time.perf_counter() - t0
+
+
+def _calibrate():
+    ev, dt = _oracle_sample((0, 40, 123))                 # the first 40 iterations
+    return ev / dt, ev / 40.0
+
+
+def _oracle_pool_run(cores: int, n_iters: int, seed: int):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_sample, [(r, n_iters, seed) for r in range(cores)])
+    return sum(e for e, _ in res), time.perf_counter() - t0
+
+
+def cpu_baseline(seconds: float, replicas: int):
+    """The oracle as it stands, one replica per host process (spawned before any GPU work),
+    each running the first n iterations of the workload; n is set so the sample takes about
+    `seconds` of wall time."""
+    from oracle import build as obuild
+    obuild.build()
+    cores = max(1, min(replicas, os.cpu_count() or 1))
+    rate, per_iter = _calibrate()
+    n_iters = int(max(40, min(ITERS, seconds * rate / max(per_iter * 2.5, 1.0))))
+    events, wall = _oracle_pool_run(cores, n_iters, 0)
+    return {"value": events / wall, "unit": "SSA events/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} replica(s) x first {n_iters} of {ITERS} iterations of the workload, "
+                      f"one host process each; {events} events in {wall:.1f} s"}
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle on the same config
+# ------------------------------------------------------------------------------------------
+def run_reference(a):
+    """The CPU oracle timed on this host's cores on the same workload: every step is a bounded
+    sample (each replica process runs the first n iterations), sized so that the whole run
+    takes about --cpu-seconds per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import build as obuild
+    obuild.build()
+    cores = max(1, min(a.replicas, os.cpu_count() or 1))
+    rate, per_iter = _calibrate()
+    n_iters = int(max(40, min(a.iters, a.cpu_seconds * rate / max(per_iter * 2.5, 1.0))))
+    for w in range(a.warmup):
+        _oracle_pool_run(cores, 20, 10_000 + w)
+    tot_ev, tot_s = 0, 0.0
+    for s in range(a.steps):
+        ev, dt = _oracle_pool_run(cores, n_iters, s)
+        tot_ev += ev
+        tot_s += dt
+    v = tot_ev / tot_s
+    cb = {"value": v, "unit": "SSA events/s", "cores": cores, "kind": "oracle",
+          "sample": f"per step {cores} replica(s) x first {n_iters} of {a.iters} iterations, one host "
+                    f"process each; {tot_ev} events in {tot_s:.1f} s over {a.steps} steps"}
+    line = {"impl": "reference", "metric": "SSA events/sec and WE iterations/sec on 1 GB300; MFPT rel. error per GPU-s",
+            "value": v, "unit": "SSA events/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * tot_s / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "SSA events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_config(a):
+    return {"workload": (f"Schloegl MFPT weighted ensemble (Sec. III.B): 80 bins x 20 walkers, tau=0.05, "
+                         f"{a.iters} iterations, recycle X>=550 -> 85, {a.replicas} independent replicas per GPU"),
+            "replicas_per_gpu": a.replicas, "iterations": a.iters, "capacity_per_replica": 1600,
+            "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x {a.gpus} GPU(s)"}
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cb = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cb = cpu_baseline(a.cpu_seconds, a.replicas)       # before the first GPU call
+
+    import numpy as np
+    import torch
+    import paper_1303_5986_gb300 as P
+    import workloads as W
+    from paper_1303_5986_gb300 import build as pbuild
+
+    pbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    mk = lambda seed: W.schlogl_mfpt_we(n_iters=a.iters, n_runs=a.replicas, seed=seed)
+    base = mk(0)
+    net = P.network_from_spec(base.network)
+    bm = P.we_binmap_grid(base.bins.species, base.bins.edges)
+
+    def ensemble(seed):
+        cfg = mk(seed)
+        c, keep = P.run_config_from(cfg, record_iters=a.iters)
+        return P.we_ensemble_create(net, bm, c, keep)
+
+    seeds = [1_000_003 * (rank + 1) + s for s in range(a.warmup + a.steps + 1)]
+    # every ensemble of the timed region is uploaded before timing starts (inputs resident)
+    warm = [ensemble(s) for s in seeds[:a.warmup]]
+    timed = [ensemble(s) for s in seeds[a.warmup:a.warmup + a.steps]]
+    for e in warm:
+        e.step(a.iters)
+        e.sync()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = Clocks(local)
+    step_ms, prop_ms = [], []
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for e in timed:
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pm = e.step_timed(a.iters)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        prop_ms.append(pm)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    for e in timed:
+        e.sync()
+
+    events = [int(e.per_iter(P.WE_OUT_EVENTS).sum()) for e in timed]
+    fluxes = [e.per_iter(P.WE_OUT_FLUX) for e in timed]              # iters x replicas
+    total_ms = float(sum(step_ms))
+    ev_total = float(sum(events))
+    prop_total_ms = float(sum(p.sum() for p in prop_ms))
+    n_launch = sum(len(p) for p in prop_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms, ev_total, prop_total_ms], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms, ev_total = float(tmax[0]), float(t[1])
+    value = ev_total / (total_ms * 1e-3)
+    we_iters_per_s = a.steps * a.iters / (total_ms * 1e-3)
+
+    # MFPT = 1/flux over the replicas of all timed steps (Eq. "mfpt"); error vs the closed form
+    fl = np.concatenate([f[DISCARD:].mean(axis=0) for f in fluxes]) / base.tau
+    mfpt = 1.0 / fl.mean()
+    exact = exact_mfpt()
+    rel_err = abs(mfpt - exact) / exact
+    se = fl.std(ddof=1) / np.sqrt(len(fl)) / fl.mean() if len(fl) > 1 else None
+
+    # roofline of the dominant kernel (the SSA kernel), from the events around each launch
+    prop_s = prop_total_ms * 1e-3
+    ev_rank = float(sum(events))
+    achieved = FLOPS_PER_EVENT * ev_rank / prop_s / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
+                "kernel": "k_propagate_thread<4,2>", "launches": n_launch,
+                "avg_launch_ms": prop_total_ms / max(n_launch, 1),
+                "share_of_step": prop_total_ms / total_ms if dist is None else None,
+                "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz (recipe: 1.25 TFLOP/s FP64, FMA=2)",
+                "flops_per_event": FLOPS_PER_EVENT}
+
+    # end to end: one we_run() call per step from host buffers, observables back to the host
+    e2e = None
+    if rank == 0:
+        cfg = mk(seeds[-1])
+        c, keep = P.run_config_from(cfg, record_iters=a.iters)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ens = P.we_run(net, bm, c, keep)
+        fh = ens.get(P.WE_OUT_FLUX)
+        evh = ens.get(P.WE_OUT_EVENTS)
+        t1 = time.perf_counter()
+        S, R, cap = cfg.network.n_species, cfg.n_runs, cfg.capacity
+        h2d = 4 * S * R * cap + 8 * R * cap + 4 * R * cap + 16 * R
+        d2h = fh.nbytes + evh.nbytes
+        e2e = {"value": float(evh.sum()) / (t1 - t0), "unit": "SSA events/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "wall_s": t1 - t0, "path": "we_run() + we_ensemble_get(host)"}
+        ens.close()
+
+    if rank == 0:
+        line = {
+            "metric": "SSA events/sec and WE iterations/sec on 1 GB300; MFPT rel. error per GPU-s",
+            "value": value, "unit": "SSA events/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a), "we_iters_per_s": we_iters_per_s,
+            "replica_iters_per_s": we_iters_per_s * a.replicas * world,
+            "mfpt_s": mfpt, "mfpt_exact_s": exact, "mfpt_rel_error": rel_err, "mfpt_rel_se": se,
+            "mfpt_rel_error_per_gpu_s": rel_err / (total_ms * 1e-3 / a.steps),
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+            "gpu_launches": KERNELS_PER_ITER * a.iters * a.steps, "clocks": clk,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

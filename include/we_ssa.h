@@ -1,0 +1,249 @@
+/*
+ * we_ssa.h -- C ABI of the GB300 (sm_103a) weighted-ensemble Gillespie-SSA library.
+ *
+ * The library runs the data-parallel hot path of the weighted-ensemble (WE) method for
+ * stochastic chemical kinetics of Donovan, Sedgewick, Faeder & Zuckerman (arXiv:1303.5986):
+ * many weighted walkers ("trajectory segments") are propagated with Gillespie's direct SSA
+ * for one interval tau (Sec. II.A), then binned and split or merged inside each bin so that
+ * every occupied bin holds M_targ walkers while the total weight is kept (Sec. II.B and its WE
+ * algorithm listing).  Optional steady-state recycling ("feedback", Sec. II.B.2) moves walkers
+ * that reach a target set B back to a source state and records the weight that arrived, whose
+ * rate is the flux with MFPT = 1/flux (Eq. "mfpt").
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a we_status (0 = WE_OK, negative = error) and never throws,
+ *     aborts or traps; the message of the last failure on the calling thread is returned by
+ *     we_last_error().
+ *   - Host inputs are borrowed for the duration of the call and copied; handles are owned by
+ *     the library and released by the matching *_destroy.
+ *   - Device work is issued on the cudaStream_t passed as `stream` (NULL = the legacy default
+ *     stream).  Entry points that return data to the host synchronise that stream; the others
+ *     only enqueue work.
+ *   - Device memory of an ensemble is either carved from a caller-owned device buffer
+ *     (`workspace`, e.g. a PyTorch tensor) or, when workspace is NULL, allocated by the library.
+ *   - Device-side failures (step cap, count overflow) are reported through a per-run status
+ *     word that the host reads back (we_ensemble_get WE_OUT_STATUS, or the return of a
+ *     synchronising call).  Every device wait in the library is bounded.
+ *   - Species counts are int32 and never exceed WE_MAX_COUNT; times, propensities and weights
+ *     are IEEE double.
+ */
+#ifndef WE_SSA_H
+#define WE_SSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t we_status;
+#define WE_OK 0
+#define WE_EINVAL (-1)         /* an argument is invalid (message in we_last_error) */
+#define WE_ENOMEM (-2)         /* host or device allocation failed, or workspace too small */
+#define WE_ECUDA (-3)          /* a CUDA runtime call failed */
+#define WE_EOVERFLOW (-4)      /* a species count would pass WE_MAX_COUNT, or walkers passed capacity */
+#define WE_ESTEPCAP (-5)       /* a walker needed more than max_steps events in one interval */
+#define WE_ETIMEOUT (-6)       /* a bounded device wait gave up */
+#define WE_ENOTSUPPORTED (-7)  /* the request is valid but not implemented for these sizes */
+
+/* Largest count a species may reach.  Products of three counts then fit in int64, which keeps
+ * every combinatorial propensity factor exact. */
+#define WE_MAX_COUNT 2097151
+
+/* Events one walker may fire in one interval when the configuration sets no cap of its own;
+ * past it the walker stops with WE_ESTEPCAP, so every SSA loop is bounded. */
+#define WE_DEFAULT_MAX_STEPS (1ll << 26)
+
+/* Rate laws (Sec. III): mass action with combinatorial factors C(x, m) per reactant taken m
+ * times (the convention that puts the Schloegl model's stable states at X=82 and X=563,
+ * Sec. III.B.3), or Hill repression c/(1 + (y/K)^n) of a zeroth-order production reaction
+ * (the epigenetic switch, Sec. III.C.1), evaluated as (c K^n)/(K^n + y^n). */
+#define WE_MASS_ACTION 0
+#define WE_HILL_REPRESSION 1
+
+/* Target-set clause operators: x[species] >= threshold, x[species] <= threshold. */
+#define WE_OP_GE 0
+#define WE_OP_LE 1
+
+/* Thread-to-walker mapping of the SSA kernel. */
+#define WE_MAP_AUTO 0          /* let the autotuner pick */
+#define WE_MAP_THREAD 1        /* one thread per walker, propensity tree in registers */
+#define WE_MAP_WARP 2          /* one warp per walker, propensity tree in shared memory */
+
+const char *we_status_string(we_status s);
+/* Message of the last failing call on this thread ("" if none).  Valid until the next call. */
+const char *we_last_error(void);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t we_version(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Reaction network (Sec. II.A; models of Sec. III).
+ *
+ * n_species S >= 1, n_reactions M >= 1.  Reactants and products are CSR lists over reactions:
+ * reaction j has reactant entries [reac_ptr[j], reac_ptr[j+1]) of (species, multiplicity 1..3)
+ * and product entries likewise (multiplicity >= 0); repeated species are summed; the total
+ * reactant order of a reaction is at most 3.  rate is n_param_sets x M row-major (c_j of each
+ * parameter set; runs of a batch pick a set).  rate_law (M, NULL = all mass action);
+ * hill_species / hill_n (M, n in 1..3) and hill_K (hill_K_rows x M, hill_K_rows = 1 or
+ * n_param_sets) are read for WE_HILL_REPRESSION reactions only, which must have no dynamic
+ * reactant; the regulator count y is the state's entry for hill_species.  Rate constants must
+ * be finite and >= 0; K finite and > 0.  fixed_count (S, NULL = none): -1 for a
+ * dynamic species, otherwise the constant count of a species held fixed (A and B of the
+ * Schloegl model); fixed reactants are folded into the rate constant, c_eff = c * prod C(n, m),
+ * and fixed species are never changed by a reaction.
+ * Errors: WE_EINVAL on any malformed input; WE_ENOMEM.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct we_network we_network;
+we_status we_network_create(int32_t n_species, int32_t n_reactions,
+                            const int32_t *reac_ptr, const int32_t *reac_species,
+                            const int32_t *reac_mult, const int32_t *prod_ptr,
+                            const int32_t *prod_species, const int32_t *prod_mult,
+                            int32_t n_param_sets, const double *rate, const int32_t *rate_law,
+                            const int32_t *hill_species, int32_t hill_K_rows, const double *hill_K,
+                            const int32_t *hill_n, const int32_t *fixed_count, we_network **out);
+void we_network_destroy(we_network *net);
+/* Effective (folded) rate constant of reaction j in parameter set p; for Hill reactions
+ * c*K^n.  Host-side query for tests. */
+we_status we_network_keff(const we_network *net, int32_t p, int32_t j, double *out);
+/* Number of reactions whose propensity may change when reaction j fires (dependency-graph
+ * out-degree, j itself included when affected). */
+we_status we_network_dep_degree(const we_network *net, int32_t j, int32_t *out);
+
+/* ------------------------------------------------------------------------------------------
+ * Bin maps (Sec. II.B: non-overlapping bins, regular 1-D or 2-D grids).
+ *
+ * Grid: ndim in 1..4 dimensions; dimension d bins species[d] with n_bins[d] bins given by
+ * n_bins[d]+1 ascending edges (concatenated over dimensions in `edges`).  Bin k of a dimension
+ * is [edge_k, edge_{k+1}); counts below the first edge fall in bin 0 and counts at or above the
+ * last edge in the last bin (give a last edge of +INFINITY for an overflow bin).  The flat bin
+ * index is row-major, last dimension fastest.  Errors: WE_EINVAL (non-ascending edges, NaN,
+ * more than 65536 bins in total).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct we_binmap we_binmap;
+we_status we_binmap_grid(int32_t ndim, const int32_t *species, const int32_t *n_bins,
+                         const double *edges, we_binmap **out);
+void we_binmap_destroy(we_binmap *bm);
+int32_t we_binmap_n_bins(const we_binmap *bm);
+
+/* ------------------------------------------------------------------------------------------
+ * Run configuration (the arguments of the WE procedure, Sec. II.B: tau, M_targ, the grid,
+ * the initial state, plus the recycling target of Sec. II.B.2).  A configuration describes
+ * n_runs independent WE runs executed together (a batch: replicas or a parameter sweep).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+  double tau;                      /* WE interval (> 0) */
+  int32_t m_targ;                  /* walkers per occupied bin after resampling (>= 1) */
+  int32_t n_runs;                  /* independent runs in the batch (>= 1) */
+  uint64_t seed;                   /* Philox key: word 0 = low 32 bits, word 1 = high 32 bits + run id */
+  const uint32_t *run_ids;         /* n_runs run ids (NULL: 0..n_runs-1) */
+  const int32_t *param_set;        /* n_runs parameter-set indices (NULL: run % n_param_sets) */
+  int32_t n_init;                  /* walkers per run at the start (>= 1, <= capacity) */
+  const int32_t *init_states;      /* n_runs x n_init x S species counts, walker-major */
+  const double *init_weights;      /* n_runs x n_init weights */
+  int32_t first_iter;              /* index of the first WE iteration (resume) */
+  int32_t capacity;                /* walker slots per run (0: max(m_targ * n_bins, n_init)) */
+  int32_t record_iters;            /* iterations of observables kept on the device (>= 1) */
+  int32_t feedback;                /* 1: recycle walkers that enter the target set */
+  int32_t n_clauses;               /* target set B = AND of clauses (1..4 when feedback) */
+  int32_t tgt_species[4];
+  int32_t tgt_op[4];               /* WE_OP_GE / WE_OP_LE */
+  const int32_t *tgt_threshold;    /* n_runs x n_clauses */
+  const int32_t *recycle_state;    /* n_runs x S (NULL: the run's first initial walker) */
+  int64_t max_steps;               /* events per walker per interval before WE_ESTEPCAP
+                                      (<=0: WE_DEFAULT_MAX_STEPS) */
+  int32_t hist_species;            /* species of the weighted histogram */
+  int32_t hist_len;                /* histogram entries (0: none); the last one collects x >= hist_len-1 */
+  int32_t resample;                /* 1: weighted ensemble; 0: plain SSA propagation */
+  int32_t mapping;                 /* WE_MAP_AUTO / WE_MAP_THREAD / WE_MAP_WARP */
+  int32_t block_threads;           /* threads per block of the SSA kernel (0: auto) */
+} we_run_config;
+
+/* ------------------------------------------------------------------------------------------
+ * Ensemble: the walkers of every run of a batch, resident in device memory as
+ * structure-of-arrays (counts int32[S][runs*capacity], weights double[runs*capacity]).
+ *
+ * we_ensemble_workspace_bytes: device bytes an ensemble needs for (net, bins, cfg).
+ * we_ensemble_create: validates, compiles the device tables and uploads the initial walkers.
+ *   workspace: caller-owned device buffer of at least workspace_bytes (256-byte aligned), or
+ *   NULL to let the library allocate.  The workspace must outlive the ensemble.
+ * Errors: WE_EINVAL, WE_ENOMEM (also when workspace_bytes is too small), WE_ECUDA.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct we_ensemble we_ensemble;
+we_status we_ensemble_workspace_bytes(const we_network *net, const we_binmap *bins,
+                                      const we_run_config *cfg, size_t *bytes);
+we_status we_ensemble_create(const we_network *net, const we_binmap *bins,
+                             const we_run_config *cfg, void *workspace, size_t workspace_bytes,
+                             void *stream, we_ensemble **out);
+we_status we_ensemble_destroy(we_ensemble *ens);
+
+/* One SSA interval of length tau for every live walker (Sec. II.A; the "propagate dynamics"
+ * step of the WE algorithm), with in-interval recycling when feedback is on, followed by bin
+ * assignment and the observables of the interval.  Enqueue only. */
+we_status we_ensemble_propagate(we_ensemble *ens, void *stream);
+/* Split/merge of every occupied bin of every run (Sec. II.B): afterwards each occupied bin
+ * holds m_targ walkers and each bin keeps its total weight.  Advances the iteration counter.
+ * Enqueue only. */
+we_status we_ensemble_resample(we_ensemble *ens, void *stream);
+/* n_iters full WE iterations (propagate + resample), replayed from a CUDA graph captured on
+ * the first call.  Enqueue only.  Errors: WE_EOVERFLOW if record_iters would be exceeded. */
+we_status we_ensemble_step(we_ensemble *ens, int32_t n_iters, void *stream);
+/* The same n_iters iterations as we_ensemble_step, with the device time of every iteration's
+ * SSA kernel measured by CUDA events recorded on `stream` on either side of it; synchronises
+ * the stream and writes n_iters durations in milliseconds to propagate_ms (host array). */
+we_status we_ensemble_step_timed(we_ensemble *ens, int32_t n_iters, void *stream,
+                                 float *propagate_ms);
+/* Synchronise the stream and return the first non-OK device status of any run (or WE_OK). */
+we_status we_ensemble_sync(we_ensemble *ens, void *stream);
+
+/* Outputs.  `what` selects an array; `run` selects a run (or -1 for all runs, concatenated).
+ * dst may be host or device memory (copied with cudaMemcpyDefault after synchronising the
+ * stream); dst == NULL only returns the byte count in *needed.  Layouts:
+ *   WE_OUT_COUNTS    int32[runs]                    live walkers per run
+ *   WE_OUT_STATES    int32[n_live x S]              walker-major counts of one run
+ *   WE_OUT_WEIGHTS   double[n_live]
+ *   WE_OUT_PARENT    int32[n_live]                  slot before the last resampling
+ *   WE_OUT_FLUX      double[iters x runs]           recycled weight per interval
+ *   WE_OUT_TOTAL_W   double[iters x runs]           sum of weights after resampling
+ *   WE_OUT_NWALKERS  int32[iters x runs]            walkers after resampling
+ *   WE_OUT_EVENTS    int64[iters x runs]            SSA events fired per interval
+ *   WE_OUT_HIST      double[iters x runs x hist_len] weighted histogram after propagation
+ *   WE_OUT_STATUS    int32[runs]                    first device status of each run
+ *   WE_OUT_ITER      int32[1]                       next iteration index
+ *   WE_OUT_RECORDED  int32[1]                       iterations of observables recorded
+ *   WE_OUT_TLAST     double[n_prev]                 time of each walker's last event in the
+ *                                                   last propagated interval (0 if none), by
+ *                                                   the slot it held then (before resampling)
+ * Per-iteration arrays hold the recorded iterations in order. */
+#define WE_OUT_COUNTS 1
+#define WE_OUT_STATES 2
+#define WE_OUT_WEIGHTS 3
+#define WE_OUT_PARENT 4
+#define WE_OUT_FLUX 5
+#define WE_OUT_TOTAL_W 6
+#define WE_OUT_NWALKERS 7
+#define WE_OUT_EVENTS 8
+#define WE_OUT_HIST 9
+#define WE_OUT_STATUS 10
+#define WE_OUT_ITER 11
+#define WE_OUT_RECORDED 12
+#define WE_OUT_TLAST 13
+we_status we_ensemble_get(we_ensemble *ens, int32_t what, int32_t run, void *dst,
+                          size_t dst_bytes, size_t *needed, void *stream);
+
+/* Whole WE procedure in one call (Sec. II.B): create an ensemble in library-owned memory,
+ * run cfg->record_iters iterations, synchronise, and return the ensemble for we_ensemble_get.
+ * Host inputs, host or device outputs. */
+we_status we_run(const we_network *net, const we_binmap *bins, const we_run_config *cfg,
+                 void *stream, we_ensemble **out);
+
+/* Autotuner: time the SSA kernel mappings and block sizes on a short probe of this
+ * configuration and return the fastest (mapping, block_threads).  Results are cached per
+ * (S, M, walkers, device) for the life of the process. */
+we_status we_autotune(const we_network *net, const we_binmap *bins, const we_run_config *cfg,
+                      void *stream, int32_t *mapping, int32_t *block_threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -43,7 +43,7 @@ class WEConfigC(C.Structure):
 class WEOut(C.Structure):
     _fields_ = [("flux_weight", _F64P), ("total_weight", _F64P), ("n_walkers", _I32P),
                 ("events", _I64P), ("hist", _F64P), ("states", _I32P), ("weights", _F64P),
-                ("parent", _I32P), ("n_final", C.c_int32), ("status", C.c_int32)]
+                ("parent", _I32P), ("t_last", _F64P), ("n_final", C.c_int32), ("status", C.c_int32)]
 
 
 _lib = None
@@ -69,7 +69,7 @@ def lib():
         L.orc_tree_select.argtypes = [C.c_int32, _F64P, C.c_double]
         L.orc_tree_select.restype = C.c_int32
         L.orc_propagate.argtypes = [C.c_void_p, C.POINTER(WEConfigC), C.c_int32, C.c_int32, _I32P,
-                                    _I64P, _I32P]
+                                    _I64P, _I32P, _F64P]
         L.orc_propagate.restype = C.c_int
         L.orc_bin_of.argtypes = [C.POINTER(WEConfigC), _I32P]
         L.orc_bin_of.restype = C.c_int32
@@ -206,14 +206,16 @@ def we_run(cfg, run: int = 0, n_iters: int | None = None, first_iter: int | None
         "flux_weight": np.zeros(n), "total_weight": np.zeros(n),
         "n_walkers": np.zeros(n, dtype=np.int32), "events": np.zeros(n, dtype=np.int64),
         "hist": np.zeros((n, max(cfg.hist_len, 1))), "states": np.zeros((cap, S), dtype=np.int32),
-        "weights": np.zeros(cap), "parent": np.zeros(cap, dtype=np.int32),
+        "weights": np.zeros(cap), "parent": np.zeros(cap, dtype=np.int32), "t_last": np.zeros(cap),
     }
     out = WEOut(_p(o["flux_weight"], _F64P), _p(o["total_weight"], _F64P),
                 _p(o["n_walkers"], _I32P), _p(o["events"], _I64P),
                 _p(o["hist"], _F64P) if cfg.hist_len > 0 else None,
-                _p(o["states"], _I32P), _p(o["weights"], _F64P), _p(o["parent"], _I32P), 0, 0)
+                _p(o["states"], _I32P), _p(o["weights"], _F64P), _p(o["parent"], _I32P),
+                _p(o["t_last"], _F64P), 0, 0)
     lib().orc_we_run(net.h, C.byref(c), C.byref(out))
     nf = out.n_final
+    o["t_last_prev"] = o["t_last"]
     o["states"] = o["states"][:nf]
     o["weights"] = o["weights"][:nf]
     o["parent"] = o["parent"][:nf]
@@ -231,7 +233,9 @@ def propagate_one(cfg, x, iteration: int, slot: int, run: int = 0, net: Network 
     xs = np.ascontiguousarray(x, dtype=np.int32).copy()
     ev = C.c_int64(0)
     rec = C.c_int32(0)
-    rc = lib().orc_propagate(net.h, C.byref(c), iteration, slot, _p(xs, _I32P), C.byref(ev), C.byref(rec))
+    tl = C.c_double(0.0)
+    rc = lib().orc_propagate(net.h, C.byref(c), iteration, slot, _p(xs, _I32P), C.byref(ev), C.byref(rec),
+                             C.byref(tl))
     return xs, ev.value, rec.value, rc
 
 

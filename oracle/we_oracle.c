@@ -262,7 +262,7 @@ static int in_target(const orc_we_config *cfg, const int32_t *x) {
  * running for the rest of the interval (first passage is detected at the event that crosses).
  * ------------------------------------------------------------------------------------------ */
 int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int32_t slot,
-                  int32_t *x, int64_t *n_ev, int32_t *n_rec) {
+                  int32_t *x, int64_t *n_ev, int32_t *n_rec, double *t_last) {
   const int32_t S = n->S, M = n->M;
   double *a = (double *)malloc(sizeof(double) * M);
   int32_t *xn = (int32_t *)malloc(sizeof(int32_t) * S);
@@ -287,7 +287,7 @@ int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int3
     double dt = e / a0;
     double tn = t + dt;
     if (tn > cfg->tau) break;
-    if (cfg->max_steps > 0 && ev >= cfg->max_steps) { status = ORC_ESTEPCAP; break; }
+    if (ev >= (cfg->max_steps > 0 ? cfg->max_steps : ORC_DEFAULT_MAX_STEPS)) { status = ORC_ESTEPCAP; break; }
     double target = u2 * a0;
     int32_t j = orc_tree_select(M, a, target);
     memcpy(xn, x, sizeof(int32_t) * S);
@@ -310,6 +310,7 @@ int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int3
   free(a); free(xn);
   *n_ev = ev;
   *n_rec = rec;
+  if (t_last) *t_last = t;
   return status;
 }
 
@@ -451,7 +452,8 @@ int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
     int64_t events = 0;
     for (int32_t s = 0; s < nw; ++s) {
       int64_t ev = 0;
-      int32_t rc = orc_propagate(n, cfg, iter, s, st + (size_t)s * S, &ev, &nrec[s]);
+      int32_t rc = orc_propagate(n, cfg, iter, s, st + (size_t)s * S, &ev, &nrec[s],
+                                 out->t_last ? &out->t_last[s] : NULL);
       events += ev;
       if (rc != ORC_OK && status == ORC_OK) status = rc;
     }

@@ -38,6 +38,8 @@ enum { ORC_MASS_ACTION = 0, ORC_HILL_REPRESSION = 1 };
 enum { ORC_OP_GE = 0, ORC_OP_LE = 1 };
 /* Largest species count a walker may hold; products of up to three counts then fit in int64. */
 #define ORC_MAX_COUNT 2097151
+/* Events one walker may fire in one interval when no cap is configured (then ORC_ESTEPCAP). */
+#define ORC_DEFAULT_MAX_STEPS (1ll << 26)
 
 typedef struct {
   int32_t n_species, n_reactions;
@@ -71,7 +73,7 @@ typedef struct {
   int32_t n_clauses;                 /* target set = AND of clauses  x[species] op threshold */
   int32_t tgt_species[4], tgt_op[4], tgt_threshold[4];
   const int32_t *recycle_state;      /* S */
-  int64_t max_steps;                 /* per walker per interval; <=0 means no cap */
+  int64_t max_steps;                 /* per walker per interval; <=0: ORC_DEFAULT_MAX_STEPS */
   int32_t capacity;                  /* walker slots */
   int32_t hist_species, hist_len;    /* weighted histogram of one species, last entry = overflow */
   int32_t resample;                  /* 0: plain propagation (no split/merge) */
@@ -88,6 +90,8 @@ typedef struct {
   int32_t *states;                   /* capacity x S */
   double *weights;
   int32_t *parent;                   /* slot of the parent in the previous interval */
+  double *t_last;                    /* capacity: last event time of each walker in the last
+                                        interval, by slot before resampling (may be NULL) */
   int32_t n_final;
   int32_t status;
 } orc_we_out;
@@ -110,9 +114,10 @@ double orc_tree_total(int32_t n, const double *a);
 /* Reaction selected by a tree descent on target in [0, total). */
 int32_t orc_tree_select(int32_t n, const double *a, double target);
 
-/* One walker for one interval; returns status.  *n_rec = recycles, *n_ev = events fired. */
+/* One walker for one interval; returns status.  *n_rec = recycles, *n_ev = events fired,
+ * *t_last = time of the last event fired in the interval (0 if none; may be NULL). */
 int orc_propagate(const orc_net *net, const orc_we_config *cfg, int32_t iter, int32_t slot,
-                  int32_t *x, int64_t *n_ev, int32_t *n_rec);
+                  int32_t *x, int64_t *n_ev, int32_t *n_rec, double *t_last);
 int32_t orc_bin_of(const orc_we_config *cfg, const int32_t *x);
 
 /* Split/merge of one ensemble, given every walker's bin.  Inputs are n walkers (states S wide).

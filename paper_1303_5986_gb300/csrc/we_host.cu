@@ -1,0 +1,854 @@
+// we_host.cu -- host side of the C ABI declared in include/we_ssa.h: validation, network
+// compilation (constant folding, net changes, dependency graph), device workspace layout,
+// kernel launches and CUDA-graph replay of whole WE iterations.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/we_ssa.h"
+#include "we_internal.cuh"
+
+namespace we {
+cudaError_t launch_propagate_thread(const PropagateParams &prm, int block, cudaStream_t st);
+cudaError_t launch_propagate_warp(const PropagateParams &prm, int block, cudaStream_t st);
+size_t propagate_thread_smem(const NetView &N, int block);
+size_t propagate_warp_smem(const NetView &N, int block);
+cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st);
+cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st);
+cudaError_t launch_pack_states(const EnsView &E, int r, int32_t *out, cudaStream_t st);
+}  // namespace we
+
+using namespace we;
+
+// ------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static we_status fail(we_status code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+static we_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(WE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define WE_CUDA_TRY(call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+  } while (0)
+
+extern "C" const char *we_status_string(we_status s) {
+  switch (s) {
+    case WE_OK: return "WE_OK";
+    case WE_EINVAL: return "WE_EINVAL";
+    case WE_ENOMEM: return "WE_ENOMEM";
+    case WE_ECUDA: return "WE_ECUDA";
+    case WE_EOVERFLOW: return "WE_EOVERFLOW";
+    case WE_ESTEPCAP: return "WE_ESTEPCAP";
+    case WE_ETIMEOUT: return "WE_ETIMEOUT";
+    case WE_ENOTSUPPORTED: return "WE_ENOTSUPPORTED";
+    default: return "WE_UNKNOWN";
+  }
+}
+
+extern "C" const char *we_last_error(void) { return g_last_error.c_str(); }
+extern "C" int32_t we_version(void) { return 100; }
+
+// ------------------------------------------------------------------------------------------
+// network compilation
+// ------------------------------------------------------------------------------------------
+struct we_network {
+  int32_t S = 0, M = 0, P = 1, log2P = 0, nps = 1;
+  std::vector<RxnMeta> meta;        // P
+  std::vector<double> keff, Kn;     // nps x P
+  std::vector<int32_t> d_sp, d_val;
+  std::vector<int32_t> dep_ptr, dep_idx;
+  std::vector<int32_t> fixed;       // S
+};
+
+static long long binom_small_h(long long x, int m) {
+  return m == 1 ? x : (m == 2 ? x * (x - 1) / 2 : x * (x - 1) * (x - 2) / 6);
+}
+
+extern "C" we_status we_network_create(int32_t S, int32_t M, const int32_t *reac_ptr,
+                                       const int32_t *reac_species, const int32_t *reac_mult,
+                                       const int32_t *prod_ptr, const int32_t *prod_species,
+                                       const int32_t *prod_mult, int32_t nps, const double *rate,
+                                       const int32_t *rate_law, const int32_t *hill_species,
+                                       int32_t hill_K_rows, const double *hill_K,
+                                       const int32_t *hill_n, const int32_t *fixed_count,
+                                       we_network **out) {
+  if (!out) return fail(WE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (S < 1 || M < 1) return fail(WE_EINVAL, "need n_species >= 1 and n_reactions >= 1");
+  if (nps < 1) return fail(WE_EINVAL, "n_param_sets must be >= 1");
+  if (!reac_ptr || !prod_ptr || !rate) return fail(WE_EINVAL, "reac_ptr, prod_ptr and rate are required");
+  if (reac_ptr[0] != 0 || prod_ptr[0] != 0) return fail(WE_EINVAL, "CSR pointers must start at 0");
+  for (int j = 0; j < M; ++j)
+    if (reac_ptr[j + 1] < reac_ptr[j] || prod_ptr[j + 1] < prod_ptr[j])
+      return fail(WE_EINVAL, "CSR pointers must be non-decreasing (reaction %d)", j);
+  if ((reac_ptr[M] > 0 && (!reac_species || !reac_mult)) || (prod_ptr[M] > 0 && (!prod_species || !prod_mult)))
+    return fail(WE_EINVAL, "species/multiplicity arrays are required");
+  bool any_hill = false;
+  if (rate_law)
+    for (int j = 0; j < M; ++j) {
+      if (rate_law[j] != WE_MASS_ACTION && rate_law[j] != WE_HILL_REPRESSION)
+        return fail(WE_EINVAL, "reaction %d: unknown rate law %d", j, rate_law[j]);
+      any_hill |= rate_law[j] == WE_HILL_REPRESSION;
+    }
+  if (any_hill && (!hill_species || !hill_K || !hill_n || (hill_K_rows != 1 && hill_K_rows != nps)))
+    return fail(WE_EINVAL, "Hill reactions need hill_species, hill_n and hill_K with 1 or n_param_sets rows");
+  std::vector<int32_t> fixed(S, -1);
+  if (fixed_count)
+    for (int s = 0; s < S; ++s) {
+      if (fixed_count[s] < -1 || fixed_count[s] > WE_MAX_COUNT)
+        return fail(WE_EINVAL, "fixed_count[%d] out of range", s);
+      fixed[s] = fixed_count[s];
+    }
+  for (int i = 0; i < nps * M; ++i)
+    if (!(rate[i] >= 0.0) || std::isinf(rate[i])) return fail(WE_EINVAL, "rate[%d] must be finite and >= 0", i);
+
+  we_network *n = new (std::nothrow) we_network();
+  if (!n) return fail(WE_ENOMEM, "host allocation");
+  n->S = S; n->M = M; n->nps = nps; n->fixed = fixed;
+  int P = 1, L = 0;
+  while (P < M) { P <<= 1; ++L; }
+  n->P = P; n->log2P = L;
+  n->meta.assign(P, RxnMeta{});
+  n->keff.assign((size_t)nps * P, 0.0);
+  n->Kn.assign((size_t)nps * P, 0.0);
+  std::vector<std::vector<int32_t>> reads(M);       // dynamic species each propensity reads
+  std::vector<std::vector<int32_t>> changes(M);     // dynamic species each reaction changes
+  std::vector<long long> rm(S), net(S);
+  for (int j = 0; j < M; ++j) {
+    std::fill(rm.begin(), rm.end(), 0);
+    std::fill(net.begin(), net.end(), 0);
+    int order = 0;
+    for (int e = reac_ptr[j]; e < reac_ptr[j + 1]; ++e) {
+      const int s = reac_species[e], m = reac_mult[e];
+      if (s < 0 || s >= S || m < 1 || m > 3) { delete n; return fail(WE_EINVAL, "reaction %d: bad reactant entry", j); }
+      rm[s] += m; net[s] -= m; order += m;
+    }
+    for (int e = prod_ptr[j]; e < prod_ptr[j + 1]; ++e) {
+      const int s = prod_species[e], m = prod_mult[e];
+      if (s < 0 || s >= S || m < 0) { delete n; return fail(WE_EINVAL, "reaction %d: bad product entry", j); }
+      net[s] += m;
+    }
+    if (order > 3) { delete n; return fail(WE_EINVAL, "reaction %d: reactant order %d > 3", j, order); }
+    const int law = rate_law ? rate_law[j] : WE_MASS_ACTION;
+    RxnMeta &mt = n->meta[j];
+    mt.law = law;
+    // held-constant reactants fold into the rate constant, ascending species order
+    std::vector<double> fold(nps);
+    for (int p = 0; p < nps; ++p) fold[p] = rate[(size_t)p * M + j];
+    int nr = 0;
+    for (int s = 0; s < S; ++s) {
+      if (rm[s] == 0) continue;
+      if (fixed[s] >= 0) {
+        const double f = (double)binom_small_h(fixed[s], (int)rm[s]);
+        for (int p = 0; p < nps; ++p) fold[p] = fold[p] * f;
+      } else {
+        mt.sp[nr] = s; mt.m[nr] = (int)rm[s]; ++nr;
+        reads[j].push_back(s);
+      }
+    }
+    mt.n_reac = nr;
+    if (law == WE_HILL_REPRESSION) {
+      const int hs = hill_species[j], hn = hill_n[j];
+      if (nr != 0) { delete n; return fail(WE_EINVAL, "Hill reaction %d must have no dynamic reactant", j); }
+      if (hs < 0 || hs >= S || hn < 1 || hn > 3) { delete n; return fail(WE_EINVAL, "Hill reaction %d: bad species or exponent", j); }
+      mt.hsp = hs; mt.hn = hn;
+      if (fixed[hs] < 0) reads[j].push_back(hs);
+      for (int p = 0; p < nps; ++p) {
+        const double K = hill_K[(size_t)(hill_K_rows == 1 ? 0 : p) * M + j];
+        if (!(K > 0.0) || std::isinf(K)) { delete n; return fail(WE_EINVAL, "Hill reaction %d: K must be finite and > 0", j); }
+        double Kn = K;
+        for (int q = 1; q < hn; ++q) Kn = Kn * K;
+        n->Kn[(size_t)p * P + j] = Kn;
+        n->keff[(size_t)p * P + j] = fold[p] * Kn;
+      }
+    } else {
+      for (int p = 0; p < nps; ++p) n->keff[(size_t)p * P + j] = fold[p];
+    }
+    mt.d_begin = (int32_t)n->d_sp.size();
+    for (int s = 0; s < S; ++s) {
+      if (fixed[s] >= 0 || net[s] == 0) continue;
+      n->d_sp.push_back(s);
+      n->d_val.push_back((int32_t)net[s]);
+      changes[j].push_back(s);
+    }
+    mt.d_end = (int32_t)n->d_sp.size();
+  }
+  for (int j = M; j < P; ++j) { n->meta[j].d_begin = n->meta[j].d_end = (int32_t)n->d_sp.size(); }
+  // dependency graph: i depends on j when i reads a species that j changes
+  std::vector<std::vector<int32_t>> readers(S);
+  for (int i = 0; i < M; ++i)
+    for (int s : reads[i]) readers[s].push_back(i);
+  n->dep_ptr.assign(P + 1, 0);
+  for (int j = 0; j < P; ++j) {
+    std::set<int32_t> d;
+    if (j < M)
+      for (int s : changes[j])
+        for (int i : readers[s]) d.insert(i);
+    n->dep_ptr[j] = (int32_t)n->dep_idx.size();
+    n->dep_idx.insert(n->dep_idx.end(), d.begin(), d.end());
+  }
+  n->dep_ptr[P] = (int32_t)n->dep_idx.size();
+  *out = n;
+  return WE_OK;
+}
+
+extern "C" void we_network_destroy(we_network *n) { delete n; }
+
+extern "C" we_status we_network_keff(const we_network *n, int32_t p, int32_t j, double *out) {
+  if (!n || !out || p < 0 || p >= n->nps || j < 0 || j >= n->M) return fail(WE_EINVAL, "bad arguments");
+  *out = n->keff[(size_t)p * n->P + j];
+  return WE_OK;
+}
+
+extern "C" we_status we_network_dep_degree(const we_network *n, int32_t j, int32_t *out) {
+  if (!n || !out || j < 0 || j >= n->M) return fail(WE_EINVAL, "bad arguments");
+  *out = n->dep_ptr[j + 1] - n->dep_ptr[j];
+  return WE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// bin maps
+// ------------------------------------------------------------------------------------------
+struct we_binmap {
+  int32_t ndim = 0, n_bins = 1;
+  int32_t species[kMaxBinDims] = {0, 0, 0, 0};
+  int32_t nb[kMaxBinDims] = {1, 1, 1, 1};
+  int32_t edge_off[kMaxBinDims] = {0, 0, 0, 0};
+  std::vector<double> edges;
+};
+
+extern "C" we_status we_binmap_grid(int32_t ndim, const int32_t *species, const int32_t *n_bins,
+                                    const double *edges, we_binmap **out) {
+  if (!out) return fail(WE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (ndim < 1 || ndim > kMaxBinDims || !species || !n_bins || !edges)
+    return fail(WE_EINVAL, "ndim must be 1..%d with species, n_bins and edges given", kMaxBinDims);
+  we_binmap *b = new (std::nothrow) we_binmap();
+  if (!b) return fail(WE_ENOMEM, "host allocation");
+  b->ndim = ndim;
+  long long total = 1;
+  int off = 0;
+  for (int d = 0; d < ndim; ++d) {
+    if (n_bins[d] < 1 || species[d] < 0) { delete b; return fail(WE_EINVAL, "dimension %d: bad species or bin count", d); }
+    b->species[d] = species[d];
+    b->nb[d] = n_bins[d];
+    b->edge_off[d] = off;
+    for (int k = 0; k <= n_bins[d]; ++k) {
+      const double e = edges[off + k];
+      if (std::isnan(e)) { delete b; return fail(WE_EINVAL, "dimension %d: NaN edge", d); }
+      if (k > 0 && !(e > edges[off + k - 1])) { delete b; return fail(WE_EINVAL, "dimension %d: edges must ascend", d); }
+      b->edges.push_back(e);
+    }
+    off += n_bins[d] + 1;
+    total *= n_bins[d];
+    if (total > 65536) { delete b; return fail(WE_EINVAL, "more than 65536 bins"); }
+  }
+  b->n_bins = (int32_t)total;
+  *out = b;
+  return WE_OK;
+}
+
+extern "C" void we_binmap_destroy(we_binmap *b) { delete b; }
+extern "C" int32_t we_binmap_n_bins(const we_binmap *b) { return b ? b->n_bins : 0; }
+
+// ------------------------------------------------------------------------------------------
+// ensemble: workspace layout
+// ------------------------------------------------------------------------------------------
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+struct Offsets {
+  size_t meta, keff, Kn, d_sp, d_val, dep_ptr, dep_idx, edges;
+  size_t run_id, param_set, tgt_thr, recycle;
+  size_t x0, x1, w0, w1, p0, p1, bin, nrec, tlast;
+  size_t count, prev_count, run_off, status, iter, bin_count, n_tasks, tasks, cursor, sorted_slot, sorted_w, alive;
+  size_t flux, totw, nw, events, hist, pack;
+  size_t total;
+};
+
+static Offsets layout(const we_network *n, const we_binmap *b, const we_run_config *c, int cap) {
+  Layout L;
+  Offsets o{};
+  const size_t R = c->n_runs, RC = R * cap, rec = c->record_iters;
+  o.meta = L.take(sizeof(RxnMeta) * n->P);
+  o.keff = L.take(8 * n->keff.size());
+  o.Kn = L.take(8 * n->Kn.size());
+  o.d_sp = L.take(4 * (n->d_sp.size() + 1));
+  o.d_val = L.take(4 * (n->d_val.size() + 1));
+  o.dep_ptr = L.take(4 * n->dep_ptr.size());
+  o.dep_idx = L.take(4 * (n->dep_idx.size() + 1));
+  o.edges = L.take(8 * b->edges.size());
+  o.run_id = L.take(4 * R);
+  o.param_set = L.take(4 * R);
+  o.tgt_thr = L.take(4 * R * (c->n_clauses > 0 ? c->n_clauses : 1));
+  o.recycle = L.take(4 * R * n->S);
+  o.x0 = L.take(4 * RC * n->S);
+  o.x1 = L.take(4 * RC * n->S);
+  o.w0 = L.take(8 * RC);
+  o.w1 = L.take(8 * RC);
+  o.p0 = L.take(4 * RC);
+  o.p1 = L.take(4 * RC);
+  o.bin = L.take(4 * RC);
+  o.nrec = L.take(4 * RC);
+  o.tlast = L.take(8 * RC);
+  o.count = L.take(4 * R);
+  o.prev_count = L.take(4 * R);
+  o.run_off = L.take(4 * (R + 1));
+  o.status = L.take(4 * R);
+  o.iter = L.take(4);
+  o.bin_count = L.take(4 * R * b->n_bins);
+  o.n_tasks = L.take(4 * R);
+  o.tasks = L.take(16 * R * b->n_bins);
+  o.cursor = L.take(4 * R * b->n_bins);
+  o.sorted_slot = L.take(4 * RC);
+  o.sorted_w = L.take(8 * RC);
+  o.alive = L.take(4 * RC);
+  o.flux = L.take(8 * rec * R);
+  o.totw = L.take(8 * rec * R);
+  o.nw = L.take(4 * rec * R);
+  o.events = L.take(8 * rec * R);
+  o.hist = L.take(8 * rec * R * (c->hist_len > 0 ? c->hist_len : 1));
+  o.pack = L.take(4 * (size_t)cap * n->S);
+  o.total = L.off;
+  return o;
+}
+
+struct we_ensemble {
+  we_run_config cfg{};
+  int32_t S = 0, cap = 0, n_bins = 0;
+  int32_t mapping = WE_MAP_THREAD, block = 128;
+  void *ws = nullptr;
+  bool owns_ws = false;
+  Offsets off{};
+  PropagateParams prm{};
+  int32_t iters_enqueued = 0;       // iterations recorded so far (host view)
+  bool phase_propagated = false;
+  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t timed_graph = nullptr;
+  cudaGraphNode_t ev_node_start = nullptr, ev_node_end = nullptr;
+  cudaStream_t cap_stream = nullptr;
+};
+
+static we_status check_config(const we_network *n, const we_binmap *b, const we_run_config *c, int *cap_out) {
+  if (!n || !b || !c) return fail(WE_EINVAL, "network, bins and config are required");
+  if (!(c->tau > 0.0) || std::isinf(c->tau)) return fail(WE_EINVAL, "tau must be finite and > 0");
+  if (c->m_targ < 1) return fail(WE_EINVAL, "m_targ must be >= 1");
+  if (c->n_runs < 1) return fail(WE_EINVAL, "n_runs must be >= 1");
+  if (c->n_init < 1 || !c->init_states || !c->init_weights) return fail(WE_EINVAL, "need n_init >= 1 initial walkers with states and weights");
+  if (c->record_iters < 1) return fail(WE_EINVAL, "record_iters must be >= 1");
+  if (c->first_iter < 0) return fail(WE_EINVAL, "first_iter must be >= 0");
+  for (int d = 0; d < b->ndim; ++d)
+    if (b->species[d] >= n->S) return fail(WE_EINVAL, "bin dimension %d names species %d >= S", d, b->species[d]);
+  long long cap = c->capacity > 0 ? c->capacity : std::max<long long>((long long)c->m_targ * b->n_bins, c->n_init);
+  if (cap < c->n_init) return fail(WE_EINVAL, "capacity %lld < n_init %d", cap, c->n_init);
+  if (cap * c->n_runs > (1ll << 30)) return fail(WE_EINVAL, "runs x capacity too large");
+  if (c->feedback) {
+    if (c->n_clauses < 1 || c->n_clauses > kMaxClauses || !c->tgt_threshold) return fail(WE_EINVAL, "feedback needs 1..4 target clauses with thresholds");
+    for (int k = 0; k < c->n_clauses; ++k) {
+      if (c->tgt_species[k] < 0 || c->tgt_species[k] >= n->S) return fail(WE_EINVAL, "target clause %d: bad species", k);
+      if (c->tgt_op[k] != WE_OP_GE && c->tgt_op[k] != WE_OP_LE) return fail(WE_EINVAL, "target clause %d: bad operator", k);
+    }
+  }
+  if (c->hist_len < 0 || (c->hist_len > 0 && (c->hist_species < 0 || c->hist_species >= n->S)))
+    return fail(WE_EINVAL, "bad histogram species/length");
+  if (c->param_set)
+    for (int r = 0; r < c->n_runs; ++r)
+      if (c->param_set[r] < 0 || c->param_set[r] >= n->nps) return fail(WE_EINVAL, "run %d: parameter set out of range", r);
+  for (long long i = 0; i < (long long)c->n_runs * c->n_init * n->S; ++i) {
+    const int v = c->init_states[i];
+    if (v < 0 || v > WE_MAX_COUNT) return fail(WE_EINVAL, "initial count %lld out of range", i);
+  }
+  for (long long i = 0; i < (long long)c->n_runs * c->n_init; ++i)
+    if (!(c->init_weights[i] >= 0.0) || std::isinf(c->init_weights[i])) return fail(WE_EINVAL, "initial weight %lld must be finite and >= 0", i);
+  *cap_out = (int)cap;
+  return WE_OK;
+}
+
+extern "C" we_status we_ensemble_workspace_bytes(const we_network *n, const we_binmap *b,
+                                                 const we_run_config *c, size_t *bytes) {
+  if (!bytes) return fail(WE_EINVAL, "bytes is NULL");
+  int cap = 0;
+  we_status st = check_config(n, b, c, &cap);
+  if (st) return st;
+  *bytes = layout(n, b, c, cap).total;
+  return WE_OK;
+}
+
+template <typename T>
+static T *at(void *base, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(base) + off); }
+
+static int choose_mapping(const we_network *n, const we_run_config *c) {
+  if (c->mapping == WE_MAP_THREAD || c->mapping == WE_MAP_WARP) return c->mapping;
+  return (n->P <= kThreadMaxLeaves && n->S <= kThreadMaxSpecies) ? WE_MAP_THREAD : WE_MAP_WARP;
+}
+
+extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
+                                        const we_run_config *c, void *workspace,
+                                        size_t workspace_bytes, void *stream, we_ensemble **out) {
+  if (!out) return fail(WE_EINVAL, "out is NULL");
+  *out = nullptr;
+  int cap = 0;
+  we_status st = check_config(n, b, c, &cap);
+  if (st) return st;
+  const int mapping = choose_mapping(n, c);
+  if (mapping == WE_MAP_THREAD && (n->P > kThreadMaxLeaves || n->S > kThreadMaxSpecies))
+    return fail(WE_ENOTSUPPORTED, "thread mapping needs <= %d reactions and <= %d species", kThreadMaxLeaves, kThreadMaxSpecies);
+  const int block = c->block_threads > 0 ? c->block_threads : (mapping == WE_MAP_THREAD ? 128 : 256);
+  if (mapping == WE_MAP_THREAD && block != 32 && block != 64 && block != 96 && block != 128)
+    return fail(WE_EINVAL, "thread mapping supports block_threads of 32, 64, 96 or 128");
+  Offsets o = layout(n, b, c, cap);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void *ws = workspace;
+  bool owns = false;
+  if (ws) {
+    if (workspace_bytes < o.total) return fail(WE_ENOMEM, "workspace of %zu bytes < %zu needed", workspace_bytes, o.total);
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(WE_EINVAL, "workspace must be 256-byte aligned");
+  } else {
+    cudaError_t e = cudaMalloc(&ws, o.total);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(WE_ENOMEM, "cudaMalloc(%zu): %s", o.total, cudaGetErrorString(e)); }
+    owns = true;
+  }
+  we_ensemble *E = new (std::nothrow) we_ensemble();
+  if (!E) { if (owns) cudaFree(ws); return fail(WE_ENOMEM, "host allocation"); }
+  E->cfg = *c;
+  E->cfg.capacity = cap;
+  E->S = n->S; E->cap = cap; E->n_bins = b->n_bins;
+  E->mapping = mapping; E->block = block;
+  E->ws = ws; E->owns_ws = owns; E->off = o;
+  auto cleanup = [&](we_status code) { if (owns) cudaFree(ws); delete E; return code; };
+
+  const int R = c->n_runs, S = n->S;
+  const size_t RC = (size_t)R * cap;
+  // host images of everything uploaded
+  std::vector<int32_t> run_id(R), pset(R), thr(R * (c->n_clauses > 0 ? c->n_clauses : 1), 0), rec((size_t)R * S);
+  for (int r = 0; r < R; ++r) {
+    run_id[r] = c->run_ids ? (int32_t)c->run_ids[r] : r;
+    pset[r] = c->param_set ? c->param_set[r] : r % n->nps;
+    for (int k = 0; k < c->n_clauses && c->feedback; ++k) thr[r * c->n_clauses + k] = c->tgt_threshold[r * c->n_clauses + k];
+    for (int sp = 0; sp < S; ++sp)
+      rec[(size_t)r * S + sp] = c->recycle_state ? c->recycle_state[(size_t)r * S + sp] : c->init_states[(size_t)r * c->n_init * S + sp];
+  }
+  if (c->feedback)
+    for (int r = 0; r < R; ++r) {
+      bool in = true;
+      for (int k = 0; k < c->n_clauses; ++k) {
+        const int v = rec[(size_t)r * S + c->tgt_species[k]];
+        in = in && (c->tgt_op[k] == WE_OP_GE ? v >= thr[r * c->n_clauses + k] : v <= thr[r * c->n_clauses + k]);
+      }
+      if (in) return cleanup(fail(WE_EINVAL, "run %d: the recycle state lies inside the target set", r));
+    }
+  const int par0 = c->first_iter & 1;
+  std::vector<int32_t> xh((size_t)S * RC, 0), ph(RC, -1), cnt(R, c->n_init), roff(R + 1);
+  std::vector<double> wh(RC, 0.0);
+  for (int r = 0; r < R; ++r)
+    for (int w = 0; w < c->n_init; ++w) {
+      const size_t g = (size_t)r * cap + w;
+      for (int sp = 0; sp < S; ++sp) xh[(size_t)sp * RC + g] = c->init_states[((size_t)r * c->n_init + w) * S + sp];
+      wh[g] = c->init_weights[(size_t)r * c->n_init + w];
+    }
+  for (int r = 0; r <= R; ++r) roff[r] = r * c->n_init;
+  int32_t it0 = c->first_iter;
+  auto up = [&](size_t offs, const void *src, size_t bytes) -> cudaError_t {
+    if (!bytes) return cudaSuccess;
+    return cudaMemcpyAsync(at<char>(ws, offs), src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMemsetAsync(ws, 0, o.total, s);
+  e = e ? e : up(o.meta, n->meta.data(), sizeof(RxnMeta) * n->P);
+  e = e ? e : up(o.keff, n->keff.data(), 8 * n->keff.size());
+  e = e ? e : up(o.Kn, n->Kn.data(), 8 * n->Kn.size());
+  e = e ? e : up(o.d_sp, n->d_sp.data(), 4 * n->d_sp.size());
+  e = e ? e : up(o.d_val, n->d_val.data(), 4 * n->d_val.size());
+  e = e ? e : up(o.dep_ptr, n->dep_ptr.data(), 4 * n->dep_ptr.size());
+  e = e ? e : up(o.dep_idx, n->dep_idx.data(), 4 * n->dep_idx.size());
+  e = e ? e : up(o.edges, b->edges.data(), 8 * b->edges.size());
+  e = e ? e : up(o.run_id, run_id.data(), 4 * R);
+  e = e ? e : up(o.param_set, pset.data(), 4 * R);
+  e = e ? e : up(o.tgt_thr, thr.data(), 4 * thr.size());
+  e = e ? e : up(o.recycle, rec.data(), 4 * rec.size());
+  e = e ? e : up(par0 ? o.x1 : o.x0, xh.data(), 4 * xh.size());
+  e = e ? e : up(par0 ? o.w1 : o.w0, wh.data(), 8 * wh.size());
+  e = e ? e : up(par0 ? o.p1 : o.p0, ph.data(), 4 * ph.size());
+  e = e ? e : up(o.count, cnt.data(), 4 * R);
+  e = e ? e : up(o.prev_count, cnt.data(), 4 * R);
+  e = e ? e : up(o.run_off, roff.data(), 4 * (R + 1));
+  e = e ? e : up(o.iter, &it0, 4);
+  e = e ? e : cudaStreamSynchronize(s);
+  if (e) { cudaGetLastError(); return cleanup(cuda_fail(e, "ensemble upload")); }
+
+  NetView &N = E->prm.net;
+  N.S = S; N.M = n->M; N.P = n->P; N.log2P = n->log2P; N.n_param_sets = n->nps;
+  N.n_delta = (int32_t)n->d_sp.size();
+  N.meta = at<RxnMeta>(ws, o.meta);
+  N.keff = at<double>(ws, o.keff);
+  N.hill_Kn = at<double>(ws, o.Kn);
+  N.d_sp = at<int32_t>(ws, o.d_sp);
+  N.d_val = at<int32_t>(ws, o.d_val);
+  N.dep_ptr = at<int32_t>(ws, o.dep_ptr);
+  N.dep_idx = at<int32_t>(ws, o.dep_idx);
+  BinView &Bv = E->prm.bins;
+  Bv.ndim = b->ndim; Bv.n_bins = b->n_bins;
+  for (int d = 0; d < kMaxBinDims; ++d) { Bv.species[d] = b->species[d]; Bv.nb[d] = b->nb[d]; Bv.edge_off[d] = b->edge_off[d]; }
+  Bv.edges = at<double>(ws, o.edges);
+  EnsView &V = E->prm.ens;
+  V.R = R; V.cap = cap; V.S = S; V.m_targ = c->m_targ; V.record_iters = c->record_iters;
+  V.first_iter = c->first_iter; V.hist_species = c->hist_species; V.hist_len = c->hist_len;
+  V.feedback = c->feedback ? 1 : 0; V.n_clauses = c->feedback ? c->n_clauses : 0;
+  for (int k = 0; k < kMaxClauses; ++k) { V.tgt_species[k] = c->tgt_species[k]; V.tgt_op[k] = c->tgt_op[k]; }
+  V.max_steps = c->max_steps > 0 ? c->max_steps : WE_DEFAULT_MAX_STEPS;
+  V.tau = c->tau; V.seed = c->seed;
+  V.run_id = at<uint32_t>(ws, o.run_id);
+  V.param_set = at<int32_t>(ws, o.param_set);
+  V.tgt_thr = at<int32_t>(ws, o.tgt_thr);
+  V.recycle = at<int32_t>(ws, o.recycle);
+  V.x[0] = at<int32_t>(ws, o.x0); V.x[1] = at<int32_t>(ws, o.x1);
+  V.w[0] = at<double>(ws, o.w0); V.w[1] = at<double>(ws, o.w1);
+  V.parent[0] = at<int32_t>(ws, o.p0); V.parent[1] = at<int32_t>(ws, o.p1);
+  V.bin = at<int32_t>(ws, o.bin); V.nrec = at<int32_t>(ws, o.nrec); V.tlast = at<double>(ws, o.tlast);
+  V.count = at<int32_t>(ws, o.count); V.prev_count = at<int32_t>(ws, o.prev_count);
+  V.run_off = at<int32_t>(ws, o.run_off);
+  V.status = at<int32_t>(ws, o.status); V.iter = at<int32_t>(ws, o.iter);
+  V.bin_count = at<int32_t>(ws, o.bin_count); V.n_tasks = at<int32_t>(ws, o.n_tasks);
+  V.tasks = at<int4>(ws, o.tasks); V.cursor = at<int32_t>(ws, o.cursor);
+  V.sorted_slot = at<int32_t>(ws, o.sorted_slot);
+  V.sorted_w = at<double>(ws, o.sorted_w); V.alive = at<int32_t>(ws, o.alive);
+  V.obs_flux = at<double>(ws, o.flux); V.obs_totw = at<double>(ws, o.totw);
+  V.obs_nw = at<int32_t>(ws, o.nw); V.obs_events = at<unsigned long long>(ws, o.events);
+  V.obs_hist = at<double>(ws, o.hist);
+  E->prm.resample = c->resample ? 1 : 0;
+  *out = E;
+  return WE_OK;
+}
+
+extern "C" we_status we_ensemble_destroy(we_ensemble *E) {
+  if (!E) return WE_OK;
+  if (E->graph) cudaGraphExecDestroy(E->graph);
+  if (E->timed_graph) cudaGraphExecDestroy(E->timed_graph);
+  if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
+  if (E->owns_ws) cudaFree(E->ws);
+  delete E;
+  return WE_OK;
+}
+
+static cudaError_t enqueue_propagate(we_ensemble *E, cudaStream_t s) {
+  if (E->mapping == WE_MAP_WARP) return launch_propagate_warp(E->prm, E->block, s);
+  return launch_propagate_thread(E->prm, E->block, s);
+}
+
+static cudaError_t enqueue_resample(we_ensemble *E, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (E->prm.resample) e = launch_resample_chain(E->prm, s);
+  if (e) return e;
+  return launch_gather_finalize(E->prm, s);
+}
+
+extern "C" we_status we_ensemble_propagate(we_ensemble *E, void *stream) {
+  if (!E) return fail(WE_EINVAL, "ensemble is NULL");
+  if (E->phase_propagated) return fail(WE_EINVAL, "propagate called twice without resample");
+  if (E->iters_enqueued >= E->cfg.record_iters) return fail(WE_EOVERFLOW, "record_iters (%d) exhausted", E->cfg.record_iters);
+  cudaError_t e = enqueue_propagate(E, static_cast<cudaStream_t>(stream));
+  if (e) return cuda_fail(e, "propagate launch");
+  E->phase_propagated = true;
+  return WE_OK;
+}
+
+extern "C" we_status we_ensemble_resample(we_ensemble *E, void *stream) {
+  if (!E) return fail(WE_EINVAL, "ensemble is NULL");
+  if (!E->phase_propagated) return fail(WE_EINVAL, "resample called before propagate");
+  cudaError_t e = enqueue_resample(E, static_cast<cudaStream_t>(stream));
+  if (e) return cuda_fail(e, "resample launch");
+  E->phase_propagated = false;
+  E->iters_enqueued += 1;
+  return WE_OK;
+}
+
+extern "C" we_status we_ensemble_step(we_ensemble *E, int32_t n_iters, void *stream) {
+  if (!E) return fail(WE_EINVAL, "ensemble is NULL");
+  if (n_iters < 0) return fail(WE_EINVAL, "n_iters must be >= 0");
+  if (E->phase_propagated) return fail(WE_EINVAL, "step called between propagate and resample");
+  if (E->iters_enqueued + n_iters > E->cfg.record_iters)
+    return fail(WE_EOVERFLOW, "%d more iterations would exceed record_iters (%d)", n_iters, E->cfg.record_iters);
+  if (n_iters == 0) return WE_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!E->graph) {
+    WE_CUDA_TRY(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
+    WE_CUDA_TRY(cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = enqueue_propagate(E, E->cap_stream);
+    cudaError_t e2 = e1 ? e1 : enqueue_resample(E, E->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(E->cap_stream, &g);
+    if (e2 || e3) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return cuda_fail(e2 ? e2 : e3, "graph capture"); }
+    cudaError_t e4 = cudaGraphInstantiate(&E->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e4) { E->graph = nullptr; return cuda_fail(e4, "graph instantiate"); }
+  }
+  for (int i = 0; i < n_iters; ++i) WE_CUDA_TRY(cudaGraphLaunch(E->graph, s));
+  E->iters_enqueued += n_iters;
+  return WE_OK;
+}
+
+// Timed replay: the same iteration graph, captured with an event-record node on each side of
+// the SSA kernel; before every replay the two nodes are pointed at that iteration's events.
+static we_status build_timed_graph(we_ensemble *E) {
+  if (!E->cap_stream) WE_CUDA_TRY(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
+  cudaEvent_t ea, eb;
+  WE_CUDA_TRY(cudaEventCreate(&ea));
+  WE_CUDA_TRY(cudaEventCreate(&eb));
+  WE_CUDA_TRY(cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e1 = cudaEventRecord(ea, E->cap_stream);
+  e1 = e1 ? e1 : enqueue_propagate(E, E->cap_stream);
+  e1 = e1 ? e1 : cudaEventRecord(eb, E->cap_stream);
+  e1 = e1 ? e1 : enqueue_resample(E, E->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(E->cap_stream, &g);
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  if (e1 || e2) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return cuda_fail(e1 ? e1 : e2, "timed graph capture"); }
+  size_t n = 0;
+  cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  cudaGraphGetNodes(g, nodes.data(), &n);
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    cudaGraphNodeGetType(nd, &t);
+    if (t != cudaGraphNodeTypeEventRecord) continue;
+    size_t nd_deps = 0;
+    cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps);
+    if (nd_deps == 0) E->ev_node_start = nd; else E->ev_node_end = nd;
+  }
+  cudaError_t e3 = (E->ev_node_start && E->ev_node_end) ? cudaGraphInstantiate(&E->timed_graph, g, 0) : cudaErrorUnknown;
+  cudaGraphDestroy(g);
+  if (e3) { E->timed_graph = nullptr; return cuda_fail(e3, "timed graph instantiate"); }
+  return WE_OK;
+}
+
+extern "C" we_status we_ensemble_step_timed(we_ensemble *E, int32_t n_iters, void *stream,
+                                            float *propagate_ms) {
+  if (!E || !propagate_ms) return fail(WE_EINVAL, "ensemble and propagate_ms are required");
+  if (n_iters < 0) return fail(WE_EINVAL, "n_iters must be >= 0");
+  if (E->phase_propagated) return fail(WE_EINVAL, "step called between propagate and resample");
+  if (E->iters_enqueued + n_iters > E->cfg.record_iters)
+    return fail(WE_EOVERFLOW, "%d more iterations would exceed record_iters (%d)", n_iters, E->cfg.record_iters);
+  if (n_iters == 0) return WE_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!E->timed_graph) {
+    we_status st = build_timed_graph(E);
+    if (st) return st;
+  }
+  std::vector<cudaEvent_t> ev(2 * (size_t)n_iters, nullptr);
+  auto release = [&]() { for (auto e : ev) if (e) cudaEventDestroy(e); };
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); release(); return fail(WE_ECUDA, "event creation"); }
+  for (int i = 0; i < n_iters; ++i) {
+    cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(E->timed_graph, E->ev_node_start, ev[2 * i]);
+    e = e ? e : cudaGraphExecEventRecordNodeSetEvent(E->timed_graph, E->ev_node_end, ev[2 * i + 1]);
+    e = e ? e : cudaGraphLaunch(E->timed_graph, s);
+    if (e) { cudaGetLastError(); release(); return cuda_fail(e, "timed graph launch"); }
+  }
+  E->iters_enqueued += n_iters;
+  cudaError_t e = cudaEventSynchronize(ev[2 * (size_t)n_iters - 1]);
+  for (int i = 0; i < n_iters && !e; ++i) e = cudaEventElapsedTime(&propagate_ms[i], ev[2 * i], ev[2 * i + 1]);
+  release();
+  if (e) return cuda_fail(e, "event timing");
+  return WE_OK;
+}
+
+extern "C" we_status we_ensemble_sync(we_ensemble *E, void *stream) {
+  if (!E) return fail(WE_EINVAL, "ensemble is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WE_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int32_t> st(E->cfg.n_runs);
+  WE_CUDA_TRY(cudaMemcpy(st.data(), E->prm.ens.status, 4 * st.size(), cudaMemcpyDeviceToHost));
+  for (int r = 0; r < E->cfg.n_runs; ++r)
+    if (st[r]) return fail(st[r], "run %d reported %s on the device", r, we_status_string(st[r]));
+  return WE_OK;
+}
+
+extern "C" we_status we_ensemble_get(we_ensemble *E, int32_t what, int32_t run, void *dst,
+                                     size_t dst_bytes, size_t *needed, void *stream) {
+  if (!E) return fail(WE_EINVAL, "ensemble is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const EnsView &V = E->prm.ens;
+  const int R = E->cfg.n_runs;
+  if (run < -1 || run >= R) return fail(WE_EINVAL, "run %d out of range", run);
+  WE_CUDA_TRY(cudaStreamSynchronize(s));
+  int32_t iter = 0;
+  WE_CUDA_TRY(cudaMemcpy(&iter, V.iter, 4, cudaMemcpyDeviceToHost));
+  const int rec = std::min(E->iters_enqueued, E->cfg.record_iters);
+  const int par = iter & 1;
+  std::vector<int32_t> counts(R);
+  WE_CUDA_TRY(cudaMemcpy(counts.data(), V.count, 4 * R, cudaMemcpyDeviceToHost));
+  auto per_walker = [&](const void *base, size_t elem) -> we_status {
+    if (run < 0) return fail(WE_EINVAL, "walker arrays need a single run");
+    const size_t bytes = elem * counts[run];
+    if (needed) *needed = bytes;
+    if (!dst) return WE_OK;
+    if (dst_bytes < bytes) return fail(WE_EINVAL, "dst too small (%zu < %zu)", dst_bytes, bytes);
+    if (bytes) WE_CUDA_TRY(cudaMemcpy(dst, static_cast<const char *>(base) + elem * (size_t)run * E->cap, bytes, cudaMemcpyDefault));
+    return WE_OK;
+  };
+  auto per_iter = [&](const void *base, size_t elem_per_run) -> we_status {
+    const size_t rows = rec;
+    const size_t bytes = run < 0 ? rows * R * elem_per_run : rows * elem_per_run;
+    if (needed) *needed = bytes;
+    if (!dst) return WE_OK;
+    if (dst_bytes < bytes) return fail(WE_EINVAL, "dst too small (%zu < %zu)", dst_bytes, bytes);
+    if (!bytes) return WE_OK;
+    if (run < 0) WE_CUDA_TRY(cudaMemcpy(dst, base, bytes, cudaMemcpyDefault));
+    else WE_CUDA_TRY(cudaMemcpy2D(dst, elem_per_run, static_cast<const char *>(base) + (size_t)run * elem_per_run,
+                                  (size_t)R * elem_per_run, elem_per_run, rows, cudaMemcpyDefault));
+    return WE_OK;
+  };
+  auto scalar = [&](const void *src, size_t bytes) -> we_status {
+    if (needed) *needed = bytes;
+    if (!dst) return WE_OK;
+    if (dst_bytes < bytes) return fail(WE_EINVAL, "dst too small");
+    WE_CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));
+    return WE_OK;
+  };
+  switch (what) {
+    case WE_OUT_COUNTS: {
+      if (run >= 0) return scalar(&counts[run], 4);
+      return scalar(counts.data(), 4 * R);
+    }
+    case WE_OUT_STATES: {
+      if (run < 0) return fail(WE_EINVAL, "walker arrays need a single run");
+      const size_t bytes = (size_t)4 * counts[run] * E->S;
+      if (needed) *needed = bytes;
+      if (!dst) return WE_OK;
+      if (dst_bytes < bytes) return fail(WE_EINVAL, "dst too small (%zu < %zu)", dst_bytes, bytes);
+      if (!bytes) return WE_OK;
+      int32_t *pack = at<int32_t>(E->ws, E->off.pack);
+      cudaError_t e = launch_pack_states(V, run, pack, s);
+      if (e) return cuda_fail(e, "pack states");
+      WE_CUDA_TRY(cudaStreamSynchronize(s));
+      WE_CUDA_TRY(cudaMemcpy(dst, pack, bytes, cudaMemcpyDefault));
+      return WE_OK;
+    }
+    case WE_OUT_WEIGHTS: return per_walker(V.w[par], 8);
+    case WE_OUT_PARENT: return per_walker(V.parent[par], 4);
+    case WE_OUT_FLUX: return per_iter(V.obs_flux, 8);
+    case WE_OUT_TOTAL_W: return per_iter(V.obs_totw, 8);
+    case WE_OUT_NWALKERS: return per_iter(V.obs_nw, 4);
+    case WE_OUT_EVENTS: return per_iter(V.obs_events, 8);
+    case WE_OUT_HIST: return per_iter(V.obs_hist, 8 * (size_t)(E->cfg.hist_len > 0 ? E->cfg.hist_len : 1));
+    case WE_OUT_STATUS: {
+      std::vector<int32_t> st(R);
+      WE_CUDA_TRY(cudaMemcpy(st.data(), V.status, 4 * R, cudaMemcpyDeviceToHost));
+      if (run >= 0) return scalar(&st[run], 4);
+      return scalar(st.data(), 4 * R);
+    }
+    case WE_OUT_TLAST: {
+      if (run < 0) return fail(WE_EINVAL, "walker arrays need a single run");
+      int32_t pc = 0;
+      WE_CUDA_TRY(cudaMemcpy(&pc, V.prev_count + run, 4, cudaMemcpyDeviceToHost));
+      const size_t bytes = (size_t)8 * pc;
+      if (needed) *needed = bytes;
+      if (!dst) return WE_OK;
+      if (dst_bytes < bytes) return fail(WE_EINVAL, "dst too small (%zu < %zu)", dst_bytes, bytes);
+      if (bytes) WE_CUDA_TRY(cudaMemcpy(dst, V.tlast + (size_t)run * E->cap, bytes, cudaMemcpyDefault));
+      return WE_OK;
+    }
+    case WE_OUT_ITER: return scalar(&iter, 4);
+    case WE_OUT_RECORDED: { int32_t v = rec; return scalar(&v, 4); }
+    default: return fail(WE_EINVAL, "unknown output selector %d", what);
+  }
+}
+
+extern "C" we_status we_run(const we_network *n, const we_binmap *b, const we_run_config *c,
+                            void *stream, we_ensemble **out) {
+  if (!out) return fail(WE_EINVAL, "out is NULL");
+  *out = nullptr;
+  we_ensemble *E = nullptr;
+  we_status st = we_ensemble_create(n, b, c, nullptr, 0, stream, &E);
+  if (st) return st;
+  st = we_ensemble_step(E, c->record_iters, stream);
+  if (!st) st = we_ensemble_sync(E, stream);
+  if (st && st != WE_ESTEPCAP && st != WE_EOVERFLOW) { we_ensemble_destroy(E); return st; }
+  *out = E;
+  return st;
+}
+
+// ------------------------------------------------------------------------------------------
+// autotuner: time every supported (mapping, block) on a short probe, cache per shape
+// ------------------------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+extern "C" we_status we_autotune(const we_network *n, const we_binmap *b, const we_run_config *c,
+                                 void *stream, int32_t *mapping, int32_t *block_threads) {
+  if (!mapping || !block_threads) return fail(WE_EINVAL, "outputs are NULL");
+  int cap = 0;
+  we_status st = check_config(n, b, c, &cap);
+  if (st) return st;
+  int dev = 0;
+  WE_CUDA_TRY(cudaGetDevice(&dev));
+  auto key = std::make_tuple(n->S, n->M, c->n_runs * cap, dev, c->n_init);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) { *mapping = it->second.first; *block_threads = it->second.second; return WE_OK; }
+  }
+  std::vector<std::pair<int, int>> cands;
+  if (n->P <= kThreadMaxLeaves && n->S <= kThreadMaxSpecies)
+    for (int bt : {32, 64, 128}) cands.push_back({WE_MAP_THREAD, bt});
+  for (int bt : {128, 256}) cands.push_back({WE_MAP_WARP, bt});
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float best = 1e30f;
+  std::pair<int, int> pick = cands.front();
+  cudaEvent_t e0, e1;
+  WE_CUDA_TRY(cudaEventCreate(&e0));
+  WE_CUDA_TRY(cudaEventCreate(&e1));
+  for (auto cd : cands) {
+    we_run_config cc = *c;
+    cc.mapping = cd.first; cc.block_threads = cd.second; cc.record_iters = 4;
+    we_ensemble *E = nullptr;
+    if (we_ensemble_create(n, b, &cc, nullptr, 0, stream, &E) != WE_OK) continue;
+    bool ok = we_ensemble_step(E, 1, stream) == WE_OK && cudaStreamSynchronize(s) == cudaSuccess;
+    cudaEventRecord(e0, s);
+    ok = ok && we_ensemble_step(E, 3, stream) == WE_OK;
+    cudaEventRecord(e1, s);
+    ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0;
+    if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) { best = ms; pick = cd; }
+    we_ensemble_destroy(E);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = pick;
+  }
+  *mapping = pick.first;
+  *block_threads = pick.second;
+  return WE_OK;
+}

@@ -1,0 +1,110 @@
+// we_internal.cuh -- device-side data layout and kernel parameters shared by the library's
+// host code and kernels.  Not part of the public ABI (include/we_ssa.h is).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace we {
+
+constexpr int kMaxClauses = 4;
+constexpr int kMaxBinDims = 4;
+constexpr int kMaxReactantSlots = 3;
+constexpr int kThreadMaxLeaves = 16;     // thread-per-walker kernel: propensity tree in registers
+constexpr int kThreadMaxSpecies = 32;    // thread-per-walker kernel: counts staged in shared memory
+constexpr int32_t kMaxCount = 2097151;   // same bound as WE_MAX_COUNT
+
+// Per-reaction description used by every SSA kernel (int32 words, 16 per reaction).
+//   n_reac: dynamic reactant slots (0..3); sp[k], m[k]: species and multiplicity;
+//   law: 0 mass action, 1 Hill repression; hsp, hn: regulator species and Hill exponent;
+//   d_begin/d_end: range of this reaction's net changes in the delta arrays.
+struct RxnMeta {
+  int32_t n_reac;
+  int32_t sp[kMaxReactantSlots];
+  int32_t m[kMaxReactantSlots];
+  int32_t law;
+  int32_t hsp;
+  int32_t hn;
+  int32_t d_begin;
+  int32_t d_end;
+  int32_t pad[4];
+};
+static_assert(sizeof(RxnMeta) == 64, "RxnMeta is 64 bytes");
+
+// Device view of a compiled network (all pointers into the ensemble workspace).
+struct NetView {
+  int32_t S, M, P, log2P;      // P = leaves of the canonical tree (power of two >= M)
+  int32_t n_param_sets;
+  int32_t n_delta;             // total net-change entries
+  const RxnMeta *meta;         // P entries (padding reactions: n_reac = 0, keff = 0)
+  const double *keff;          // n_param_sets x P (mass action: folded c; Hill: c*K^n)
+  const double *hill_Kn;       // n_param_sets x P
+  const int32_t *d_sp;         // n_delta
+  const int32_t *d_val;        // n_delta
+  // dependency graph: reactions whose propensity reads a species changed by j (CSR over P)
+  const int32_t *dep_ptr;      // P + 1
+  const int32_t *dep_idx;
+};
+
+struct BinView {
+  int32_t ndim;
+  int32_t n_bins;
+  int32_t species[kMaxBinDims];
+  int32_t nb[kMaxBinDims];
+  int32_t edge_off[kMaxBinDims];
+  const double *edges;
+};
+
+// Ensemble state on the device.  Global slot g = run * cap + w.
+struct EnsView {
+  int32_t R, cap, S;
+  int32_t m_targ;
+  int32_t record_iters;
+  int32_t first_iter;
+  int32_t hist_species, hist_len;
+  int32_t feedback, n_clauses;
+  int32_t tgt_species[kMaxClauses];
+  int32_t tgt_op[kMaxClauses];
+  int64_t max_steps;
+  double tau;
+  uint64_t seed;
+  // per-run constants
+  const uint32_t *run_id;      // R
+  const int32_t *param_set;    // R
+  const int32_t *tgt_thr;      // R x n_clauses
+  const int32_t *recycle;      // R x S
+  // walker arrays, double-buffered by iteration parity
+  int32_t *x[2];               // S x (R*cap)
+  double *w[2];                // R*cap
+  int32_t *parent[2];          // R*cap
+  int32_t *bin;                // R*cap  bin of each walker after propagation
+  int32_t *nrec;               // R*cap  recycles of each walker in the last interval
+  double *tlast;               // R*cap  time of each walker's last event in the last interval
+  // per-run bookkeeping
+  int32_t *count;              // R      live walkers
+  int32_t *prev_count;         // R      walkers propagated in the last interval
+  int32_t *run_off;            // R + 1  exclusive prefix of count
+  int32_t *status;             // R
+  int32_t *iter;               // 1      current iteration index (absolute)
+  int32_t *bin_count;          // R x n_bins
+  int32_t *n_tasks;            // R
+  int4 *tasks;                 // R x n_bins: (bin, in_offset, count, out_offset)
+  int32_t *cursor;             // R x n_bins: next free position of each bin while grouping
+  int32_t *sorted_slot;        // R*cap   walkers grouped by bin (scratch)
+  double *sorted_w;            // R*cap
+  int32_t *alive;              // R*cap
+  // observables, record_iters x R (x hist_len)
+  double *obs_flux;
+  double *obs_totw;
+  int32_t *obs_nw;
+  unsigned long long *obs_events;
+  double *obs_hist;
+};
+
+struct PropagateParams {
+  NetView net;
+  BinView bins;
+  EnsView ens;
+  int32_t resample;            // 1: WE; 0: plain SSA (bookkeeping of parents is identity)
+};
+
+}  // namespace we

@@ -1,0 +1,568 @@
+// we_kernels.cu -- the device side of the weighted-ensemble Gillespie-SSA path.
+//
+//   k_propagate_thread<P>  one SSA interval per walker, one thread per walker (Sec. II.A; the
+//                          "propagate dynamics" step of the WE algorithm, Sec. II.B), with
+//                          in-interval recycling (Sec. II.B.2), bin assignment and observables
+//   k_scan_bins            per run: bin occupancy -> task list and output offsets
+//   k_resample             one warp per occupied bin: merge / split (Sec. II.B)
+//   k_gather               copy species counts of the new ensemble from their parents
+//   k_finalize             per-run counts and offsets, iteration counter
+//
+// Floating-point rules shared with the definition of the method (and its CPU restatement):
+// every propensity, tree node, target and weight operation is a single IEEE double operation
+// written with an explicit round-to-nearest intrinsic, so no multiply-add is ever fused.
+// Comparisons between non-negative doubles are made on their bit patterns (the IEEE order of
+// non-negative doubles is the integer order of their bits), which keeps them off the FP64 pipe.
+#include "we_internal.cuh"
+
+namespace we {
+
+constexpr int32_t kStatusStepCap = -5;
+constexpr int32_t kStatusOverflow = -4;
+
+// ------------------------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64 multiplies
+// whose high halves are xored with the other counter words and the key; the key advances by
+// the Weyl constants between rounds.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t &c0, uint32_t &c1, uint32_t &c2,
+                                              uint32_t &c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// (2m+1)/2^53 with m = hi<<20 | lo>>12: the double 1 + m/2^52 built from bits, minus
+// (1 - 2^-53).  The difference is representable, so the subtraction is exact.
+__device__ __forceinline__ double u01(uint32_t hi, uint32_t lo) {
+  const unsigned long long m = ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
+  const double one_plus = __longlong_as_double((long long)(0x3FF0000000000000ull | m));
+  return __dsub_rn(one_plus, 0x1.fffffffffffffp-1);
+}
+
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+
+__device__ __forceinline__ long long binom_small(long long x, int m) {
+  return m == 1 ? x : (m == 2 ? x * (x - 1) / 2 : x * (x - 1) * (x - 2) / 6);
+}
+
+// Propensity of one reaction from counts held at xs[species * stride].
+__device__ __forceinline__ double propensity(const RxnMeta &mt, double keff, double Kn,
+                                             const int32_t *xs, int stride) {
+  if (mt.law == 1) {
+    const long long y = xs[mt.hsp * stride];
+    long long yn = y;
+    if (mt.hn >= 2) yn *= y;
+    if (mt.hn >= 3) yn *= y;
+    const double den = __dadd_rn(Kn, __ll2double_rn(yn));
+    return __ddiv_rn(keff, den);
+  }
+  long long h = 1;
+  for (int k = 0; k < mt.n_reac; ++k) h *= binom_small(xs[mt.sp[k] * stride], mt.m[k]);
+  return __dmul_rn(keff, __ll2double_rn(h));
+}
+
+__device__ __forceinline__ int bin_of(const BinView &bv, const int32_t *xs, int stride) {
+  int flat = 0;
+#pragma unroll 1
+  for (int d = 0; d < bv.ndim; ++d) {
+    const double v = (double)xs[bv.species[d] * stride];
+    const double *e = bv.edges + bv.edge_off[d];
+    int lo = 0, hi = bv.nb[d] - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (e[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    flat = flat * bv.nb[d] + lo;
+  }
+  return flat;
+}
+
+__device__ __forceinline__ bool in_target(const EnsView &E, int r, const int32_t *xs, int stride) {
+  bool in = true;
+#pragma unroll 1
+  for (int c = 0; c < E.n_clauses; ++c) {
+    const int v = xs[E.tgt_species[c] * stride];
+    const int thr = E.tgt_thr[r * E.n_clauses + c];
+    in = in && (E.tgt_op[c] == 0 ? v >= thr : v <= thr);
+  }
+  return in;
+}
+
+__device__ __forceinline__ int find_run(const int32_t *run_off, int R, int f) {
+  int lo = 0, hi = R;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (run_off[mid] <= f) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------------------------------
+// One thread per walker.  The canonical propensity tree (P leaves, node k = node 2k + node
+// 2k+1, rounded) lives in registers; every index into it is a compile-time constant after
+// unrolling, and the descent picks children with predicated selects.  Species counts are
+// staged in shared memory so that reactions can name them by runtime index.
+// ------------------------------------------------------------------------------------------
+template <int P, int LOG2P>
+__global__ void __launch_bounds__(128) k_propagate_thread(PropagateParams prm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const NetView &N = prm.net;
+  const EnsView &E = prm.ens;
+  const int B = blockDim.x, tid = threadIdx.x;
+  RxnMeta *s_meta = reinterpret_cast<RxnMeta *>(smem_raw);
+  double *s_keff = reinterpret_cast<double *>(s_meta + P);
+  double *s_Kn = s_keff + N.n_param_sets * P;
+  int32_t *s_dsp = reinterpret_cast<int32_t *>(s_Kn + N.n_param_sets * P);
+  int32_t *s_dval = s_dsp + N.n_delta;
+  int32_t *xs = s_dval + N.n_delta;
+  for (int i = tid; i < P * 16; i += B)
+    reinterpret_cast<int32_t *>(s_meta)[i] = reinterpret_cast<const int32_t *>(N.meta)[i];
+  for (int i = tid; i < N.n_param_sets * P; i += B) { s_keff[i] = N.keff[i]; s_Kn[i] = N.hill_Kn[i]; }
+  for (int i = tid; i < N.n_delta; i += B) { s_dsp[i] = N.d_sp[i]; s_dval[i] = N.d_val[i]; }
+  __syncthreads();
+
+  const int iter = *E.iter;
+  const int total = E.run_off[E.R];
+  const int f = blockIdx.x * B + tid;
+  if (f >= total) return;
+  const int r = E.R == 1 ? 0 : find_run(E.run_off, E.R, f);
+  const int w = f - E.run_off[r];
+  const int g = r * E.cap + w;
+  const int par = iter & 1;
+  const int ld = E.R * E.cap;
+  int32_t *X = E.x[par];
+  int32_t *xme = xs + tid;
+  for (int s = 0; s < E.S; ++s) xme[s * B] = X[(size_t)s * ld + g];
+  const int ps = E.param_set[r];
+  const double *keff = s_keff + ps * P;
+  const double *Kn = s_Kn + ps * P;
+  const uint32_t k0 = (uint32_t)E.seed;
+  const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
+
+  double nd[2 * P];
+  auto rebuild = [&]() {
+#pragma unroll
+    for (int j = 0; j < P; ++j) nd[P + j] = propensity(s_meta[j], keff[j], Kn[j], xme, B);
+#pragma unroll
+    for (int k = P - 1; k >= 1; --k) nd[k] = __dadd_rn(nd[2 * k], nd[2 * k + 1]);
+  };
+  rebuild();
+
+  const long long tau_bits = bits(E.tau);
+  double t = 0.0;
+  uint32_t draw = 0;
+  long long nev = 0;
+  int nrec = 0;
+  int status = 0;
+  for (;;) {
+    const double a0 = nd[1];
+    if (bits(a0) == 0) break;                        // nothing can fire: idle to tau
+    uint32_t c0 = draw, c1 = (uint32_t)iter, c2 = (uint32_t)w, c3 = 0u;
+    ++draw;
+    philox4x32_10(c0, c1, c2, c3, k0, k1);
+    const double u1 = u01(c0, c1);
+    const double u2 = u01(c2, c3);
+    const double e = -log(u1);
+    const double dt = __ddiv_rn(e, a0);
+    const double tn = __dadd_rn(t, dt);
+    if (bits(tn) > tau_bits) break;                  // the next event falls after tau
+    if (nev >= E.max_steps) { status = kStatusStepCap; break; }
+    double target = __dmul_rn(u2, a0);
+    int k = 1;
+#pragma unroll
+    for (int lvl = 0; lvl < LOG2P; ++lvl) {
+      double L = 0.0, R = 0.0;
+#pragma unroll
+      for (int c = (1 << lvl); c < (2 << lvl); ++c)
+        if (k == c) { L = nd[2 * c]; R = nd[2 * c + 1]; }
+      const bool right = (bits(R) != 0) && !(bits(target) < bits(L));
+      if (right) { target = __dsub_rn(target, L); k = 2 * k + 1; }
+      else { k = 2 * k; }
+    }
+    const RxnMeta &mt = s_meta[k - P];
+    bool over = false;
+    for (int q = mt.d_begin; q < mt.d_end; ++q)
+      over |= (xme[s_dsp[q] * B] + s_dval[q]) > kMaxCount;
+    if (over) { status = kStatusOverflow; break; }
+    for (int q = mt.d_begin; q < mt.d_end; ++q) xme[s_dsp[q] * B] += s_dval[q];
+    ++nev;
+    t = tn;
+    if (E.feedback && in_target(E, r, xme, B)) {
+      ++nrec;
+      for (int s = 0; s < E.S; ++s) xme[s * B] = E.recycle[r * E.S + s];
+    }
+    rebuild();
+  }
+
+  for (int s = 0; s < E.S; ++s) X[(size_t)s * ld + g] = xme[s * B];
+  E.nrec[g] = nrec;
+  E.tlast[g] = t;
+  if (status) atomicCAS(&E.status[r], 0, status);
+  const int b = bin_of(prm.bins, xme, B);
+  E.bin[g] = b;
+  if (prm.resample) atomicAdd(&E.bin_count[r * prm.bins.n_bins + b], 1);
+  const int slot = iter - E.first_iter;
+  if (slot >= 0 && slot < E.record_iters) {
+    const double wt = E.w[par][g];
+    const int o = slot * E.R + r;
+    if (nrec) atomicAdd(&E.obs_flux[o], __dmul_rn((double)nrec, wt));
+    if (nev) atomicAdd(&E.obs_events[o], (unsigned long long)nev);
+    if (E.hist_len > 0) {
+      const int v = xme[E.hist_species * B];
+      const int idx = v < E.hist_len - 1 ? v : E.hist_len - 1;
+      atomicAdd(&E.obs_hist[(size_t)o * E.hist_len + idx], wt);
+    }
+    if (!prm.resample) atomicAdd(&E.obs_totw[o], wt);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Per run (one block): exclusive scans of bin counts and of bin occupancy give, for every
+// occupied bin, where its walkers go when grouped by bin (in_offset) and where its M_targ
+// resampled walkers go in the new ensemble (out_offset = M_targ * occupied bins before it).
+// ------------------------------------------------------------------------------------------
+__global__ void k_scan_bins(EnsView E, int n_bins) {
+  const int r = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = B >> 5;
+  __shared__ int s_cnt[32], s_occ[32];
+  __shared__ int s_base_cnt, s_base_occ;
+  if (tid == 0) { s_base_cnt = 0; s_base_occ = 0; }
+  __syncthreads();
+  int *bc = E.bin_count + (size_t)r * n_bins;
+  int4 *tasks = E.tasks + (size_t)r * n_bins;
+  for (int base = 0; base < n_bins; base += B) {
+    const int b = base + tid;
+    const int c = b < n_bins ? bc[b] : 0;
+    const int o = c > 0 ? 1 : 0;
+    int ic = c, io = o;                                   // inclusive warp scans
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int yc = __shfl_up_sync(0xffffffffu, ic, d);
+      const int yo = __shfl_up_sync(0xffffffffu, io, d);
+      if (lane >= d) { ic += yc; io += yo; }
+    }
+    if (lane == 31) { s_cnt[wid] = ic; s_occ[wid] = io; }
+    __syncthreads();
+    if (wid == 0) {
+      int vc = lane < nw ? s_cnt[lane] : 0, vo = lane < nw ? s_occ[lane] : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int yc = __shfl_up_sync(0xffffffffu, vc, d);
+        const int yo = __shfl_up_sync(0xffffffffu, vo, d);
+        if (lane >= d) { vc += yc; vo += yo; }
+      }
+      if (lane < nw) { s_cnt[lane] = vc; s_occ[lane] = vo; }
+    }
+    __syncthreads();
+    const int wc = wid ? s_cnt[wid - 1] : 0, wo = wid ? s_occ[wid - 1] : 0;
+    const int ex_c = s_base_cnt + wc + ic - c;
+    const int ex_o = s_base_occ + wo + io - o;
+    if (o) {
+      tasks[ex_o] = make_int4(b, ex_c, c, ex_o * E.m_targ);
+      E.cursor[(size_t)r * n_bins + b] = ex_c;
+    }
+    if (b < n_bins) bc[b] = 0;                            // ready for the next interval
+    __syncthreads();
+    if (tid == 0) { s_base_cnt += s_cnt[nw - 1]; s_base_occ += s_occ[nw - 1]; }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    E.n_tasks[r] = s_base_occ;
+    if ((long long)s_base_occ * E.m_targ > E.cap) atomicCAS(&E.status[r], 0, kStatusOverflow);
+  }
+}
+
+// Walkers of every run grouped by bin: each live walker takes the next free position of its
+// bin (positions start at the bin's in_offset).  The order inside a bin is arbitrary; every
+// later decision is keyed by the walker's slot, never by its position.
+__global__ void k_place(EnsView E, int n_bins) {
+  const int iter = *E.iter;
+  const int par = iter & 1;
+  const int ld = E.R * E.cap;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ld; g += gridDim.x * blockDim.x) {
+    const int r = g / E.cap, w = g - r * E.cap;
+    if (w >= E.count[r]) continue;
+    const int b = E.bin[g];
+    const int pos = atomicAdd(&E.cursor[(size_t)r * n_bins + b], 1);
+    const size_t q = (size_t)r * E.cap + pos;
+    E.sorted_slot[q] = w;
+    E.sorted_w[q] = E.w[par][g];
+    E.alive[q] = 1;
+  }
+}
+
+// Warp argmin over the live entries of a bin list, keyed by (weight bits, slot).
+__device__ __forceinline__ void warp_argmin(const double *sw, const int32_t *ss, const int32_t *al,
+                                            int cnt, int exclude, int &best_i) {
+  const int lane = threadIdx.x & 31;
+  long long bw = 0x7FFFFFFFFFFFFFFFll;
+  int bs = 0x7FFFFFFF, bi = -1;
+  for (int i = lane; i < cnt; i += 32) {
+    if (!al[i] || i == exclude) continue;
+    const long long v = bits(sw[i]);
+    const int sl = ss[i];
+    if (v < bw || (v == bw && sl < bs)) { bw = v; bs = sl; bi = i; }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const long long ow = __shfl_xor_sync(0xffffffffu, bw, d);
+    const int os = __shfl_xor_sync(0xffffffffu, bs, d);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, d);
+    if (ow < bw || (ow == bw && os < bs)) { bw = ow; bs = os; bi = oi; }
+  }
+  best_i = bi;
+}
+
+// ------------------------------------------------------------------------------------------
+// Split/merge, one warp per occupied bin (Sec. II.B).  A bin's walkers are ordered by slot:
+//   more than M_targ: merge the two lightest (ties: lower slot); of the pair, the lower-slot
+//     walker p survives iff u < w_p/(w_p+w_q), u from Philox counter (k, iter, bin, 1) with k
+//     the merge index, and takes the summed weight; repeat;
+//   fewer than M_targ: give the next copy to the walker with the largest w_i/c_i (ties: lower
+//     slot), until M_targ copies; each copy carries w_i/c_i.
+// The resampled walkers are written in slot order, copies right after their parent, at the
+// bin's output offset.
+// ------------------------------------------------------------------------------------------
+__global__ void k_resample(EnsView E, int n_bins) {
+  const int r = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n_warps = (gridDim.x * blockDim.x) >> 5;
+  const int nt = E.n_tasks[r];
+  const int iter = *E.iter;
+  const int par = iter & 1;
+  const int M = E.m_targ;
+  const size_t base = (size_t)r * E.cap;
+  double *W2 = E.w[par ^ 1] + base;
+  int32_t *P2 = E.parent[par ^ 1] + base;
+  const uint32_t k0 = (uint32_t)E.seed;
+  const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
+  const int slot_obs = iter - E.first_iter;
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  for (int t = warp; t < nt; t += n_warps) {
+    const int4 tk = E.tasks[(size_t)r * n_bins + t];
+    const int b = tk.x, in0 = tk.y, cnt = tk.z, out0 = tk.w;
+    if (out0 + M > E.cap) continue;                       // capacity overflow, already flagged
+    int32_t *lss = E.sorted_slot + base + in0;
+    double *lsw = E.sorted_w + base + in0;
+    int32_t *lal = E.alive + base + in0;
+    if (cnt > M) {
+      uint32_t kmerge = 0;
+      for (int live = cnt; live > M; --live) {
+        int ia, ib;
+        warp_argmin(lsw, lss, lal, cnt, -1, ia);
+        warp_argmin(lsw, lss, lal, cnt, ia, ib);
+        if (lane == 0) {
+          const bool a_first = lss[ia] < lss[ib];
+          const int p = a_first ? ia : ib, q = a_first ? ib : ia;
+          uint32_t c0 = kmerge, c1 = (uint32_t)iter, c2 = (uint32_t)b, c3 = 1u;
+          philox4x32_10(c0, c1, c2, c3, k0, k1);
+          const double u = u01(c0, c1);
+          const double wsum = __dadd_rn(lsw[p], lsw[q]);
+          const double prob = __ddiv_rn(lsw[p], wsum);
+          if (bits(u) < bits(prob)) { lsw[p] = wsum; lal[q] = 0; }
+          else { lsw[q] = wsum; lal[p] = 0; }
+        }
+        ++kmerge;
+        __syncwarp();
+      }
+    } else if (cnt < M) {
+      for (int extra = cnt; extra < M; ++extra) {
+        long long bv = -1;
+        int bs = 0x7FFFFFFF, bi = -1;
+        for (int i = lane; i < cnt; i += 32) {
+          const long long v = bits(__ddiv_rn(lsw[i], (double)lal[i]));
+          const int sl = lss[i];
+          if (v > bv || (v == bv && sl < bs)) { bv = v; bs = sl; bi = i; }
+        }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+          const long long ov = __shfl_xor_sync(0xffffffffu, bv, d);
+          const int os = __shfl_xor_sync(0xffffffffu, bs, d);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, d);
+          if (ov > bv || (ov == bv && os < bs)) { bv = ov; bs = os; bi = oi; }
+        }
+        if (lane == 0) lal[bi] += 1;
+        __syncwarp();
+      }
+    }
+    // Compact the surviving entries (copies > 0) to the front of the list, order kept.
+    int k = 0;
+    for (int i0 = 0; i0 < cnt; i0 += 32) {
+      const int i = i0 + lane;
+      int sl = 0, c = 0;
+      double wv = 0.0;
+      if (i < cnt) { sl = lss[i]; c = lal[i]; wv = lsw[i]; }
+      const unsigned m = __ballot_sync(0xffffffffu, c > 0);
+      __syncwarp();
+      if (c > 0) {
+        const int d = k + __popc(m & lt_mask);
+        lss[d] = sl; lal[d] = c; lsw[d] = wv;
+      }
+      k += __popc(m);
+      __syncwarp();
+    }
+    // Output offset of each survivor: copies of all survivors with a lower slot.
+    double wsum_local = 0.0;
+    for (int i = lane; i < k; i += 32) {
+      const int si = lss[i];
+      int off = 0;
+      for (int j = 0; j < k; ++j) off += (lss[j] < si) ? lal[j] : 0;
+      const int c = lal[i];
+      const double wc = (cnt < M) ? __ddiv_rn(lsw[i], (double)c) : lsw[i];
+      for (int q = 0; q < c; ++q) {
+        W2[out0 + off + q] = wc;
+        P2[out0 + off + q] = si;
+        wsum_local = __dadd_rn(wsum_local, wc);
+      }
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) wsum_local = __dadd_rn(wsum_local, __shfl_xor_sync(0xffffffffu, wsum_local, d));
+    if (lane == 0 && slot_obs >= 0 && slot_obs < E.record_iters)
+      atomicAdd(&E.obs_totw[slot_obs * E.R + r], wsum_local);
+    __syncwarp();
+  }
+}
+
+// New counts of every run: M_targ per occupied bin (resampling) or unchanged (plain SSA).
+__device__ __forceinline__ int new_count(const EnsView &E, int r, int resample) {
+  if (!resample) return E.count[r];
+  const long long c = (long long)E.n_tasks[r] * E.m_targ;
+  return c > E.cap ? E.cap : (int)c;
+}
+
+// Species counts of the new ensemble, gathered from each walker's parent.  With plain SSA the
+// parent is the walker itself and its weight is carried over.
+__global__ void k_gather(EnsView E, int resample) {
+  const int iter = *E.iter;
+  const int par = iter & 1;
+  const int ld = E.R * E.cap;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ld; g += gridDim.x * blockDim.x) {
+    const int r = g / E.cap, w = g - r * E.cap;
+    if (w >= new_count(E, r, resample)) continue;
+    int src = w;
+    if (resample) src = E.parent[par ^ 1][g];
+    else { E.parent[par ^ 1][g] = w; E.w[par ^ 1][g] = E.w[par][g]; }
+    const int gs = r * E.cap + src;
+    for (int s = 0; s < E.S; ++s) E.x[par ^ 1][(size_t)s * ld + g] = E.x[par][(size_t)s * ld + gs];
+  }
+}
+
+// One block: counts, run offsets and the walker-count observable; advance the iteration.
+__global__ void k_finalize(EnsView E, int resample) {
+  __shared__ int s_new[1024];
+  const int iter = *E.iter;
+  const int slot = iter - E.first_iter;
+  for (int r = threadIdx.x; r < E.R; r += blockDim.x) {
+    const int c = new_count(E, r, resample);
+    if (r < 1024) s_new[r] = c;
+    if (slot >= 0 && slot < E.record_iters) E.obs_nw[slot * E.R + r] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int r = 0; r < E.R; ++r) {
+      const int c = r < 1024 ? s_new[r] : new_count(E, r, resample);
+      E.run_off[r] = acc;
+      acc += c;
+    }
+    E.run_off[E.R] = acc;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < E.R; r += blockDim.x) {
+    const int c = r < 1024 ? s_new[r] : new_count(E, r, resample);
+    E.prev_count[r] = E.count[r];
+    E.count[r] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *E.iter = iter + 1;
+}
+
+// Walker-major copy of one run's counts (for output).
+__global__ void k_pack_states(EnsView E, int r, int32_t *out) {
+  const int iter = *E.iter;
+  const int par = iter & 1;
+  const int n = E.count[r];
+  const int ld = E.R * E.cap;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * E.S; i += gridDim.x * blockDim.x) {
+    const int w = i / E.S, s = i - w * E.S;
+    out[i] = E.x[par][(size_t)s * ld + (size_t)r * E.cap + w];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Host-side launch helpers (called from we_host.cu).
+// ------------------------------------------------------------------------------------------
+size_t propagate_thread_smem(const NetView &N, int block) {
+  return (size_t)N.P * sizeof(RxnMeta) + 2 * (size_t)N.n_param_sets * N.P * sizeof(double) +
+         2 * (size_t)N.n_delta * sizeof(int32_t) + (size_t)N.S * block * sizeof(int32_t);
+}
+
+template <int P, int L>
+static cudaError_t launch_thread(const PropagateParams &prm, int grid, int block, size_t smem,
+                                 cudaStream_t st) {
+  auto kern = k_propagate_thread<P, L>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, block, smem, st>>>(prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_thread(const PropagateParams &prm, int block, cudaStream_t st) {
+  const int total_slots = prm.ens.R * prm.ens.cap;
+  const int grid = (total_slots + block - 1) / block;
+  const size_t smem = propagate_thread_smem(prm.net, block);
+  switch (prm.net.P) {
+    case 1: return launch_thread<1, 0>(prm, grid, block, smem, st);
+    case 2: return launch_thread<2, 1>(prm, grid, block, smem, st);
+    case 4: return launch_thread<4, 2>(prm, grid, block, smem, st);
+    case 8: return launch_thread<8, 3>(prm, grid, block, smem, st);
+    case 16: return launch_thread<16, 4>(prm, grid, block, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st) {
+  const EnsView &E = prm.ens;
+  const int nb = prm.bins.n_bins;
+  k_scan_bins<<<E.R, 256, 0, st>>>(E, nb);
+  const int ld = E.R * E.cap;
+  int pgrid = (ld + 255) / 256;
+  if (pgrid > 152 * 8) pgrid = 152 * 8;
+  k_place<<<pgrid, 256, 0, st>>>(E, nb);
+  int per_run_tasks = nb < E.cap ? nb : E.cap;
+  int bx = (per_run_tasks + 3) / 4;                 // 4 warps per block
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  k_resample<<<dim3(bx, E.R), 128, 0, st>>>(E, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st) {
+  const EnsView &E = prm.ens;
+  const int ld = E.R * E.cap;
+  int grid = (ld + 255) / 256;
+  if (grid > 152 * 8) grid = 152 * 8;
+  k_gather<<<grid, 256, 0, st>>>(E, prm.resample);
+  k_finalize<<<1, 256, 0, st>>>(E, prm.resample);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_states(const EnsView &E, int r, int32_t *out, cudaStream_t st) {
+  k_pack_states<<<64, 256, 0, st>>>(E, r, out);
+  return cudaGetLastError();
+}
+
+}  // namespace we

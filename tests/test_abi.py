@@ -1,0 +1,108 @@
+"""The C-ABI library loads, exports every entry point include/we_ssa.h declares, and its host-only
+entry points (network compilation, bin maps, validation) behave -- no GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1303_5986_gb300 as P
+import workloads as W
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "we_ssa.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(we_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1303_5986_gb300 import build
+    build.build()
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    lib = ctypes.CDLL(P._lib.LIB_PATH)
+    declared = _declared_functions()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(lib, name), name
+    bound = {n for n, _, _ in P.SIGNATURES}
+    assert set(declared) == bound
+
+
+def test_run_config_struct_layout_matches_header():
+    # offsets follow the C declaration order with natural alignment
+    c = P._lib.we_run_config
+    assert c.tau.offset == 0 and c.seed.offset == 16 and c.init_states.offset == 48
+    assert c.tgt_threshold.offset == 120 and c.max_steps.offset == 136
+    assert ctypes.sizeof(c) == 168
+
+
+def test_status_strings_and_last_error():
+    lib = P.lib()
+    assert lib.we_status_string(0) == b"WE_OK"
+    assert lib.we_status_string(-5) == b"WE_ESTEPCAP"
+    assert lib.we_version() >= 100
+    with pytest.raises(P.WEError) as ei:
+        P.we_binmap_grid([0], [[0.0, 5.0, 5.0]])
+    assert ei.value.status == P.WE_EINVAL
+    assert b"ascend" in lib.we_last_error()
+
+
+@pytest.mark.parametrize("factory", [W.birth_death, W.schlogl, W.futile_cycle, W.epigenetic_switch,
+                                     lambda: W.toggle_switch([20.0, 33.3, 59.9], [41.0, 22.2, 30.1]),
+                                     W.synthetic_large])
+def test_folded_rate_constants_match_oracle_bits(factory):
+    spec = factory()
+    net = P.network_from_spec(spec)
+    for p in range(spec.n_param_sets):
+        onet = O.Network(spec, p)
+        for j in range(spec.n_reactions):
+            assert net.keff(p, j) == onet.keff(j)
+
+
+def test_dependency_graph_degrees():
+    net = P.network_from_spec(W.schlogl())
+    assert [net.dep_degree(j) for j in range(4)] == [3, 3, 3, 3]
+    tog = P.network_from_spec(W.toggle_switch([30.0], [30.0]))
+    # U production changes U: U decay and V's Hill production read U
+    assert tog.dep_degree(0) == 2 and tog.dep_degree(2) == 2
+    syn = W.synthetic_large()
+    net = P.network_from_spec(syn)
+    degs = np.array([net.dep_degree(j) for j in range(syn.n_reactions)])
+    assert 30 < degs.mean() < 55 and degs.max() <= 120
+
+
+def test_network_validation_errors():
+    bad = W.NetworkSpec(species=["X"], reactants=[[(0, 2), (0, 2)]], products=[[]], rate=[[1.0]])
+    with pytest.raises(P.WEError):
+        P.network_from_spec(bad)
+    bad = W.NetworkSpec(species=["X"], reactants=[[]], products=[[(0, 1)]], rate=[[np.inf]])
+    with pytest.raises(P.WEError):
+        P.network_from_spec(bad)
+    hill_with_reactant = W.NetworkSpec(species=["X"], reactants=[[(0, 1)]], products=[[]], rate=[[1.0]],
+                                       rate_law=[1], hill_species=[0], hill_K=[[1.0]], hill_n=[2])
+    with pytest.raises(P.WEError):
+        P.network_from_spec(hill_with_reactant)
+
+
+def test_config_validation_without_gpu():
+    cfg = W.schlogl_mfpt_we(n_iters=4)
+    net = P.network_from_spec(cfg.network)
+    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+    c, keep = P.run_config_from(cfg)
+    assert P.we_ensemble_workspace_bytes(net, bm, c) > 0
+    c.tau = -1.0
+    with pytest.raises(P.WEError):
+        P.we_ensemble_workspace_bytes(net, bm, c)
+    c.tau = 0.05
+    c.m_targ = 0
+    with pytest.raises(P.WEError):
+        P.we_ensemble_workspace_bytes(net, bm, c)

@@ -1,0 +1,223 @@
+"""GPU path (through the C ABI) against the CPU oracle on identical seeded inputs.
+
+Bar: bit-exact species counts, walker order, parents and weights after every resampling, exact
+event counts; event times within 1e-12 relative; observables that device atomics sum in
+arbitrary order within 1e-12 relative."""
+import numpy as np
+import pytest
+
+import paper_1303_5986_gb300 as P
+import workloads as W
+from oracle import oracle as O
+
+from gpu_helpers import assert_run_parity, gpu_outputs, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1303_5986_gb300 import build
+    build.build()
+
+
+def _parity(cfg, n_iters, runs=None, **kw):
+    ens = gpu_run(cfg, n_iters, **kw)
+    ens.sync()
+    runs = range(cfg.n_runs) if runs is None else runs
+    for r in runs:
+        g = gpu_outputs(ens, r)
+        o = oracle_run(cfg, r, n_iters=n_iters, resample=kw.get("resample", True),
+                       max_steps=kw.get("max_steps"))
+        assert_run_parity(g, o, label=f"{cfg.name} run {r}")
+    return ens
+
+
+def test_birth_death_we():
+    _parity(W.birth_death_we(n_iters=60), 60)
+
+
+def test_birth_death_we_with_recycling():
+    _parity(W.birth_death_we(n_iters=60, target=130), 60)
+
+
+def test_schlogl_mfpt_batched_replicas():
+    _parity(W.schlogl_mfpt_we(n_iters=40, n_runs=3), 40)
+
+
+def test_toggle_batch_uneven_runs():
+    cfg = W.toggle_batch_we(n_runs=8, n_iters=30)
+    ens = _parity(cfg, 30)
+    counts = ens.get(P.WE_OUT_COUNTS)
+    assert len(set(counts.tolist())) > 1          # uneven live-walker counts across runs
+
+
+def test_epigenetic_switch_paper_bins():
+    """The paper's switch (n=3, m=1) with its non-uniform 15 x 31 bins (Sec. III.C.2)."""
+    spec = W.epigenetic_switch()
+    e1 = np.concatenate([np.arange(0, 11, dtype=float), [20.0, 30.0, 40.0, 50.0, np.inf]])
+    e2 = np.concatenate([np.arange(0, 31, dtype=float), [np.inf]])
+    cfg = W.WEConfig(network=spec, bins=W.GridBins([0, 1], [e1, e2]), tau=0.1, m_targ=16,
+                     n_iters=25, x0=[150, 0], hist_species=1, hist_len=64, name="epigenetic")
+    _parity(cfg, 25)
+
+
+def test_futile_cycle():
+    spec = W.futile_cycle()
+    cfg = W.WEConfig(network=spec, bins=W.GridBins([0], [W.uniform_edges(0, 1, 101)]), tau=1.0,
+                     m_targ=10, n_iters=15, x0=[50, 50, 1, 1, 0, 0], hist_species=0, hist_len=102,
+                     name="futile")
+    _parity(cfg, 15)
+
+
+@pytest.mark.parametrize("block", [32, 64, 128])
+def test_plain_ssa_counts_and_times(block):
+    """No resampling: 3000 Schloegl walkers for three intervals; counts bit-exact, last event
+    times within 1e-12 relative (device log vs host log may differ in the last bit)."""
+    cfg = W.schlogl_mfpt_we(n_iters=3)
+    cfg.target = None
+    n = 3000
+    rng = np.random.default_rng(4)
+    init = np.zeros((1, n, 3), dtype=np.int32)
+    init[0, :, 0] = rng.integers(0, 700, size=n)
+    init[0, :, 1], init[0, :, 2] = 100000, 200000
+    w = np.full((1, n), 1.0 / n)
+    cfg.capacity = n
+    ens = gpu_run(cfg, 3, resample=False, init_states=init, init_weights=w, block_threads=block)
+    ens.sync()
+    o = oracle_run(cfg, 0, n_iters=3, resample=False, init_states=init, init_weights=w)
+    g = gpu_outputs(ens, 0)
+    assert_run_parity(g, o, "plain ssa")
+    tl = ens.get(P.WE_OUT_TLAST, 0)
+    np.testing.assert_allclose(tl, o["t_last"][:n], rtol=1e-12, atol=0)
+    assert np.all(tl <= cfg.tau) and np.count_nonzero(tl) > n // 2
+
+
+def test_zero_propensity_walkers_idle():
+    dead = W.NetworkSpec(species=["X", "Y"], reactants=[[(0, 1)], [(1, 2)]], products=[[(1, 1)], []],
+                         rate=[[1.0, 2.0]])
+    cfg = W.WEConfig(network=dead, bins=W.GridBins([0], [W.uniform_edges(0, 1, 4)]), tau=1.0,
+                     m_targ=3, n_iters=4, x0=[0, 1], hist_species=1, hist_len=4, name="dead")
+    _parity(cfg, 4)
+
+
+def test_many_merges_in_one_bin():
+    """600 walkers of random weight in one bin merged down to M=3 (the serial merge path)."""
+    spec = W.birth_death(kb=1e-9, kd=1e-9)
+    n = 600
+    rng = np.random.default_rng(8)
+    init = np.full((1, n, 1), 7, dtype=np.int32)
+    w = rng.exponential(size=(1, n)) * 10.0 ** rng.uniform(-30, 0, size=(1, n))
+    w /= w.sum()
+    cfg = W.WEConfig(network=spec, bins=W.GridBins([0], [W.uniform_edges(0, 5, 4)]), tau=0.1,
+                     m_targ=3, n_iters=2, x0=[7], init_states=init, init_weights=w, capacity=n,
+                     hist_species=0, hist_len=16, name="merges")
+    _parity(cfg, 2)
+
+
+def test_single_walker_m1_and_split_to_many():
+    cfg = W.birth_death_we(n_iters=10)
+    cfg.m_targ = 1
+    cfg.init_states = cfg.init_states[:, :1]
+    cfg.init_weights = np.ones((1, 1))
+    cfg.capacity = 61
+    _parity(cfg, 10)
+    cfg2 = W.birth_death_we(n_iters=6)
+    cfg2.m_targ = 37
+    cfg2.init_states = cfg2.init_states[:, :1]
+    cfg2.init_weights = np.ones((1, 1))
+    cfg2.capacity = 37 * 61
+    _parity(cfg2, 6)
+
+
+def test_recycle_on_first_event():
+    cfg = W.birth_death_we(n_iters=8, target=101)
+    _parity(cfg, 8)
+
+
+def test_step_cap_status():
+    cfg = W.schlogl_mfpt_we(n_iters=3)
+    ens = gpu_run(cfg, 3, max_steps=5)
+    with pytest.raises(P.WEError) as ei:
+        ens.sync()
+    assert ei.value.status == P.WE_ESTEPCAP
+    o = oracle_run(cfg, 0, n_iters=3, max_steps=5)
+    assert o["status"] == P.WE_ESTEPCAP and int(ens.status()[0]) == P.WE_ESTEPCAP
+
+
+def test_count_overflow_status():
+    grow = W.NetworkSpec(species=["X"], reactants=[[]], products=[[(0, 1)]], rate=[[1e9]])
+    cfg = W.WEConfig(network=grow, bins=W.GridBins([0], [W.uniform_edges(0, 1e6, 4)]), tau=1.0,
+                     m_targ=2, n_iters=1, x0=[P.WE_MAX_COUNT - 3], name="overflow")
+    ens = gpu_run(cfg, 1)
+    with pytest.raises(P.WEError) as ei:
+        ens.sync()
+    assert ei.value.status == P.WE_EOVERFLOW
+    o = oracle_run(cfg, 0, n_iters=1)
+    assert o["status"] == P.WE_EOVERFLOW
+    s = ens.states(0)
+    assert np.all(s[:, 0] == P.WE_MAX_COUNT)
+
+
+def test_checkpoint_resume_is_bit_identical():
+    cfg = W.schlogl_mfpt_we(n_iters=24, n_runs=2)
+    full = gpu_run(cfg, 24)
+    full.sync()
+    first = gpu_run(cfg, 12)
+    first.sync()
+    R = cfg.n_runs
+    states = [first.states(r) for r in range(R)]
+    weights = [first.weights(r) for r in range(R)]
+    n = min(len(w) for w in weights)
+    # resume each run separately from its checkpoint (walker counts may differ per run)
+    for r in range(R):
+        c1 = W.schlogl_mfpt_we(n_iters=12, n_runs=1)
+        c1.run_ids = np.array([r], dtype=np.uint32)
+        c1.first_iter = 12
+        ens = gpu_run(c1, 12, init_states=states[r][None], init_weights=weights[r][None], first_iter=12)
+        ens.sync()
+        assert np.array_equal(ens.states(0), full.states(r))
+        assert np.array_equal(ens.weights(0).view(np.int64), full.weights(r).view(np.int64))
+        assert np.array_equal(ens.per_iter(P.WE_OUT_EVENTS, 0), full.per_iter(P.WE_OUT_EVENTS, r)[12:])
+    assert n > 0
+
+
+def test_repeat_runs_are_identical():
+    cfg = W.toggle_batch_we(n_runs=4, n_iters=20)
+    a = gpu_run(cfg, 20)
+    b = gpu_run(cfg, 20)
+    for r in range(4):
+        assert np.array_equal(a.states(r), b.states(r))
+        assert np.array_equal(a.weights(r).view(np.int64), b.weights(r).view(np.int64))
+
+
+def test_phase_api_matches_step():
+    """propagate()/resample() issued one by one equal the graph-replayed step()."""
+    cfg = W.schlogl_mfpt_we(n_iters=6, n_runs=2)
+    a = gpu_run(cfg, 6)
+    b = gpu_run(cfg, 0, record_iters=6)
+    for _ in range(6):
+        b.propagate()
+        b.resample()
+    b.sync()
+    for r in range(2):
+        assert np.array_equal(a.states(r), b.states(r))
+        assert np.array_equal(a.per_iter(P.WE_OUT_NWALKERS, r), b.per_iter(P.WE_OUT_NWALKERS, r))
+
+
+def test_we_run_one_call_host_outputs():
+    cfg = W.birth_death_we(n_iters=20)
+    net = P.network_from_spec(cfg.network)
+    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+    c, keep = P.run_config_from(cfg, record_iters=20)
+    ens = P.we_run(net, bm, c, keep)
+    assert ens.run_status == 0
+    o = oracle_run(cfg, 0, n_iters=20)
+    assert_run_parity(gpu_outputs(ens, 0), o, "we_run")
+
+
+def test_library_owned_workspace():
+    cfg = W.birth_death_we(n_iters=5)
+    ens = gpu_run(cfg, 5, workspace=None)
+    ens.sync()
+    assert_run_parity(gpu_outputs(ens, 0), oracle_run(cfg, 0, n_iters=5), "own workspace")

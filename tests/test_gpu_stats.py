@@ -1,0 +1,53 @@
+"""WE observables of the GPU path against the mathematics and the paper's printed values,
+within 3 standard errors over independent replicas (the replicate protocol of Sec. III.B.3)."""
+import numpy as np
+import pytest
+
+import paper_1303_5986_gb300 as P
+import workloads as W
+from oracle import exact as E
+
+from gpu_helpers import gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1303_5986_gb300 import build
+    build.build()
+
+
+def test_schlogl_tail_probability_matches_paper():
+    """Paper-scale Schloegl PDF run (802 unit bins, 100 walkers per bin, tau = 0.05, 101
+    iterations from X = 82; Sec. III.B.2): P(X >= 700, t = 5) against the CME value printed in
+    Sec. III.B.3, 1.148e-9, over 10 replicas."""
+    cfg = W.schlogl_pdf_we(n_iters=101, n_runs=10)
+    ens = gpu_run(cfg, 101)
+    ens.sync()
+    H = ens.per_iter(P.WE_OUT_HIST)              # iters x runs x len; iteration 99 ends at t = 5
+    est = H[99, :, 700:].sum(axis=1)
+    b, d = E.schlogl_rates()
+    exact = E.bd_transient(b, d, 82, 5.0, 2000)[700:].sum()
+    assert abs(exact - 1.148e-9) < 0.001e-9      # the paper's CME value
+    se = est.std(ddof=1) / np.sqrt(len(est))
+    assert abs(est.mean() - exact) < 3 * se + 0.02 * exact, (est.mean(), exact, se)
+    tot = ens.per_iter(P.WE_OUT_TOTAL_W)
+    assert np.all(np.abs(tot - 1.0) < 1e-12)
+
+
+def test_schlogl_mfpt_matches_closed_form():
+    """Steady-state WE with recycling at X >= 550 from X0 = 85 (80 bins of width 10, 20 walkers
+    per bin, tau = 0.05): MFPT = 1/flux (Eq. "mfpt") against the birth-death closed form
+    (50,307 s; the paper quotes about 5e4 s for 82 -> 563), over 10 replicas."""
+    cfg = W.schlogl_mfpt_we(n_iters=1000, n_runs=10)
+    ens = gpu_run(cfg, 1000)
+    ens.sync()
+    flux = ens.per_iter(P.WE_OUT_FLUX)          # iters x runs
+    per_run = flux[300:].mean(axis=0) / cfg.tau
+    b, d = E.schlogl_rates()
+    exact = 1.0 / E.bd_mfpt(85, 550, b, d)
+    se = per_run.std(ddof=1) / np.sqrt(len(per_run))
+    assert abs(per_run.mean() - exact) < 3 * se + 0.05 * exact, (1 / per_run.mean(), 1 / exact, se / exact)
+    tot = ens.per_iter(P.WE_OUT_TOTAL_W)
+    assert np.all(np.abs(tot - 1.0) < 1e-12)
