@@ -353,6 +353,8 @@ struct we_ensemble {
   bool phase_propagated = false;
   cudaGraphExec_t graph = nullptr;
   cudaGraphExec_t timed_graph = nullptr;
+  cudaGraph_t timed_graph_src = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   cudaGraphNode_t ev_node_start = nullptr, ev_node_end = nullptr;
   cudaStream_t cap_stream = nullptr;
 };
@@ -552,6 +554,9 @@ extern "C" we_status we_ensemble_destroy(we_ensemble *E) {
   if (!E) return WE_OK;
   if (E->graph) cudaGraphExecDestroy(E->graph);
   if (E->timed_graph) cudaGraphExecDestroy(E->timed_graph);
+  if (E->timed_graph_src) cudaGraphDestroy(E->timed_graph_src);
+  if (E->ev_a) cudaEventDestroy(E->ev_a);
+  if (E->ev_b) cudaEventDestroy(E->ev_b);
   if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
   if (E->owns_ws) cudaFree(E->ws);
   delete E;
@@ -619,18 +624,19 @@ extern "C" we_status we_ensemble_step(we_ensemble *E, int32_t n_iters, void *str
 // the SSA kernel; before every replay the two nodes are pointed at that iteration's events.
 static we_status build_timed_graph(we_ensemble *E) {
   if (!E->cap_stream) WE_CUDA_TRY(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
-  cudaEvent_t ea, eb;
-  WE_CUDA_TRY(cudaEventCreate(&ea));
-  WE_CUDA_TRY(cudaEventCreate(&eb));
+  // the placeholder events stay alive with the graph: its event-record nodes refer to them
+  if (!E->ev_a) WE_CUDA_TRY(cudaEventCreate(&E->ev_a));
+  if (!E->ev_b) WE_CUDA_TRY(cudaEventCreate(&E->ev_b));
+  cudaEvent_t ea = E->ev_a, eb = E->ev_b;
   WE_CUDA_TRY(cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e1 = cudaEventRecord(ea, E->cap_stream);
+  // External records become event-record nodes of the graph (a plain record inside a capture
+  // only orders streams).
+  cudaError_t e1 = cudaEventRecordWithFlags(ea, E->cap_stream, cudaEventRecordExternal);
   e1 = e1 ? e1 : enqueue_propagate(E, E->cap_stream);
-  e1 = e1 ? e1 : cudaEventRecord(eb, E->cap_stream);
+  e1 = e1 ? e1 : cudaEventRecordWithFlags(eb, E->cap_stream, cudaEventRecordExternal);
   e1 = e1 ? e1 : enqueue_resample(E, E->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(E->cap_stream, &g);
-  cudaEventDestroy(ea);
-  cudaEventDestroy(eb);
   if (e1 || e2) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return cuda_fail(e1 ? e1 : e2, "timed graph capture"); }
   size_t n = 0;
   cudaGraphGetNodes(g, nullptr, &n);
@@ -644,9 +650,15 @@ static we_status build_timed_graph(we_ensemble *E) {
     cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps);
     if (nd_deps == 0) E->ev_node_start = nd; else E->ev_node_end = nd;
   }
-  cudaError_t e3 = (E->ev_node_start && E->ev_node_end) ? cudaGraphInstantiate(&E->timed_graph, g, 0) : cudaErrorUnknown;
-  cudaGraphDestroy(g);
-  if (e3) { E->timed_graph = nullptr; return cuda_fail(e3, "timed graph instantiate"); }
+  if (!E->ev_node_start || !E->ev_node_end) {
+    cudaGraphDestroy(g);
+    return fail(WE_ECUDA, "timed graph: event-record nodes not found in the capture");
+  }
+  cudaError_t e3 = cudaGraphInstantiate(&E->timed_graph, g, 0);
+  if (e3) { cudaGraphDestroy(g); E->timed_graph = nullptr; return cuda_fail(e3, "timed graph instantiate"); }
+  // the event-record node handles used to retarget the executable graph belong to this graph,
+  // so it lives as long as the ensemble
+  E->timed_graph_src = g;
   return WE_OK;
 }
 
@@ -676,6 +688,9 @@ extern "C" we_status we_ensemble_step_timed(we_ensemble *E, int32_t n_iters, voi
   E->iters_enqueued += n_iters;
   cudaError_t e = cudaEventSynchronize(ev[2 * (size_t)n_iters - 1]);
   for (int i = 0; i < n_iters && !e; ++i) e = cudaEventElapsedTime(&propagate_ms[i], ev[2 * i], ev[2 * i + 1]);
+  // point the nodes back at the ensemble's own events before the per-iteration ones go away
+  cudaGraphExecEventRecordNodeSetEvent(E->timed_graph, E->ev_node_start, E->ev_a);
+  cudaGraphExecEventRecordNodeSetEvent(E->timed_graph, E->ev_node_end, E->ev_b);
   release();
   if (e) return cuda_fail(e, "event timing");
   return WE_OK;

@@ -221,3 +221,15 @@ def test_library_owned_workspace():
     ens = gpu_run(cfg, 5, workspace=None)
     ens.sync()
     assert_run_parity(gpu_outputs(ens, 0), oracle_run(cfg, 0, n_iters=5), "own workspace")
+
+
+def test_timed_step_matches_step_and_reports_kernel_times():
+    cfg = W.schlogl_mfpt_we(n_iters=12, n_runs=2)
+    a = gpu_run(cfg, 12)
+    b = gpu_run(cfg, 0, record_iters=12)
+    ms = b.step_timed(12)
+    b.sync()
+    assert ms.shape == (12,) and np.all(ms > 0)
+    for r in range(2):
+        assert np.array_equal(a.states(r), b.states(r))
+        assert np.array_equal(a.per_iter(P.WE_OUT_EVENTS, r), b.per_iter(P.WE_OUT_EVENTS, r))
