@@ -237,6 +237,34 @@ we_status we_ensemble_get(we_ensemble *ens, int32_t what, int32_t run, void *dst
 we_status we_run(const we_network *net, const we_binmap *bins, const we_run_config *cfg,
                  void *stream, we_ensemble **out);
 
+/* ------------------------------------------------------------------------------------------
+ * Split/merge without allocation.  The paper has no counterpart: this is a service for callers
+ * that may not allocate device memory -- for instance a host framework whose caching allocator
+ * already holds all of the GPU's memory, or a loop in which a cudaMalloc (which can synchronise
+ * the device and can fail under memory pressure) is not allowed after set-up.
+ *
+ * It applies the same per-bin split/merge as we_ensemble_resample to one run given as plain
+ * device arrays: n walkers with their bins (int32, 0..n_bins-1) and weights (double); `iter`,
+ * `seed` and `run_id` key the merge draws exactly as in an ensemble.  Outputs (device memory,
+ * capacity entries): out_weights and out_parent (input slot of each new walker), in the order
+ * the ensemble uses; out_count[0] receives the new walker count, or a negative we_status
+ * (WE_EINVAL for a bin out of range, WE_EOVERFLOW when capacity is too small).
+ *
+ * Working memory is one array of about 1.4 MB in device global memory, part of the library
+ * image, that every GPU loading the library keeps until the process exits.  Limits: n and
+ * capacity at most WE_STATIC_MAX_WALKERS, n_bins at most WE_STATIC_MAX_BINS (larger sizes
+ * return WE_EINVAL); capacity >= n.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream capture.  Every
+ * call shares the array: calls whose GPU work can overlap (other streams, other threads) race
+ * and give wrong results; order them on one stream.  Enqueue only; the call allocates nothing.
+ * ------------------------------------------------------------------------------------------ */
+#define WE_STATIC_MAX_WALKERS 65536
+#define WE_STATIC_MAX_BINS 4096
+we_status we_resample_static(int32_t n, const int32_t *bins, const double *weights,
+                             int32_t n_bins, int32_t m_targ, int32_t iter, uint64_t seed,
+                             uint32_t run_id, int32_t capacity, double *out_weights,
+                             int32_t *out_parent, int32_t *out_count, void *stream);
+
 /* Autotuner: time the SSA kernel mappings and block sizes on a short probe of this
  * configuration and return the fastest (mapping, block_threads).  Results are cached per
  * (S, M, walkers, device) for the life of the process. */

@@ -86,6 +86,8 @@ SIGNATURES = [
                                     C.POINTER(C.c_size_t), _VP]),
     ("we_run", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, C.POINTER(_VP)]),
     ("we_autotune", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, _I32P, _I32P]),
+    ("we_resample_static", C.c_int32, [C.c_int32, _VP, _VP, C.c_int32, C.c_int32, C.c_int32,
+                                       C.c_uint64, C.c_uint32, C.c_int32, _VP, _VP, _VP, _VP]),
 ]
 
 _lib = None

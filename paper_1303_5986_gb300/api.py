@@ -310,3 +310,17 @@ def we_autotune(net: Network, bins: BinMap, cfg, stream=None):
     b = C.c_int32()
     check(lib().we_autotune(net.h, bins.h, C.byref(cfg), _stream_handle(stream), C.byref(m), C.byref(b)))
     return m.value, b.value
+
+
+def we_resample_static(bins, weights, n_bins: int, m_targ: int, iteration: int, seed: int,
+                       run_id: int, out_weights, out_parent, out_count, stream=None):
+    """Split/merge of one run held in device tensors, with no allocation by the library
+    (for callers that may not allocate device memory).  Arguments are CUDA tensors: bins int32,
+    weights float64, out_weights float64 and out_parent int32 of the same capacity, out_count
+    int32[1] (new count, or a negative status)."""
+    n = int(bins.numel())
+    check(lib().we_resample_static(n, C.c_void_p(bins.data_ptr()), C.c_void_p(weights.data_ptr()),
+                                   int(n_bins), int(m_targ), int(iteration), int(seed), int(run_id),
+                                   int(out_weights.numel()), C.c_void_p(out_weights.data_ptr()),
+                                   C.c_void_p(out_parent.data_ptr()), C.c_void_p(out_count.data_ptr()),
+                                   _stream_handle(stream)))
