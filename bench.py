@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--iters", type=int, default=ITERS)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block", type=int, default=0, help="threads per block of the SSA kernel (0: auto)")
     return ap.parse_args()
 
 
@@ -234,7 +235,7 @@ def main():
 
     def ensemble(seed):
         cfg = mk(seed)
-        c, keep = P.run_config_from(cfg, record_iters=a.iters)
+        c, keep = P.run_config_from(cfg, record_iters=a.iters, block_threads=a.block)
         return P.we_ensemble_create(net, bm, c, keep)
 
     seeds = [1_000_003 * (rank + 1) + s for s in range(a.warmup + a.steps + 1)]

@@ -70,6 +70,8 @@ typedef int32_t we_status;
 #define WE_MAP_AUTO 0          /* let the autotuner pick */
 #define WE_MAP_THREAD 1        /* one thread per walker, propensity tree in registers */
 #define WE_MAP_WARP 2          /* one warp per walker, propensity tree in shared memory */
+#define WE_MAP_THREAD_TABLE 3  /* one thread per walker, propensity tree looked up by count
+                                  (networks whose propensities all read one species) */
 
 const char *we_status_string(we_status s);
 /* Message of the last failing call on this thread ("" if none).  Valid until the next call. */
@@ -156,7 +158,10 @@ typedef struct {
   int32_t hist_len;                /* histogram entries (0: none); the last one collects x >= hist_len-1 */
   int32_t resample;                /* 1: weighted ensemble; 0: plain SSA propagation */
   int32_t mapping;                 /* WE_MAP_AUTO / WE_MAP_THREAD / WE_MAP_WARP */
-  int32_t block_threads;           /* threads per block of the SSA kernel (0: auto) */
+  int32_t block_threads;           /* threads per block of the SSA kernel (0: auto).  Thread
+                                      mappings: 128 = one event warp fed by three draw warps
+                                      per 32 walkers (default); 32, 64, 96 = every thread
+                                      makes its own draws */
 } we_run_config;
 
 /* ------------------------------------------------------------------------------------------

@@ -26,6 +26,7 @@ WE_OP_LE = 1
 WE_MAP_AUTO = 0
 WE_MAP_THREAD = 1
 WE_MAP_WARP = 2
+WE_MAP_THREAD_TABLE = 3
 WE_OUT_COUNTS = 1
 WE_OUT_STATES = 2
 WE_OUT_WEIGHTS = 3

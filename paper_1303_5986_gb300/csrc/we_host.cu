@@ -17,9 +17,12 @@
 #include "we_internal.cuh"
 
 namespace we {
-cudaError_t launch_propagate_thread(const PropagateParams &prm, int block, cudaStream_t st);
+cudaError_t launch_propagate_thread(const PropagateParams &prm, int block, bool table, cudaStream_t st);
+cudaError_t launch_propagate_ws(const PropagateParams &prm, bool table, cudaStream_t st);
 cudaError_t launch_propagate_warp(const PropagateParams &prm, int block, cudaStream_t st);
-size_t propagate_thread_smem(const NetView &N, int block);
+cudaError_t launch_init_log_tables(LogTables *T, cudaStream_t st);
+cudaError_t launch_build_table(const NetView &N, const int32_t *base, int species, int len,
+                               double *rows, cudaStream_t st);
 size_t propagate_warp_smem(const NetView &N, int block);
 cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st);
@@ -80,6 +83,7 @@ struct we_network {
   std::vector<int32_t> d_sp, d_val;
   std::vector<int32_t> dep_ptr, dep_idx;
   std::vector<int32_t> fixed;       // S
+  int32_t table_species = -1;       // the one species every propensity reads (-1: none)
 };
 
 static long long binom_small_h(long long x, int m) {
@@ -210,6 +214,15 @@ extern "C" we_status we_network_create(int32_t S, int32_t M, const int32_t *reac
     n->dep_idx.insert(n->dep_idx.end(), d.begin(), d.end());
   }
   n->dep_ptr[P] = (int32_t)n->dep_idx.size();
+  // State-indexed tables apply when one dynamic species is the only one any propensity reads
+  // and the only one any reaction changes.
+  int ts = -1;
+  bool ok = true;
+  for (int j = 0; j < M && ok; ++j) {
+    for (int sp : reads[j]) { if (ts < 0) ts = sp; ok = ok && sp == ts; }
+    for (int sp : changes[j]) { if (ts < 0) ts = sp; ok = ok && sp == ts; }
+  }
+  n->table_species = (ok && ts >= 0) ? ts : -1;
   *out = n;
   return WE_OK;
 }
@@ -291,12 +304,25 @@ struct Offsets {
   size_t x0, x1, w0, w1, p0, p1, bin, nrec, tlast;
   size_t count, prev_count, run_off, status, iter, bin_count, n_tasks, tasks, cursor, sorted_slot, sorted_w, alive;
   size_t flux, totw, nw, events, hist, pack;
+  size_t logt, table, base;
+  int32_t table_len;
   size_t total;
 };
+
+static int table_len_for(const we_network *n) {
+  if (n->table_species < 0 || n->P > kThreadMaxLeaves || n->S > kThreadMaxSpecies) return 0;
+  int len = 4096;
+  while (len > 256 && (size_t)n->nps * len * 2 * n->P * 8 > (64u << 20)) len >>= 1;
+  return len;
+}
 
 static Offsets layout(const we_network *n, const we_binmap *b, const we_run_config *c, int cap) {
   Layout L;
   Offsets o{};
+  o.table_len = table_len_for(n);
+  o.logt = L.take(sizeof(LogTables));
+  o.table = L.take((size_t)n->nps * o.table_len * 2 * n->P * 8);
+  o.base = L.take(4 * (size_t)n->S);
   const size_t R = c->n_runs, RC = R * cap, rec = c->record_iters;
   o.meta = L.take(sizeof(RxnMeta) * n->P);
   o.keff = L.take(8 * n->keff.size());
@@ -408,9 +434,13 @@ template <typename T>
 static T *at(void *base, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(base) + off); }
 
 static int choose_mapping(const we_network *n, const we_run_config *c) {
-  if (c->mapping == WE_MAP_THREAD || c->mapping == WE_MAP_WARP) return c->mapping;
+  if (c->mapping == WE_MAP_THREAD || c->mapping == WE_MAP_WARP || c->mapping == WE_MAP_THREAD_TABLE)
+    return c->mapping;
+  if (table_len_for(n) > 0) return WE_MAP_THREAD_TABLE;
   return (n->P <= kThreadMaxLeaves && n->S <= kThreadMaxSpecies) ? WE_MAP_THREAD : WE_MAP_WARP;
 }
+
+
 
 extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
                                         const we_run_config *c, void *workspace,
@@ -421,10 +451,13 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   we_status st = check_config(n, b, c, &cap);
   if (st) return st;
   const int mapping = choose_mapping(n, c);
-  if (mapping == WE_MAP_THREAD && (n->P > kThreadMaxLeaves || n->S > kThreadMaxSpecies))
+  const bool thread_map = mapping == WE_MAP_THREAD || mapping == WE_MAP_THREAD_TABLE;
+  if (thread_map && (n->P > kThreadMaxLeaves || n->S > kThreadMaxSpecies))
     return fail(WE_ENOTSUPPORTED, "thread mapping needs <= %d reactions and <= %d species", kThreadMaxLeaves, kThreadMaxSpecies);
-  const int block = c->block_threads > 0 ? c->block_threads : (mapping == WE_MAP_THREAD ? 128 : 256);
-  if (mapping == WE_MAP_THREAD && block != 32 && block != 64 && block != 96 && block != 128)
+  if (mapping == WE_MAP_THREAD_TABLE && table_len_for(n) == 0)
+    return fail(WE_ENOTSUPPORTED, "table mapping needs every propensity to read one species only");
+  const int block = c->block_threads > 0 ? c->block_threads : (thread_map ? 128 : 256);
+  if (thread_map && block != 32 && block != 64 && block != 96 && block != 128)
     return fail(WE_EINVAL, "thread mapping supports block_threads of 32, 64, 96 or 128");
   Offsets o = layout(n, b, c, cap);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -503,7 +536,10 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   e = e ? e : up(o.prev_count, cnt.data(), 4 * R);
   e = e ? e : up(o.run_off, roff.data(), 4 * (R + 1));
   e = e ? e : up(o.iter, &it0, 4);
-  e = e ? e : cudaStreamSynchronize(s);
+  std::vector<int32_t> base(S, 0);
+  for (int sp = 0; sp < S; ++sp) base[sp] = n->fixed[sp] >= 0 ? n->fixed[sp] : 0;
+  e = e ? e : up(o.base, base.data(), 4 * S);
+  e = e ? e : launch_init_log_tables(at<LogTables>(ws, o.logt), s);
   if (e) { cudaGetLastError(); return cleanup(cuda_fail(e, "ensemble upload")); }
 
   NetView &N = E->prm.net;
@@ -546,6 +582,17 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   V.obs_nw = at<int32_t>(ws, o.nw); V.obs_events = at<unsigned long long>(ws, o.events);
   V.obs_hist = at<double>(ws, o.hist);
   E->prm.resample = c->resample ? 1 : 0;
+  E->prm.logt = at<LogTables>(ws, o.logt);
+  E->prm.tab.species = -1;
+  if (mapping == WE_MAP_THREAD_TABLE) {
+    E->prm.tab.rows = at<double>(ws, o.table);
+    E->prm.tab.len = o.table_len;
+    E->prm.tab.species = n->table_species;
+    e = launch_build_table(N, at<int32_t>(ws, o.base), n->table_species, o.table_len,
+                           at<double>(ws, o.table), s);
+  }
+  e = e ? e : cudaStreamSynchronize(s);
+  if (e) { cudaGetLastError(); return cleanup(cuda_fail(e, "ensemble set-up")); }
   *out = E;
   return WE_OK;
 }
@@ -563,9 +610,14 @@ extern "C" we_status we_ensemble_destroy(we_ensemble *E) {
   return WE_OK;
 }
 
+// Thread mappings: 128-thread blocks run the warp-specialised kernel (one event warp and three
+// draw warps per 32 walkers); 32/64/96-thread blocks run the plain kernel in which each thread
+// makes its own draws.
 static cudaError_t enqueue_propagate(we_ensemble *E, cudaStream_t s) {
   if (E->mapping == WE_MAP_WARP) return launch_propagate_warp(E->prm, E->block, s);
-  return launch_propagate_thread(E->prm, E->block, s);
+  const bool table = E->mapping == WE_MAP_THREAD_TABLE;
+  if (E->block == 128) return launch_propagate_ws(E->prm, table, s);
+  return launch_propagate_thread(E->prm, E->block, table, s);
 }
 
 static cudaError_t enqueue_resample(we_ensemble *E, cudaStream_t s) {
@@ -833,6 +885,8 @@ extern "C" we_status we_autotune(const we_network *n, const we_binmap *b, const 
     if (it != g_tune_cache.end()) { *mapping = it->second.first; *block_threads = it->second.second; return WE_OK; }
   }
   std::vector<std::pair<int, int>> cands;
+  if (table_len_for(n) > 0)
+    for (int bt : {32, 64, 128}) cands.push_back({WE_MAP_THREAD_TABLE, bt});
   if (n->P <= kThreadMaxLeaves && n->S <= kThreadMaxSpecies)
     for (int bt : {32, 64, 128}) cands.push_back({WE_MAP_THREAD, bt});
   for (int bt : {128, 256}) cands.push_back({WE_MAP_WARP, bt});

@@ -100,10 +100,28 @@ struct EnsView {
   double *obs_hist;
 };
 
+// Tables of the waiting-time logarithm (see neg_log_u01), each value as an unevaluated sum
+// of two floats (hi, lo): 1/c_j, -log(c_j / 2), i ln 2.
+struct LogTables {
+  float2 inv_c[128];
+  float2 b[128];
+  float2 n_ln2[64];
+};
+
+// State-indexed propensity tables for networks whose propensities all depend on one species:
+// row x (x < len) holds [1/a0, tree node 1 (= a0), node 2, ..., node 2P-1] at that count.
+struct TableView {
+  const double *rows;          // n_param_sets x len x 2P
+  int32_t len;                 // counts covered; larger counts are evaluated directly
+  int32_t species;             // the one species the propensities read (-1: no tables)
+};
+
 struct PropagateParams {
   NetView net;
   BinView bins;
   EnsView ens;
+  TableView tab;
+  const LogTables *logt;
   int32_t resample;            // 1: WE; 0: plain SSA (bookkeeping of parents is identity)
 };
 

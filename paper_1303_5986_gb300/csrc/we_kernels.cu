@@ -1,229 +1,16 @@
-// we_kernels.cu -- the device side of the weighted-ensemble Gillespie-SSA path.
+// we_kernels.cu -- the resampling side of a WE iteration and the bookkeeping around it.
 //
-//   k_propagate_thread<P>  one SSA interval per walker, one thread per walker (Sec. II.A; the
-//                          "propagate dynamics" step of the WE algorithm, Sec. II.B), with
-//                          in-interval recycling (Sec. II.B.2), bin assignment and observables
-//   k_scan_bins            per run: bin occupancy -> task list and output offsets
-//   k_resample             one warp per occupied bin: merge / split (Sec. II.B)
-//   k_gather               copy species counts of the new ensemble from their parents
-//   k_finalize             per-run counts and offsets, iteration counter
+//   k_scan_bins   per run: bin occupancy -> task list, grouping cursors and output offsets
+//   k_place       group each run's walkers by bin
+//   k_resample    one warp per occupied bin: merge / split (Sec. II.B)
+//   k_gather      copy species counts of the new ensemble from their parents
+//   k_finalize    per-run counts and offsets, iteration counter
 //
-// Floating-point rules shared with the definition of the method (and its CPU restatement):
-// every propensity, tree node, target and weight operation is a single IEEE double operation
-// written with an explicit round-to-nearest intrinsic, so no multiply-add is ever fused.
-// Comparisons between non-negative doubles are made on their bit patterns (the IEEE order of
-// non-negative doubles is the integer order of their bits), which keeps them off the FP64 pipe.
-#include "we_internal.cuh"
+// Every weight operation is a single IEEE double operation with an explicit round-to-nearest
+// intrinsic; comparisons between non-negative doubles use their bit patterns.
+#include "we_ssa_common.cuh"
 
 namespace we {
-
-constexpr int32_t kStatusStepCap = -5;
-constexpr int32_t kStatusOverflow = -4;
-
-// ------------------------------------------------------------------------------------------
-// Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64 multiplies
-// whose high halves are xored with the other counter words and the key; the key advances by
-// the Weyl constants between rounds.
-// ------------------------------------------------------------------------------------------
-__device__ __forceinline__ void philox4x32_10(uint32_t &c0, uint32_t &c1, uint32_t &c2,
-                                              uint32_t &c3, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    c0 = hi1 ^ c1 ^ k0;
-    c1 = lo1;
-    c2 = hi0 ^ c3 ^ k1;
-    c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-}
-
-// (2m+1)/2^53 with m = hi<<20 | lo>>12: the double 1 + m/2^52 built from bits, minus
-// (1 - 2^-53).  The difference is representable, so the subtraction is exact.
-__device__ __forceinline__ double u01(uint32_t hi, uint32_t lo) {
-  const unsigned long long m = ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
-  const double one_plus = __longlong_as_double((long long)(0x3FF0000000000000ull | m));
-  return __dsub_rn(one_plus, 0x1.fffffffffffffp-1);
-}
-
-__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
-
-__device__ __forceinline__ long long binom_small(long long x, int m) {
-  return m == 1 ? x : (m == 2 ? x * (x - 1) / 2 : x * (x - 1) * (x - 2) / 6);
-}
-
-// Propensity of one reaction from counts held at xs[species * stride].
-__device__ __forceinline__ double propensity(const RxnMeta &mt, double keff, double Kn,
-                                             const int32_t *xs, int stride) {
-  if (mt.law == 1) {
-    const long long y = xs[mt.hsp * stride];
-    long long yn = y;
-    if (mt.hn >= 2) yn *= y;
-    if (mt.hn >= 3) yn *= y;
-    const double den = __dadd_rn(Kn, __ll2double_rn(yn));
-    return __ddiv_rn(keff, den);
-  }
-  long long h = 1;
-  for (int k = 0; k < mt.n_reac; ++k) h *= binom_small(xs[mt.sp[k] * stride], mt.m[k]);
-  return __dmul_rn(keff, __ll2double_rn(h));
-}
-
-__device__ __forceinline__ int bin_of(const BinView &bv, const int32_t *xs, int stride) {
-  int flat = 0;
-#pragma unroll 1
-  for (int d = 0; d < bv.ndim; ++d) {
-    const double v = (double)xs[bv.species[d] * stride];
-    const double *e = bv.edges + bv.edge_off[d];
-    int lo = 0, hi = bv.nb[d] - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (e[mid] <= v) lo = mid; else hi = mid - 1;
-    }
-    flat = flat * bv.nb[d] + lo;
-  }
-  return flat;
-}
-
-__device__ __forceinline__ bool in_target(const EnsView &E, int r, const int32_t *xs, int stride) {
-  bool in = true;
-#pragma unroll 1
-  for (int c = 0; c < E.n_clauses; ++c) {
-    const int v = xs[E.tgt_species[c] * stride];
-    const int thr = E.tgt_thr[r * E.n_clauses + c];
-    in = in && (E.tgt_op[c] == 0 ? v >= thr : v <= thr);
-  }
-  return in;
-}
-
-__device__ __forceinline__ int find_run(const int32_t *run_off, int R, int f) {
-  int lo = 0, hi = R;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (run_off[mid] <= f) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// ------------------------------------------------------------------------------------------
-// One thread per walker.  The canonical propensity tree (P leaves, node k = node 2k + node
-// 2k+1, rounded) lives in registers; every index into it is a compile-time constant after
-// unrolling, and the descent picks children with predicated selects.  Species counts are
-// staged in shared memory so that reactions can name them by runtime index.
-// ------------------------------------------------------------------------------------------
-template <int P, int LOG2P>
-__global__ void __launch_bounds__(128) k_propagate_thread(PropagateParams prm) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const NetView &N = prm.net;
-  const EnsView &E = prm.ens;
-  const int B = blockDim.x, tid = threadIdx.x;
-  RxnMeta *s_meta = reinterpret_cast<RxnMeta *>(smem_raw);
-  double *s_keff = reinterpret_cast<double *>(s_meta + P);
-  double *s_Kn = s_keff + N.n_param_sets * P;
-  int32_t *s_dsp = reinterpret_cast<int32_t *>(s_Kn + N.n_param_sets * P);
-  int32_t *s_dval = s_dsp + N.n_delta;
-  int32_t *xs = s_dval + N.n_delta;
-  for (int i = tid; i < P * 16; i += B)
-    reinterpret_cast<int32_t *>(s_meta)[i] = reinterpret_cast<const int32_t *>(N.meta)[i];
-  for (int i = tid; i < N.n_param_sets * P; i += B) { s_keff[i] = N.keff[i]; s_Kn[i] = N.hill_Kn[i]; }
-  for (int i = tid; i < N.n_delta; i += B) { s_dsp[i] = N.d_sp[i]; s_dval[i] = N.d_val[i]; }
-  __syncthreads();
-
-  const int iter = *E.iter;
-  const int total = E.run_off[E.R];
-  const int f = blockIdx.x * B + tid;
-  if (f >= total) return;
-  const int r = E.R == 1 ? 0 : find_run(E.run_off, E.R, f);
-  const int w = f - E.run_off[r];
-  const int g = r * E.cap + w;
-  const int par = iter & 1;
-  const int ld = E.R * E.cap;
-  int32_t *X = E.x[par];
-  int32_t *xme = xs + tid;
-  for (int s = 0; s < E.S; ++s) xme[s * B] = X[(size_t)s * ld + g];
-  const int ps = E.param_set[r];
-  const double *keff = s_keff + ps * P;
-  const double *Kn = s_Kn + ps * P;
-  const uint32_t k0 = (uint32_t)E.seed;
-  const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
-
-  double nd[2 * P];
-  auto rebuild = [&]() {
-#pragma unroll
-    for (int j = 0; j < P; ++j) nd[P + j] = propensity(s_meta[j], keff[j], Kn[j], xme, B);
-#pragma unroll
-    for (int k = P - 1; k >= 1; --k) nd[k] = __dadd_rn(nd[2 * k], nd[2 * k + 1]);
-  };
-  rebuild();
-
-  const long long tau_bits = bits(E.tau);
-  double t = 0.0;
-  uint32_t draw = 0;
-  long long nev = 0;
-  int nrec = 0;
-  int status = 0;
-  for (;;) {
-    const double a0 = nd[1];
-    if (bits(a0) == 0) break;                        // nothing can fire: idle to tau
-    uint32_t c0 = draw, c1 = (uint32_t)iter, c2 = (uint32_t)w, c3 = 0u;
-    ++draw;
-    philox4x32_10(c0, c1, c2, c3, k0, k1);
-    const double u1 = u01(c0, c1);
-    const double u2 = u01(c2, c3);
-    const double e = -log(u1);
-    const double dt = __ddiv_rn(e, a0);
-    const double tn = __dadd_rn(t, dt);
-    if (bits(tn) > tau_bits) break;                  // the next event falls after tau
-    if (nev >= E.max_steps) { status = kStatusStepCap; break; }
-    double target = __dmul_rn(u2, a0);
-    int k = 1;
-#pragma unroll
-    for (int lvl = 0; lvl < LOG2P; ++lvl) {
-      double L = 0.0, R = 0.0;
-#pragma unroll
-      for (int c = (1 << lvl); c < (2 << lvl); ++c)
-        if (k == c) { L = nd[2 * c]; R = nd[2 * c + 1]; }
-      const bool right = (bits(R) != 0) && !(bits(target) < bits(L));
-      if (right) { target = __dsub_rn(target, L); k = 2 * k + 1; }
-      else { k = 2 * k; }
-    }
-    const RxnMeta &mt = s_meta[k - P];
-    bool over = false;
-    for (int q = mt.d_begin; q < mt.d_end; ++q)
-      over |= (xme[s_dsp[q] * B] + s_dval[q]) > kMaxCount;
-    if (over) { status = kStatusOverflow; break; }
-    for (int q = mt.d_begin; q < mt.d_end; ++q) xme[s_dsp[q] * B] += s_dval[q];
-    ++nev;
-    t = tn;
-    if (E.feedback && in_target(E, r, xme, B)) {
-      ++nrec;
-      for (int s = 0; s < E.S; ++s) xme[s * B] = E.recycle[r * E.S + s];
-    }
-    rebuild();
-  }
-
-  for (int s = 0; s < E.S; ++s) X[(size_t)s * ld + g] = xme[s * B];
-  E.nrec[g] = nrec;
-  E.tlast[g] = t;
-  if (status) atomicCAS(&E.status[r], 0, status);
-  const int b = bin_of(prm.bins, xme, B);
-  E.bin[g] = b;
-  if (prm.resample) atomicAdd(&E.bin_count[r * prm.bins.n_bins + b], 1);
-  const int slot = iter - E.first_iter;
-  if (slot >= 0 && slot < E.record_iters) {
-    const double wt = E.w[par][g];
-    const int o = slot * E.R + r;
-    if (nrec) atomicAdd(&E.obs_flux[o], __dmul_rn((double)nrec, wt));
-    if (nev) atomicAdd(&E.obs_events[o], (unsigned long long)nev);
-    if (E.hist_len > 0) {
-      const int v = xme[E.hist_species * B];
-      const int idx = v < E.hist_len - 1 ? v : E.hist_len - 1;
-      atomicAdd(&E.obs_hist[(size_t)o * E.hist_len + idx], wt);
-    }
-    if (!prm.resample) atomicAdd(&E.obs_totw[o], wt);
-  }
-}
 
 // ------------------------------------------------------------------------------------------
 // Per run (one block): exclusive scans of bin counts and of bin occupancy give, for every
@@ -503,37 +290,6 @@ __global__ void k_pack_states(EnsView E, int r, int32_t *out) {
 // ------------------------------------------------------------------------------------------
 // Host-side launch helpers (called from we_host.cu).
 // ------------------------------------------------------------------------------------------
-size_t propagate_thread_smem(const NetView &N, int block) {
-  return (size_t)N.P * sizeof(RxnMeta) + 2 * (size_t)N.n_param_sets * N.P * sizeof(double) +
-         2 * (size_t)N.n_delta * sizeof(int32_t) + (size_t)N.S * block * sizeof(int32_t);
-}
-
-template <int P, int L>
-static cudaError_t launch_thread(const PropagateParams &prm, int grid, int block, size_t smem,
-                                 cudaStream_t st) {
-  auto kern = k_propagate_thread<P, L>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  kern<<<grid, block, smem, st>>>(prm);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_propagate_thread(const PropagateParams &prm, int block, cudaStream_t st) {
-  const int total_slots = prm.ens.R * prm.ens.cap;
-  const int grid = (total_slots + block - 1) / block;
-  const size_t smem = propagate_thread_smem(prm.net, block);
-  switch (prm.net.P) {
-    case 1: return launch_thread<1, 0>(prm, grid, block, smem, st);
-    case 2: return launch_thread<2, 1>(prm, grid, block, smem, st);
-    case 4: return launch_thread<4, 2>(prm, grid, block, smem, st);
-    case 8: return launch_thread<8, 3>(prm, grid, block, smem, st);
-    case 16: return launch_thread<16, 4>(prm, grid, block, smem, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st) {
   const EnsView &E = prm.ens;
   const int nb = prm.bins.n_bins;

@@ -33,21 +33,40 @@ def _parity(cfg, n_iters, runs=None, **kw):
     return ens
 
 
-def test_birth_death_we():
-    _parity(W.birth_death_we(n_iters=60), 60)
+MAPPINGS = [P.WE_MAP_AUTO, P.WE_MAP_THREAD]        # auto picks the state-indexed tables here
 
 
-def test_birth_death_we_with_recycling():
-    _parity(W.birth_death_we(n_iters=60, target=130), 60)
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_birth_death_we(mapping):
+    _parity(W.birth_death_we(n_iters=60), 60, mapping=mapping)
 
 
-def test_schlogl_mfpt_batched_replicas():
-    _parity(W.schlogl_mfpt_we(n_iters=40, n_runs=3), 40)
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_birth_death_we_with_recycling(mapping):
+    _parity(W.birth_death_we(n_iters=60, target=130), 60, mapping=mapping)
 
 
-def test_toggle_batch_uneven_runs():
+@pytest.mark.parametrize("mapping", MAPPINGS)
+@pytest.mark.parametrize("block", [0, 32])
+def test_schlogl_mfpt_batched_replicas(mapping, block):
+    _parity(W.schlogl_mfpt_we(n_iters=40, n_runs=3), 40, mapping=mapping, block_threads=block)
+
+
+def test_schlogl_table_beyond_its_range():
+    """Walkers above the table's last count take the directly evaluated row."""
+    cfg = W.schlogl_pdf_we(n_iters=6, m_targ=4, n_unit_bins=80)
+    cfg.bins = W.GridBins([0], [W.uniform_edges(0, 100, 80)])
+    cfg.x0[:, 0] = 5000
+    cfg.init_states[:, :, 0] = 5000
+    cfg.recycle_state[:, 0] = 5000
+    cfg.capacity = 4 * 80
+    _parity(cfg, 6, mapping=P.WE_MAP_THREAD_TABLE)
+
+
+@pytest.mark.parametrize("block", [0, 64])
+def test_toggle_batch_uneven_runs(block):
     cfg = W.toggle_batch_we(n_runs=8, n_iters=30)
-    ens = _parity(cfg, 30)
+    ens = _parity(cfg, 30, block_threads=block)
     counts = ens.get(P.WE_OUT_COUNTS)
     assert len(set(counts.tolist())) > 1          # uneven live-walker counts across runs
 
@@ -70,8 +89,9 @@ def test_futile_cycle():
     _parity(cfg, 15)
 
 
-@pytest.mark.parametrize("block", [32, 64, 128])
-def test_plain_ssa_counts_and_times(block):
+@pytest.mark.parametrize("mapping", MAPPINGS)
+@pytest.mark.parametrize("block", [32, 96, 128])
+def test_plain_ssa_counts_and_times(block, mapping):
     """No resampling: 3000 Schloegl walkers for three intervals; counts bit-exact, last event
     times within 1e-12 relative (device log vs host log may differ in the last bit)."""
     cfg = W.schlogl_mfpt_we(n_iters=3)
@@ -83,13 +103,16 @@ def test_plain_ssa_counts_and_times(block):
     init[0, :, 1], init[0, :, 2] = 100000, 200000
     w = np.full((1, n), 1.0 / n)
     cfg.capacity = n
-    ens = gpu_run(cfg, 3, resample=False, init_states=init, init_weights=w, block_threads=block)
+    ens = gpu_run(cfg, 3, resample=False, init_states=init, init_weights=w, block_threads=block,
+                  mapping=mapping)
     ens.sync()
     o = oracle_run(cfg, 0, n_iters=3, resample=False, init_states=init, init_weights=w)
     g = gpu_outputs(ens, 0)
     assert_run_parity(g, o, "plain ssa")
     tl = ens.get(P.WE_OUT_TLAST, 0)
     np.testing.assert_allclose(tl, o["t_last"][:n], rtol=1e-12, atol=0)
+    rel = np.abs(tl - o["t_last"][:n]) / np.maximum(o["t_last"][:n], 1e-300)
+    assert rel.max() < 1e-13                          # the float-float logarithm: ~1e-14
     assert np.all(tl <= cfg.tau) and np.count_nonzero(tl) > n // 2
 
 
