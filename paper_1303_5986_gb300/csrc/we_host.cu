@@ -456,9 +456,11 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
     return fail(WE_ENOTSUPPORTED, "thread mapping needs <= %d reactions and <= %d species", kThreadMaxLeaves, kThreadMaxSpecies);
   if (mapping == WE_MAP_THREAD_TABLE && table_len_for(n) == 0)
     return fail(WE_ENOTSUPPORTED, "table mapping needs every propensity to read one species only");
-  const int block = c->block_threads > 0 ? c->block_threads : (thread_map ? 128 : 256);
+  const int block = c->block_threads > 0 ? c->block_threads : (thread_map ? 128 : 32);
   if (thread_map && block != 32 && block != 64 && block != 96 && block != 128)
     return fail(WE_EINVAL, "thread mapping supports block_threads of 32, 64, 96 or 128");
+  if (mapping == WE_MAP_WARP && 16ull * n->P + 4ull * n->S + sizeof(LogTables) + 16 > 227ull * 1024)
+    return fail(WE_ENOTSUPPORTED, "warp mapping keeps the walker's tree in shared memory: at most ~13,000 reactions");
   Offsets o = layout(n, b, c, cap);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void *ws = workspace;
@@ -889,7 +891,7 @@ extern "C" we_status we_autotune(const we_network *n, const we_binmap *b, const 
     for (int bt : {32, 64, 128}) cands.push_back({WE_MAP_THREAD_TABLE, bt});
   if (n->P <= kThreadMaxLeaves && n->S <= kThreadMaxSpecies)
     for (int bt : {32, 64, 128}) cands.push_back({WE_MAP_THREAD, bt});
-  for (int bt : {128, 256}) cands.push_back({WE_MAP_WARP, bt});
+  cands.push_back({WE_MAP_WARP, 32});
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float best = 1e30f;
   std::pair<int, int> pick = cands.front();

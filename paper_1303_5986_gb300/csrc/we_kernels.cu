@@ -119,7 +119,7 @@ __device__ __forceinline__ void warp_argmin(const double *sw, const int32_t *ss,
 // The resampled walkers are written in slot order, copies right after their parent, at the
 // bin's output offset.
 // ------------------------------------------------------------------------------------------
-__global__ void k_resample(EnsView E, int n_bins) {
+__global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
   const int r = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -163,6 +163,50 @@ __global__ void k_resample(EnsView E, int n_bins) {
         ++kmerge;
         __syncwarp();
       }
+    } else if (cnt < M && cnt <= 128) {
+      // Up to 128 walkers: each lane keeps its entries' per-copy weights w_i/c_i in registers,
+      // so a round divides once (for the walker that received the copy), not once per walker.
+      double wv[4];
+      long long vv[4];
+      int cc[4], sl[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        if (i < cnt) { wv[q] = lsw[i]; vv[q] = bits(wv[q]); cc[q] = 1; sl[q] = lss[i]; }
+        else { wv[q] = 0.0; vv[q] = -1; cc[q] = 0; sl[q] = 0x7FFFFFFF; }
+      }
+      for (int extra = cnt; extra < M; ++extra) {
+        long long bv = -1;
+        int bs = 0x7FFFFFFF, bo = -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (vv[q] > bv || (vv[q] == bv && sl[q] < bs)) { bv = vv[q]; bs = sl[q]; bo = lane * 4 + q; }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+          const long long ov = __shfl_xor_sync(0xffffffffu, bv, d);
+          const int os = __shfl_xor_sync(0xffffffffu, bs, d);
+          const int oo = __shfl_xor_sync(0xffffffffu, bo, d);
+          if (ov > bv || (ov == bv && os < bs)) { bv = ov; bs = os; bo = oo; }
+        }
+        double wsel = wv[0];
+        int csel = cc[0];
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+          if ((bo & 3) == q) { wsel = wv[q]; csel = cc[q]; }
+        csel += 1;
+        const long long vnew = bits(__ddiv_rn(wsel, (double)csel));   // one division per round
+        if ((bo >> 2) == lane) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if ((bo & 3) == q) { cc[q] = csel; vv[q] = vnew; }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        if (i < cnt) lal[i] = cc[q];
+      }
+      __syncwarp();
     } else if (cnt < M) {
       for (int extra = cnt; extra < M; ++extra) {
         long long bv = -1;

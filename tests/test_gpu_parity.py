@@ -256,3 +256,44 @@ def test_timed_step_matches_step_and_reports_kernel_times():
     for r in range(2):
         assert np.array_equal(a.states(r), b.states(r))
         assert np.array_equal(a.per_iter(P.WE_OUT_EVENTS, r), b.per_iter(P.WE_OUT_EVENTS, r))
+
+
+# ------------------------------------------------------------------ warp per walker ----------
+@pytest.mark.parametrize("factory", ["schlogl", "toggle", "futile"])
+def test_warp_mapping_small_networks(factory):
+    """The warp-per-walker kernel on networks the thread kernels also handle."""
+    if factory == "schlogl":
+        cfg = W.schlogl_mfpt_we(n_iters=12, n_runs=2)
+    elif factory == "toggle":
+        cfg = W.toggle_batch_we(n_runs=4, n_iters=12)
+    else:
+        cfg = W.WEConfig(network=W.futile_cycle(), bins=W.GridBins([0], [W.uniform_edges(0, 1, 101)]),
+                         tau=1.0, m_targ=6, n_iters=8, x0=[50, 50, 1, 1, 0, 0], hist_species=0,
+                         hist_len=102, name="futile")
+    _parity(cfg, cfg.n_iters, mapping=P.WE_MAP_WARP)
+
+
+def _small_synthetic(n_walkers=24, m_targ=2, tau=2e-5, n_iters=3):
+    cfg = W.synthetic_large_we(n_walkers=n_walkers, n_iters=n_iters, m_targ=m_targ)
+    cfg.tau = tau
+    cfg.capacity = max(n_walkers, m_targ * cfg.bins.n_bins)
+    return cfg
+
+
+def test_warp_mapping_synthetic_354x3680():
+    """FceRI-sized random network (354 species, 3680 reactions): dependency-graph updates of the
+    shared-memory tree against the oracle's full recomputation, through resampling."""
+    cfg = _small_synthetic()
+    ens = _parity(cfg, cfg.n_iters, mapping=P.WE_MAP_WARP)
+    ev = ens.per_iter(P.WE_OUT_EVENTS, 0)
+    assert ev.min() > 1000                      # hundreds of events per walker per interval
+
+
+def test_warp_mapping_synthetic_plain_ssa_times():
+    cfg = _small_synthetic(n_walkers=40, n_iters=2)
+    ens = gpu_run(cfg, 2, resample=False, mapping=P.WE_MAP_WARP)
+    ens.sync()
+    o = oracle_run(cfg, 0, n_iters=2, resample=False)
+    assert_run_parity(gpu_outputs(ens, 0), o, "synthetic plain")
+    tl = ens.get(P.WE_OUT_TLAST, 0)
+    np.testing.assert_allclose(tl, o["t_last"][:40], rtol=1e-12, atol=0)
