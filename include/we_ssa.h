@@ -130,6 +130,37 @@ void we_binmap_destroy(we_binmap *bm);
 int32_t we_binmap_n_bins(const we_binmap *bm);
 
 /* ------------------------------------------------------------------------------------------
+ * Learned progress coordinate.  WE is unbiased under any binning (Sec. II.B), and choosing bins
+ * automatically is the open problem named in Sec. IV.B; these entry points fit a small MLP
+ * z(x) = w3 . silu(W2 silu(W1 phi + b1) + b2) + b3, phi_s = log1p(x_s) over every species, so that
+ * sigmoid(z) estimates the probability of reaching the target set (labels come from the
+ * library's own SSA runs), and bin walkers by intervals of z.
+ *
+ * we_mlp_create: n_in = number of species, hidden <= 64; params (host, FP32) in the layout
+ *   W1[hidden][n_in], b1[hidden], W2[hidden][hidden], b2[hidden], w3[hidden], b3.
+ * we_mlp_train: `steps` Adam steps (beta 0.9/0.999, eps 1e-8) on consecutive batches of the
+ *   device arrays states (n x n_in int32, sample-major) and labels (n float in [0,1]) with the
+ *   batch-mean BCE-with-logits loss; loss_per_step (host, steps floats, may be NULL).
+ * we_mlp_gradient: the batch-mean loss and its gradient (device, n_params floats) over all n
+ *   samples, without changing the weights (for gradient checks).
+ * Training is FP32 with sums in sample order (deterministic).  Errors: WE_EINVAL, WE_ENOMEM,
+ * WE_ECUDA.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct we_mlp we_mlp;
+we_status we_mlp_create(int32_t n_in, int32_t hidden, const float *params, we_mlp **out);
+void we_mlp_destroy(we_mlp *mlp);
+int32_t we_mlp_n_params(const we_mlp *mlp);
+we_status we_mlp_get_params(const we_mlp *mlp, float *dst, size_t dst_floats);
+we_status we_mlp_train(we_mlp *mlp, const int32_t *states, const float *labels, int32_t n,
+                       int32_t steps, int32_t batch, float lr, float *loss_per_step, void *stream);
+we_status we_mlp_gradient(const we_mlp *mlp, const int32_t *states, const float *labels, int32_t n,
+                          float *grad, float *loss, void *stream);
+/* Bin map on the learned coordinate: a snapshot of the MLP's weights rounded to BF16 (inference
+ * runs in FP32 on those weights), with n_bins intervals [edges[k], edges[k+1]) of z (values
+ * outside fall in the end bins).  Binning runs in a kernel of its own after the SSA kernel. */
+we_status we_binmap_learned(const we_mlp *mlp, int32_t n_bins, const float *edges, we_binmap **out);
+
+/* ------------------------------------------------------------------------------------------
  * Run configuration (the arguments of the WE procedure, Sec. II.B: tau, M_targ, the grid,
  * the initial state, plus the recycling target of Sec. II.B.2).  A configuration describes
  * n_runs independent WE runs executed together (a batch: replicas or a parameter sweep).
@@ -220,6 +251,9 @@ we_status we_ensemble_sync(we_ensemble *ens, void *stream);
  *   WE_OUT_TLAST     double[n_prev]                 time of each walker's last event in the
  *                                                   last propagated interval (0 if none), by
  *                                                   the slot it held then (before resampling)
+ *   WE_OUT_Z         float[n_prev]                  learned coordinate of each walker at the end
+ *                                                   of the last interval (learned bin maps)
+ *   WE_OUT_NREC      int32[n_prev]                  recycles of each walker in the last interval
  * Per-iteration arrays hold the recorded iterations in order. */
 #define WE_OUT_COUNTS 1
 #define WE_OUT_STATES 2
@@ -234,6 +268,8 @@ we_status we_ensemble_sync(we_ensemble *ens, void *stream);
 #define WE_OUT_ITER 11
 #define WE_OUT_RECORDED 12
 #define WE_OUT_TLAST 13
+#define WE_OUT_Z 14
+#define WE_OUT_NREC 15
 we_status we_ensemble_get(we_ensemble *ens, int32_t what, int32_t run, void *dst,
                           size_t dst_bytes, size_t *needed, void *stream);
 

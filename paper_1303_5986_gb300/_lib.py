@@ -40,10 +40,13 @@ WE_OUT_STATUS = 10
 WE_OUT_ITER = 11
 WE_OUT_RECORDED = 12
 WE_OUT_TLAST = 13
+WE_OUT_Z = 14
+WE_OUT_NREC = 15
 
 _I32P = C.POINTER(C.c_int32)
 _U32P = C.POINTER(C.c_uint32)
 _F64P = C.POINTER(C.c_double)
+_F32P = C.POINTER(C.c_float)
 _VP = C.c_void_p
 
 
@@ -87,6 +90,13 @@ SIGNATURES = [
                                     C.POINTER(C.c_size_t), _VP]),
     ("we_run", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, C.POINTER(_VP)]),
     ("we_autotune", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, _I32P, _I32P]),
+    ("we_mlp_create", C.c_int32, [C.c_int32, C.c_int32, _F32P, C.POINTER(_VP)]),
+    ("we_mlp_destroy", None, [_VP]),
+    ("we_mlp_n_params", C.c_int32, [_VP]),
+    ("we_mlp_get_params", C.c_int32, [_VP, _F32P, C.c_size_t]),
+    ("we_mlp_train", C.c_int32, [_VP, _VP, _VP, C.c_int32, C.c_int32, C.c_int32, C.c_float, _F32P, _VP]),
+    ("we_mlp_gradient", C.c_int32, [_VP, _VP, _VP, C.c_int32, _VP, _F32P, _VP]),
+    ("we_binmap_learned", C.c_int32, [_VP, C.c_int32, _F32P, C.POINTER(_VP)]),
     ("we_resample_static", C.c_int32, [C.c_int32, _VP, _VP, C.c_int32, C.c_int32, C.c_int32,
                                        C.c_uint64, C.c_uint32, C.c_int32, _VP, _VP, _VP, _VP]),
 ]

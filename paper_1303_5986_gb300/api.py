@@ -182,7 +182,7 @@ _OUT_DTYPES = {
     L.WE_OUT_PARENT: np.int32, L.WE_OUT_FLUX: np.float64, L.WE_OUT_TOTAL_W: np.float64,
     L.WE_OUT_NWALKERS: np.int32, L.WE_OUT_EVENTS: np.int64, L.WE_OUT_HIST: np.float64,
     L.WE_OUT_STATUS: np.int32, L.WE_OUT_ITER: np.int32, L.WE_OUT_RECORDED: np.int32,
-    L.WE_OUT_TLAST: np.float64,
+    L.WE_OUT_TLAST: np.float64, L.WE_OUT_Z: np.float32, L.WE_OUT_NREC: np.int32,
 }
 
 
@@ -324,3 +324,91 @@ def we_resample_static(bins, weights, n_bins: int, m_targ: int, iteration: int, 
                                    int(out_weights.numel()), C.c_void_p(out_weights.data_ptr()),
                                    C.c_void_p(out_parent.data_ptr()), C.c_void_p(out_count.data_ptr()),
                                    _stream_handle(stream)))
+
+
+# ------------------------------------------------------------------------------ learned bins
+_F32P = C.POINTER(C.c_float)
+
+
+class MLP:
+    """A we_mlp handle (device-resident FP32 master weights and Adam moments)."""
+
+    def __init__(self, handle, n_in, hidden):
+        self.h = handle
+        self.n_in, self.hidden = n_in, hidden
+        self.n_params = lib().we_mlp_n_params(handle)
+
+    def close(self):
+        if getattr(self, "h", None) and L._lib is not None:
+            L._lib.we_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        check(lib().we_mlp_get_params(self.h, out.ctypes.data_as(_F32P), out.size))
+        return out
+
+    def train(self, states, labels, steps: int, batch: int, lr: float, stream=None) -> np.ndarray:
+        """Adam steps on device tensors states (n x n_in int32) and labels (n float32)."""
+        losses = np.zeros(max(int(steps), 1), dtype=np.float32)
+        check(lib().we_mlp_train(self.h, C.c_void_p(states.data_ptr()), C.c_void_p(labels.data_ptr()),
+                                 int(labels.numel()), int(steps), int(batch), float(lr),
+                                 losses.ctypes.data_as(_F32P), _stream_handle(stream)))
+        return losses[:int(steps)]
+
+    def gradient(self, states, labels, stream=None):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=labels.device)
+        loss = np.zeros(1, dtype=np.float32)
+        check(lib().we_mlp_gradient(self.h, C.c_void_p(states.data_ptr()), C.c_void_p(labels.data_ptr()),
+                                    int(labels.numel()), C.c_void_p(g.data_ptr()),
+                                    loss.ctypes.data_as(_F32P), _stream_handle(stream)))
+        return g.cpu().numpy(), float(loss[0])
+
+
+def we_mlp_create(n_in: int, hidden: int, params) -> MLP:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    h = C.c_void_p()
+    check(lib().we_mlp_create(int(n_in), int(hidden), p.ctypes.data_as(_F32P), C.byref(h)))
+    return MLP(h, n_in, hidden)
+
+
+def we_binmap_learned(mlp: MLP, edges) -> BinMap:
+    e = np.ascontiguousarray(edges, dtype=np.float32)
+    h = C.c_void_p()
+    check(lib().we_binmap_learned(mlp.h, len(e) - 1, e.ctypes.data_as(_F32P), C.byref(h)))
+    return BinMap(h)
+
+
+def first_passage_labels(net: Network, states, horizon: float, target, recycle_state, seed: int = 0,
+                         param_set: int = 0, stream=None):
+    """Shooting labels for training a progress coordinate: label 1 where a plain SSA trajectory
+    (Sec. II.A) started at a state enters the target set within `horizon` (or starts inside it),
+    else 0.  states: (n, S) int; target: (species, ops, thresholds (clauses,)).  Runs one
+    unresampled interval of length `horizon` through the SSA kernel with the target as a
+    recycling set and reads each walker's recycle count.  Returns float32 labels on the device."""
+    import torch
+    st = np.ascontiguousarray(states, dtype=np.int32)
+    n, S = st.shape
+    sp, ops, thr = target
+    thr = np.asarray(thr, dtype=np.int32).reshape(1, -1)
+    c, keep = make_run_config(horizon, 1, st.reshape(1, n, S), np.full((1, n), 1.0 / n), n_runs=1,
+                              seed=seed, param_set=[param_set], capacity=n, record_iters=1,
+                              target=(sp, ops, thr), recycle_state=np.asarray(recycle_state).reshape(1, S),
+                              resample=False)
+    bm = we_binmap_grid([0], [np.array([0.0, 2.0 ** 31])])
+    ens = we_ensemble_create(net, bm, c, keep, stream=stream)
+    ens.propagate(stream)
+    dev = ens.workspace.device
+    nrec = torch.empty(n, dtype=torch.int32, device=dev)
+    ens.get(L.WE_OUT_NREC, 0, out=nrec, stream=stream)
+    x = torch.as_tensor(st, device=dev)
+    inside = torch.ones(n, dtype=torch.bool, device=dev)
+    for s_, o_, t_ in zip(sp, ops, thr[0]):
+        inside &= (x[:, s_] >= int(t_)) if o_ == L.WE_OP_GE else (x[:, s_] <= int(t_))
+    labels = ((nrec > 0) | inside).to(torch.float32)
+    ens.close()
+    return labels

@@ -15,6 +15,7 @@
 
 #include "../../include/we_ssa.h"
 #include "we_internal.cuh"
+#include "we_mlp.cuh"
 
 namespace we {
 cudaError_t launch_propagate_thread(const PropagateParams &prm, int block, bool table, cudaStream_t st);
@@ -27,6 +28,7 @@ size_t propagate_warp_smem(const NetView &N, int block);
 cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_pack_states(const EnsView &E, int r, int32_t *out, cudaStream_t st);
+cudaError_t launch_learned_bins(const PropagateParams &prm, cudaStream_t st);
 }  // namespace we
 
 using namespace we;
@@ -250,7 +252,23 @@ struct we_binmap {
   int32_t nb[kMaxBinDims] = {1, 1, 1, 1};
   int32_t edge_off[kMaxBinDims] = {0, 0, 0, 0};
   std::vector<double> edges;
+  bool learned = false;
+  we_learned_bins lb;
 };
+
+extern "C" we_status we_binmap_learned(const we_mlp *mlp, int32_t n_bins, const float *edges, we_binmap **out) {
+  if (!out) return fail(WE_EINVAL, "out is NULL");
+  *out = nullptr;
+  we_binmap *b = new (std::nothrow) we_binmap();
+  if (!b) return fail(WE_ENOMEM, "host allocation");
+  we_status st = make_learned_snapshot(mlp, n_bins, edges, &b->lb);
+  if (st) { delete b; return fail(st, "learned bin map: need an MLP, 1..65536 bins and ascending edges"); }
+  b->learned = true;
+  b->n_bins = n_bins;
+  b->edges.assign(1, 0.0);
+  *out = b;
+  return WE_OK;
+}
 
 extern "C" we_status we_binmap_grid(int32_t ndim, const int32_t *species, const int32_t *n_bins,
                                     const double *edges, we_binmap **out) {
@@ -305,6 +323,7 @@ struct Offsets {
   size_t count, prev_count, run_off, status, iter, bin_count, n_tasks, tasks, cursor, sorted_slot, sorted_w, alive;
   size_t flux, totw, nw, events, hist, pack;
   size_t logt, table, base;
+  size_t lw1, lw2, lw3, lb, lz, zout;
   int32_t table_len;
   size_t total;
 };
@@ -321,6 +340,15 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
   Offsets o{};
   o.table_len = table_len_for(n);
   o.logt = L.take(sizeof(LogTables));
+  if (b->learned) {
+    const we_learned_bins &lb = b->lb;
+    o.lw1 = L.take(2 * lb.w1.size());
+    o.lw2 = L.take(2 * lb.w2.size());
+    o.lw3 = L.take(2 * lb.w3.size());
+    o.lb = L.take(4 * (2 * (size_t)lb.H + 1));
+    o.lz = L.take(4 * lb.zedges.size());
+    o.zout = L.take(4 * (size_t)c->n_runs * (size_t)cap);
+  }
   o.table = L.take((size_t)n->nps * o.table_len * 2 * n->P * 8);
   o.base = L.take(4 * (size_t)n->S);
   const size_t R = c->n_runs, RC = R * cap, rec = c->record_iters;
@@ -395,6 +423,8 @@ static we_status check_config(const we_network *n, const we_binmap *b, const we_
   if (c->first_iter < 0) return fail(WE_EINVAL, "first_iter must be >= 0");
   for (int d = 0; d < b->ndim; ++d)
     if (b->species[d] >= n->S) return fail(WE_EINVAL, "bin dimension %d names species %d >= S", d, b->species[d]);
+  if (b->learned && b->lb.n_in != n->S)
+    return fail(WE_EINVAL, "learned bin map reads %d species, the network has %d", b->lb.n_in, n->S);
   long long cap = c->capacity > 0 ? c->capacity : std::max<long long>((long long)c->m_targ * b->n_bins, c->n_init);
   if (cap < c->n_init) return fail(WE_EINVAL, "capacity %lld < n_init %d", cap, c->n_init);
   if (cap * c->n_runs > (1ll << 30)) return fail(WE_EINVAL, "runs x capacity too large");
@@ -541,6 +571,17 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   std::vector<int32_t> base(S, 0);
   for (int sp = 0; sp < S; ++sp) base[sp] = n->fixed[sp] >= 0 ? n->fixed[sp] : 0;
   e = e ? e : up(o.base, base.data(), 4 * S);
+  if (b->learned) {
+    const we_learned_bins &lb = b->lb;
+    std::vector<float> bias(lb.b1);
+    bias.insert(bias.end(), lb.b2.begin(), lb.b2.end());
+    bias.push_back(lb.b3[0]);
+    e = e ? e : up(o.lw1, lb.w1.data(), 2 * lb.w1.size());
+    e = e ? e : up(o.lw2, lb.w2.data(), 2 * lb.w2.size());
+    e = e ? e : up(o.lw3, lb.w3.data(), 2 * lb.w3.size());
+    e = e ? e : up(o.lb, bias.data(), 4 * bias.size());
+    e = e ? e : up(o.lz, lb.zedges.data(), 4 * lb.zedges.size());
+  }
   e = e ? e : launch_init_log_tables(at<LogTables>(ws, o.logt), s);
   if (e) { cudaGetLastError(); return cleanup(cuda_fail(e, "ensemble upload")); }
 
@@ -558,6 +599,19 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   Bv.ndim = b->ndim; Bv.n_bins = b->n_bins;
   for (int d = 0; d < kMaxBinDims; ++d) { Bv.species[d] = b->species[d]; Bv.nb[d] = b->nb[d]; Bv.edge_off[d] = b->edge_off[d]; }
   Bv.edges = at<double>(ws, o.edges);
+  Bv.learned = b->learned ? 1 : 0;
+  if (b->learned) {
+    Bv.mlp.n_in = b->lb.n_in;
+    Bv.mlp.hidden = b->lb.H;
+    Bv.mlp.w1 = at<uint16_t>(ws, o.lw1);
+    Bv.mlp.w2 = at<uint16_t>(ws, o.lw2);
+    Bv.mlp.w3 = at<uint16_t>(ws, o.lw3);
+    Bv.mlp.b1 = at<float>(ws, o.lb);
+    Bv.mlp.b2 = at<float>(ws, o.lb) + b->lb.H;
+    Bv.mlp.b3 = at<float>(ws, o.lb) + 2 * b->lb.H;
+    Bv.zedges = at<float>(ws, o.lz);
+    Bv.zout = at<float>(ws, o.zout);
+  }
   EnsView &V = E->prm.ens;
   V.R = R; V.cap = cap; V.S = S; V.m_targ = c->m_targ; V.record_iters = c->record_iters;
   V.first_iter = c->first_iter; V.hist_species = c->hist_species; V.hist_len = c->hist_len;
@@ -615,11 +669,17 @@ extern "C" we_status we_ensemble_destroy(we_ensemble *E) {
 // Thread mappings: 128-thread blocks run the warp-specialised kernel (one event warp and three
 // draw warps per 32 walkers); 32/64/96-thread blocks run the plain kernel in which each thread
 // makes its own draws.
-static cudaError_t enqueue_propagate(we_ensemble *E, cudaStream_t s) {
+static cudaError_t enqueue_ssa(we_ensemble *E, cudaStream_t s) {
   if (E->mapping == WE_MAP_WARP) return launch_propagate_warp(E->prm, E->block, s);
   const bool table = E->mapping == WE_MAP_THREAD_TABLE;
   if (E->block == 128) return launch_propagate_ws(E->prm, table, s);
   return launch_propagate_thread(E->prm, E->block, table, s);
+}
+
+static cudaError_t enqueue_propagate(we_ensemble *E, cudaStream_t s) {
+  cudaError_t e = enqueue_ssa(E, s);
+  if (!e && E->prm.bins.learned) e = launch_learned_bins(E->prm, s);
+  return e;
 }
 
 static cudaError_t enqueue_resample(we_ensemble *E, cudaStream_t s) {
@@ -844,6 +904,21 @@ extern "C" we_status we_ensemble_get(we_ensemble *E, int32_t what, int32_t run, 
       if (!dst) return WE_OK;
       if (dst_bytes < bytes) return fail(WE_EINVAL, "dst too small (%zu < %zu)", dst_bytes, bytes);
       if (bytes) WE_CUDA_TRY(cudaMemcpy(dst, V.tlast + (size_t)run * E->cap, bytes, cudaMemcpyDefault));
+      return WE_OK;
+    }
+    case WE_OUT_Z:
+    case WE_OUT_NREC: {
+      if (run < 0) return fail(WE_EINVAL, "walker arrays need a single run");
+      if (what == WE_OUT_Z && !E->prm.bins.learned) return fail(WE_EINVAL, "WE_OUT_Z needs a learned bin map");
+      int32_t pc = 0;
+      WE_CUDA_TRY(cudaMemcpy(&pc, V.prev_count + run, 4, cudaMemcpyDeviceToHost));
+      const size_t bytes = (size_t)4 * pc;
+      if (needed) *needed = bytes;
+      if (!dst) return WE_OK;
+      if (dst_bytes < bytes) return fail(WE_EINVAL, "dst too small (%zu < %zu)", dst_bytes, bytes);
+      const void *src = what == WE_OUT_Z ? (const void *)(E->prm.bins.zout + (size_t)run * E->cap)
+                                         : (const void *)(V.nrec + (size_t)run * E->cap);
+      if (bytes) WE_CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));
       return WE_OK;
     }
     case WE_OUT_ITER: return scalar(&iter, 4);

@@ -45,6 +45,17 @@ struct NetView {
   const int32_t *dep_idx;
 };
 
+// Learned progress coordinate: z = w3 . silu(W2 silu(W1 phi + b1) + b2) + b3 with
+// phi_s = log1p(x_s) for every species, weights in BF16 (rounded from FP32 master weights),
+// arithmetic in FP32.
+struct MlpView {
+  int32_t n_in, hidden;
+  const uint16_t *w1;          // hidden x n_in, BF16 bits
+  const uint16_t *w2;          // hidden x hidden
+  const uint16_t *w3;          // hidden
+  const float *b1, *b2, *b3;   // hidden, hidden, 1
+};
+
 struct BinView {
   int32_t ndim;
   int32_t n_bins;
@@ -52,6 +63,10 @@ struct BinView {
   int32_t nb[kMaxBinDims];
   int32_t edge_off[kMaxBinDims];
   const double *edges;
+  int32_t learned;             // 1: bins are intervals of the learned coordinate z
+  MlpView mlp;
+  const float *zedges;         // n_bins + 1 ascending edges on z
+  float *zout;                 // per walker slot: z of the last interval (may be null)
 };
 
 // Ensemble state on the device.  Global slot g = run * cap + w.

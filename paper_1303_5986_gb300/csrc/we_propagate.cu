@@ -127,9 +127,11 @@ __device__ __forceinline__ void finish_walker(const PropagateParams &prm, int r,
   E.nrec[g] = nrec;
   E.tlast[g] = t;
   if (status) atomicCAS(&E.status[r], 0, status);
-  const int b = bin_of(prm.bins, xme, B);
-  E.bin[g] = b;
-  if (prm.resample) atomicAdd(&E.bin_count[r * prm.bins.n_bins + b], 1);
+  if (!prm.bins.learned) {
+    const int b = bin_of(prm.bins, xme, B);
+    E.bin[g] = b;
+    if (prm.resample) atomicAdd(&E.bin_count[r * prm.bins.n_bins + b], 1);
+  }
   const int slot = *E.iter - E.first_iter;
   if (slot >= 0 && slot < E.record_iters) {
     const double wt = E.w[par][g];

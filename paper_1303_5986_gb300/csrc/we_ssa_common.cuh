@@ -65,6 +65,48 @@ __device__ __forceinline__ double propensity(const RxnMeta &mt, double keff, dou
   return __dmul_rn(keff, __ll2double_rn(h));
 }
 
+__device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+__device__ __forceinline__ float silu_f(float a) { return __fdiv_rn(a, __fadd_rn(1.0f, expf(-a))); }
+
+// The learned coordinate of one state (see MlpView): layer 1 is accumulated input by input so
+// that each log1p is taken once; layer 2 is folded output by output into the final dot product.
+// Hidden width at most 64.
+__device__ __forceinline__ float mlp_coordinate(const MlpView &m, const int32_t *xs, int stride) {
+  float h1[64];
+#pragma unroll
+  for (int o = 0; o < 64; ++o) h1[o] = 0.0f;
+  for (int i = 0; i < m.n_in; ++i) {
+    const float phi = log1pf((float)xs[i * stride]);
+#pragma unroll
+    for (int o = 0; o < 64; ++o)
+      if (o < m.hidden) h1[o] = __fmaf_rn(bf16_to_f32(m.w1[o * m.n_in + i]), phi, h1[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < 64; ++o)
+    if (o < m.hidden) h1[o] = silu_f(__fadd_rn(h1[o], m.b1[o]));
+  float z = m.b3[0];
+  for (int o = 0; o < m.hidden; ++o) {
+    float a = m.b2[o];
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+      if (i < m.hidden) a = __fmaf_rn(bf16_to_f32(m.w2[o * m.hidden + i]), h1[i], a);
+    z = __fmaf_rn(bf16_to_f32(m.w3[o]), silu_f(a), z);
+  }
+  return z;
+}
+
+// Bin of a z value among n_bins intervals [zedges[k], zedges[k+1]) (clamped at both ends).
+__device__ __forceinline__ int z_bin(const BinView &bv, float z) {
+  int lo = 0, hi = bv.n_bins - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bv.zedges[mid] <= z) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Grid bin of a state (learned bins are assigned by k_learned_bins after the SSA kernel).
 __device__ __forceinline__ int bin_of(const BinView &bv, const int32_t *xs, int stride) {
   int flat = 0;
 #pragma unroll 1

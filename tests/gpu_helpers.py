@@ -8,15 +8,15 @@ from oracle import oracle as O
 
 def gpu_run(cfg, n_iters=None, resample=True, mapping=P.WE_MAP_AUTO, block_threads=0,
             max_steps=None, init_states=None, init_weights=None, first_iter=None, workspace="torch",
-            record_iters=None):
+            record_iters=None, bins=None, capacity=None):
     n_iters = cfg.n_iters if n_iters is None else n_iters
     net = P.network_from_spec(cfg.network)
-    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges) if bins is None else bins
     rec = max(n_iters, 1) if record_iters is None else record_iters
     c, keep = P.run_config_from(cfg, record_iters=rec, resample=resample, mapping=mapping,
                                 block_threads=block_threads, max_steps=max_steps,
                                 init_states=init_states, init_weights=init_weights,
-                                first_iter=first_iter)
+                                first_iter=first_iter, capacity=capacity)
     ens = P.we_ensemble_create(net, bm, c, keep, workspace=workspace)
     ens._net, ens._bm = net, bm
     if n_iters:
