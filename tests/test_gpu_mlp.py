@@ -198,29 +198,30 @@ def test_first_passage_labels():
 
 
 def test_we_with_learned_bins_is_unbiased():
-    """Immigration-death chain (kb = 10, kd = 0.1, X0 = 100), tau = 0.1, 50 intervals, 10 walkers
-    per bin on 100 bins of a coordinate trained on soft labels sigmoid((x - 130)/8): the
-    weighted tail P(X >= k, t = 5) against the exact transient distribution, over 8 replicas."""
+    """Immigration-death chain (kb = 10, kd = 0.1, X0 = 100), tau = 0.1, 200 intervals, 10 walkers
+    per bin on 100 bins of a coordinate trained on soft labels sigmoid((x - 130)/8): the weighted
+    tail P(X >= k, t = 20) against the exact transient distribution over 16 replicas -- and the
+    same for the plain species-count grid (60 bins of width 5 plus overflow) as the control."""
     n_in, H = 1, 64
     xs = np.arange(0, 301, dtype=np.int32).reshape(-1, 1)
     ys = (1.0 / (1.0 + np.exp(-(xs[:, 0] - 130.0) / 8.0))).astype(np.float32)
     mlp = P.we_mlp_create(n_in, H, W.mlp_init_params(n_in, H, seed=1))
     losses = mlp.train(_dev(xs, _i32()), _dev(ys, _f32()), 2000, 301, 1e-2)
+    assert losses[-1] < losses[0]
     z = M.forward(mlp.params(), np.arange(60, 220).reshape(-1, 1), n_in, H)
     assert np.all(np.diff(z) > 0), "coordinate not monotone on [60, 220)"
     edges = W.logit_edges(100, -10.0, 12.0)
-    bm = P.we_binmap_learned(mlp, edges)
-    cfg = W.birth_death_we(n_iters=50, n_runs=8, seed=5)
-    cfg.hist_len = 401
-    ens = gpu_run(cfg, 50, bins=bm, capacity=10 * 100 + 64)
-    ens.sync()
-    Hh = ens.per_iter(P.WE_OUT_HIST)               # iters x runs x len; iteration 49 ends at t = 5
-    exact = E.immigration_death_pmf(100, 10.0, 0.1, 5.0, 400)
-    for k in (130, 150, 170):
-        est = Hh[49, :, k:].sum(axis=1)
-        ex = exact[k:].sum()
-        se = est.std(ddof=1) / np.sqrt(len(est))
-        assert abs(est.mean() - ex) < 3 * se + 0.05 * ex, (k, est.mean(), ex, se)
-    tot = ens.per_iter(P.WE_OUT_TOTAL_W)
-    assert np.all(np.abs(tot - 1.0) < 1e-12)
-    assert losses[-1] < losses[0]
+    exact = E.immigration_death_pmf(100, 10.0, 0.1, 20.0, 400)
+    for learned in (True, False):
+        cfg = W.birth_death_we(n_iters=200, n_runs=16, seed=5)
+        bm = P.we_binmap_learned(mlp, edges) if learned else None
+        ens = gpu_run(cfg, 200, bins=bm, capacity=10 * 100 + 64)
+        ens.sync()
+        Hh = ens.per_iter(P.WE_OUT_HIST)           # iters x runs x len; iteration 199 ends at t = 20
+        for k in (120, 130, 140):
+            est = Hh[199, :, k:].sum(axis=1)
+            ex = exact[k:].sum()
+            se = est.std(ddof=1) / np.sqrt(len(est))
+            assert abs(est.mean() - ex) < 3 * se + 0.05 * ex, (learned, k, est.mean(), ex, se)
+        tot = ens.per_iter(P.WE_OUT_TOTAL_W)
+        assert np.all(np.abs(tot - 1.0) < 1e-12)
