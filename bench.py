@@ -12,6 +12,11 @@ relative error against the closed form, the SSA kernel's roofline position, the 
 timed on this host, and an end-to-end figure through the one-call C ABI with host buffers.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--workload toggle_learned` instead compares, on one GPU, the GPU time that plain species-count
+binning and the learned progress coordinate need to reach a 10% MFPT error on a bistable
+two-gene toggle switch (a_U = a_V = 40, K = 1, n = 2, d = 1; exact MFPT from the truncated
+master equation), the learned arm paying for its own training data, labels and training.
 """
 from __future__ import annotations
 
@@ -50,6 +55,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the SSA kernel (0: auto)")
+    ap.add_argument("--workload", choices=["schlogl", "toggle_learned"], default="schlogl")
+    ap.add_argument("--plain-iters", type=int, default=40000, help="toggle_learned: plain-binning iterations")
+    ap.add_argument("--learned-iters", type=int, default=2000, help="toggle_learned: learned-binning iterations")
     return ap.parse_args()
 
 
@@ -198,8 +206,150 @@ def workload_config(a):
 # ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
+# ------------------------------------------------------------------------------------------
+# learned binning against plain binning (MFPT error per GPU-second)
+# ------------------------------------------------------------------------------------------
+TOGGLE_A = 40.0
+
+
+def _toggle_cfg(W, np, R, n_iters, m_targ, seed):
+    import math
+    a = TOGGLE_A
+    cfg = W.toggle_batch_we(n_runs=R, n_iters=n_iters, seed=seed, m_targ=m_targ)
+    cfg.network = W.toggle_switch([a], [a])
+    cfg.param_set = np.zeros(R, np.int32)
+    x0 = np.tile(np.array([[int(a), 0]], np.int32), (R, 1))
+    cfg.x0, cfg.recycle_state = x0, x0.copy()
+    cfg.init_states = np.repeat(x0[:, None, :], m_targ, axis=1)
+    cfg.init_weights = np.full((R, m_targ), 1.0 / m_targ)
+    cfg.target.threshold = np.tile(np.array([[math.ceil(a / 2), math.floor(a / 4)]], np.int32), (R, 1))
+    cfg.hist_len = 0
+    return cfg
+
+
+def _checkpointed_run(P, np, torch, ens, cfg, n_iters, n_ckpt, exact, t_fixed):
+    """Advance in n_ckpt chunks; after each, the per-replica MFPT = tau/mean(flux) over the last
+    80% of the iterations so far, its rms and mean relative error, and the wall time so far."""
+    curve = []
+    chunk = max(1, n_iters // n_ckpt)
+    t = t_fixed
+    done = 0
+    while done < n_iters:
+        k = min(chunk, n_iters - done)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ens.step(k)
+        ens.sync()
+        t += time.perf_counter() - t0
+        done += k
+        f = ens.per_iter(P.WE_OUT_FLUX)[:done]
+        rate = f[done // 5:].mean(axis=0) / cfg.tau
+        rel = np.where(rate > 0, 1.0 / np.maximum(rate, 1e-300) / exact - 1.0, np.inf)
+        rms = float(np.sqrt(np.mean(rel ** 2))) if np.all(np.isfinite(rel)) else float("inf")
+        curve.append({"iters": done, "gpu_s": round(t, 4), "rms_rel": rms,
+                      "mean_rel": float(np.mean(rel)) if np.isfinite(rms) else None})
+    return curve
+
+
+def _time_to(curve, tol):
+    """GPU time of the first checkpoint from which the rms error stays within tol."""
+    for i, c in enumerate(curve):
+        if all(d["rms_rel"] <= tol for d in curve[i:]):
+            return c["gpu_s"]
+    return None
+
+
+def run_toggle_learned(a):
+    import math
+    import numpy as np
+    import torch
+    import paper_1303_5986_gb300 as P
+    import workloads as W
+    from oracle import exact as E
+    from paper_1303_5986_gb300 import build as pbuild
+    from paper_1303_5986_gb300 import learned as LN
+
+    pbuild.build()
+    R, A = 16, TOGGLE_A
+    thrV, thrU = math.ceil(A / 2), math.floor(A / 4)
+    exact = E.toggle_mfpt(A, A, (int(A), 0), lambda u, v: v >= thrV and u <= thrU,
+                          Umax=int(2.5 * A) + 20, Vmax=int(2.5 * A) + 20)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    # plain arm: 30 x 30 grid of width-4 bins on (U, V), 8 walkers per bin
+    cfg = _toggle_cfg(W, np, R, a.plain_iters, 8, 1)
+    net = P.network_from_spec(cfg.network)
+    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c, keep = P.run_config_from(cfg, record_iters=a.plain_iters)
+    ens = P.we_ensemble_create(net, bm, c, keep)
+    torch.cuda.synchronize()
+    plain = _checkpointed_run(P, np, torch, ens, cfg, a.plain_iters, 40, exact, time.perf_counter() - t0)
+    plain_walkers = int(ens.get(P.WE_OUT_COUNTS).sum())
+    ens.close()
+    # learned arm: states from a 300-iteration plain run, first-passage labels (horizon 1),
+    # 2000 Adam steps, 100 bins on z, 164 walkers per bin (about 16384 walkers per replica)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hcfg = _toggle_cfg(W, np, R, 300, 8, 2)
+    hc, hkeep = P.run_config_from(hcfg, record_iters=300)
+    hens = P.we_ensemble_create(net, bm, hc, hkeep)
+    states = LN.harvest_states(hens, 300)
+    hens.close()
+    t_harvest = time.perf_counter() - t0
+    tgt = ([1, 0], [P.WE_OP_GE, P.WE_OP_LE], [thrV, thrU])
+    mlp, xs, labels, losses = LN.fit_coordinate(net, states, tgt, [int(A), 0], 1.0, steps=2000,
+                                                batch=4096, lr=3e-3, seed=3)
+    edges = LN.coordinate_edges(mlp, xs, 100)
+    lbm = P.we_binmap_learned(mlp, edges)
+    M = 164
+    lcfg = _toggle_cfg(W, np, R, a.learned_iters, M, 4)
+    lc, lkeep = P.run_config_from(lcfg, record_iters=a.learned_iters, capacity=M * 100 + 64)
+    lens = P.we_ensemble_create(net, lbm, lc, lkeep)
+    torch.cuda.synchronize()
+    t_fixed = time.perf_counter() - t0
+    learned = _checkpointed_run(P, np, torch, lens, lcfg, a.learned_iters, 20, exact, t_fixed)
+    learned_walkers = int(lens.get(P.WE_OUT_COUNTS).sum())
+    clk = clocks.stop()
+    tp, tl = _time_to(plain, 0.10), _time_to(learned, 0.10)
+    if tp is not None and tl is not None:
+        value, bound = tp / tl, "measured"
+    elif tl is not None:
+        value, bound = plain[-1]["gpu_s"] / tl, "lower bound: plain binning never reached 10% in its run"
+    else:
+        value, bound = None, "learned binning did not reach 10%"
+    line = {
+        "metric": "MFPT rel. error per GPU-s (learned vs plain species-count binning)",
+        "value": value, "unit": "x less GPU time to 10% rms MFPT error", "value_kind": bound,
+        "n_gpus": 1, "higher_is_better": True, "dtype": "f64 (SSA), fp32/bf16 (coordinate)",
+        "data": "synthetic", "vs_baseline": None,
+        "config": {"workload": (f"two-gene toggle a_U=a_V={A:g}, K=1, n=2, d=1; MFPT (40,0) -> "
+                                f"{{V>={thrV}, U<={thrU}}}, tau=0.1, {R} replicas in one batched launch"),
+                   "exact_mfpt_s": exact,
+                   "plain": f"30x30 grid (width 4) x 8 walkers, {a.plain_iters} iterations",
+                   "learned": (f"MLP 2->64->64->1 on log1p counts, {len(states)} harvested states, "
+                               f"first-passage labels (horizon 1), 2000 Adam steps of 4096; 100 bins x {M} "
+                               f"walkers, {a.learned_iters} iterations")},
+        "plain": {"gpu_s_to_10pct": tp, "final": plain[-1], "walkers_end": plain_walkers, "curve": plain},
+        "learned": {"gpu_s_to_10pct": tl, "final": learned[-1], "walkers_end": learned_walkers,
+                    "fixed_cost_s": t_fixed, "harvest_s": t_harvest,
+                    "train_loss_first_last": [float(losses[0]), float(losses[-50:].mean())],
+                    "label_mean": float(labels.mean()), "curve": learned},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
+    if a.workload == "toggle_learned":
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the learned-binning comparison has no CPU "
+                              "oracle arm; its baseline is the plain-binning arm on the same GPU"}))
+            return
+        run_toggle_learned(a)
+        return
     if a.impl == "reference":
         run_reference(a)
         return

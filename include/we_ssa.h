@@ -143,6 +143,9 @@ int32_t we_binmap_n_bins(const we_binmap *bm);
  *   batch-mean BCE-with-logits loss; loss_per_step (host, steps floats, may be NULL).
  * we_mlp_gradient: the batch-mean loss and its gradient (device, n_params floats) over all n
  *   samples, without changing the weights (for gradient checks).
+ * we_mlp_forward: z (device, n floats) of n states (device, n x n_in int32) from the FP32
+ *   weights (bf16 = 0) or from their BF16 roundings (bf16 = 1: the same z as a learned bin map
+ *   made from this MLP computes, bit for bit).
  * Training is FP32 with sums in sample order (deterministic).  Errors: WE_EINVAL, WE_ENOMEM,
  * WE_ECUDA.
  * ------------------------------------------------------------------------------------------ */
@@ -155,6 +158,8 @@ we_status we_mlp_train(we_mlp *mlp, const int32_t *states, const float *labels, 
                        int32_t steps, int32_t batch, float lr, float *loss_per_step, void *stream);
 we_status we_mlp_gradient(const we_mlp *mlp, const int32_t *states, const float *labels, int32_t n,
                           float *grad, float *loss, void *stream);
+we_status we_mlp_forward(const we_mlp *mlp, const int32_t *states, int32_t n, int32_t bf16, float *z,
+                         void *stream);
 /* Bin map on the learned coordinate: a snapshot of the MLP's weights rounded to BF16 (inference
  * runs in FP32 on those weights), with n_bins intervals [edges[k], edges[k+1]) of z (values
  * outside fall in the end bins).  Binning runs in a kernel of its own after the SSA kernel. */
@@ -237,7 +242,8 @@ we_status we_ensemble_sync(we_ensemble *ens, void *stream);
  * dst may be host or device memory (copied with cudaMemcpyDefault after synchronising the
  * stream); dst == NULL only returns the byte count in *needed.  Layouts:
  *   WE_OUT_COUNTS    int32[runs]                    live walkers per run
- *   WE_OUT_STATES    int32[n_live x S]              walker-major counts of one run
+ *   WE_OUT_STATES    int32[n_live x S]              walker-major counts of one run (run = -1:
+ *                                                   of all runs, concatenated in run order)
  *   WE_OUT_WEIGHTS   double[n_live]
  *   WE_OUT_PARENT    int32[n_live]                  slot before the last resampling
  *   WE_OUT_FLUX      double[iters x runs]           recycled weight per interval

@@ -96,6 +96,7 @@ SIGNATURES = [
     ("we_mlp_get_params", C.c_int32, [_VP, _F32P, C.c_size_t]),
     ("we_mlp_train", C.c_int32, [_VP, _VP, _VP, C.c_int32, C.c_int32, C.c_int32, C.c_float, _F32P, _VP]),
     ("we_mlp_gradient", C.c_int32, [_VP, _VP, _VP, C.c_int32, _VP, _F32P, _VP]),
+    ("we_mlp_forward", C.c_int32, [_VP, _VP, C.c_int32, C.c_int32, _VP, _VP]),
     ("we_binmap_learned", C.c_int32, [_VP, C.c_int32, _F32P, C.POINTER(_VP)]),
     ("we_resample_static", C.c_int32, [C.c_int32, _VP, _VP, C.c_int32, C.c_int32, C.c_int32,
                                        C.c_uint64, C.c_uint32, C.c_int32, _VP, _VP, _VP, _VP]),

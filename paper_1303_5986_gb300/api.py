@@ -359,6 +359,15 @@ class MLP:
                                  losses.ctypes.data_as(_F32P), _stream_handle(stream)))
         return losses[:int(steps)]
 
+    def forward(self, states, bf16: bool = False, stream=None):
+        """z of device states (n x n_in int32) as a device float32 tensor."""
+        import torch
+        n = int(states.shape[0])
+        z = torch.empty(n, dtype=torch.float32, device=states.device)
+        check(lib().we_mlp_forward(self.h, C.c_void_p(states.data_ptr()), n, 1 if bf16 else 0,
+                                   C.c_void_p(z.data_ptr()), _stream_handle(stream)))
+        return z
+
     def gradient(self, states, labels, stream=None):
         import torch
         g = torch.empty(self.n_params, dtype=torch.float32, device=labels.device)

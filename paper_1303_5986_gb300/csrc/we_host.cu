@@ -390,7 +390,7 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
   o.nw = L.take(4 * rec * R);
   o.events = L.take(8 * rec * R);
   o.hist = L.take(8 * rec * R * (c->hist_len > 0 ? c->hist_len : 1));
-  o.pack = L.take(4 * (size_t)cap * n->S);
+  o.pack = L.take(4 * (size_t)R * cap * n->S);
   o.total = L.off;
   return o;
 }
@@ -869,8 +869,10 @@ extern "C" we_status we_ensemble_get(we_ensemble *E, int32_t what, int32_t run, 
       return scalar(counts.data(), 4 * R);
     }
     case WE_OUT_STATES: {
-      if (run < 0) return fail(WE_EINVAL, "walker arrays need a single run");
-      const size_t bytes = (size_t)4 * counts[run] * E->S;
+      size_t live = 0;
+      if (run < 0) for (int r = 0; r < R; ++r) live += (size_t)counts[r];
+      else live = (size_t)counts[run];
+      const size_t bytes = (size_t)4 * live * E->S;
       if (needed) *needed = bytes;
       if (!dst) return WE_OK;
       if (dst_bytes < bytes) return fail(WE_EINVAL, "dst too small (%zu < %zu)", dst_bytes, bytes);

@@ -320,14 +320,20 @@ __global__ void k_finalize(EnsView E, int resample) {
 }
 
 // Walker-major copy of one run's counts (for output).
+// Walker-major copy of the live walkers' counts: of run r, or (r < 0) of all runs in run order.
 __global__ void k_pack_states(EnsView E, int r, int32_t *out) {
   const int iter = *E.iter;
   const int par = iter & 1;
-  const int n = E.count[r];
+  const long long n = r < 0 ? E.run_off[E.R] : E.count[r];
   const int ld = E.R * E.cap;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * E.S; i += gridDim.x * blockDim.x) {
-    const int w = i / E.S, s = i - w * E.S;
-    out[i] = E.x[par][(size_t)s * ld + (size_t)r * E.cap + w];
+  for (long long i = blockIdx.x * blockDim.x + threadIdx.x; i < n * E.S; i += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(i / E.S), s = (int)(i - (long long)f * E.S);
+    int rr = r, w = f;
+    if (r < 0) {
+      rr = E.R == 1 ? 0 : find_run(E.run_off, E.R, f);
+      w = f - E.run_off[rr];
+    }
+    out[i] = E.x[par][(size_t)s * ld + (size_t)rr * E.cap + w];
   }
 }
 
@@ -361,7 +367,7 @@ cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st) 
 }
 
 cudaError_t launch_pack_states(const EnsView &E, int r, int32_t *out, cudaStream_t st) {
-  k_pack_states<<<64, 256, 0, st>>>(E, r, out);
+  k_pack_states<<<152, 256, 0, st>>>(E, r, out);
   return cudaGetLastError();
 }
 

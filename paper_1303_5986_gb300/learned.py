@@ -1,0 +1,68 @@
+"""Learned bins for WE: harvest walker states from a plain WE run, label them by first passage
+with the SSA kernel, fit the progress coordinate with the training kernels, and place bin
+edges on it.  WE stays unbiased under any binning (Sec. II.B); choosing bins automatically is
+the open problem of Sec. IV.B.  Every step runs in the library's kernels; this module only
+moves arrays between the calls.
+"""
+import numpy as np
+
+from .api import MLP, first_passage_labels, we_binmap_learned, we_mlp_create
+
+
+def harvest_states(ens, n_iters: int, every: int = 1, runs=None) -> np.ndarray:
+    """Advance `ens` by n_iters WE iterations and collect the walkers' states (after each
+    resampling, every `every` iterations, over the given runs).  Returns (n, S) int32."""
+    out = []
+    for it in range(n_iters):
+        ens.step(1)
+        if (it + 1) % every == 0:
+            if runs is None:
+                out.append(ens.states(-1))
+            else:
+                out.extend(ens.states(r) for r in runs)
+    return np.concatenate(out, axis=0) if out else np.zeros((0, ens.n_species), np.int32)
+
+
+def init_params(n_in: int, hidden: int, seed: int) -> np.ndarray:
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and zero biases, FP32."""
+    rng = np.random.default_rng(seed)
+    return np.concatenate([rng.uniform(-1, 1, hidden * n_in) / np.sqrt(n_in), np.zeros(hidden),
+                           rng.uniform(-1, 1, hidden * hidden) / np.sqrt(hidden), np.zeros(hidden),
+                           rng.uniform(-1, 1, hidden) / np.sqrt(hidden), np.zeros(1)]).astype(np.float32)
+
+
+def fit_coordinate(net, states, target, recycle_state, horizon: float, hidden: int = 64,
+                   steps: int = 2000, batch: int = 4096, lr: float = 3e-3, seed: int = 0,
+                   param_set: int = 0, max_states: int = 2_000_000, stream=None):
+    """Label `states` by first passage into `target` within `horizon` (one SSA shot each) and
+    train a fresh MLP on them.  Returns (mlp, device states, device labels, losses)."""
+    import torch
+    st = np.ascontiguousarray(states, dtype=np.int32)
+    rng = np.random.default_rng(seed)
+    if len(st) > max_states:
+        st = st[rng.choice(len(st), size=max_states, replace=False)]
+    st = st[rng.permutation(len(st))]
+    labels = first_passage_labels(net, st, horizon, target, recycle_state, seed=seed,
+                                  param_set=param_set, stream=stream)
+    xs = torch.as_tensor(st, device=labels.device)
+    mlp = we_mlp_create(st.shape[1], hidden, init_params(st.shape[1], hidden, seed))
+    losses = mlp.train(xs, labels, steps, batch, lr, stream=stream)
+    return mlp, xs, labels, losses
+
+
+def coordinate_edges(mlp: MLP, states_dev, n_bins: int, lo_q: float = 0.001, hi_q: float = 1.0,
+                     stream=None) -> np.ndarray:
+    """n_bins equal intervals of z between two quantiles of z over the given states (computed
+    with the BF16 weights that the bin map will use)."""
+    z = mlp.forward(states_dev, bf16=True, stream=stream).cpu().numpy().astype(np.float64)
+    lo, hi = np.quantile(z, lo_q), np.quantile(z, hi_q)
+    if not hi > lo:
+        hi = lo + 1.0
+    return np.linspace(lo, hi, n_bins + 1).astype(np.float32)
+
+
+def learned_binmap(mlp: MLP, edges):
+    return we_binmap_learned(mlp, edges)
+
+
+__all__ = ["harvest_states", "init_params", "fit_coordinate", "coordinate_edges", "learned_binmap"]

@@ -159,6 +159,12 @@ def test_learned_bins_match_oracle():
         np.testing.assert_allclose(z, zo, rtol=1e-5, atol=2e-5)
         far = np.min(np.abs(zo[:, None] - edges[None, :].astype(np.float64)), axis=1) > 1e-4
         assert np.array_equal(M.bins_of(z, edges)[far], M.bins_of(zo, edges)[far])
+        # the standalone forward pass: BF16 form equals the binning kernel's z bit for bit;
+        # FP32 form against the reference with unrounded weights
+        Xd = _dev(X, _i32())
+        assert np.array_equal(ens._mlp.forward(Xd, bf16=True).cpu().numpy().view(np.uint32), z.view(np.uint32))
+        np.testing.assert_allclose(ens._mlp.forward(Xd).cpu().numpy(), M.forward(p, X, n_in, H),
+                                   rtol=1e-5, atol=2e-5)
         zs.append(z)
     ens.resample()
     counts = ens.get(P.WE_OUT_COUNTS)
@@ -225,3 +231,17 @@ def test_we_with_learned_bins_is_unbiased():
             assert abs(est.mean() - ex) < 3 * se + 0.05 * ex, (learned, k, est.mean(), ex, se)
         tot = ens.per_iter(P.WE_OUT_TOTAL_W)
         assert np.all(np.abs(tot - 1.0) < 1e-12)
+
+
+def test_harvest_states_all_runs():
+    """States of all runs in one call (run = -1) equal the per-run arrays concatenated, and the
+    harvest collects them after every iteration."""
+    from paper_1303_5986_gb300 import learned as LN
+    cfg = W.toggle_batch_we(n_runs=5, n_iters=3, seed=2)
+    ens = gpu_run(cfg, 2)
+    allx = ens.states(-1)
+    per = np.concatenate([ens.states(r) for r in range(cfg.n_runs)])
+    assert np.array_equal(allx, per)
+    assert len(allx) == ens.get(P.WE_OUT_COUNTS).sum()
+    h = LN.harvest_states(ens, 2)
+    assert h.shape[1] == 2 and len(h) > len(allx)
