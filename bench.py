@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the SSA kernel (0: auto)")
     ap.add_argument("--workload", choices=["schlogl", "toggle_learned"], default="schlogl")
-    ap.add_argument("--plain-iters", type=int, default=40000, help="toggle_learned: plain-binning iterations")
+    ap.add_argument("--plain-iters", type=int, default=120000, help="toggle_learned: plain-binning iterations")
     ap.add_argument("--learned-iters", type=int, default=2000, help="toggle_learned: learned-binning iterations")
     return ap.parse_args()
 
@@ -276,18 +276,24 @@ def run_toggle_learned(a):
                           Umax=int(2.5 * A) + 20, Vmax=int(2.5 * A) + 20)
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    # plain arm: 30 x 30 grid of width-4 bins on (U, V), 8 walkers per bin
-    cfg = _toggle_cfg(W, np, R, a.plain_iters, 8, 1)
-    net = P.network_from_spec(cfg.network)
-    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    c, keep = P.run_config_from(cfg, record_iters=a.plain_iters)
-    ens = P.we_ensemble_create(net, bm, c, keep)
-    torch.cuda.synchronize()
-    plain = _checkpointed_run(P, np, torch, ens, cfg, a.plain_iters, 40, exact, time.perf_counter() - t0)
-    plain_walkers = int(ens.get(P.WE_OUT_COUNTS).sum())
-    ens.close()
+    # plain arms: 30 x 30 grid of width-4 bins on (U, V), 8 walkers per bin (the batched toggle
+    # configuration) and 64 walkers per bin (more of the GPU in use per iteration)
+    plains = {}
+    bm = None
+    for m_targ, n_it in ((8, a.plain_iters), (64, a.plain_iters // 4)):
+        cfg = _toggle_cfg(W, np, R, n_it, m_targ, 1)
+        net = P.network_from_spec(cfg.network)
+        bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c, keep = P.run_config_from(cfg, record_iters=n_it)
+        ens = P.we_ensemble_create(net, bm, c, keep)
+        torch.cuda.synchronize()
+        curve = _checkpointed_run(P, np, torch, ens, cfg, n_it, 40, exact, time.perf_counter() - t0)
+        plains[m_targ] = {"gpu_s_to_10pct": _time_to(curve, 0.10), "final": curve[-1],
+                          "walkers_end": int(ens.get(P.WE_OUT_COUNTS).sum()), "iterations": n_it,
+                          "curve": curve}
+        ens.close()
     # learned arm: states from a 300-iteration plain run, first-passage labels (horizon 1),
     # 2000 Adam steps, 100 bins on z, 164 walkers per bin (about 16384 walkers per replica)
     torch.cuda.synchronize()
@@ -312,11 +318,13 @@ def run_toggle_learned(a):
     learned = _checkpointed_run(P, np, torch, lens, lcfg, a.learned_iters, 20, exact, t_fixed)
     learned_walkers = int(lens.get(P.WE_OUT_COUNTS).sum())
     clk = clocks.stop()
-    tp, tl = _time_to(plain, 0.10), _time_to(learned, 0.10)
-    if tp is not None and tl is not None:
-        value, bound = tp / tl, "measured"
+    tl = _time_to(learned, 0.10)
+    reached = [v["gpu_s_to_10pct"] for v in plains.values() if v["gpu_s_to_10pct"] is not None]
+    if tl is not None and reached:
+        value, bound = min(reached) / tl, "measured against the faster plain arm"
     elif tl is not None:
-        value, bound = plain[-1]["gpu_s"] / tl, "lower bound: plain binning never reached 10% in its run"
+        value = min(v["final"]["gpu_s"] for v in plains.values()) / tl
+        bound = "lower bound: no plain arm reached 10% within its run"
     else:
         value, bound = None, "learned binning did not reach 10%"
     line = {
@@ -327,11 +335,12 @@ def run_toggle_learned(a):
         "config": {"workload": (f"two-gene toggle a_U=a_V={A:g}, K=1, n=2, d=1; MFPT (40,0) -> "
                                 f"{{V>={thrV}, U<={thrU}}}, tau=0.1, {R} replicas in one batched launch"),
                    "exact_mfpt_s": exact,
-                   "plain": f"30x30 grid (width 4) x 8 walkers, {a.plain_iters} iterations",
+                   "plain": (f"30x30 grid (width 4) x 8 walkers, {a.plain_iters} iterations; "
+                             f"x 64 walkers, {a.plain_iters // 4} iterations"),
                    "learned": (f"MLP 2->64->64->1 on log1p counts, {len(states)} harvested states, "
                                f"first-passage labels (horizon 1), 2000 Adam steps of 4096; 100 bins x {M} "
                                f"walkers, {a.learned_iters} iterations")},
-        "plain": {"gpu_s_to_10pct": tp, "final": plain[-1], "walkers_end": plain_walkers, "curve": plain},
+        "plain_m8": plains[8], "plain_m64": plains[64],
         "learned": {"gpu_s_to_10pct": tl, "final": learned[-1], "walkers_end": learned_walkers,
                     "fixed_cost_s": t_fixed, "harvest_s": t_harvest,
                     "train_loss_first_last": [float(losses[0]), float(losses[-50:].mean())],
@@ -446,7 +455,7 @@ def main():
     achieved = FLOPS_PER_EVENT * ev_rank / prop_s / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "GFLOP/s",
                 "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
-                "kernel": "k_propagate_thread<4,2>", "launches": n_launch,
+                "kernel": "k_propagate_ws<4,2,true> (thread per walker, state-indexed tables)", "launches": n_launch,
                 "avg_launch_ms": prop_total_ms / max(n_launch, 1),
                 "share_of_step": prop_total_ms / total_ms if dist is None else None,
                 "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz (recipe: 1.25 TFLOP/s FP64, FMA=2)",

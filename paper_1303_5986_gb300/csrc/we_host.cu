@@ -22,8 +22,8 @@ cudaError_t launch_propagate_thread(const PropagateParams &prm, int block, bool 
 cudaError_t launch_propagate_ws(const PropagateParams &prm, bool table, cudaStream_t st);
 cudaError_t launch_propagate_warp(const PropagateParams &prm, int block, cudaStream_t st);
 cudaError_t launch_init_log_tables(LogTables *T, cudaStream_t st);
-cudaError_t launch_build_table(const NetView &N, const int32_t *base, int species, int len,
-                               double *rows, cudaStream_t st);
+cudaError_t launch_build_table(const NetView &N, const int32_t *base, int species, int len, double clock_scale,
+                               unsigned long long *rows, cudaStream_t st);
 size_t propagate_warp_smem(const NetView &N, int block);
 cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st);
@@ -331,7 +331,7 @@ struct Offsets {
 static int table_len_for(const we_network *n) {
   if (n->table_species < 0 || n->P > kThreadMaxLeaves || n->S > kThreadMaxSpecies) return 0;
   int len = 4096;
-  while (len > 256 && (size_t)n->nps * len * 2 * n->P * 8 > (64u << 20)) len >>= 1;
+  while (len > 256 && (size_t)n->nps * len * n->P * 8 > (64u << 20)) len >>= 1;
   return len;
 }
 
@@ -349,7 +349,7 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
     o.lz = L.take(4 * lb.zedges.size());
     o.zout = L.take(4 * (size_t)c->n_runs * (size_t)cap);
   }
-  o.table = L.take((size_t)n->nps * o.table_len * 2 * n->P * 8);
+  o.table = L.take((size_t)n->nps * o.table_len * n->P * 8);
   o.base = L.take(4 * (size_t)n->S);
   const size_t R = c->n_runs, RC = R * cap, rec = c->record_iters;
   o.meta = L.take(sizeof(RxnMeta) * n->P);
@@ -640,12 +640,14 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   E->prm.resample = c->resample ? 1 : 0;
   E->prm.logt = at<LogTables>(ws, o.logt);
   E->prm.tab.species = -1;
+  E->prm.tab.smem_rows = 0;
   if (mapping == WE_MAP_THREAD_TABLE) {
-    E->prm.tab.rows = at<double>(ws, o.table);
+    E->prm.tab.rows = at<unsigned long long>(ws, o.table);
     E->prm.tab.len = o.table_len;
     E->prm.tab.species = n->table_species;
+    E->prm.tab.clock_scale = std::ldexp(1.0 / c->tau, kClockBits);   // 2^62 / tau
     e = launch_build_table(N, at<int32_t>(ws, o.base), n->table_species, o.table_len,
-                           at<double>(ws, o.table), s);
+                           E->prm.tab.clock_scale, at<unsigned long long>(ws, o.table), s);
   }
   e = e ? e : cudaStreamSynchronize(s);
   if (e) { cudaGetLastError(); return cleanup(cuda_fail(e, "ensemble set-up")); }

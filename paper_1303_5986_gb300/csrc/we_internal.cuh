@@ -125,10 +125,19 @@ struct LogTables {
 
 // State-indexed propensity tables for networks whose propensities all depend on one species:
 // row x (x < len) holds [1/a0, tree node 1 (= a0), node 2, ..., node 2P-1] at that count.
+// Fixed-point clock of the table kernels: integer units of tau / 2^kClockBits.
+constexpr int kClockBits = 62;
+constexpr long long kClockTau = 1ll << kClockBits;
+
+// State-indexed table: per parameter set, `len` rows of P 64-bit words:
+//   word 0      float-float (2^62 / tau) / a0 (hi in the low half; 0 when a0 = 0)
+//   words 1..   the P-1 breakpoints b_i on the 52-bit uniform index (see k_build_table)
 struct TableView {
-  const double *rows;          // n_param_sets x len x 2P
+  const unsigned long long *rows;
   int32_t len;                 // counts covered; larger counts are evaluated directly
   int32_t species;             // the one species the propensities read (-1: no tables)
+  int32_t smem_rows;           // rows a block of the warp-specialised kernel stages in shared memory
+  double clock_scale;          // 2^62 / tau, for rows evaluated on the fly
 };
 
 struct PropagateParams {

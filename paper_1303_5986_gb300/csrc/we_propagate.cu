@@ -12,6 +12,8 @@
 // Both kernels draw the next event's random numbers and waiting-time logarithm while the
 // current event is processed (the draw does not depend on the state), keeping the ~700-cycle
 // FP64 chain of the logarithm off the event-to-event critical path.
+#include <algorithm>
+
 #include "we_ssa_common.cuh"
 
 namespace we {
@@ -47,14 +49,28 @@ __device__ __forceinline__ int descend(const double *nd, unsigned long long m) {
   return k - P;
 }
 
-// Row x of the state-indexed table: [1/a0, a0, b_1 .. b_{P-1}, unused], where b_i is the least
+// Row x of the state-indexed table (P 64-bit words): the float-float (2^62 / tau) / a0 that
+// turns -log u1 into clock units, then the breakpoints b_1 .. b_{P-1}, b_i being the least
 // uniform index m whose descent picks a reaction >= i.  The descent is monotone in m (the
 // target fl(u2 a0) grows with u2, each comparison is a threshold, each subtraction is monotone),
 // so the reaction for m is the number of b_i <= m: the hot loop selects with integer compares
 // and reaches exactly the reaction the floating-point descent would.  base holds the counts of
 // the species other than `species`.
+__device__ __forceinline__ unsigned long long pack_ff(float2 f) {
+  return ((unsigned long long)__float_as_uint(f.y) << 32) | (unsigned long long)__float_as_uint(f.x);
+}
+__device__ __forceinline__ float2 unpack_ff(unsigned long long v) {
+  return make_float2(__uint_as_float((uint32_t)v), __uint_as_float((uint32_t)(v >> 32)));
+}
+
+// (2^62 / tau) / a0 as a float-float, or zero when nothing can fire.
+__device__ __forceinline__ float2 wait_scale(double a0, double clock_scale) {
+  return bits(a0) > 0 ? split_ff(__ddiv_rn(clock_scale, a0)) : make_float2(0.0f, 0.0f);
+}
+
 template <int P, int LOG2P>
-__global__ void k_build_table(NetView N, const int32_t *base, int species, int len, double *rows) {
+__global__ void k_build_table(NetView N, const int32_t *base, int species, int len, double clock_scale,
+                              unsigned long long *rows) {
   const int ps = blockIdx.y;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < len; x += gridDim.x * blockDim.x) {
     int32_t xs[kThreadMaxSpecies];
@@ -66,9 +82,8 @@ __global__ void k_build_table(NetView N, const int32_t *base, int species, int l
       nd[P + j] = propensity(N.meta[j], N.keff[ps * P + j], N.hill_Kn[ps * P + j], xs, 1);
 #pragma unroll
     for (int k = P - 1; k >= 1; --k) nd[k] = __dadd_rn(nd[2 * k], nd[2 * k + 1]);
-    double *row = rows + ((size_t)ps * len + x) * (2 * P);
-    row[0] = bits(nd[1]) > 0 ? __ddiv_rn(1.0, nd[1]) : 0.0;
-    row[1] = nd[1];
+    unsigned long long *row = rows + ((size_t)ps * len + x) * P;
+    row[0] = pack_ff(wait_scale(nd[1], clock_scale));
     for (int i = 1; i < P; ++i) {
       unsigned long long lo = 0, hi = 1ull << 52;            // m = 2^52 stands for "never"
       if (bits(nd[1]) > 0) {
@@ -77,11 +92,64 @@ __global__ void k_build_table(NetView N, const int32_t *base, int species, int l
           if (descend<P, LOG2P>(nd, mid) >= i) hi = mid; else lo = mid + 1;
         }
       }
-      row[1 + i] = __longlong_as_double((long long)lo);
+      row[i] = lo;
     }
-    for (int k = P + 1; k < 2 * P; ++k) row[k] = 0.0;
   }
 }
+
+// A table walker's current row in registers: the wait scale and the breakpoints, or (for
+// counts beyond the table, `direct`) the canonical tree evaluated on the fly into fb, an array
+// of the caller's kept apart so that the row itself stays in registers.
+template <int P, int LOG2P>
+struct TableRow {
+  float2 w;
+  unsigned long long bp[P > 1 ? P - 1 : 1];
+  bool direct;
+
+  // rw: a row of P words, 16-byte aligned when P is even (read two words at a time)
+  __device__ __forceinline__ void read(const unsigned long long *rw) {
+    unsigned long long v[P];
+    if (P % 2 == 0) {
+#pragma unroll
+      for (int i = 0; i < P; i += 2) {
+        const ulonglong2 q = reinterpret_cast<const ulonglong2 *>(rw)[i / 2];
+        v[i] = q.x;
+        v[i + 1 < P ? i + 1 : i] = q.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < P; ++i) v[i] = rw[i];
+    }
+    w = unpack_ff(v[0]);
+#pragma unroll
+    for (int i = 1; i < P; ++i) bp[i - 1] = v[i];
+    direct = false;
+  }
+  // counts xme (stride B) are current, including the table species
+  __device__ __forceinline__ void evaluate(double *fb, const RxnMeta *meta, const double *keff,
+                                           const double *Kn, const int32_t *xme, int B, double clock_scale) {
+#pragma unroll
+    for (int j = 0; j < P; ++j) fb[P + j] = propensity(meta[j], keff[j], Kn[j], xme, B);
+#pragma unroll
+    for (int k = P - 1; k >= 1; --k) fb[k] = __dadd_rn(fb[2 * k], fb[2 * k + 1]);
+    w = wait_scale(fb[1], clock_scale);
+    direct = true;
+  }
+  __device__ __forceinline__ bool idle() const { return __float_as_uint(w.x) == 0u; }
+  __device__ __forceinline__ int select_table(unsigned long long m2) const {
+    int j = 0;                                            // reaction = breakpoints at or below m2
+#pragma unroll
+    for (int i = 0; i + 1 < P; ++i) j += (long long)m2 >= (long long)bp[i] ? 1 : 0;
+    return j;
+  }
+  __device__ __forceinline__ int select(unsigned long long m2, const double *fb) const {
+    if (direct) return descend<P, LOG2P>(fb, m2);
+    int j = 0;                                            // reaction = breakpoints at or below m2
+#pragma unroll
+    for (int i = 0; i + 1 < P; ++i) j += (long long)m2 >= (long long)bp[i] ? 1 : 0;
+    return j;
+  }
+};
 
 // Shared prologue: network records, rate constants, net changes and log tables to shared
 // memory.  Returns the per-thread count slots (S x blockDim, species-major).
@@ -232,9 +300,9 @@ __global__ void __launch_bounds__(128) k_propagate_direct(PropagateParams prm) {
 // ------------------------------------------------------------------------------------------
 // State-indexed tables: all propensities read one species x, so the whole canonical tree and
 // 1/a0 are functions of x alone.  Row x of the table (built by k_build_table with the direct
-// kernel's arithmetic) replaces the recomputation; counts beyond the table are evaluated into
-// a per-thread row.  Per event: the waiting time (one product, one sum), the target (one
-// product) and up to log2 P descent subtractions.
+// kernel's arithmetic) replaces the recomputation; counts beyond the table are evaluated on
+// the fly.  Per event: the waiting time in clock units (FP32 products, integer rounding and
+// sum), the reaction by integer compares, and the next row.
 // ------------------------------------------------------------------------------------------
 template <int P, int LOG2P>
 __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
@@ -265,93 +333,71 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
   const int ps = E.param_set[r];
   const double *keff = sm.keff + ps * P;
   const double *Kn = sm.Kn + ps * P;
-  const double *tab = TV.rows + (size_t)ps * TV.len * (2 * P);
+  const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * P;
   const uint32_t k0 = (uint32_t)E.seed;
   const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
   const int sx = TV.species;
 
-  // Row for counts beyond the table, in thread-local memory: `row` may point here or into the
-  // table, so it is read with generic loads (a global-only load of a local address faults).
+  TableRow<P, LOG2P> row;
   double fb[2 * P];
-  auto locate = [&](int x) -> const double * {
-    if (x < TV.len) return tab + (size_t)x * (2 * P);
-    for (int j = 0; j < P; ++j) fb[P + j] = propensity(sm.meta[j], keff[j], Kn[j], xme, B);
-    for (int k = P - 1; k >= 1; --k) fb[k] = __dadd_rn(fb[2 * k], fb[2 * k + 1]);
-    fb[0] = bits(fb[1]) > 0 ? __ddiv_rn(1.0, fb[1]) : 0.0;   // fb[1] = a0 as in a table row
-    return fb;
+  auto load_row = [&](int xv) {
+    if (xv < TV.len) row.read(tab + (size_t)xv * P);
+    else row.evaluate(fb, sm.meta, keff, Kn, xme, B, TV.clock_scale);
   };
   int x = xme[sx * B];
-  const double *row = locate(x);
+  load_row(x);
 
-  const long long tau_bits = bits(E.tau);
-  double t = 0.0;
+  long long clk = 0;
   long long nev = 0;
   int nrec = 0, status = 0;
   DrawQueue dq;
   dq.init((uint32_t)iter, (uint32_t)w, k0, k1, *sm.logt);
   for (;;) {
-    const double a0 = row[1];
-    if (bits(a0) == 0) break;
+    if (row.idle()) break;                           // nothing can fire: idle to tau
     unsigned long long m2;
     float2 e;
     dq.pop((uint32_t)iter, (uint32_t)w, k0, k1, *sm.logt, m2, e);
-    const double tn = advance_clock(t, e, row[0]);
-    if (bits(tn) > tau_bits) break;
+    long long dt;
+    if (!wait_units(e, row.w, dt) || clk + dt > kClockTau) break;   // next event after tau
     if (nev >= E.max_steps) { status = kStatusStepCap; break; }
-    int j;
-    if (row != fb) {
-      j = 0;                                         // reaction = breakpoints at or below m2
-#pragma unroll
-      for (int i = 1; i < P; ++i) j += (long long)m2 >= bits(row[1 + i]) ? 1 : 0;
-    } else {
-      j = descend<P, LOG2P>(fb, m2);
-    }
-    const int nx = x + s_dx[j];
+    const int nx = x + s_dx[row.select(m2, fb)];
     if (nx > kMaxCount) { status = kStatusOverflow; break; }
     x = nx;
     xme[sx * B] = x;
     ++nev;
-    t = tn;
+    clk += dt;
     if (E.feedback && in_target(E, r, xme, B)) {
       ++nrec;
       for (int s = 0; s < E.S; ++s) xme[s * B] = E.recycle[r * E.S + s];
       x = xme[sx * B];
     }
-    row = locate(x);
+    load_row(x);
   }
-  finish_walker(prm, r, g, par, xme, B, t, nev, nrec, status);
+  finish_walker(prm, r, g, par, xme, B, clock_time(clk, E.tau), nev, nrec, status);
 }
 
 // ------------------------------------------------------------------------------------------
-// Warp-specialised form of both kernels.  A block of four warps serves 32 walkers (one per
-// lane).  Warp 0 runs the event loops; warps 1-3, on the other sub-partitions of the SM,
-// generate the next round of kRoundDraws draws per walker (Philox + logarithm, most of the
-// instructions of an event) into a shared-memory buffer while warp 0 consumes the current
-// one.  The two buffers alternate at a __syncthreads per round; the loop ends when warp 0
-// reports that all its walkers are done, so every wait is a block barrier that all warps reach.
+// Warp-specialised kernels: a block of four warps serves 32 walkers (one per lane), and the
+// draws (Philox + logarithm, most of the instructions of an event) come from other warps than
+// the event chain, through shared-memory buffers that alternate at block barriers.  Every
+// wait is a block barrier that all warps reach; a loop ends when every walker is done.
 // ------------------------------------------------------------------------------------------
 constexpr int kRoundDraws = 16;
+constexpr int kWindowMargin = 96;    // table rows staged beyond a block's range of counts
 
-template <int P, int LOG2P, bool TABLE>
+// General networks.  Warp 0 runs the event loops (FP64 propensities and tree, rebuilt after
+// each event); warps 1-3 generate the next round of kRoundDraws draws per walker meanwhile.
+template <int P, int LOG2P>
 __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Smem sm = load_smem<P>(prm, smem_raw);
   const EnsView &E = prm.ens;
-  const TableView &TV = prm.tab;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int W = 32;                                  // walkers per block
-  int32_t *s_dx = sm.xs + E.S * W;                       // net change of the table species
   unsigned long long *qm = reinterpret_cast<unsigned long long *>(
-      (reinterpret_cast<uintptr_t>(s_dx + P) + 15) & ~(uintptr_t)15);   // [2][kRoundDraws][W]
-  float2 *qe = reinterpret_cast<float2 *>(qm + 2 * kRoundDraws * W);    // [2][kRoundDraws][W]
+      (reinterpret_cast<uintptr_t>(sm.xs + E.S * W) + 15) & ~(uintptr_t)15);   // [2][kRoundDraws][W]
+  float2 *qe = reinterpret_cast<float2 *>(qm + 2 * kRoundDraws * W);            // [2][kRoundDraws][W]
   __shared__ int s_more;
-  if (TABLE)
-    for (int j = threadIdx.x; j < P; j += blockDim.x) {
-      int dx = 0;
-      for (int q = sm.meta[j].d_begin; q < sm.meta[j].d_end; ++q)
-        if (sm.dsp[q] == TV.species) dx += sm.dval[q];
-      s_dx[j] = dx;
-    }
 
   const int iter = *E.iter;
   const int total = E.run_off[E.R];
@@ -362,8 +408,11 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
   const uint32_t k0 = (uint32_t)E.seed;
   const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
   const LogTables &LT = *sm.logt;
+  const int g = r * E.cap + w;
+  const int par = iter & 1;
+  const int ld = E.R * E.cap;
+  const int ps = live ? E.param_set[r] : 0;
 
-  // draws [base, base + kRoundDraws) of this lane's walker into buffer b (producer warps)
   auto produce = [&](int b, uint32_t base, int first, int stride) {
     if (!live) return;
 #pragma unroll 2
@@ -378,12 +427,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
   produce(0, 0u, warp, 4);                               // round 0: all four warps
   __syncthreads();
 
-  // consumer state (warp 0)
-  const int g = r * E.cap + w;
-  const int par = iter & 1;
-  const int ld = E.R * E.cap;
   int32_t *xme = sm.xs + lane;
-  const int ps = live ? E.param_set[r] : 0;
   const double *keff = sm.keff + ps * P;
   const double *Kn = sm.Kn + ps * P;
   const long long tau_bits = bits(E.tau);
@@ -391,50 +435,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
   long long nev = 0;
   int nrec = 0, status = 0;
   bool done = !live;
-  // table path: the current row in registers
-  int x = 0, dxr[P];
-  double inv = 0.0, a0r = 0.0;
-  long long bp[P > 1 ? P - 1 : 1];
-  bool fallback = false;
-  double nd[TABLE ? 1 : 2 * P];
-  double fb[TABLE ? 2 * P : 1];
-  const double *tab = TABLE ? TV.rows + (size_t)ps * TV.len * (2 * P) : nullptr;
-  // target set seen from the table species: x in [xlo, xhi] while the other clauses hold
-  int xlo = 0, xhi = 0, xrec = 0;
-  bool others_ok = false;
-  auto load_row = [&](int xv) {
-    if (xv < TV.len) {
-      const double *p = tab + (size_t)xv * (2 * P);
-      inv = p[0];
-      a0r = p[1];
-#pragma unroll
-      for (int i = 1; i < P; ++i) bp[i - 1] = bits(p[1 + i]);
-      fallback = false;
-    } else {
-      xme[TV.species * W] = xv;
-      for (int j = 0; j < P; ++j) fb[P + j] = propensity(sm.meta[j], keff[j], Kn[j], xme, W);
-      for (int k = P - 1; k >= 1; --k) fb[k] = __dadd_rn(fb[2 * k], fb[2 * k + 1]);
-      a0r = fb[1];
-      inv = bits(a0r) > 0 ? __ddiv_rn(1.0, a0r) : 0.0;
-      fallback = true;
-    }
-  };
-  // Clauses on the table species become the window [xlo, xhi]; the others read species that no
-  // reaction changes, so they are evaluated once (and again after a recycle).
-  auto target_window = [&]() {
-    xlo = -1;
-    xhi = kMaxCount + 1;
-    others_ok = true;
-    for (int c = 0; c < E.n_clauses; ++c) {
-      const int thr = E.tgt_thr[r * E.n_clauses + c];
-      if (E.tgt_species[c] == TV.species) {
-        if (E.tgt_op[c] == 0) xlo = max(xlo, thr); else xhi = min(xhi, thr);
-      } else {
-        const int v = xme[E.tgt_species[c] * W];
-        others_ok = others_ok && (E.tgt_op[c] == 0 ? v >= thr : v <= thr);
-      }
-    }
-  };
+  double nd[2 * P];
   auto rebuild = [&]() {
 #pragma unroll
     for (int j = 0; j < P; ++j) nd[P + j] = propensity(sm.meta[j], keff[j], Kn[j], xme, W);
@@ -443,18 +444,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
   };
   if (warp == 0 && live) {
     for (int s = 0; s < E.S; ++s) xme[s * W] = E.x[par][(size_t)s * ld + g];
-    if (TABLE) {
-#pragma unroll
-      for (int j = 0; j < P; ++j) dxr[j] = s_dx[j];
-      x = xme[TV.species * W];
-      if (E.feedback) {
-        target_window();
-        xrec = E.recycle[r * E.S + TV.species];
-      }
-      load_row(x);
-    } else {
-      rebuild();
-    }
+    rebuild();
   }
 
   for (int round = 0;; ++round) {
@@ -463,66 +453,36 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
       for (int k = 0; k < kRoundDraws && !done; ++k) {
         const unsigned long long m2 = qm[(b * kRoundDraws + k) * W + lane];
         const float2 e = qe[(b * kRoundDraws + k) * W + lane];
-        if (TABLE) {
-          if (bits(a0r) == 0) { done = true; break; }      // nothing can fire: idle to tau
-          const double tn = advance_clock(t, e, inv);
-          int j;
-          if (!fallback) {
-            j = 0;                                        // reaction = breakpoints at or below m2
+        const double a0 = nd[1];
+        if (bits(a0) == 0) { done = true; break; }
+        const double tn = advance_clock(t, e, rcp_pos(a0));
+        if (bits(tn) > tau_bits) { done = true; break; }
+        if (nev >= E.max_steps) { status = kStatusStepCap; done = true; break; }
+        double target = __dmul_rn(u01_index(m2), a0);
+        int kk = 1;
 #pragma unroll
-            for (int i = 0; i + 1 < P; ++i) j += (long long)m2 >= bp[i] ? 1 : 0;
-          } else {
-            j = descend<P, LOG2P>(fb, m2);
-          }
-          int dx = dxr[0];
+        for (int lvl = 0; lvl < LOG2P; ++lvl) {
+          double L = 0.0, R = 0.0;
 #pragma unroll
-          for (int i = 1; i < P; ++i) dx = (j == i) ? dxr[i] : dx;
-          const int nx = x + dx;
-          if (bits(tn) > tau_bits) { done = true; break; }  // the next event falls after tau
-          if (nev >= E.max_steps) { status = kStatusStepCap; done = true; break; }
-          if (nx > kMaxCount) { status = kStatusOverflow; done = true; break; }
-          x = nx;
-          ++nev;
-          t = tn;
-          if (E.feedback && others_ok && x >= xlo && x <= xhi) {
-            ++nrec;                                       // recycle: the whole state is reset
-            for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
-            x = xrec;
-            target_window();
-          }
-          load_row(x);
-        } else {
-          const double a0 = nd[1];
-          if (bits(a0) == 0) { done = true; break; }
-          const double tn = advance_clock(t, e, rcp_pos(a0));
-          if (bits(tn) > tau_bits) { done = true; break; }
-          if (nev >= E.max_steps) { status = kStatusStepCap; done = true; break; }
-          double target = __dmul_rn(u01_index(m2), a0);
-          int kk = 1;
-#pragma unroll
-          for (int lvl = 0; lvl < LOG2P; ++lvl) {
-            double L = 0.0, R = 0.0;
-#pragma unroll
-            for (int c = (1 << lvl); c < (2 << lvl); ++c)
-              if (kk == c) { L = nd[2 * c]; R = nd[2 * c + 1]; }
-            const bool right = (bits(R) != 0) && !(bits(target) < bits(L));
-            if (right) { target = __dsub_rn(target, L); kk = 2 * kk + 1; }
-            else { kk = 2 * kk; }
-          }
-          const RxnMeta &mt = sm.meta[kk - P];
-          bool over = false;
-          for (int q = mt.d_begin; q < mt.d_end; ++q)
-            over |= (xme[sm.dsp[q] * W] + sm.dval[q]) > kMaxCount;
-          if (over) { status = kStatusOverflow; done = true; break; }
-          for (int q = mt.d_begin; q < mt.d_end; ++q) xme[sm.dsp[q] * W] += sm.dval[q];
-          ++nev;
-          t = tn;
-          if (E.feedback && in_target(E, r, xme, W)) {
-            ++nrec;
-            for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
-          }
-          rebuild();
+          for (int c = (1 << lvl); c < (2 << lvl); ++c)
+            if (kk == c) { L = nd[2 * c]; R = nd[2 * c + 1]; }
+          const bool right = (bits(R) != 0) && !(bits(target) < bits(L));
+          if (right) { target = __dsub_rn(target, L); kk = 2 * kk + 1; }
+          else { kk = 2 * kk; }
         }
+        const RxnMeta &mt = sm.meta[kk - P];
+        bool over = false;
+        for (int q = mt.d_begin; q < mt.d_end; ++q)
+          over |= (xme[sm.dsp[q] * W] + sm.dval[q]) > kMaxCount;
+        if (over) { status = kStatusOverflow; done = true; break; }
+        for (int q = mt.d_begin; q < mt.d_end; ++q) xme[sm.dsp[q] * W] += sm.dval[q];
+        ++nev;
+        t = tn;
+        if (E.feedback && in_target(E, r, xme, W)) {
+          ++nrec;
+          for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
+        }
+        rebuild();
       }
       const int more = __any_sync(0xffffffffu, !done);
       if (lane == 0) s_more = more;
@@ -533,26 +493,276 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
     if (!s_more) break;
     __syncthreads();                                      // s_more is rewritten next round
   }
+  if (warp == 0 && live) finish_walker(prm, r, g, par, xme, W, t, nev, nrec, status);
+}
+
+// Off-table rows: the canonical tree evaluated on the fly (counts beyond the table), kept out
+// of line so that the event chain stays short.
+template <int P, int LOG2P>
+__device__ __noinline__ float2 evaluate_row(double *fb, const RxnMeta *meta, const double *keff,
+                                            const double *Kn, const int32_t *xme, int B, double clock_scale) {
+#pragma unroll
+  for (int j = 0; j < P; ++j) fb[P + j] = propensity(meta[j], keff[j], Kn[j], xme, B);
+#pragma unroll
+  for (int k = P - 1; k >= 1; --k) fb[k] = __dadd_rn(fb[2 * k], fb[2 * k + 1]);
+  return wait_scale(fb[1], clock_scale);
+}
+template <int P, int LOG2P>
+__device__ __noinline__ int descend_row(const double *fb, unsigned long long m2) {
+  return descend<P, LOG2P>(fb, m2);
+}
+
+// State-indexed tables, pipelined.  The chain of states does not depend on the clock (a draw
+// picks the reaction from the current row; the count moves; a recycle resets it), so a block
+// splits each walker's events into three streams that run one round apart:
+//   warp 0     the state chain of round p as if every draw fires: for each draw, the wait scale
+//              of the current row and the count after the event, plus flags for a row that
+//              cannot fire (a0 = 0), an event that would overflow, and an event that recycles;
+//   warp 1     round p-1: every draw's waiting time in clock units (independent of one
+//              another), then the clock in draw order -- the first draw that cannot fire (idle,
+//              past tau, step cap, overflow) ends the interval and fixes the committed state;
+//   warps 2-3  the draws (Philox + logarithm) of round p+1.
+// A phase ends at one block barrier.  Draw buffers rotate over three rounds and the state
+// buffers over two; done flags reach warp 0 one phase after warp 1 sets them, so warp 0 may
+// run one round past a walker's end (that work is discarded).  The committed arithmetic is
+// the same as the serial loop's: the same reaction for each draw, the same waiting time, the
+// same order of clock additions.
+template <int P, int LOG2P>
+__global__ void __launch_bounds__(128) k_propagate_pipe(PropagateParams prm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem sm = load_smem<P>(prm, smem_raw);
+  const EnsView &E = prm.ens;
+  const TableView &TV = prm.tab;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int W = 32, K = kRoundDraws;
+  int32_t *s_dx = sm.xs + E.S * W;                                       // P
+  unsigned long long *qm = reinterpret_cast<unsigned long long *>(
+      (reinterpret_cast<uintptr_t>(s_dx + P) + 15) & ~(uintptr_t)15);    // [3][K][W]
+  float2 *qe = reinterpret_cast<float2 *>(qm + 3 * K * W);              // [3][K][W]
+  float2 *sw = qe + 3 * K * W;                                          // [2][K][W] wait scales
+  int32_t *sx = reinterpret_cast<int32_t *>(sw + 2 * K * W);            // [2][K][W] counts
+  uint32_t *sfl = reinterpret_cast<uint32_t *>(sx + 2 * K * W);         // [2][3][W] flag masks
+  unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(
+      (reinterpret_cast<uintptr_t>(sfl + 2 * 3 * W) + 15) & ~(uintptr_t)15);
+  __shared__ int s_more[2], s_win, s_win_n;
+  __shared__ int s_done[2][W];
+  for (int j = threadIdx.x; j < P; j += blockDim.x) {
+    int dx = 0;
+    for (int q = sm.meta[j].d_begin; q < sm.meta[j].d_end; ++q)
+      if (sm.dsp[q] == TV.species) dx += sm.dval[q];
+    s_dx[j] = dx;
+  }
+
+  const int iter = *E.iter;
+  const int total = E.run_off[E.R];
+  const int f = blockIdx.x * W + lane;
+  const bool live = f < total;
+  const int r = !live ? 0 : (E.R == 1 ? 0 : find_run(E.run_off, E.R, f));
+  const int w = live ? f - E.run_off[r] : 0;
+  const uint32_t k0 = (uint32_t)E.seed;
+  const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
+  const LogTables &LT = *sm.logt;
+  const int g = r * E.cap + w;
+  const int par = iter & 1;
+  const int ld = E.R * E.cap;
+  const int ps = live ? E.param_set[r] : 0;
+  const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * P;
+
+  // table rows for a window of counts around this block's walkers, in shared memory
+  int win_lo = 0, win_n = 0;
+  if (TV.smem_rows > 0) {
+    if (warp == 0) {
+      int lo = 0x7fffffff, hi = -1;
+      if (live) lo = hi = E.x[par][(size_t)TV.species * ld + g];
+      lo = __reduce_min_sync(0xffffffffu, lo);
+      hi = __reduce_max_sync(0xffffffffu, hi);
+      const int ps0 = __shfl_sync(0xffffffffu, ps, 0);
+      const bool one_set = __all_sync(0xffffffffu, !live || ps == ps0);
+      if (lane == 0) {
+        const int n = min(TV.smem_rows, hi - lo + 1 + 2 * kWindowMargin);
+        int start = (lo + hi) / 2 - n / 2;
+        start = max(min(start, TV.len - n), 0);
+        s_win = (one_set && hi >= 0) ? start : -1;           // no live walker: nothing to stage
+        s_win_n = n;
+      }
+    }
+    __syncthreads();
+    if (s_win >= 0) {
+      win_lo = s_win;
+      win_n = s_win_n;
+      const int ps0 = E.param_set[E.R == 1 ? 0 : find_run(E.run_off, E.R, blockIdx.x * W)];
+      const unsigned long long *src = TV.rows + ((size_t)ps0 * TV.len + win_lo) * P;
+      for (int i = threadIdx.x; i < win_n * P; i += blockDim.x) s_tab[i] = src[i];
+    }
+  }
+
+  auto produce = [&](int buf, uint32_t base, int first, int stride) {
+    if (!live) return;
+#pragma unroll 2
+    for (int k = first; k < K; k += stride) {
+      unsigned long long m2;
+      float2 e;
+      ssa_draw(base + (uint32_t)k, (uint32_t)iter, (uint32_t)w, k0, k1, LT, m2, e);
+      qm[(buf * K + k) * W + lane] = m2;
+      qe[(buf * K + k) * W + lane] = e;
+    }
+  };
+  produce(0, 0u, warp, 4);                               // round 0: all four warps
+  if (warp == 1) {
+    s_done[1][lane] = !live;
+    if (lane == 0) s_more[1] = 1;
+  }
+
+  int32_t *xme = sm.xs + lane;
+  const double *keff = sm.keff + ps * P;
+  const double *Kn = sm.Kn + ps * P;
+  // warp 0: the speculative state chain
+  int x = 0, dxr[P];
+  TableRow<P, LOG2P> row;
+  double fb[2 * P];
+  int xlo = -1, xhi = kMaxCount + 1, xrec = 0;
+  bool ok = false, ok_rec = false;
+  auto load_row = [&](int xv) {
+    const unsigned off = (unsigned)(xv - win_lo);
+    if (off < (unsigned)win_n) {
+      row.read(s_tab + (size_t)off * P);
+    } else if (xv < TV.len) {
+      row.read(tab + (size_t)xv * P);
+    } else {
+      xme[TV.species * W] = xv;
+      row.w = evaluate_row<P, LOG2P>(fb, sm.meta, keff, Kn, xme, W, TV.clock_scale);
+      row.direct = true;
+    }
+  };
+  // warp 1: the committed walker
+  long long clk = 0, nev = 0;
+  int xc = 0, nrec = 0, status = 0;
+  bool done = !live, recycled = false;
+  if (live && warp <= 1) {
+    if (warp == 0)
+      for (int s = 0; s < E.S; ++s) xme[s * W] = E.x[par][(size_t)s * ld + g];
+    xc = E.x[par][(size_t)TV.species * ld + g];
+  }
+  __syncthreads();
   if (warp == 0 && live) {
-    if (TABLE) xme[TV.species * W] = x;
-    finish_walker(prm, r, g, par, xme, W, t, nev, nrec, status);
+#pragma unroll
+    for (int j = 0; j < P; ++j) dxr[j] = s_dx[j];
+    x = xc;
+    if (E.feedback) {
+      ok = true;
+      ok_rec = true;
+      for (int c = 0; c < E.n_clauses; ++c) {
+        const int thr = E.tgt_thr[r * E.n_clauses + c];
+        const int sp = E.tgt_species[c];
+        if (sp == TV.species) {
+          if (E.tgt_op[c] == 0) xlo = max(xlo, thr); else xhi = min(xhi, thr);
+        } else {
+          const int v = xme[sp * W], vr = E.recycle[r * E.S + sp];
+          ok = ok && (E.tgt_op[c] == 0 ? v >= thr : v <= thr);
+          ok_rec = ok_rec && (E.tgt_op[c] == 0 ? vr >= thr : vr <= thr);
+        }
+      }
+      xrec = E.recycle[r * E.S + TV.species];
+    }
+    load_row(x);
+  }
+
+  for (int p = 0;; ++p) {
+    if (warp == 0) {
+      const int qb = p % 3, sb = p & 1;
+      if (live && !s_done[sb ^ 1][lane]) {
+        uint32_t idle_m = 0u, ovf_m = 0u, rec_m = 0u;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const unsigned long long m2 = qm[(qb * K + k) * W + lane];
+          sw[(sb * K + k) * W + lane] = row.w;
+          if (row.idle()) idle_m |= 1u << k;
+          const int j = row.direct ? descend_row<P, LOG2P>(fb, m2) : row.select_table(m2);
+          int dx = dxr[0];
+#pragma unroll
+          for (int i = 1; i < P; ++i) dx = (j == i) ? dxr[i] : dx;
+          int nx = x + dx;
+          if (nx > kMaxCount) { ovf_m |= 1u << k; nx = x; }
+          if (E.feedback && ok && nx >= xlo && nx <= xhi) { rec_m |= 1u << k; nx = xrec; ok = ok_rec; }
+          sx[(sb * K + k) * W + lane] = nx;
+          x = nx;
+          load_row(x);
+        }
+        sfl[(sb * 3 + 0) * W + lane] = idle_m;
+        sfl[(sb * 3 + 1) * W + lane] = ovf_m;
+        sfl[(sb * 3 + 2) * W + lane] = rec_m;
+      }
+    } else if (warp == 1) {
+      const int sb = p & 1;
+      if (p >= 1) {
+        const int qb = (p - 1) % 3, pb = sb ^ 1;
+        if (!done) {
+          long long dts[K];
+          uint32_t far_m = 0u;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const float2 e = qe[(qb * K + k) * W + lane];
+            const float2 wv = sw[(pb * K + k) * W + lane];
+            if (!wait_units(e, wv, dts[k])) far_m |= 1u << k;
+          }
+          const uint32_t idle_m = sfl[(pb * 3 + 0) * W + lane];
+          const uint32_t ovf_m = sfl[(pb * 3 + 1) * W + lane];
+          const uint32_t rec_m = sfl[(pb * 3 + 2) * W + lane];
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            if (done) continue;
+            const uint32_t bit = 1u << k;
+            if ((idle_m & bit) || (far_m & bit) || clk + dts[k] > kClockTau) { done = true; continue; }
+            if (nev >= E.max_steps) { status = kStatusStepCap; done = true; continue; }
+            if (ovf_m & bit) { status = kStatusOverflow; done = true; continue; }
+            clk += dts[k];
+            ++nev;
+            xc = sx[(pb * K + k) * W + lane];
+            if (rec_m & bit) { ++nrec; recycled = true; }
+          }
+        }
+        s_done[sb][lane] = done;
+        const int more = __any_sync(0xffffffffu, !done);
+        if (lane == 0) s_more[sb] = more;
+      } else {
+        s_done[0][lane] = done;
+        if (lane == 0) s_more[0] = 1;
+      }
+    } else {
+      produce((p + 1) % 3, (uint32_t)((p + 1) * K), warp - 2, 2);
+    }
+    __syncthreads();
+    if (!s_more[p & 1]) break;
+  }
+  if (warp == 1 && live) {
+    if (recycled)                                        // the other species take the recycle state
+      for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
+    xme[TV.species * W] = xc;
+    finish_walker(prm, r, g, par, xme, W, clock_time(clk, E.tau), (long long)nev, nrec, status);
   }
 }
 
-// ------------------------------------------------------------------------------------------
-// host-side launch helpers
-// ------------------------------------------------------------------------------------------
 size_t propagate_thread_smem(const NetView &N, int block, bool table) {
   return sizeof(LogTables) + (size_t)N.P * sizeof(RxnMeta) +
          2 * (size_t)N.n_param_sets * N.P * sizeof(double) + 2 * (size_t)N.n_delta * sizeof(int32_t) +
          (size_t)N.S * block * sizeof(int32_t) + (table ? (size_t)N.P * sizeof(int32_t) : 0);
 }
 
-size_t propagate_ws_smem(const NetView &N) {
+static size_t smem_prologue(const NetView &N) {
   return sizeof(LogTables) + (size_t)N.P * sizeof(RxnMeta) +
          2 * (size_t)N.n_param_sets * N.P * sizeof(double) + 2 * (size_t)N.n_delta * sizeof(int32_t) +
-         (size_t)N.S * 32 * sizeof(int32_t) + (size_t)N.P * sizeof(int32_t) + 16 +
-         2 * (size_t)kRoundDraws * 32 * (sizeof(unsigned long long) + sizeof(float2));
+         (size_t)N.S * 32 * sizeof(int32_t);
+}
+
+size_t propagate_ws_smem(const NetView &N) {
+  return smem_prologue(N) + 16 + 2 * (size_t)kRoundDraws * 32 * (sizeof(unsigned long long) + sizeof(float2));
+}
+
+size_t propagate_pipe_smem(const NetView &N, int table_rows) {
+  return smem_prologue(N) + (size_t)N.P * sizeof(int32_t) + 16 +
+         3 * (size_t)kRoundDraws * 32 * (sizeof(unsigned long long) + sizeof(float2)) +
+         2 * (size_t)kRoundDraws * 32 * (sizeof(float2) + sizeof(int32_t)) + 2 * 3 * 32 * sizeof(uint32_t) + 16 +
+         (size_t)table_rows * N.P * sizeof(unsigned long long);
 }
 
 cudaError_t launch_init_log_tables(LogTables *T, cudaStream_t st) {
@@ -562,20 +772,20 @@ cudaError_t launch_init_log_tables(LogTables *T, cudaStream_t st) {
 
 template <int P, int L>
 static cudaError_t build_table_p(const NetView &N, const int32_t *base, int species, int len,
-                                 double *rows, cudaStream_t st) {
+                                 double clock_scale, unsigned long long *rows, cudaStream_t st) {
   dim3 grid((len + 127) / 128, N.n_param_sets);
-  k_build_table<P, L><<<grid, 128, 0, st>>>(N, base, species, len, rows);
+  k_build_table<P, L><<<grid, 128, 0, st>>>(N, base, species, len, clock_scale, rows);
   return cudaGetLastError();
 }
 
 cudaError_t launch_build_table(const NetView &N, const int32_t *base, int species, int len,
-                               double *rows, cudaStream_t st) {
+                               double clock_scale, unsigned long long *rows, cudaStream_t st) {
   switch (N.P) {
-    case 1: return build_table_p<1, 0>(N, base, species, len, rows, st);
-    case 2: return build_table_p<2, 1>(N, base, species, len, rows, st);
-    case 4: return build_table_p<4, 2>(N, base, species, len, rows, st);
-    case 8: return build_table_p<8, 3>(N, base, species, len, rows, st);
-    case 16: return build_table_p<16, 4>(N, base, species, len, rows, st);
+    case 1: return build_table_p<1, 0>(N, base, species, len, clock_scale, rows, st);
+    case 2: return build_table_p<2, 1>(N, base, species, len, clock_scale, rows, st);
+    case 4: return build_table_p<4, 2>(N, base, species, len, clock_scale, rows, st);
+    case 8: return build_table_p<8, 3>(N, base, species, len, clock_scale, rows, st);
+    case 16: return build_table_p<16, 4>(N, base, species, len, clock_scale, rows, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -591,14 +801,48 @@ static cudaError_t launch_k(K kern, const PropagateParams &prm, int grid, int bl
   return cudaGetLastError();
 }
 
+// Rows of the table a block of the warp-specialised kernel may stage: as many as fit while
+// every block of the launch stays resident at once (up to the kernel's register limit of
+// blocks per SM), and no more than the table has.
+static int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+template <typename K>
+static int pipe_table_rows(K kern, const PropagateParams &prm, int grid) {
+  if (prm.tab.species < 0 || prm.tab.len <= 0) return 0;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) { cudaGetLastError(); return 0; }
+  const int by_regs = std::max(1, 65536 / std::max(1, fa.numRegs * 128));
+  const int sms = num_sms();
+  const int per_sm = std::min(by_regs, std::max(1, (grid + sms - 1) / sms));
+  const size_t budget = (size_t)(227 * 1024) / per_sm - 1024;
+  const size_t base = propagate_pipe_smem(prm.net, 0);
+  if (base >= budget) return 0;
+  const size_t rows = (budget - base) / ((size_t)prm.net.P * sizeof(unsigned long long));
+  return (int)std::min<size_t>(rows, (size_t)prm.tab.len);
+}
+
+template <typename K>
+static cudaError_t launch_pipe(K kern, const PropagateParams &prm_in, int grid, cudaStream_t st) {
+  PropagateParams prm = prm_in;
+  prm.tab.smem_rows = pipe_table_rows(kern, prm, grid);
+  return launch_k(kern, prm, grid, 128, propagate_pipe_smem(prm.net, prm.tab.smem_rows), st);
+}
+
 cudaError_t launch_propagate_ws(const PropagateParams &prm, bool table, cudaStream_t st) {
   const int total_slots = prm.ens.R * prm.ens.cap;
   const int grid = (total_slots + 31) / 32;
   const size_t smem = propagate_ws_smem(prm.net);
 #define WE_CASE(PP, LL)                                                                  \
   case PP:                                                                               \
-    return table ? launch_k(k_propagate_ws<PP, LL, true>, prm, grid, 128, smem, st)      \
-                 : launch_k(k_propagate_ws<PP, LL, false>, prm, grid, 128, smem, st);
+    return table ? launch_pipe(k_propagate_pipe<PP, LL>, prm, grid, st)                  \
+                 : launch_k(k_propagate_ws<PP, LL>, prm, grid, 128, smem, st);
   switch (prm.net.P) {
     WE_CASE(1, 0)
     WE_CASE(2, 1)

@@ -263,6 +263,47 @@ __device__ __forceinline__ double advance_clock(double t, float2 e, double inv_a
   return __fma_rn(f2d_bits(e.y), inv_a0, __fma_rn(f2d_bits(e.x), inv_a0, t));
 }
 
+// ------------------------------------------------------------------------------------------
+// Fixed-point clock of the table kernels.  Within an interval the clock runs in integer units
+// of tau / 2^62: waiting times are added exactly (no rounding per event), the event-fires test
+// t + dt <= tau is an integer compare, and no FP64 operation is left on the event-to-event
+// chain.  A waiting time dt = e / a0 comes from e (float-float) times the row's float-float
+// (2^62 / tau) / a0, an error-free float product plus the cross terms (relative error about
+// 2^-47, below the logarithm's), rounded to the nearest unit.
+// ------------------------------------------------------------------------------------------
+constexpr uint32_t kClockBeyondBits = (uint32_t)(127 + kClockBits) << 23;   // float bits of 2^62
+
+// Nearest integer to a float f with |f| < 2^62, by integer operations on its bits and without
+// branches: |f| = m 2^(E-150) = (m 2^39) / 2^(189-E), so one rounding right shift of m 2^39
+// (below 2^63, so adding the rounding half, at most 2^62, cannot wrap).  The shift is held in
+// [1, 63]; only |f| < 1/2 is affected by the upper limit, which then gives 1 instead of 0.
+__device__ __forceinline__ long long f2ll_near(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t ex = (b >> 23) & 0xffu;
+  const unsigned long long mm = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << 39;
+  const uint32_t sh = min(189u - min(ex, 188u), 63u);              // 1 .. 63
+  const unsigned long long v = (mm + (1ull << (sh - 1))) >> sh;
+  const long long sv = (long long)v;
+  return (b >> 31) ? -sv : sv;
+}
+
+// Waiting time in clock units for e = -log u1 and w = (2^62 / tau) / a0 (both float-float,
+// non-negative).  Returns false when it is at least 2^62 units (beyond the interval, including
+// an infinite w); dt is then unspecified.
+__device__ __forceinline__ bool wait_units(float2 e, float2 w, long long &dt) {
+  const float p = __fmul_rn(e.x, w.x);
+  const bool within = (__float_as_uint(p) & 0x7fffffffu) < kClockBeyondBits;
+  const float err = __fmaf_rn(e.x, w.x, -p);
+  const float lo = __fmaf_rn(e.x, w.y, __fmaf_rn(e.y, w.x, err));
+  dt = f2ll_near(p) + f2ll_near(lo);
+  return within;
+}
+
+// Clock units back to time: t = units * tau / 2^62 (one rounding).
+__device__ __forceinline__ double clock_time(long long units, double tau) {
+  return __dmul_rn(__ll2double_rn(units), ldexp(tau, -kClockBits));
+}
+
 // Draws do not depend on the state, so they are made kDrawBatch at a time: the batch's
 // independent Philox and logarithm chains interleave in one instruction stream (each chain
 // alone is a few hundred cycles of dependent integer and FP32 operations), instead of one

@@ -238,7 +238,7 @@ def test_harvest_states_all_runs():
     harvest collects them after every iteration."""
     from paper_1303_5986_gb300 import learned as LN
     cfg = W.toggle_batch_we(n_runs=5, n_iters=3, seed=2)
-    ens = gpu_run(cfg, 2)
+    ens = gpu_run(cfg, 2, record_iters=4)
     allx = ens.states(-1)
     per = np.concatenate([ens.states(r) for r in range(cfg.n_runs)])
     assert np.array_equal(allx, per)
