@@ -204,9 +204,6 @@ def workload_config(a):
 
 
 # ------------------------------------------------------------------------------------------
-# our arm
-# ------------------------------------------------------------------------------------------
-# ------------------------------------------------------------------------------------------
 # learned binning against plain binning (MFPT error per GPU-second)
 # ------------------------------------------------------------------------------------------
 TOGGLE_A = 40.0
@@ -350,6 +347,36 @@ def run_toggle_learned(a):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------------------------------
+# ranks: every rank runs its own replicas (weak scaling, no data-path collective); the job's
+# figures are the slowest rank's time and the sum of every rank's work
+# ------------------------------------------------------------------------------------------
+def rank_seeds(rank: int, n: int) -> list:
+    """Seeds of a rank's ensembles: disjoint across ranks, one per warm-up/timed/e2e step."""
+    return [1_000_003 * (rank + 1) + s for s in range(n)]
+
+
+def combine_ranks(dist, device, total_ms: float, events: float, flux_per_replica):
+    """(max time over ranks, total events, every rank's per-replica flux means in rank order).
+    flux_per_replica has the same length on every rank."""
+    import numpy as np
+    import torch
+    fl = np.asarray(flux_per_replica, dtype=np.float64)
+    if dist is None:
+        return total_ms, events, fl
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ev = torch.tensor([events], dtype=torch.float64, device=device)
+    dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+    mine = torch.as_tensor(fl, device=device)
+    parts = [torch.empty_like(mine) for _ in range(dist.get_world_size())]
+    dist.all_gather(parts, mine)
+    return float(t[0]), float(ev[0]), torch.cat(parts).cpu().numpy()
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
 def main():
     a = parse()
     if a.workload == "toggle_learned":
@@ -397,7 +424,7 @@ def main():
         c, keep = P.run_config_from(cfg, record_iters=a.iters, block_threads=a.block)
         return P.we_ensemble_create(net, bm, c, keep)
 
-    seeds = [1_000_003 * (rank + 1) + s for s in range(a.warmup + a.steps + 1)]
+    seeds = rank_seeds(rank, a.warmup + a.steps + 1)
     # every ensemble of the timed region is uploaded before timing starts (inputs resident)
     warm = [ensemble(s) for s in seeds[:a.warmup]]
     timed = [ensemble(s) for s in seeds[a.warmup:a.warmup + a.steps]]
@@ -429,21 +456,13 @@ def main():
 
     events = [int(e.per_iter(P.WE_OUT_EVENTS).sum()) for e in timed]
     fluxes = [e.per_iter(P.WE_OUT_FLUX) for e in timed]              # iters x replicas
-    total_ms = float(sum(step_ms))
-    ev_total = float(sum(events))
     prop_total_ms = float(sum(p.sum() for p in prop_ms))
     n_launch = sum(len(p) for p in prop_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms, ev_total, prop_total_ms], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms, ev_total = float(tmax[0]), float(t[1])
+    # MFPT = 1/flux over the replicas of all timed steps of all ranks (Eq. "mfpt")
+    fl_rank = np.concatenate([f[DISCARD:].mean(axis=0) for f in fluxes]) / base.tau
+    total_ms, ev_total, fl = combine_ranks(dist, "cuda", float(sum(step_ms)), float(sum(events)), fl_rank)
     value = ev_total / (total_ms * 1e-3)
     we_iters_per_s = a.steps * a.iters / (total_ms * 1e-3)
-
-    # MFPT = 1/flux over the replicas of all timed steps (Eq. "mfpt"); error vs the closed form
-    fl = np.concatenate([f[DISCARD:].mean(axis=0) for f in fluxes]) / base.tau
     mfpt = 1.0 / fl.mean()
     exact = exact_mfpt()
     rel_err = abs(mfpt - exact) / exact
