@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
 // Off-table rows: the canonical tree evaluated on the fly (counts beyond the table), kept out
 // of line so that the event chain stays short.
 template <int P, int LOG2P>
-__device__ __noinline__ float2 evaluate_row(double *fb, const RxnMeta *meta, const double *keff,
+__device__ __forceinline__ float2 evaluate_row(double *fb, const RxnMeta *meta, const double *keff,
                                             const double *Kn, const int32_t *xme, int B, double clock_scale) {
 #pragma unroll
   for (int j = 0; j < P; ++j) fb[P + j] = propensity(meta[j], keff[j], Kn[j], xme, B);
@@ -508,7 +508,7 @@ __device__ __noinline__ float2 evaluate_row(double *fb, const RxnMeta *meta, con
   return wait_scale(fb[1], clock_scale);
 }
 template <int P, int LOG2P>
-__device__ __noinline__ int descend_row(const double *fb, unsigned long long m2) {
+__device__ __forceinline__ int descend_row(const double *fb, unsigned long long m2) {
   return descend<P, LOG2P>(fb, m2);
 }
 
@@ -528,7 +528,7 @@ __device__ __noinline__ int descend_row(const double *fb, unsigned long long m2)
 // the same as the serial loop's: the same reaction for each draw, the same waiting time, the
 // same order of clock additions.
 template <int P, int LOG2P>
-__global__ void __launch_bounds__(128) k_propagate_pipe(PropagateParams prm) {
+__global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Smem sm = load_smem<P>(prm, smem_raw);
   const EnsView &E = prm.ens;
@@ -672,12 +672,13 @@ __global__ void __launch_bounds__(128) k_propagate_pipe(PropagateParams prm) {
       const int qb = p % 3, sb = p & 1;
       if (live && !s_done[sb ^ 1][lane]) {
         uint32_t idle_m = 0u, ovf_m = 0u, rec_m = 0u;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
+        // one draw of the chain; `fast` rows come from the table only (no calls in the
+        // unrolled loop), rows beyond it are evaluated in the tail loop below
+        auto step = [&](int k, bool fast) {
           const unsigned long long m2 = qm[(qb * K + k) * W + lane];
           sw[(sb * K + k) * W + lane] = row.w;
           if (row.idle()) idle_m |= 1u << k;
-          const int j = row.direct ? descend_row<P, LOG2P>(fb, m2) : row.select_table(m2);
+          const int j = (!fast && row.direct) ? descend_row<P, LOG2P>(fb, m2) : row.select_table(m2);
           int dx = dxr[0];
 #pragma unroll
           for (int i = 1; i < P; ++i) dx = (j == i) ? dxr[i] : dx;
@@ -686,6 +687,36 @@ __global__ void __launch_bounds__(128) k_propagate_pipe(PropagateParams prm) {
           if (E.feedback && ok && nx >= xlo && nx <= xhi) { rec_m |= 1u << k; nx = xrec; ok = ok_rec; }
           sx[(sb * K + k) * W + lane] = nx;
           x = nx;
+        };
+        int k = 0;
+        if (!row.direct) {
+          // the first draw after which the count leaves the table (its later draws in this
+          // loop ran on a stale row and are redone below from the state saved here)
+          int out_at = K;
+          int x_out = 0;
+          bool ok_out = false;
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) {
+            step(kk, true);
+            const unsigned off = (unsigned)(x - win_lo);
+            if (off < (unsigned)win_n) row.read(s_tab + (size_t)off * P);
+            else if (x < TV.len) row.read(tab + (size_t)x * P);
+            else if (out_at == K) { out_at = kk; x_out = x; ok_out = ok; }
+          }
+          k = K;
+          if (out_at < K) {
+            const uint32_t keep = (2u << out_at) - 1u;      // draws 0 .. out_at stand
+            idle_m &= keep;
+            ovf_m &= keep;
+            rec_m &= keep;
+            x = x_out;
+            ok = ok_out;
+            load_row(x);
+            k = out_at + 1;
+          }
+        }
+        for (; k < K; ++k) {                                // rows beyond the table
+          step(k, false);
           load_row(x);
         }
         sfl[(sb * 3 + 0) * W + lane] = idle_m;
@@ -697,28 +728,44 @@ __global__ void __launch_bounds__(128) k_propagate_pipe(PropagateParams prm) {
       if (p >= 1) {
         const int qb = (p - 1) % 3, pb = sb ^ 1;
         if (!done) {
+          // waiting times (independent), the clock after each draw, and the first draw that
+          // cannot fire: idle row, waiting time or clock past tau (no status), else the step
+          // cap, else an overflow -- the order of the checks in the serial loop
           long long dts[K];
-          uint32_t far_m = 0u;
+          uint32_t far_m = 0u, over_m = 0u;
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             const float2 e = qe[(qb * K + k) * W + lane];
             const float2 wv = sw[(pb * K + k) * W + lane];
             if (!wait_units(e, wv, dts[k])) far_m |= 1u << k;
           }
+          long long c = clk;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            c += dts[k];                                  // meaningful up to the first stop
+            if (c > kClockTau) over_m |= 1u << k;
+          }
           const uint32_t idle_m = sfl[(pb * 3 + 0) * W + lane];
           const uint32_t ovf_m = sfl[(pb * 3 + 1) * W + lane];
           const uint32_t rec_m = sfl[(pb * 3 + 2) * W + lane];
+          const long long room = E.max_steps - nev;       // draws that may still fire
+          const uint32_t cap_m = room >= K ? 0u : ((0xffffu << (int)room) & 0xffffu);
+          const uint32_t quiet_m = idle_m | far_m | over_m;
+          const uint32_t stop_m = (quiet_m | cap_m | ovf_m) & 0xffffu;
+          const int kstop = stop_m ? __ffs(stop_m) - 1 : K;
+          const uint32_t fired = (1u << kstop) - 1u;
+          long long cs = clk;
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            if (done) continue;
-            const uint32_t bit = 1u << k;
-            if ((idle_m & bit) || (far_m & bit) || clk + dts[k] > kClockTau) { done = true; continue; }
-            if (nev >= E.max_steps) { status = kStatusStepCap; done = true; continue; }
-            if (ovf_m & bit) { status = kStatusOverflow; done = true; continue; }
-            clk += dts[k];
-            ++nev;
-            xc = sx[(pb * K + k) * W + lane];
-            if (rec_m & bit) { ++nrec; recycled = true; }
+          for (int k = 0; k < K; ++k) cs += (k < kstop) ? dts[k] : 0ll;
+          clk = cs;
+          nev += kstop;
+          nrec += __popc(rec_m & fired);
+          recycled = recycled || (rec_m & fired) != 0u;
+          if (kstop > 0) xc = sx[(pb * K + kstop - 1) * W + lane];
+          if (kstop < K) {
+            done = true;
+            const uint32_t bit = 1u << kstop;
+            if (!(quiet_m & bit)) status = (cap_m & bit) ? kStatusStepCap : kStatusOverflow;
           }
         }
         s_done[sb][lane] = done;
