@@ -109,6 +109,25 @@ __device__ __forceinline__ void warp_argmin(const double *sw, const int32_t *ss,
   best_i = bi;
 }
 
+// Lightest live entry (weight bits >= 0) of a register-resident bin list, entries lane * 4 + q,
+// keyed by (weight bits, slot), skipping entry `skip`; the result on every lane.
+__device__ __forceinline__ void reg_argmin(const long long (&vv)[4], const int (&sl)[4], int lane, int skip,
+                                           long long &bw, int &bs, int &bo) {
+  bw = 0x7FFFFFFFFFFFFFFFll; bs = 0x7FFFFFFF; bo = -1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool ok = vv[q] >= 0 && lane * 4 + q != skip;
+    if (ok && (vv[q] < bw || (vv[q] == bw && sl[q] < bs))) { bw = vv[q]; bs = sl[q]; bo = lane * 4 + q; }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const long long ow = __shfl_xor_sync(0xffffffffu, bw, d);
+    const int os = __shfl_xor_sync(0xffffffffu, bs, d);
+    const int oo = __shfl_xor_sync(0xffffffffu, bo, d);
+    if (ow < bw || (ow == bw && os < bs)) { bw = ow; bs = os; bo = oo; }
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Split/merge, one warp per occupied bin (Sec. II.B).  A bin's walkers are ordered by slot:
 //   more than M_targ: merge the two lightest (ties: lower slot); of the pair, the lower-slot
@@ -143,7 +162,61 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
     int32_t *lss = E.sorted_slot + base + in0;
     double *lsw = E.sorted_w + base + in0;
     int32_t *lal = E.alive + base + in0;
-    if (cnt > M) {
+    if (cnt > M && cnt <= 128) {
+      // Up to 128 walkers: entries i = lane + 32 q in registers, the argmins by shuffles, and
+      // every merge's uniform drawn up front (merge k's counter does not depend on the others).
+      long long vv[4];                                     // weight bits; -1: merged away
+      int sl[4];
+      unsigned long long ub[4];                            // bits of u for merges lane + 32 q
+      const int n_merge = cnt - M;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        if (i < cnt) { vv[q] = bits(lsw[i]); sl[q] = lss[i]; }
+        else { vv[q] = -1; sl[q] = 0x7FFFFFFF; }
+        ub[q] = 0;
+        if (i < n_merge) {
+          uint32_t c0 = (uint32_t)i, c1 = (uint32_t)iter, c2 = (uint32_t)b, c3 = 1u;
+          philox4x32_10(c0, c1, c2, c3, k0, k1);
+          ub[q] = (unsigned long long)bits(u01(c0, c1));
+        }
+      }
+      for (int km = 0; km < n_merge; ++km) {
+        long long wa, wb;
+        int sa, sb, oa, ob;
+        reg_argmin(vv, sl, lane, -1, wa, sa, oa);
+        reg_argmin(vv, sl, lane, oa, wb, sb, ob);
+        const bool a_first = sa < sb;                        // p: the lower slot of the pair
+        const long long wp = a_first ? wa : wb, wq = a_first ? wb : wa;
+        const int op = a_first ? oa : ob, oq = a_first ? ob : oa;
+        unsigned long long u_k = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) if ((km >> 5) == q) u_k = ub[q];
+        u_k = __shfl_sync(0xffffffffu, u_k, km & 31);
+        int keep_p = 0;
+        long long wsum_bits = 0;
+        if (lane == 0) {
+          const double wsum = __dadd_rn(__longlong_as_double(wp), __longlong_as_double(wq));
+          const double prob = __ddiv_rn(__longlong_as_double(wp), wsum);
+          keep_p = (long long)u_k < bits(prob) ? 1 : 0;
+          wsum_bits = bits(wsum);
+        }
+        keep_p = __shfl_sync(0xffffffffu, keep_p, 0);
+        wsum_bits = __shfl_sync(0xffffffffu, wsum_bits, 0);
+        const int osurv = keep_p ? op : oq, odead = keep_p ? oq : op;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (lane * 4 + q == osurv) vv[q] = wsum_bits;
+          if (lane * 4 + q == odead) vv[q] = -1;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        if (i < cnt) { lal[i] = vv[q] >= 0 ? 1 : 0; if (vv[q] >= 0) lsw[i] = __longlong_as_double(vv[q]); }
+      }
+      __syncwarp();
+    } else if (cnt > M) {
       uint32_t kmerge = 0;
       for (int live = cnt; live > M; --live) {
         int ia, ib;
@@ -163,6 +236,9 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
         ++kmerge;
         __syncwarp();
       }
+    } else if (cnt == 1 && M > 1) {
+      if (lane == 0) lal[0] = M;                            // every copy goes to the one walker
+      __syncwarp();
     } else if (cnt < M && cnt <= 128) {
       // Up to 128 walkers: each lane keeps its entries' per-copy weights w_i/c_i in registers,
       // so a round divides once (for the walker that received the copy), not once per walker.
@@ -194,8 +270,8 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
         for (int q = 1; q < 4; ++q)
           if ((bo & 3) == q) { wsel = wv[q]; csel = cc[q]; }
         csel += 1;
-        const long long vnew = bits(__ddiv_rn(wsel, (double)csel));   // one division per round
-        if ((bo >> 2) == lane) {
+        if ((bo >> 2) == lane) {                          // one division per round, by the owner
+          const long long vnew = bits(__ddiv_rn(wsel, (double)csel));
 #pragma unroll
           for (int q = 0; q < 4; ++q)
             if ((bo & 3) == q) { cc[q] = csel; vv[q] = vnew; }
@@ -250,12 +326,14 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
       int off = 0;
       for (int j = 0; j < k; ++j) off += (lss[j] < si) ? lal[j] : 0;
       const int c = lal[i];
-      const double wc = (cnt < M) ? __ddiv_rn(lsw[i], (double)c) : lsw[i];
+      const double wi = lsw[i];
+      const double wc = (cnt < M) ? __ddiv_rn(wi, (double)c) : wi;
       for (int q = 0; q < c; ++q) {
         W2[out0 + off + q] = wc;
         P2[out0 + off + q] = si;
-        wsum_local = __dadd_rn(wsum_local, wc);
       }
+      // the c copies' weight, c * wc rounded once (the exact sum of the copies, rounded)
+      wsum_local = __dadd_rn(wsum_local, c == 1 ? wc : __dmul_rn((double)c, wc));
     }
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) wsum_local = __dadd_rn(wsum_local, __shfl_xor_sync(0xffffffffu, wsum_local, d));
