@@ -35,13 +35,18 @@ if ROOT not in sys.path:
 
 ITERS = 1000
 DISCARD = 300              # iterations before the flux average (steady state, Sec. III.C.3 protocol)
-# FP64 operations the direct method needs per Schloegl event with dependency-graph updates:
-# 3 propensities (x keff), 3 tree additions, target u2*a0, 2 descent subtractions, log, divide,
-# clock addition.  Peak: 152 SMs x 2 FP64 lanes/clock x 2.07 GHz (1.25 TFLOP/s counting an FMA
-# as two operations).
-FLOPS_PER_EVENT = 12
-FP64_PEAK_GOPS = 152 * 2 * 2.07
+# Integer/FP32 lane operations one direct-method event needs on the state-indexed table path:
+# Philox-4x32-10 (10 rounds x [2 multiply-high, 2 multiply-low, 4 xor, 2 key additions] = 100),
+# the uniform's index and the float-float -log u1 (~68), the waiting time in clock units and
+# the clock (~26), the reaction from P - 1 = 3 breakpoints (~9), the count update with its
+# overflow and target checks (~7).  Peak: the issue limit, 152 SMs x 4 sub-partitions x one
+# 32-lane instruction per clock x 2.07 GHz.
+OPS_PER_EVENT = 210
+ISSUE_PEAK_GOPS = 152 * 4 * 32 * 2.07
 KERNELS_PER_ITER = 6       # SSA, bin scan, placement, split/merge, gather, finalize
+# DRAM bytes (read + write) of one SSA launch on this workload, from the ncu capture summarised
+# in profiles/schlogl_mfpt_ssa_kernel.md (a 16,000-walker launch, as in every timed launch)
+SSA_TRAFFIC_BYTES = 390656
 
 
 def parse():
@@ -471,14 +476,14 @@ def main():
     # roofline of the dominant kernel (the SSA kernel), from the events around each launch
     prop_s = prop_total_ms * 1e-3
     ev_rank = float(sum(events))
-    achieved = FLOPS_PER_EVENT * ev_rank / prop_s / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
-                "kernel": "k_propagate_ws<4,2,true> (thread per walker, state-indexed tables)", "launches": n_launch,
-                "avg_launch_ms": prop_total_ms / max(n_launch, 1),
+    achieved = OPS_PER_EVENT * ev_rank / prop_s / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK_GOPS, "unit": "G lane-ops/s",
+                "frac": achieved / ISSUE_PEAK_GOPS, "traffic": SSA_TRAFFIC_BYTES,
+                "kernel": "k_propagate_pipe<4,2> (state chain / clock / draw warps, state-indexed table)",
+                "launches": n_launch, "avg_launch_ms": prop_total_ms / max(n_launch, 1),
                 "share_of_step": prop_total_ms / total_ms if dist is None else None,
-                "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz (recipe: 1.25 TFLOP/s FP64, FMA=2)",
-                "flops_per_event": FLOPS_PER_EVENT}
+                "peak_source": "derived: 152 SMs x 4 SMSPs x 32 lanes x 2.07 GHz (issue limit)",
+                "ops_per_event": OPS_PER_EVENT, "events_per_launch": ev_rank / max(n_launch, 1)}
 
     # end to end: one we_run() call per step from host buffers, observables back to the host
     e2e = None
