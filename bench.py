@@ -307,8 +307,9 @@ def run_toggle_learned(a):
     hens.close()
     t_harvest = time.perf_counter() - t0
     tgt = ([1, 0], [P.WE_OP_GE, P.WE_OP_LE], [thrV, thrU])
+    fit_t = {}
     mlp, xs, labels, losses = LN.fit_coordinate(net, states, tgt, [int(A), 0], 1.0, steps=2000,
-                                                batch=4096, lr=3e-3, seed=3)
+                                                batch=4096, lr=3e-3, seed=3, timings=fit_t)
     edges = LN.coordinate_edges(mlp, xs, 100)
     lbm = P.we_binmap_learned(mlp, edges)
     M = 164
@@ -344,7 +345,8 @@ def run_toggle_learned(a):
                                f"walkers, {a.learned_iters} iterations")},
         "plain_m8": plains[8], "plain_m64": plains[64],
         "learned": {"gpu_s_to_10pct": tl, "final": learned[-1], "walkers_end": learned_walkers,
-                    "fixed_cost_s": t_fixed, "harvest_s": t_harvest,
+                    "fixed_cost_s": t_fixed, "harvest_s": t_harvest, "labels_s": fit_t.get("labels_s"),
+                    "train_s": fit_t.get("train_s"),
                     "train_loss_first_last": [float(losses[0]), float(losses[-50:].mean())],
                     "label_mean": float(labels.mean()), "curve": learned},
         "clocks": clk,

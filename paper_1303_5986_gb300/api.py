@@ -412,12 +412,9 @@ def first_passage_labels(net: Network, states, horizon: float, target, recycle_s
     ens = we_ensemble_create(net, bm, c, keep, stream=stream)
     ens.propagate(stream)
     dev = ens.workspace.device
-    nrec = torch.empty(n, dtype=torch.int32, device=dev)
-    ens.get(L.WE_OUT_NREC, 0, out=nrec, stream=stream)
-    x = torch.as_tensor(st, device=dev)
-    inside = torch.ones(n, dtype=torch.bool, device=dev)
-    for s_, o_, t_ in zip(sp, ops, thr[0]):
-        inside &= (x[:, s_] >= int(t_)) if o_ == L.WE_OP_GE else (x[:, s_] <= int(t_))
-    labels = ((nrec > 0) | inside).to(torch.float32)
+    nrec = ens.get(L.WE_OUT_NREC, 0, stream=stream)               # host copy of the recycle counts
     ens.close()
-    return labels
+    inside = np.ones(n, dtype=bool)
+    for s_, o_, t_ in zip(sp, ops, thr[0]):
+        inside &= (st[:, s_] >= int(t_)) if o_ == L.WE_OP_GE else (st[:, s_] <= int(t_))
+    return torch.as_tensor(((nrec > 0) | inside).astype(np.float32), device=dev)

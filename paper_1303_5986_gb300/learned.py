@@ -33,20 +33,30 @@ def init_params(n_in: int, hidden: int, seed: int) -> np.ndarray:
 
 def fit_coordinate(net, states, target, recycle_state, horizon: float, hidden: int = 64,
                    steps: int = 2000, batch: int = 4096, lr: float = 3e-3, seed: int = 0,
-                   param_set: int = 0, max_states: int = 2_000_000, stream=None):
+                   param_set: int = 0, max_states: int = 2_000_000, stream=None, timings=None):
     """Label `states` by first passage into `target` within `horizon` (one SSA shot each) and
-    train a fresh MLP on them.  Returns (mlp, device states, device labels, losses)."""
+    train a fresh MLP on them.  Returns (mlp, device states, device labels, losses).  With a dict
+    `timings`, the wall time of the labelling and of the training (device synchronised) go in
+    'labels_s' and 'train_s'."""
+    import time
     import torch
     st = np.ascontiguousarray(states, dtype=np.int32)
     rng = np.random.default_rng(seed)
     if len(st) > max_states:
         st = st[rng.choice(len(st), size=max_states, replace=False)]
     st = st[rng.permutation(len(st))]
+    t0 = time.perf_counter()
     labels = first_passage_labels(net, st, horizon, target, recycle_state, seed=seed,
                                   param_set=param_set, stream=stream)
     xs = torch.as_tensor(st, device=labels.device)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     mlp = we_mlp_create(st.shape[1], hidden, init_params(st.shape[1], hidden, seed))
     losses = mlp.train(xs, labels, steps, batch, lr, stream=stream)
+    torch.cuda.synchronize()
+    if timings is not None:
+        timings["labels_s"] = t1 - t0
+        timings["train_s"] = time.perf_counter() - t1
     return mlp, xs, labels, losses
 
 
