@@ -15,6 +15,7 @@
 
 #include "../../include/we_ssa.h"
 #include "we_internal.cuh"
+#include "we_exact.cuh"
 #include "we_mlp.cuh"
 
 namespace we {
@@ -320,7 +321,7 @@ struct Offsets {
   size_t meta, keff, Kn, d_sp, d_val, dep_ptr, dep_idx, edges;
   size_t run_id, param_set, tgt_thr, recycle;
   size_t x0, x1, w0, w1, p0, p1, bin, nrec, tlast;
-  size_t count, prev_count, run_off, status, iter, bin_count, n_tasks, tasks, cursor, sorted_slot, sorted_w, alive;
+  size_t count, prev_count, run_off, status, iter, bin_count, n_tasks, tasks, cursor, sorted_slot, sorted_w, alive, div_magic;
   size_t flux, totw, nw, events, hist, pack;
   size_t logt, table, base;
   size_t lw1, lw2, lw3, lb, lz, zout;
@@ -385,6 +386,7 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
   o.sorted_slot = L.take(4 * RC);
   o.sorted_w = L.take(8 * RC);
   o.alive = L.take(4 * RC);
+  o.div_magic = L.take(8 * ((size_t)c->m_targ + 1));
   o.flux = L.take(8 * rec * R);
   o.totw = L.take(8 * rec * R);
   o.nw = L.take(4 * rec * R);
@@ -547,8 +549,11 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
     if (!bytes) return cudaSuccess;
     return cudaMemcpyAsync(at<char>(ws, offs), src, bytes, cudaMemcpyHostToDevice, s);
   };
+  std::vector<unsigned long long> magic((size_t)c->m_targ + 1, 0ull);   // lives past the copies
+  for (int k = 2; k <= c->m_targ; ++k) magic[k] = ex_div_magic((unsigned)k);
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMemsetAsync(ws, 0, o.total, s);
+  e = e ? e : up(o.div_magic, magic.data(), 8 * magic.size());
   e = e ? e : up(o.meta, n->meta.data(), sizeof(RxnMeta) * n->P);
   e = e ? e : up(o.keff, n->keff.data(), 8 * n->keff.size());
   e = e ? e : up(o.Kn, n->Kn.data(), 8 * n->Kn.size());
@@ -634,6 +639,7 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   V.tasks = at<int4>(ws, o.tasks); V.cursor = at<int32_t>(ws, o.cursor);
   V.sorted_slot = at<int32_t>(ws, o.sorted_slot);
   V.sorted_w = at<double>(ws, o.sorted_w); V.alive = at<int32_t>(ws, o.alive);
+  V.div_magic = at<unsigned long long>(ws, o.div_magic);
   V.obs_flux = at<double>(ws, o.flux); V.obs_totw = at<double>(ws, o.totw);
   V.obs_nw = at<int32_t>(ws, o.nw); V.obs_events = at<unsigned long long>(ws, o.events);
   V.obs_hist = at<double>(ws, o.hist);

@@ -107,6 +107,7 @@ struct EnsView {
   int32_t *sorted_slot;        // R*cap   walkers grouped by bin (scratch)
   double *sorted_w;            // R*cap
   int32_t *alive;              // R*cap
+  const unsigned long long *div_magic;   // [m_targ + 1]: floor((2^64 - 1) / c) for c >= 2
   // observables, record_iters x R (x hist_len)
   double *obs_flux;
   double *obs_totw;

@@ -8,6 +8,7 @@
 //
 // Every weight operation is a single IEEE double operation with an explicit round-to-nearest
 // intrinsic; comparisons between non-negative doubles use their bit patterns.
+#include "we_exact.cuh"
 #include "we_ssa_common.cuh"
 
 namespace we {
@@ -109,23 +110,20 @@ __device__ __forceinline__ void warp_argmin(const double *sw, const int32_t *ss,
   best_i = bi;
 }
 
-// Lightest live entry (weight bits >= 0) of a register-resident bin list, entries lane * 4 + q,
-// keyed by (weight bits, slot), skipping entry `skip`; the result on every lane.
-__device__ __forceinline__ void reg_argmin(const long long (&vv)[4], const int (&sl)[4], int lane, int skip,
-                                           long long &bw, int &bs, int &bo) {
-  bw = 0x7FFFFFFFFFFFFFFFll; bs = 0x7FFFFFFF; bo = -1;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const bool ok = vv[q] >= 0 && lane * 4 + q != skip;
-    if (ok && (vv[q] < bw || (vv[q] == bw && sl[q] < bs))) { bw = vv[q]; bs = sl[q]; bo = lane * 4 + q; }
+// Four per-lane values as named registers (entries lane * 4 + q).  Selecting by a run-time q
+// goes through selects; an array here would be turned into indexed local memory.
+template <typename T>
+struct Four {
+  T v0, v1, v2, v3;
+  __device__ __forceinline__ T get(int q) const { return q < 2 ? (q == 0 ? v0 : v1) : (q == 2 ? v2 : v3); }
+  __device__ __forceinline__ void set(int q, T x) {
+    v0 = q == 0 ? x : v0; v1 = q == 1 ? x : v1; v2 = q == 2 ? x : v2; v3 = q == 3 ? x : v3;
   }
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) {
-    const long long ow = __shfl_xor_sync(0xffffffffu, bw, d);
-    const int os = __shfl_xor_sync(0xffffffffu, bs, d);
-    const int oo = __shfl_xor_sync(0xffffffffu, bo, d);
-    if (ow < bw || (ow == bw && os < bs)) { bw = ow; bs = os; bo = oo; }
-  }
+};
+
+// (w, s) lexicographic order on (weight bits, slot)
+__device__ __forceinline__ bool key_lt(long long wa, int sa, long long wb, int sb) {
+  return wa < wb || (wa == wb && sa < sb);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -138,7 +136,7 @@ __device__ __forceinline__ void reg_argmin(const long long (&vv)[4], const int (
 // The resampled walkers are written in slot order, copies right after their parent, at the
 // bin's output offset.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
+__global__ void __launch_bounds__(128, 4) k_resample(EnsView E, int n_bins) {
   const int r = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -154,6 +152,7 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
   const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
   const int slot_obs = iter - E.first_iter;
   const unsigned lt_mask = (1u << lane) - 1u;
+  const unsigned long long *magic = E.div_magic;
 
   for (int t = warp; t < nt; t += n_warps) {
     const int4 tk = E.tasks[(size_t)r * n_bins + t];
@@ -162,58 +161,94 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
     int32_t *lss = E.sorted_slot + base + in0;
     double *lsw = E.sorted_w + base + in0;
     int32_t *lal = E.alive + base + in0;
-    if (cnt > M && cnt <= 128) {
-      // Up to 128 walkers: entries i = lane + 32 q in registers, the argmins by shuffles, and
-      // every merge's uniform drawn up front (merge k's counter does not depend on the others).
-      long long vv[4];                                     // weight bits; -1: merged away
-      int sl[4];
-      unsigned long long ub[4];                            // bits of u for merges lane + 32 q
+
+    // Register form: up to 128 walkers (entries i = lane + 32 q as index lane * 4 + q), weights
+    // as bits.  The integer split/merge decisions need normal weights (w >= 2^-999 keeps every
+    // quotient normal) and copy counts up to 2048; other bins take the floating-point path.
+    Four<long long> vv;
+    Four<int> sl;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = lane + 32 * q;
+      vv.set(q, i < cnt ? bits(lsw[i]) : -1ll);
+      sl.set(q, i < cnt ? lss[i] : 0x7FFFFFFF);
+    }
+    bool exact = magic != nullptr && cnt <= 128 && M <= 2048;
+    if (exact) {
+      bool small = false;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) small = small || (vv.get(q) >= 0 && (vv.get(q) >> 52) < 24);
+      exact = !__any_sync(0xffffffffu, small);
+    }
+
+    if (cnt > M && exact) {
+      // Merges.  Every merge's uniform is drawn up front (merge k's counter does not depend on
+      // the others); each merge takes the two lightest live entries by (weight, slot) from one
+      // branch-free shuffle reduction; the survivor decision is the integer form of
+      // u < w_p / (w_p + w_q).
+      Four<unsigned long long> ub;
       const int n_merge = cnt - M;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int i = lane + 32 * q;
-        if (i < cnt) { vv[q] = bits(lsw[i]); sl[q] = lss[i]; }
-        else { vv[q] = -1; sl[q] = 0x7FFFFFFF; }
-        ub[q] = 0;
+        unsigned long long u = 0;
         if (i < n_merge) {
           uint32_t c0 = (uint32_t)i, c1 = (uint32_t)iter, c2 = (uint32_t)b, c3 = 1u;
           philox4x32_10(c0, c1, c2, c3, k0, k1);
-          ub[q] = (unsigned long long)bits(u01(c0, c1));
+          u = (unsigned long long)bits(u01(c0, c1));
         }
+        ub.set(q, u);
       }
       for (int km = 0; km < n_merge; ++km) {
-        long long wa, wb;
-        int sa, sb, oa, ob;
-        reg_argmin(vv, sl, lane, -1, wa, sa, oa);
-        reg_argmin(vv, sl, lane, oa, wb, sb, ob);
-        const bool a_first = sa < sb;                        // p: the lower slot of the pair
-        const long long wp = a_first ? wa : wb, wq = a_first ? wb : wa;
-        const int op = a_first ? oa : ob, oq = a_first ? ob : oa;
-        unsigned long long u_k = 0;
+        long long w1 = 0x7FFFFFFFFFFFFFFFll, w2 = 0x7FFFFFFFFFFFFFFFll;
+        int s1 = 0x7FFFFFFF, s2 = 0x7FFFFFFF, o1 = -1, o2 = -1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) if ((km >> 5) == q) u_k = ub[q];
-        u_k = __shfl_sync(0xffffffffu, u_k, km & 31);
-        int keep_p = 0;
-        long long wsum_bits = 0;
-        if (lane == 0) {
-          const double wsum = __dadd_rn(__longlong_as_double(wp), __longlong_as_double(wq));
-          const double prob = __ddiv_rn(__longlong_as_double(wp), wsum);
-          keep_p = (long long)u_k < bits(prob) ? 1 : 0;
-          wsum_bits = bits(wsum);
+        for (int q = 0; q < 4; ++q) {
+          const long long v = vv.get(q);
+          const int sq = sl.get(q), oq = lane * 4 + q;
+          const bool live = v >= 0;
+          const bool lt1 = live && key_lt(v, sq, w1, s1);
+          const bool lt2 = live && key_lt(v, sq, w2, s2);
+          w2 = lt1 ? w1 : (lt2 ? v : w2);
+          s2 = lt1 ? s1 : (lt2 ? sq : s2);
+          o2 = lt1 ? o1 : (lt2 ? oq : o2);
+          w1 = lt1 ? v : w1; s1 = lt1 ? sq : s1; o1 = lt1 ? oq : o1;
         }
-        keep_p = __shfl_sync(0xffffffffu, keep_p, 0);
-        wsum_bits = __shfl_sync(0xffffffffu, wsum_bits, 0);
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+          const long long pw1 = __shfl_xor_sync(0xffffffffu, w1, d), pw2 = __shfl_xor_sync(0xffffffffu, w2, d);
+          const int ps1 = __shfl_xor_sync(0xffffffffu, s1, d), ps2 = __shfl_xor_sync(0xffffffffu, s2, d);
+          const int po1 = __shfl_xor_sync(0xffffffffu, o1, d), po2 = __shfl_xor_sync(0xffffffffu, o2, d);
+          // the lighter of the two firsts leads; the second is the lighter of the other first
+          // and the leader's own second
+          const bool plead = key_lt(pw1, ps1, w1, s1);
+          const long long cw = plead ? w1 : pw1, dw = plead ? pw2 : w2;
+          const int cs = plead ? s1 : ps1, ds = plead ? ps2 : s2;
+          const int co = plead ? o1 : po1, dob = plead ? po2 : o2;
+          const bool clt = key_lt(cw, cs, dw, ds);
+          w2 = clt ? cw : dw; s2 = clt ? cs : ds; o2 = clt ? co : dob;
+          w1 = plead ? pw1 : w1; s1 = plead ? ps1 : s1; o1 = plead ? po1 : o1;
+        }
+        const bool a_first = s1 < s2;                        // p: the lower slot of the pair
+        const long long wp = a_first ? w1 : w2, wq = a_first ? w2 : w1;
+        const int op = a_first ? o1 : o2, oq = a_first ? o2 : o1;
+        const unsigned long long u_k = __shfl_sync(0xffffffffu, ub.get(km >> 5), km & 31);
+        const double wsum = __dadd_rn(__longlong_as_double(wp), __longlong_as_double(wq));
+        const bool keep_p = ex_u_below_quotient(u_k, (unsigned long long)wp, (unsigned long long)bits(wsum));
         const int osurv = keep_p ? op : oq, odead = keep_p ? oq : op;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          if (lane * 4 + q == osurv) vv[q] = wsum_bits;
-          if (lane * 4 + q == odead) vv[q] = -1;
+          long long v = vv.get(q);
+          v = lane * 4 + q == osurv ? bits(wsum) : v;
+          v = lane * 4 + q == odead ? -1ll : v;
+          vv.set(q, v);
         }
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int i = lane + 32 * q;
-        if (i < cnt) { lal[i] = vv[q] >= 0 ? 1 : 0; if (vv[q] >= 0) lsw[i] = __longlong_as_double(vv[q]); }
+        const long long v = vv.get(q);
+        if (i < cnt) { lal[i] = v >= 0 ? 1 : 0; if (v >= 0) lsw[i] = __longlong_as_double(v); }
       }
       __syncwarp();
     } else if (cnt > M) {
@@ -239,48 +274,49 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
     } else if (cnt == 1 && M > 1) {
       if (lane == 0) lal[0] = M;                            // every copy goes to the one walker
       __syncwarp();
-    } else if (cnt < M && cnt <= 128) {
-      // Up to 128 walkers: each lane keeps its entries' per-copy weights w_i/c_i in registers,
-      // so a round divides once (for the walker that received the copy), not once per walker.
-      double wv[4];
-      long long vv[4];
-      int cc[4], sl[4];
+    } else if (cnt < M && exact) {
+      // Splits: the next copy to the largest per-copy weight fl(w_i / c_i) (ties: lower slot);
+      // each entry keeps the value it would have after one more copy (nv), so a round is one
+      // branch-free argmax and one integer division by the lane that holds the receiver.
+      Four<unsigned long long> wo, nv;
+      Four<int> cc;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int i = lane + 32 * q;
-        if (i < cnt) { wv[q] = lsw[i]; vv[q] = bits(wv[q]); cc[q] = 1; sl[q] = lss[i]; }
-        else { wv[q] = 0.0; vv[q] = -1; cc[q] = 0; sl[q] = 0x7FFFFFFF; }
+        const long long v = vv.get(q);
+        wo.set(q, (unsigned long long)v);
+        cc.set(q, v >= 0 ? 1 : 0);
+        nv.set(q, v >= 0 ? ex_div_small((unsigned long long)v, 2u, magic[2]) : 0ull);
       }
       for (int extra = cnt; extra < M; ++extra) {
         long long bv = -1;
         int bs = 0x7FFFFFFF, bo = -1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (vv[q] > bv || (vv[q] == bv && sl[q] < bs)) { bv = vv[q]; bs = sl[q]; bo = lane * 4 + q; }
+        for (int q = 0; q < 4; ++q) {
+          const long long v = vv.get(q);
+          const int sq = sl.get(q);
+          const bool gt = v > bv || (v == bv && sq < bs);
+          bv = gt ? v : bv; bs = gt ? sq : bs; bo = gt ? lane * 4 + q : bo;
+        }
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) {
           const long long ov = __shfl_xor_sync(0xffffffffu, bv, d);
           const int os = __shfl_xor_sync(0xffffffffu, bs, d);
           const int oo = __shfl_xor_sync(0xffffffffu, bo, d);
-          if (ov > bv || (ov == bv && os < bs)) { bv = ov; bs = os; bo = oo; }
+          const bool gt = ov > bv || (ov == bv && os < bs);
+          bv = gt ? ov : bv; bs = gt ? os : bs; bo = gt ? oo : bo;
         }
-        double wsel = wv[0];
-        int csel = cc[0];
-#pragma unroll
-        for (int q = 1; q < 4; ++q)
-          if ((bo & 3) == q) { wsel = wv[q]; csel = cc[q]; }
-        csel += 1;
-        if ((bo >> 2) == lane) {                          // one division per round, by the owner
-          const long long vnew = bits(__ddiv_rn(wsel, (double)csel));
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if ((bo & 3) == q) { cc[q] = csel; vv[q] = vnew; }
+        if ((bo >> 2) == lane) {
+          const int q = bo & 3;
+          const int c = cc.get(q) + 1;
+          cc.set(q, c);
+          vv.set(q, (long long)nv.get(q));
+          nv.set(q, c + 1 <= M ? ex_div_small(wo.get(q), (unsigned)(c + 1), magic[c + 1]) : 0ull);
         }
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int i = lane + 32 * q;
-        if (i < cnt) lal[i] = cc[q];
+        if (i < cnt) lal[i] = cc.get(q);
       }
       __syncwarp();
     } else if (cnt < M) {
@@ -289,8 +325,8 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
         int bs = 0x7FFFFFFF, bi = -1;
         for (int i = lane; i < cnt; i += 32) {
           const long long v = bits(__ddiv_rn(lsw[i], (double)lal[i]));
-          const int sl = lss[i];
-          if (v > bv || (v == bv && sl < bs)) { bv = v; bs = sl; bi = i; }
+          const int sli = lss[i];
+          if (v > bv || (v == bv && sli < bs)) { bv = v; bs = sli; bi = i; }
         }
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) {
@@ -307,14 +343,14 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
     int k = 0;
     for (int i0 = 0; i0 < cnt; i0 += 32) {
       const int i = i0 + lane;
-      int sl = 0, c = 0;
+      int sli = 0, c = 0;
       double wv = 0.0;
-      if (i < cnt) { sl = lss[i]; c = lal[i]; wv = lsw[i]; }
+      if (i < cnt) { sli = lss[i]; c = lal[i]; wv = lsw[i]; }
       const unsigned m = __ballot_sync(0xffffffffu, c > 0);
       __syncwarp();
       if (c > 0) {
         const int d = k + __popc(m & lt_mask);
-        lss[d] = sl; lal[d] = c; lsw[d] = wv;
+        lss[d] = sli; lal[d] = c; lsw[d] = wv;
       }
       k += __popc(m);
       __syncwarp();
@@ -327,7 +363,10 @@ __global__ void __launch_bounds__(128) k_resample(EnsView E, int n_bins) {
       for (int j = 0; j < k; ++j) off += (lss[j] < si) ? lal[j] : 0;
       const int c = lal[i];
       const double wi = lsw[i];
-      const double wc = (cnt < M) ? __ddiv_rn(wi, (double)c) : wi;
+      double wc = wi;
+      if (cnt < M && c > 1)
+        wc = exact ? __longlong_as_double((long long)ex_div_small((unsigned long long)bits(wi), (unsigned)c, magic[c]))
+                   : __ddiv_rn(wi, (double)c);
       for (int q = 0; q < c; ++q) {
         W2[out0 + off + q] = wc;
         P2[out0 + off + q] = si;

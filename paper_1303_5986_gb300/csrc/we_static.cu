@@ -121,6 +121,7 @@ extern "C" we_status we_resample_static(int32_t n, const int32_t *bins, const do
   E.cap = capacity;
   E.S = 1;
   E.m_targ = m_targ;
+  E.div_magic = nullptr;                                 // the floating-point split/merge path
   E.record_iters = 0;                       // nothing is recorded
   E.first_iter = iter;
   E.seed = seed;
