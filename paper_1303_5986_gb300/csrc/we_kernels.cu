@@ -136,7 +136,7 @@ __device__ __forceinline__ bool key_lt(long long wa, int sa, long long wb, int s
 // The resampled walkers are written in slot order, copies right after their parent, at the
 // bin's output offset.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 4) k_resample(EnsView E, int n_bins) {
+__global__ void __launch_bounds__(128, 4) k_resample(EnsView E, int n_bins, int gather) {
   const int r = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -371,6 +371,13 @@ __global__ void __launch_bounds__(128, 4) k_resample(EnsView E, int n_bins) {
         W2[out0 + off + q] = wc;
         P2[out0 + off + q] = si;
       }
+      if (gather) {                                         // the copies' species counts
+        const int ld = E.R * E.cap;
+        for (int sp = 0; sp < E.S; ++sp) {
+          const int32_t v = E.x[par][(size_t)sp * ld + base + si];
+          for (int q = 0; q < c; ++q) E.x[par ^ 1][(size_t)sp * ld + base + out0 + off + q] = v;
+        }
+      }
       // the c copies' weight, c * wc rounded once (the exact sum of the copies, rounded)
       wsum_local = __dadd_rn(wsum_local, c == 1 ? wc : __dmul_rn((double)c, wc));
     }
@@ -457,6 +464,12 @@ __global__ void k_pack_states(EnsView E, int r, int32_t *out) {
 // ------------------------------------------------------------------------------------------
 // Host-side launch helpers (called from we_host.cu).
 // ------------------------------------------------------------------------------------------
+// Networks of up to kGatherInResample species have their species counts copied by the
+// split/merge warps; larger ones by k_gather, whose loads are coalesced across walkers.
+constexpr int kGatherInResample = 8;
+
+bool gather_in_resample(const EnsView &E) { return E.S <= kGatherInResample && E.x[0] != nullptr; }
+
 cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st) {
   const EnsView &E = prm.ens;
   const int nb = prm.bins.n_bins;
@@ -469,16 +482,18 @@ cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st) {
   int bx = (per_run_tasks + 3) / 4;                 // 4 warps per block
   if (bx > 64) bx = 64;
   if (bx < 1) bx = 1;
-  k_resample<<<dim3(bx, E.R), 128, 0, st>>>(E, nb);
+  k_resample<<<dim3(bx, E.R), 128, 0, st>>>(E, nb, gather_in_resample(E) ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st) {
   const EnsView &E = prm.ens;
-  const int ld = E.R * E.cap;
-  int grid = (ld + 255) / 256;
-  if (grid > 152 * 8) grid = 152 * 8;
-  k_gather<<<grid, 256, 0, st>>>(E, prm.resample);
+  if (!(prm.resample && gather_in_resample(E))) {
+    const int ld = E.R * E.cap;
+    int grid = (ld + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    k_gather<<<grid, 256, 0, st>>>(E, prm.resample);
+  }
   k_finalize<<<1, 256, 0, st>>>(E, prm.resample);
   return cudaGetLastError();
 }
