@@ -13,6 +13,11 @@ timed on this host, and an end-to-end figure through the one-call C ABI with hos
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+`--workload toggle_batch` times the batched toggle-switch sweep (64 runs with their own rate
+constants in one launch per phase, general FP64 SSA kernel) and `--workload synthetic_large`
+the random 354-species / 3680-reaction network (one warp per walker), each printing one JSON
+line of the same form with an FP64 roofline for its SSA kernel.
+
 `--workload toggle_learned` instead compares, on one GPU, the GPU time that plain species-count
 binning and the learned progress coordinate need to reach a 10% MFPT error on a bistable
 two-gene toggle switch (a_U = a_V = 40, K = 1, n = 2, d = 1; exact MFPT from the truncated
@@ -60,7 +65,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the SSA kernel (0: auto)")
-    ap.add_argument("--workload", choices=["schlogl", "toggle_learned"], default="schlogl")
+    ap.add_argument("--workload", choices=["schlogl", "toggle_learned", "toggle_batch", "synthetic_large"],
+                    default="schlogl")
     ap.add_argument("--plain-iters", type=int, default=120000, help="toggle_learned: plain-binning iterations")
     ap.add_argument("--learned-iters", type=int, default=2000, help="toggle_learned: learned-binning iterations")
     return ap.parse_args()
@@ -355,6 +361,110 @@ def run_toggle_learned(a):
 
 
 # ------------------------------------------------------------------------------------------
+# the batched toggle sweep and the large synthetic network (general FP64 SSA kernels)
+# ------------------------------------------------------------------------------------------
+FP64_PEAK_GOPS = 152 * 2 * 2.07      # 152 SMs x 2 FP64 lanes/clock x 2.07 GHz (FMA = one op)
+
+
+def fp64_ops_per_event(spec, dep_degree):
+    """FP64 operations one direct-method event needs on the general path: the propensities the
+    dependency graph says change (mass action: one product; Hill: power, sum, quotient), their
+    tree paths (log2 P additions each), the target product, the descent (log2 P), the
+    reciprocal of a0 and the two clock operations.  Small networks re-evaluate every leaf."""
+    import math
+    import numpy as np
+    P = 1 << max(0, math.ceil(math.log2(max(1, spec.n_reactions))))
+    L = int(math.log2(P))
+    hill = np.asarray(spec.rate_law) == 1
+    per_leaf = float(np.mean(np.where(hill, 3.0, 1.0)))
+    deg = float(np.mean(dep_degree)) if dep_degree is not None else float(spec.n_reactions)
+    if dep_degree is None:                                # full rebuild: P leaves + P - 1 nodes
+        return per_leaf * spec.n_reactions + (P - 1) + 1 + L + 1 + 2
+    return deg * (per_leaf + L) + 1 + L + 1 + 2
+
+
+def run_batch_workload(a):
+    import numpy as np
+    import torch
+    import paper_1303_5986_gb300 as P
+    import workloads as W
+    from paper_1303_5986_gb300 import build as pbuild
+
+    pbuild.build()
+    if a.workload == "toggle_batch":
+        n_iters = 500
+        mk = lambda seed: W.toggle_batch_we(n_runs=64, n_iters=n_iters, seed=seed)
+        desc = ("batched two-gene toggle sweep: 64 runs, a_U, a_V uniform in [20,60], K=1, n=2, d=1; "
+                "30x30 bins of width 4 x 8 walkers, tau=0.1, 500 iterations, recycling into "
+                "{V>=a_V/2, U<=a_U/4}, one launch per phase for all runs")
+    else:
+        n_iters = 100
+        mk = lambda seed: W.synthetic_large_we(n_walkers=4096, n_iters=n_iters, seed=seed)
+        desc = ("synthetic 354-species / 3680-reaction network (seed 7): 4096 walkers, counts "
+                "uniform in [0,200], 50 bins of width 4 on species 0 x 82 walkers, tau=0.01, "
+                "100 iterations, one warp per walker")
+    base = mk(0)
+    net = P.network_from_spec(base.network)
+    bm = P.we_binmap_grid(base.bins.species, base.bins.edges)
+    deg = None if a.workload == "toggle_batch" else [net.dep_degree(j) for j in range(net.n_reactions)]
+    seeds = rank_seeds(0, a.warmup + a.steps)
+
+    def ensemble(seed):
+        c, keep = P.run_config_from(mk(seed), record_iters=n_iters)
+        return P.we_ensemble_create(net, bm, c, keep)
+
+    warm = [ensemble(s) for s in seeds[:a.warmup]]
+    timed = [ensemble(s) for s in seeds[a.warmup:]]
+    for e in warm:
+        e.step(n_iters)
+        e.sync()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    step_ms, prop_ms = [], []
+    torch.cuda.synchronize()
+    clocks.start()
+    for e in timed:
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pm = e.step_timed(n_iters)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        prop_ms.append(pm)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    events = float(sum(int(e.per_iter(P.WE_OUT_EVENTS).sum()) for e in timed))
+    status = [int(x) for e in timed for x in e.status()]
+    total_ms = float(sum(step_ms))
+    prop_total_ms = float(sum(p.sum() for p in prop_ms))
+    n_launch = sum(len(p) for p in prop_ms)
+    ops = fp64_ops_per_event(base.network, deg)
+    achieved = ops * events / (prop_total_ms * 1e-3) / 1e9
+    mapping = "warp per walker (k_propagate_warp)" if a.workload == "synthetic_large" else \
+        "thread per walker, warp-specialised draws (k_propagate_ws<8,3>)"
+    line = {
+        "metric": "SSA events/sec and WE iterations/sec on 1 GB300",
+        "value": events / (total_ms * 1e-3), "unit": "SSA events/s", "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "iterations": n_iters, "l2": "flushed between timed steps (256 MB write)"},
+        "we_iters_per_s": a.steps * n_iters / (total_ms * 1e-3),
+        "status": sorted(set(status)),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "G FP64 ops/s",
+                     "frac": achieved / FP64_PEAK_GOPS, "traffic": None, "kernel": mapping,
+                     "launches": n_launch, "avg_launch_ms": prop_total_ms / max(n_launch, 1),
+                     "share_of_step": prop_total_ms / total_ms, "fp64_ops_per_event": ops,
+                     "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": 6 * n_iters * a.steps, "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------
 # ranks: every rank runs its own replicas (weak scaling, no data-path collective); the job's
 # figures are the slowest rank's time and the sum of every rank's work
 # ------------------------------------------------------------------------------------------
@@ -386,6 +496,13 @@ def combine_ranks(dist, device, total_ms: float, events: float, flux_per_replica
 # ------------------------------------------------------------------------------------------
 def main():
     a = parse()
+    if a.workload in ("toggle_batch", "synthetic_large"):
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm is timed on the "
+                              "default Schloegl workload only"}))
+            return
+        run_batch_workload(a)
+        return
     if a.workload == "toggle_learned":
         if a.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the learned-binning comparison has no CPU "
