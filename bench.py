@@ -445,7 +445,7 @@ def run_batch_workload(a):
     ops = fp64_ops_per_event(base.network, deg)
     achieved = ops * events / (prop_total_ms * 1e-3) / 1e9
     mapping = "warp per walker (k_propagate_warp)" if a.workload == "synthetic_large" else \
-        "thread per walker, warp-specialised draws (k_propagate_ws<8,3>)"
+        "state chain / clock / draw warps on a two-species (U, V) table (k_propagate_pipe<8,3,2>)"
     line = {
         "metric": "SSA events/sec and WE iterations/sec on 1 GB300",
         "value": events / (total_ms * 1e-3), "unit": "SSA events/s", "n_gpus": 1, "steps": a.steps,

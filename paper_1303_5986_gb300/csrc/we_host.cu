@@ -23,8 +23,8 @@ cudaError_t launch_propagate_thread(const PropagateParams &prm, int block, bool 
 cudaError_t launch_propagate_ws(const PropagateParams &prm, bool table, cudaStream_t st);
 cudaError_t launch_propagate_warp(const PropagateParams &prm, int block, cudaStream_t st);
 cudaError_t launch_init_log_tables(LogTables *T, cudaStream_t st);
-cudaError_t launch_build_table(const NetView &N, const int32_t *base, int species, int len, double clock_scale,
-                               unsigned long long *rows, cudaStream_t st);
+cudaError_t launch_build_table(const NetView &N, const int32_t *base, int species, int species2, int len,
+                               int lenB, double clock_scale, unsigned long long *rows, cudaStream_t st);
 size_t propagate_warp_smem(const NetView &N, int block);
 cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st);
@@ -86,7 +86,8 @@ struct we_network {
   std::vector<int32_t> d_sp, d_val;
   std::vector<int32_t> dep_ptr, dep_idx;
   std::vector<int32_t> fixed;       // S
-  int32_t table_species = -1;       // the one species every propensity reads (-1: none)
+  int32_t table_species = -1;       // the species every propensity reads (-1: no tables) ...
+  int32_t table_species2 = -1;      // ... and a second one (two-species tables; -1: one species)
 };
 
 static long long binom_small_h(long long x, int m) {
@@ -217,15 +218,17 @@ extern "C" we_status we_network_create(int32_t S, int32_t M, const int32_t *reac
     n->dep_idx.insert(n->dep_idx.end(), d.begin(), d.end());
   }
   n->dep_ptr[P] = (int32_t)n->dep_idx.size();
-  // State-indexed tables apply when one dynamic species is the only one any propensity reads
-  // and the only one any reaction changes.
-  int ts = -1;
-  bool ok = true;
-  for (int j = 0; j < M && ok; ++j) {
-    for (int sp : reads[j]) { if (ts < 0) ts = sp; ok = ok && sp == ts; }
-    for (int sp : changes[j]) { if (ts < 0) ts = sp; ok = ok && sp == ts; }
+  // State-indexed tables apply when one or two dynamic species are the only ones any
+  // propensity reads and any reaction changes.
+  std::set<int32_t> touched;
+  for (int j = 0; j < M; ++j) {
+    touched.insert(reads[j].begin(), reads[j].end());
+    touched.insert(changes[j].begin(), changes[j].end());
   }
-  n->table_species = (ok && ts >= 0) ? ts : -1;
+  if (touched.size() == 1 || touched.size() == 2) {
+    n->table_species = *touched.begin();
+    if (touched.size() == 2) n->table_species2 = *touched.rbegin();
+  }
   *out = n;
   return WE_OK;
 }
@@ -325,21 +328,32 @@ struct Offsets {
   size_t flux, totw, nw, events, hist, pack;
   size_t logt, table, base;
   size_t lw1, lw2, lw3, lb, lz, zout;
-  int32_t table_len;
+  int32_t table_len, table_lenB;
   size_t total;
 };
 
-static int table_len_for(const we_network *n) {
+// Counts covered by the state-indexed table: `len` values of the first species (and `lenB` of
+// the second for two-species tables), at most 64 MB over all parameter sets.  0: no table.
+static int table_len_for(const we_network *n, int *lenB_out = nullptr) {
+  if (lenB_out) *lenB_out = 1;
   if (n->table_species < 0 || n->P > kThreadMaxLeaves || n->S > kThreadMaxSpecies) return 0;
-  int len = 4096;
-  while (len > 256 && (size_t)n->nps * len * n->P * 8 > (64u << 20)) len >>= 1;
-  return len;
+  const size_t budget = 64u << 20, row = (size_t)n->P * 8;
+  if (n->table_species2 < 0) {
+    int len = 4096;
+    while (len > 256 && (size_t)n->nps * len * row > budget) len >>= 1;
+    return len;
+  }
+  int L = 256;
+  while (L > 32 && (size_t)n->nps * L * L * row > budget) L >>= 1;
+  if ((size_t)n->nps * L * L * row > budget) return 0;
+  if (lenB_out) *lenB_out = L;
+  return L;
 }
 
 static Offsets layout(const we_network *n, const we_binmap *b, const we_run_config *c, int cap) {
   Layout L;
   Offsets o{};
-  o.table_len = table_len_for(n);
+  o.table_len = table_len_for(n, &o.table_lenB);
   o.logt = L.take(sizeof(LogTables));
   if (b->learned) {
     const we_learned_bins &lb = b->lb;
@@ -350,7 +364,7 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
     o.lz = L.take(4 * lb.zedges.size());
     o.zout = L.take(4 * (size_t)c->n_runs * (size_t)cap);
   }
-  o.table = L.take((size_t)n->nps * o.table_len * n->P * 8);
+  o.table = L.take((size_t)n->nps * o.table_len * o.table_lenB * n->P * 8);
   o.base = L.take(4 * (size_t)n->S);
   const size_t R = c->n_runs, RC = R * cap, rec = c->record_iters;
   o.meta = L.take(sizeof(RxnMeta) * n->P);
@@ -646,13 +660,18 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   E->prm.resample = c->resample ? 1 : 0;
   E->prm.logt = at<LogTables>(ws, o.logt);
   E->prm.tab.species = -1;
+  E->prm.tab.species2 = -1;
+  E->prm.tab.lenB = 1;
   E->prm.tab.smem_rows = 0;
   if (mapping == WE_MAP_THREAD_TABLE) {
     E->prm.tab.rows = at<unsigned long long>(ws, o.table);
     E->prm.tab.len = o.table_len;
+    E->prm.tab.lenB = o.table_lenB;
     E->prm.tab.species = n->table_species;
+    E->prm.tab.species2 = n->table_species2;
     E->prm.tab.clock_scale = std::ldexp(1.0 / c->tau, kClockBits);   // 2^62 / tau
-    e = launch_build_table(N, at<int32_t>(ws, o.base), n->table_species, o.table_len,
+    e = launch_build_table(N, at<int32_t>(ws, o.base), n->table_species, n->table_species2,
+                           o.table_len, o.table_lenB,
                            E->prm.tab.clock_scale, at<unsigned long long>(ws, o.table), s);
   }
   e = e ? e : cudaStreamSynchronize(s);

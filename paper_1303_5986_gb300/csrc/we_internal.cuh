@@ -130,13 +130,16 @@ struct LogTables {
 constexpr int kClockBits = 62;
 constexpr long long kClockTau = 1ll << kClockBits;
 
-// State-indexed table: per parameter set, `len` rows of P 64-bit words:
+// State-indexed table: per parameter set, len x lenB rows of P 64-bit words, row x * lenB + y
+// for count x of `species` and count y of `species2` (lenB = 1, y = 0 for one species):
 //   word 0      float-float (2^62 / tau) / a0 (hi in the low half; 0 when a0 = 0)
 //   words 1..   the P-1 breakpoints b_i on the 52-bit uniform index (see k_build_table)
 struct TableView {
   const unsigned long long *rows;
-  int32_t len;                 // counts covered; larger counts are evaluated directly
-  int32_t species;             // the one species the propensities read (-1: no tables)
+  int32_t len;                 // counts of `species` covered; larger counts are evaluated directly
+  int32_t lenB;                // counts of `species2` covered (1 without a second species)
+  int32_t species;             // the species the propensities read (-1: no tables)
+  int32_t species2;            // the second one (-1: one-species table)
   int32_t smem_rows;           // rows a block of the warp-specialised kernel stages in shared memory
   double clock_scale;          // 2^62 / tau, for rows evaluated on the fly
 };

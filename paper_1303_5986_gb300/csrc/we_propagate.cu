@@ -69,20 +69,22 @@ __device__ __forceinline__ float2 wait_scale(double a0, double clock_scale) {
 }
 
 template <int P, int LOG2P>
-__global__ void k_build_table(NetView N, const int32_t *base, int species, int len, double clock_scale,
-                              unsigned long long *rows) {
+__global__ void k_build_table(NetView N, const int32_t *base, int species, int species2, int len, int lenB,
+                              double clock_scale, unsigned long long *rows) {
   const int ps = blockIdx.y;
-  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < len; x += gridDim.x * blockDim.x) {
+  const int n_rows = len * lenB;                             // row x = count of species * lenB + count of species2
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n_rows; x += gridDim.x * blockDim.x) {
     int32_t xs[kThreadMaxSpecies];
     for (int s = 0; s < N.S; ++s) xs[s] = base[s];
-    xs[species] = x;
+    xs[species] = x / lenB;
+    if (species2 >= 0) xs[species2] = x % lenB;
     double nd[2 * P];
 #pragma unroll
     for (int j = 0; j < P; ++j)
       nd[P + j] = propensity(N.meta[j], N.keff[ps * P + j], N.hill_Kn[ps * P + j], xs, 1);
 #pragma unroll
     for (int k = P - 1; k >= 1; --k) nd[k] = __dadd_rn(nd[2 * k], nd[2 * k + 1]);
-    unsigned long long *row = rows + ((size_t)ps * len + x) * P;
+    unsigned long long *row = rows + ((size_t)ps * n_rows + x) * P;
     row[0] = pack_ff(wait_scale(nd[1], clock_scale));
     for (int i = 1; i < P; ++i) {
       unsigned long long lo = 0, hi = 1ull << 52;            // m = 2^52 stands for "never"
@@ -312,11 +314,15 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
   const TableView &TV = prm.tab;
   const int B = blockDim.x, tid = threadIdx.x;
   int32_t *s_dx = sm.xs + E.S * B;                   // net change of the table species, per reaction
+  int32_t *s_dy = s_dx + P;                           // ... and of the second one
   for (int j = tid; j < P; j += B) {
-    int dx = 0;
-    for (int q = sm.meta[j].d_begin; q < sm.meta[j].d_end; ++q)
+    int dx = 0, dy = 0;
+    for (int q = sm.meta[j].d_begin; q < sm.meta[j].d_end; ++q) {
       if (sm.dsp[q] == TV.species) dx += sm.dval[q];
+      if (sm.dsp[q] == TV.species2) dy += sm.dval[q];
+    }
     s_dx[j] = dx;
+    s_dy[j] = dy;
   }
   __syncthreads();
   const int iter = *E.iter;
@@ -333,19 +339,19 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
   const int ps = E.param_set[r];
   const double *keff = sm.keff + ps * P;
   const double *Kn = sm.Kn + ps * P;
-  const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * P;
+  const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * TV.lenB * P;
   const uint32_t k0 = (uint32_t)E.seed;
   const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
-  const int sx = TV.species;
+  const int sx = TV.species, sy = TV.species2;
 
   TableRow<P, LOG2P> row;
   double fb[2 * P];
-  auto load_row = [&](int xv) {
-    if (xv < TV.len) row.read(tab + (size_t)xv * P);
+  auto load_row = [&](int xv, int yv) {           // xme holds the current counts
+    if (xv < TV.len && yv < TV.lenB) row.read(tab + ((size_t)xv * TV.lenB + yv) * P);
     else row.evaluate(fb, sm.meta, keff, Kn, xme, B, TV.clock_scale);
   };
-  int x = xme[sx * B];
-  load_row(x);
+  int x = xme[sx * B], y = sy >= 0 ? xme[sy * B] : 0;
+  load_row(x, y);
 
   long long clk = 0;
   long long nev = 0;
@@ -360,18 +366,22 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
     long long dt;
     if (!wait_units(e, row.w, dt) || clk + dt > kClockTau) break;   // next event after tau
     if (nev >= E.max_steps) { status = kStatusStepCap; break; }
-    const int nx = x + s_dx[row.select(m2, fb)];
-    if (nx > kMaxCount) { status = kStatusOverflow; break; }
+    const int j = row.select(m2, fb);
+    const int nx = x + s_dx[j], ny = sy >= 0 ? y + s_dy[j] : 0;
+    if (nx > kMaxCount || ny > kMaxCount) { status = kStatusOverflow; break; }
     x = nx;
+    y = ny;
     xme[sx * B] = x;
+    if (sy >= 0) xme[sy * B] = y;
     ++nev;
     clk += dt;
     if (E.feedback && in_target(E, r, xme, B)) {
       ++nrec;
       for (int s = 0; s < E.S; ++s) xme[s * B] = E.recycle[r * E.S + s];
       x = xme[sx * B];
+      y = sy >= 0 ? xme[sy * B] : 0;
     }
-    load_row(x);
+    load_row(x, y);
   }
   finish_walker(prm, r, g, par, xme, B, clock_time(clk, E.tau), nev, nrec, status);
 }
@@ -398,10 +408,15 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
       (reinterpret_cast<uintptr_t>(sm.xs + E.S * W) + 15) & ~(uintptr_t)15);   // [2][kRoundDraws][W]
   float2 *qe = reinterpret_cast<float2 *>(qm + 2 * kRoundDraws * W);            // [2][kRoundDraws][W]
   __shared__ int s_more;
+  // Persistent blocks: each takes groups of 32 walkers (vb) until every live walker is served,
+  // so the shared prologue above is paid once per resident block, not once per capacity slot.
+  const int n_live_all = E.run_off[E.R];
+  for (int vb = blockIdx.x; vb * 32 < n_live_all; vb += gridDim.x) {
+  __syncthreads();                                       // the previous group's buffers are free
 
   const int iter = *E.iter;
   const int total = E.run_off[E.R];
-  const int f = blockIdx.x * W + lane;
+  const int f = vb * W + lane;
   const bool live = f < total;
   const int r = !live ? 0 : (E.R == 1 ? 0 : find_run(E.run_off, E.R, f));
   const int w = live ? f - E.run_off[r] : 0;
@@ -494,6 +509,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
     __syncthreads();                                      // s_more is rewritten next round
   }
   if (warp == 0 && live) finish_walker(prm, r, g, par, xme, W, t, nev, nrec, status);
+  }
 }
 
 // Off-table rows: the canonical tree evaluated on the fly (counts beyond the table), kept out
@@ -527,7 +543,7 @@ __device__ __forceinline__ int descend_row(const double *fb, unsigned long long 
 // run one round past a walker's end (that work is discarded).  The committed arithmetic is
 // the same as the serial loop's: the same reaction for each draw, the same waiting time, the
 // same order of clock additions.
-template <int P, int LOG2P>
+template <int P, int LOG2P, int D>
 __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Smem sm = load_smem<P>(prm, smem_raw);
@@ -535,27 +551,37 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
   const TableView &TV = prm.tab;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int W = 32, K = kRoundDraws;
-  int32_t *s_dx = sm.xs + E.S * W;                                       // P
+  int32_t *s_dx = sm.xs + E.S * W;                                       // P (species)
+  int32_t *s_dy = s_dx + P;                                              // P (species2)
   unsigned long long *qm = reinterpret_cast<unsigned long long *>(
-      (reinterpret_cast<uintptr_t>(s_dx + P) + 15) & ~(uintptr_t)15);    // [3][K][W]
+      (reinterpret_cast<uintptr_t>(s_dy + P) + 15) & ~(uintptr_t)15);    // [3][K][W]
   float2 *qe = reinterpret_cast<float2 *>(qm + 3 * K * W);              // [3][K][W]
   float2 *sw = qe + 3 * K * W;                                          // [2][K][W] wait scales
   int32_t *sx = reinterpret_cast<int32_t *>(sw + 2 * K * W);            // [2][K][W] counts
-  uint32_t *sfl = reinterpret_cast<uint32_t *>(sx + 2 * K * W);         // [2][3][W] flag masks
+  int32_t *sy = sx + 2 * K * W;                                         // [2][K][W] (species2)
+  uint32_t *sfl = reinterpret_cast<uint32_t *>(sy + 2 * K * W);         // [2][3][W] flag masks
   unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(
       (reinterpret_cast<uintptr_t>(sfl + 2 * 3 * W) + 15) & ~(uintptr_t)15);
   __shared__ int s_more[2], s_win, s_win_n;
   __shared__ int s_done[2][W];
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
-    int dx = 0;
-    for (int q = sm.meta[j].d_begin; q < sm.meta[j].d_end; ++q)
+    int dx = 0, dy = 0;
+    for (int q = sm.meta[j].d_begin; q < sm.meta[j].d_end; ++q) {
       if (sm.dsp[q] == TV.species) dx += sm.dval[q];
+      if (sm.dsp[q] == TV.species2) dy += sm.dval[q];
+    }
     s_dx[j] = dx;
+    s_dy[j] = dy;
   }
+  // Persistent blocks: each takes groups of 32 walkers (vb) until every live walker is served,
+  // so the shared prologue above is paid once per resident block, not once per capacity slot.
+  const int n_live_all = E.run_off[E.R];
+  for (int vb = blockIdx.x; vb * 32 < n_live_all; vb += gridDim.x) {
+  __syncthreads();                                       // the previous group's buffers are free
 
   const int iter = *E.iter;
   const int total = E.run_off[E.R];
-  const int f = blockIdx.x * W + lane;
+  const int f = vb * W + lane;
   const bool live = f < total;
   const int r = !live ? 0 : (E.R == 1 ? 0 : find_run(E.run_off, E.R, f));
   const int w = live ? f - E.run_off[r] : 0;
@@ -566,11 +592,11 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
   const int par = iter & 1;
   const int ld = E.R * E.cap;
   const int ps = live ? E.param_set[r] : 0;
-  const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * P;
+  const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * TV.lenB * P;
 
   // table rows for a window of counts around this block's walkers, in shared memory
   int win_lo = 0, win_n = 0;
-  if (TV.smem_rows > 0) {
+  if (D == 1 && TV.smem_rows > 0) {
     if (warp == 0) {
       int lo = 0x7fffffff, hi = -1;
       if (live) lo = hi = E.x[par][(size_t)TV.species * ld + g];
@@ -590,7 +616,7 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
     if (s_win >= 0) {
       win_lo = s_win;
       win_n = s_win_n;
-      const int ps0 = E.param_set[E.R == 1 ? 0 : find_run(E.run_off, E.R, blockIdx.x * W)];
+      const int ps0 = E.param_set[E.R == 1 ? 0 : find_run(E.run_off, E.R, vb * W)];
       const unsigned long long *src = TV.rows + ((size_t)ps0 * TV.len + win_lo) * P;
       for (int i = threadIdx.x; i < win_n * P; i += blockDim.x) s_tab[i] = src[i];
     }
@@ -617,37 +643,43 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
   const double *keff = sm.keff + ps * P;
   const double *Kn = sm.Kn + ps * P;
   // warp 0: the speculative state chain
-  int x = 0, dxr[P];
+  int x = 0, y = 0, dxr[P], dyr[P];                      // y: count of species2 (D = 2)
   TableRow<P, LOG2P> row;
   double fb[2 * P];
   int xlo = -1, xhi = kMaxCount + 1, xrec = 0;
+  int ylo = -1, yhi = kMaxCount + 1, yrec = 0;
   bool ok = false, ok_rec = false;
-  auto load_row = [&](int xv) {
+  auto in_table = [&](int xv, int yv) { return xv < TV.len && (D == 1 || yv < TV.lenB); };
+  auto table_row = [&](int xv, int yv) { return tab + ((size_t)xv * TV.lenB + (D == 2 ? yv : 0)) * P; };
+  auto load_row = [&](int xv, int yv) {
     const unsigned off = (unsigned)(xv - win_lo);
-    if (off < (unsigned)win_n) {
+    if (D == 1 && off < (unsigned)win_n) {
       row.read(s_tab + (size_t)off * P);
-    } else if (xv < TV.len) {
-      row.read(tab + (size_t)xv * P);
+    } else if (in_table(xv, yv)) {
+      row.read(table_row(xv, yv));
     } else {
       xme[TV.species * W] = xv;
+      if (D == 2) xme[TV.species2 * W] = yv;
       row.w = evaluate_row<P, LOG2P>(fb, sm.meta, keff, Kn, xme, W, TV.clock_scale);
       row.direct = true;
     }
   };
   // warp 1: the committed walker
   long long clk = 0, nev = 0;
-  int xc = 0, nrec = 0, status = 0;
+  int xc = 0, yc = 0, nrec = 0, status = 0;
   bool done = !live, recycled = false;
   if (live && warp <= 1) {
     if (warp == 0)
       for (int s = 0; s < E.S; ++s) xme[s * W] = E.x[par][(size_t)s * ld + g];
     xc = E.x[par][(size_t)TV.species * ld + g];
+    if (D == 2) yc = E.x[par][(size_t)TV.species2 * ld + g];
   }
   __syncthreads();
   if (warp == 0 && live) {
 #pragma unroll
-    for (int j = 0; j < P; ++j) dxr[j] = s_dx[j];
+    for (int j = 0; j < P; ++j) { dxr[j] = s_dx[j]; dyr[j] = s_dy[j]; }
     x = xc;
+    y = yc;
     if (E.feedback) {
       ok = true;
       ok_rec = true;
@@ -656,6 +688,8 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
         const int sp = E.tgt_species[c];
         if (sp == TV.species) {
           if (E.tgt_op[c] == 0) xlo = max(xlo, thr); else xhi = min(xhi, thr);
+        } else if (D == 2 && sp == TV.species2) {
+          if (E.tgt_op[c] == 0) ylo = max(ylo, thr); else yhi = min(yhi, thr);
         } else {
           const int v = xme[sp * W], vr = E.recycle[r * E.S + sp];
           ok = ok && (E.tgt_op[c] == 0 ? v >= thr : v <= thr);
@@ -663,8 +697,9 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
         }
       }
       xrec = E.recycle[r * E.S + TV.species];
+      if (D == 2) yrec = E.recycle[r * E.S + TV.species2];
     }
-    load_row(x);
+    load_row(x, y);
   }
 
   for (int p = 0;; ++p) {
@@ -679,29 +714,33 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
           sw[(sb * K + k) * W + lane] = row.w;
           if (row.idle()) idle_m |= 1u << k;
           const int j = (!fast && row.direct) ? descend_row<P, LOG2P>(fb, m2) : row.select_table(m2);
-          int dx = dxr[0];
+          int dx = dxr[0], dy = dyr[0];
 #pragma unroll
-          for (int i = 1; i < P; ++i) dx = (j == i) ? dxr[i] : dx;
-          int nx = x + dx;
-          if (nx > kMaxCount) { ovf_m |= 1u << k; nx = x; }
-          if (E.feedback && ok && nx >= xlo && nx <= xhi) { rec_m |= 1u << k; nx = xrec; ok = ok_rec; }
+          for (int i = 1; i < P; ++i) { dx = (j == i) ? dxr[i] : dx; dy = (j == i) ? dyr[i] : dy; }
+          int nx = x + dx, ny = D == 2 ? y + dy : 0;
+          if (nx > kMaxCount || ny > kMaxCount) { ovf_m |= 1u << k; nx = x; ny = y; }
+          if (E.feedback && ok && nx >= xlo && nx <= xhi && (D == 1 || (ny >= ylo && ny <= yhi))) {
+            rec_m |= 1u << k; nx = xrec; ny = yrec; ok = ok_rec;
+          }
           sx[(sb * K + k) * W + lane] = nx;
+          if (D == 2) sy[(sb * K + k) * W + lane] = ny;
           x = nx;
+          y = ny;
         };
         int k = 0;
         if (!row.direct) {
           // the first draw after which the count leaves the table (its later draws in this
           // loop ran on a stale row and are redone below from the state saved here)
           int out_at = K;
-          int x_out = 0;
+          int x_out = 0, y_out = 0;
           bool ok_out = false;
 #pragma unroll
           for (int kk = 0; kk < K; ++kk) {
             step(kk, true);
             const unsigned off = (unsigned)(x - win_lo);
-            if (off < (unsigned)win_n) row.read(s_tab + (size_t)off * P);
-            else if (x < TV.len) row.read(tab + (size_t)x * P);
-            else if (out_at == K) { out_at = kk; x_out = x; ok_out = ok; }
+            if (D == 1 && off < (unsigned)win_n) row.read(s_tab + (size_t)off * P);
+            else if (in_table(x, y)) row.read(table_row(x, y));
+            else if (out_at == K) { out_at = kk; x_out = x; y_out = y; ok_out = ok; }
           }
           k = K;
           if (out_at < K) {
@@ -710,14 +749,15 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
             ovf_m &= keep;
             rec_m &= keep;
             x = x_out;
+            y = y_out;
             ok = ok_out;
-            load_row(x);
+            load_row(x, y);
             k = out_at + 1;
           }
         }
         for (; k < K; ++k) {                                // rows beyond the table
           step(k, false);
-          load_row(x);
+          load_row(x, y);
         }
         sfl[(sb * 3 + 0) * W + lane] = idle_m;
         sfl[(sb * 3 + 1) * W + lane] = ovf_m;
@@ -761,7 +801,10 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
           nev += kstop;
           nrec += __popc(rec_m & fired);
           recycled = recycled || (rec_m & fired) != 0u;
-          if (kstop > 0) xc = sx[(pb * K + kstop - 1) * W + lane];
+          if (kstop > 0) {
+            xc = sx[(pb * K + kstop - 1) * W + lane];
+            if (D == 2) yc = sy[(pb * K + kstop - 1) * W + lane];
+          }
           if (kstop < K) {
             done = true;
             const uint32_t bit = 1u << kstop;
@@ -785,14 +828,16 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
     if (recycled)                                        // the other species take the recycle state
       for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
     xme[TV.species * W] = xc;
+    if (D == 2) xme[TV.species2 * W] = yc;
     finish_walker(prm, r, g, par, xme, W, clock_time(clk, E.tau), (long long)nev, nrec, status);
+  }
   }
 }
 
 size_t propagate_thread_smem(const NetView &N, int block, bool table) {
   return sizeof(LogTables) + (size_t)N.P * sizeof(RxnMeta) +
          2 * (size_t)N.n_param_sets * N.P * sizeof(double) + 2 * (size_t)N.n_delta * sizeof(int32_t) +
-         (size_t)N.S * block * sizeof(int32_t) + (table ? (size_t)N.P * sizeof(int32_t) : 0);
+         (size_t)N.S * block * sizeof(int32_t) + (table ? 2 * (size_t)N.P * sizeof(int32_t) : 0);
 }
 
 static size_t smem_prologue(const NetView &N) {
@@ -806,9 +851,9 @@ size_t propagate_ws_smem(const NetView &N) {
 }
 
 size_t propagate_pipe_smem(const NetView &N, int table_rows) {
-  return smem_prologue(N) + (size_t)N.P * sizeof(int32_t) + 16 +
+  return smem_prologue(N) + 2 * (size_t)N.P * sizeof(int32_t) + 16 +
          3 * (size_t)kRoundDraws * 32 * (sizeof(unsigned long long) + sizeof(float2)) +
-         2 * (size_t)kRoundDraws * 32 * (sizeof(float2) + sizeof(int32_t)) + 2 * 3 * 32 * sizeof(uint32_t) + 16 +
+         2 * (size_t)kRoundDraws * 32 * (sizeof(float2) + 2 * sizeof(int32_t)) + 2 * 3 * 32 * sizeof(uint32_t) + 16 +
          (size_t)table_rows * N.P * sizeof(unsigned long long);
 }
 
@@ -818,21 +863,24 @@ cudaError_t launch_init_log_tables(LogTables *T, cudaStream_t st) {
 }
 
 template <int P, int L>
-static cudaError_t build_table_p(const NetView &N, const int32_t *base, int species, int len,
-                                 double clock_scale, unsigned long long *rows, cudaStream_t st) {
-  dim3 grid((len + 127) / 128, N.n_param_sets);
-  k_build_table<P, L><<<grid, 128, 0, st>>>(N, base, species, len, clock_scale, rows);
+static cudaError_t build_table_p(const NetView &N, const int32_t *base, int species, int species2, int len,
+                                 int lenB, double clock_scale, unsigned long long *rows, cudaStream_t st) {
+  const int n_rows = len * lenB;
+  int gx = (n_rows + 127) / 128;
+  if (gx > 4096) gx = 4096;
+  dim3 grid(gx, N.n_param_sets);
+  k_build_table<P, L><<<grid, 128, 0, st>>>(N, base, species, species2, len, lenB, clock_scale, rows);
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_table(const NetView &N, const int32_t *base, int species, int len,
-                               double clock_scale, unsigned long long *rows, cudaStream_t st) {
+cudaError_t launch_build_table(const NetView &N, const int32_t *base, int species, int species2, int len,
+                               int lenB, double clock_scale, unsigned long long *rows, cudaStream_t st) {
   switch (N.P) {
-    case 1: return build_table_p<1, 0>(N, base, species, len, clock_scale, rows, st);
-    case 2: return build_table_p<2, 1>(N, base, species, len, clock_scale, rows, st);
-    case 4: return build_table_p<4, 2>(N, base, species, len, clock_scale, rows, st);
-    case 8: return build_table_p<8, 3>(N, base, species, len, clock_scale, rows, st);
-    case 16: return build_table_p<16, 4>(N, base, species, len, clock_scale, rows, st);
+    case 1: return build_table_p<1, 0>(N, base, species, species2, len, lenB, clock_scale, rows, st);
+    case 2: return build_table_p<2, 1>(N, base, species, species2, len, lenB, clock_scale, rows, st);
+    case 4: return build_table_p<4, 2>(N, base, species, species2, len, lenB, clock_scale, rows, st);
+    case 8: return build_table_p<8, 3>(N, base, species, species2, len, lenB, clock_scale, rows, st);
+    case 16: return build_table_p<16, 4>(N, base, species, species2, len, lenB, clock_scale, rows, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -862,7 +910,7 @@ static int num_sms() {
 
 template <typename K>
 static int pipe_table_rows(K kern, const PropagateParams &prm, int grid) {
-  if (prm.tab.species < 0 || prm.tab.len <= 0) return 0;
+  if (prm.tab.species < 0 || prm.tab.len <= 0 || prm.tab.species2 >= 0) return 0;   // 1-D window only
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) { cudaGetLastError(); return 0; }
   const int by_regs = std::max(1, 65536 / std::max(1, fa.numRegs * 128));
@@ -875,11 +923,30 @@ static int pipe_table_rows(K kern, const PropagateParams &prm, int grid) {
   return (int)std::min<size_t>(rows, (size_t)prm.tab.len);
 }
 
+// Blocks of a persistent launch: enough for every capacity slot, at most the resident ones
+// (the kernels loop over groups of 32 walkers).
 template <typename K>
-static cudaError_t launch_pipe(K kern, const PropagateParams &prm_in, int grid, cudaStream_t st) {
+static int persistent_grid(K kern, int groups) {
+  cudaFuncAttributes fa;
+  int per_sm = 4;
+  if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0)
+    per_sm = std::max(1, std::min(16, 65536 / (fa.numRegs * 128)));
+  else
+    cudaGetLastError();
+  return std::max(1, std::min(groups, per_sm * num_sms()));
+}
+
+template <typename K>
+static cudaError_t launch_pipe(K kern, const PropagateParams &prm_in, int groups, cudaStream_t st) {
   PropagateParams prm = prm_in;
+  const int grid = persistent_grid(kern, groups);
   prm.tab.smem_rows = pipe_table_rows(kern, prm, grid);
   return launch_k(kern, prm, grid, 128, propagate_pipe_smem(prm.net, prm.tab.smem_rows), st);
+}
+
+template <typename K>
+static cudaError_t launch_ws(K kern, const PropagateParams &prm, int groups, size_t smem, cudaStream_t st) {
+  return launch_k(kern, prm, persistent_grid(kern, groups), 128, smem, st);
 }
 
 cudaError_t launch_propagate_ws(const PropagateParams &prm, bool table, cudaStream_t st) {
@@ -888,8 +955,9 @@ cudaError_t launch_propagate_ws(const PropagateParams &prm, bool table, cudaStre
   const size_t smem = propagate_ws_smem(prm.net);
 #define WE_CASE(PP, LL)                                                                  \
   case PP:                                                                               \
-    return table ? launch_pipe(k_propagate_pipe<PP, LL>, prm, grid, st)                  \
-                 : launch_k(k_propagate_ws<PP, LL>, prm, grid, 128, smem, st);
+    return table ? (prm.tab.species2 >= 0 ? launch_pipe(k_propagate_pipe<PP, LL, 2>, prm, grid, st)       \
+                                          : launch_pipe(k_propagate_pipe<PP, LL, 1>, prm, grid, st)) \
+                 : launch_ws(k_propagate_ws<PP, LL>, prm, grid, smem, st);
   switch (prm.net.P) {
     WE_CASE(1, 0)
     WE_CASE(2, 1)
