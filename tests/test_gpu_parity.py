@@ -64,6 +64,23 @@ def test_schlogl_table_beyond_its_range():
 
 
 @pytest.mark.parametrize("block", [0, 64])
+def test_two_species_table_beyond_its_range(block):
+    """A toggle whose counts run past the two-species table (256 x 256 for one parameter set):
+    walkers above it take the directly evaluated row, in the pipelined kernel (block 128) and
+    the thread kernel (block 64)."""
+    cfg = W.toggle_batch_we(n_runs=2, n_iters=8)
+    a = np.array([400.0, 300.0])
+    cfg.network = W.toggle_switch(a, a[::-1].copy())
+    cfg.x0 = np.array([[400, 0], [300, 2]], dtype=np.int32)
+    cfg.init_states = np.repeat(cfg.x0[:, None, :], cfg.m_targ, axis=1)
+    cfg.recycle_state = cfg.x0.copy()
+    cfg.target.threshold = np.array([[150, 100], [200, 75]], dtype=np.int32)
+    cfg.bins = W.GridBins(species=[0, 1], edges=[W.uniform_edges(0, 40, 12, overflow=True)] * 2)
+    cfg.capacity = cfg.m_targ * cfg.bins.n_bins
+    _parity(cfg, 8, mapping=P.WE_MAP_THREAD_TABLE, block_threads=block)
+
+
+@pytest.mark.parametrize("block", [0, 64])
 def test_toggle_batch_uneven_runs(block):
     cfg = W.toggle_batch_we(n_runs=8, n_iters=30)
     ens = _parity(cfg, 30, block_threads=block)
