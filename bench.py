@@ -598,7 +598,7 @@ def main():
     achieved = OPS_PER_EVENT * ev_rank / prop_s / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK_GOPS, "unit": "G lane-ops/s",
                 "frac": achieved / ISSUE_PEAK_GOPS, "traffic": SSA_TRAFFIC_BYTES,
-                        "kernel": "k_propagate_pipe<4,2,1> (state chain / clock / draw warps, state-indexed table)",
+                "kernel": "k_propagate_pipe<4,2,1> (state chain / clock / draw warps, state-indexed table)",
                 "launches": n_launch, "avg_launch_ms": prop_total_ms / max(n_launch, 1),
                 "share_of_step": prop_total_ms / total_ms if dist is None else None,
                 "peak_source": "derived: 152 SMs x 4 SMSPs x 32 lanes x 2.07 GHz (issue limit)",
