@@ -128,7 +128,7 @@ struct LogTables {
 // row x (x < len) holds [1/a0, tree node 1 (= a0), node 2, ..., node 2P-1] at that count.
 // Fixed-point clock of the table kernels: integer units of tau / 2^kClockBits.
 constexpr int kClockBits = 62;
-constexpr long long kClockTau = 1ll << kClockBits;
+constexpr unsigned long long kClockTau = 1ull << kClockBits;
 
 // State-indexed table: per parameter set, len x lenB rows of P 64-bit words, row x * lenB + y
 // for count x of `species` and count y of `species2` (lenB = 1, y = 0 for one species):

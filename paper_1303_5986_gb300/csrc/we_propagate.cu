@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
   int x = xme[sx * B], y = sy >= 0 ? xme[sy * B] : 0;
   load_row(x, y);
 
-  long long clk = 0;
+  unsigned long long clk = 0;                       // clock units of tau / 2^62
   long long nev = 0;
   int nrec = 0, status = 0;
   DrawQueue dq;
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
     unsigned long long m2;
     float2 e;
     dq.pop((uint32_t)iter, (uint32_t)w, k0, k1, *sm.logt, m2, e);
-    long long dt;
+    unsigned long long dt;
     if (!wait_units(e, row.w, dt) || clk + dt > kClockTau) break;   // next event after tau
     if (nev >= E.max_steps) { status = kStatusStepCap; break; }
     const int j = row.select(m2, fb);
@@ -665,7 +665,8 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
     }
   };
   // warp 1: the committed walker
-  long long clk = 0, nev = 0;
+  unsigned long long clk = 0;                           // clock units of tau / 2^62
+  long long nev = 0;
   int xc = 0, yc = 0, nrec = 0, status = 0;
   bool done = !live, recycled = false;
   if (live && warp <= 1) {
@@ -771,7 +772,7 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
           // waiting times (independent), the clock after each draw, and the first draw that
           // cannot fire: idle row, waiting time or clock past tau (no status), else the step
           // cap, else an overflow -- the order of the checks in the serial loop
-          long long dts[K];
+          unsigned long long dts[K];
           uint32_t far_m = 0u, over_m = 0u;
 #pragma unroll
           for (int k = 0; k < K; ++k) {
@@ -779,10 +780,12 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
             const float2 wv = sw[(pb * K + k) * W + lane];
             if (!wait_units(e, wv, dts[k])) far_m |= 1u << k;
           }
-          long long c = clk;
+          // the clock after each draw: exact up to the first draw that cannot fire (before it
+          // the clock is at most 2^62 and a waiting time below 2^63 + 2^40, so no wrap)
+          unsigned long long c = clk;
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            c += dts[k];                                  // meaningful up to the first stop
+            c += dts[k];
             if (c > kClockTau) over_m |= 1u << k;
           }
           const uint32_t idle_m = sfl[(pb * 3 + 0) * W + lane];
@@ -794,9 +797,9 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
           const uint32_t stop_m = (quiet_m | cap_m | ovf_m) & 0xffffu;
           const int kstop = stop_m ? __ffs(stop_m) - 1 : K;
           const uint32_t fired = (1u << kstop) - 1u;
-          long long cs = clk;
+          unsigned long long cs = clk;
 #pragma unroll
-          for (int k = 0; k < K; ++k) cs += (k < kstop) ? dts[k] : 0ll;
+          for (int k = 0; k < K; ++k) cs += (k < kstop) ? dts[k] : 0ull;
           clk = cs;
           nev += kstop;
           nrec += __popc(rec_m & fired);

@@ -269,39 +269,42 @@ __device__ __forceinline__ double advance_clock(double t, float2 e, double inv_a
 // t + dt <= tau is an integer compare, and no FP64 operation is left on the event-to-event
 // chain.  A waiting time dt = e / a0 comes from e (float-float) times the row's float-float
 // (2^62 / tau) / a0, an error-free float product plus the cross terms (relative error about
-// 2^-47, below the logarithm's), rounded to the nearest unit.
+// 2^-47, below the logarithm's), rounded to the nearest unit.  The float product alone never
+// decides whether an event fires: near the end of the interval it can round up to 2^62 while
+// the full product is below it, so only products of 2^63 and more are set aside, and the fire
+// test is made on the exact unsigned sum.
 // ------------------------------------------------------------------------------------------
-constexpr uint32_t kClockBeyondBits = (uint32_t)(127 + kClockBits) << 23;   // float bits of 2^62
+constexpr uint32_t kClockFarBits = (uint32_t)(127 + 63) << 23;    // float bits of 2^63
 
-// Nearest integer to a float f with |f| < 2^62, by integer operations on its bits and without
-// branches: |f| = m 2^(E-150) = (m 2^39) / 2^(189-E), so one rounding right shift of m 2^39
-// (below 2^63, so adding the rounding half, at most 2^62, cannot wrap).  The shift is held in
-// [1, 63]; only |f| < 1/2 is affected by the upper limit, which then gives 1 instead of 0.
+// Nearest integer to a float f with |f| < 2^63, by integer operations on its bits and without
+// branches: |f| = m 2^(E-150) = (m 2^39) / 2^(189-E), one rounding right shift of m 2^39 (below
+// 2^63, so adding the rounding half, at most 2^62, cannot wrap), or none for E = 189.  The shift
+// is held at 63 at most; only |f| < 1/2 is affected by that limit, which then gives 1, not 0.
 __device__ __forceinline__ long long f2ll_near(float f) {
   const uint32_t b = __float_as_uint(f);
-  const uint32_t ex = (b >> 23) & 0xffu;
+  const int ex = (int)((b >> 23) & 0xffu);
   const unsigned long long mm = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << 39;
-  const uint32_t sh = min(189u - min(ex, 188u), 63u);              // 1 .. 63
-  const unsigned long long v = (mm + (1ull << (sh - 1))) >> sh;
+  const int sh = min(max(189 - ex, 0), 63);
+  const unsigned long long v = sh ? (mm + (1ull << (sh - 1))) >> sh : mm;
   const long long sv = (long long)v;
   return (b >> 31) ? -sv : sv;
 }
 
 // Waiting time in clock units for e = -log u1 and w = (2^62 / tau) / a0 (both float-float,
-// non-negative).  Returns false when it is at least 2^62 units (beyond the interval, including
-// an infinite w); dt is then unspecified.
-__device__ __forceinline__ bool wait_units(float2 e, float2 w, long long &dt) {
+// non-negative).  Returns false when it is 2^63 units or more (far beyond the interval,
+// including an infinite w); dt is then unspecified.  Otherwise 0 <= dt < 2^63 + 2^40.
+__device__ __forceinline__ bool wait_units(float2 e, float2 w, unsigned long long &dt) {
   const float p = __fmul_rn(e.x, w.x);
-  const bool within = (__float_as_uint(p) & 0x7fffffffu) < kClockBeyondBits;
+  const bool near = (__float_as_uint(p) & 0x7fffffffu) < kClockFarBits;
   const float err = __fmaf_rn(e.x, w.x, -p);
   const float lo = __fmaf_rn(e.x, w.y, __fmaf_rn(e.y, w.x, err));
-  dt = f2ll_near(p) + f2ll_near(lo);
-  return within;
+  dt = (unsigned long long)(f2ll_near(p) + f2ll_near(lo));
+  return near;
 }
 
 // Clock units back to time: t = units * tau / 2^62 (one rounding).
-__device__ __forceinline__ double clock_time(long long units, double tau) {
-  return __dmul_rn(__ll2double_rn(units), ldexp(tau, -kClockBits));
+__device__ __forceinline__ double clock_time(unsigned long long units, double tau) {
+  return __dmul_rn(__ull2double_rn(units), ldexp(tau, -kClockBits));
 }
 
 // Draws do not depend on the state, so they are made kDrawBatch at a time: the batch's

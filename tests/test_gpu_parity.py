@@ -63,6 +63,36 @@ def test_schlogl_table_beyond_its_range():
     _parity(cfg, 6, mapping=P.WE_MAP_THREAD_TABLE)
 
 
+@pytest.mark.parametrize("mapping,block", [(P.WE_MAP_THREAD_TABLE, 0), (P.WE_MAP_THREAD_TABLE, 64),
+                                           (P.WE_MAP_THREAD, 0)])
+def test_event_just_before_the_end_of_the_interval(mapping, block):
+    """An interval whose only event of one walker falls 1.6e-8 tau before tau (toggle a = 40 at
+    (U, V) = (10, 2), iteration 50392, run id 11, walker slot 65): the waiting time's leading
+    float product rounds up to the end of the interval, so the fire test must use the full
+    product.  Plain SSA for one interval, against the oracle."""
+    cfg = W.toggle_batch_we(n_runs=1, n_iters=1)
+    cfg.network = W.toggle_switch([40.0], [40.0])
+    cfg.param_set = np.zeros(1, np.int32)
+    cfg.run_ids = np.array([11], dtype=np.uint32)
+    cfg.seed = 1
+    cfg.x0 = np.array([[40, 0]], dtype=np.int32)
+    cfg.recycle_state = cfg.x0.copy()
+    cfg.target.threshold = np.array([[20, 10]], dtype=np.int32)
+    n = 240
+    cfg.init_states = np.tile(np.array([10, 2], dtype=np.int32), (1, n, 1))
+    cfg.init_weights = np.full((1, n), 1.0 / n)
+    cfg.capacity = n
+    cfg.first_iter = 50392
+    ens = gpu_run(cfg, 1, resample=False, mapping=mapping, block_threads=block, first_iter=50392)
+    ens.sync()
+    g = gpu_outputs(ens, 0, hist=False)
+    o = oracle_run(cfg, 0, n_iters=1, resample=False, first_iter=50392)
+    assert np.array_equal(g["states"][65], [10, 1])        # the event at t = 0.0999999984 fires
+    assert_run_parity(g, o, label=f"end-of-interval {mapping} {block}")
+    t = ens.get(P.WE_OUT_TLAST, 0)
+    assert abs(t[65] - 0.09999999837240271) < 1e-15
+
+
 @pytest.mark.parametrize("block", [0, 64])
 def test_two_species_table_beyond_its_range(block):
     """A toggle whose counts run past the two-species table (256 x 256 for one parameter set):
