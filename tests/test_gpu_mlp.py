@@ -245,3 +245,30 @@ def test_harvest_states_all_runs():
     assert len(allx) == ens.get(P.WE_OUT_COUNTS).sum()
     h = LN.harvest_states(ens, 2)
     assert h.shape[1] == 2 and len(h) > len(allx)
+
+
+def test_learned_bins_on_the_large_network():
+    """A learned bin map on the 354-species synthetic network (warp-per-walker SSA kernel, an MLP
+    with 354 inputs): z against the FP64 reference, each occupied bin resampled to M walkers, and
+    the total weight kept."""
+    cfg = W.synthetic_large_we(n_walkers=256, n_iters=1, m_targ=6)
+    S = cfg.network.n_species
+    H = 16
+    p = _params(S, H, 21)
+    states0 = cfg.init_states[0]
+    zg = M.forward(M.inference_params(p, S, H), states0, S, H)
+    edges = np.linspace(zg.min() - 1.0, zg.max() + 1.0, 21).astype(np.float32)
+    mlp = P.we_mlp_create(S, H, p)
+    bm = P.we_binmap_learned(mlp, edges)
+    cfg.capacity = 256 + 6 * 20
+    cfg.tau = 2e-4
+    ens = gpu_run(cfg, 0, bins=bm, capacity=cfg.capacity)
+    ens.propagate()
+    X = ens.states(0)
+    z = ens.get(P.WE_OUT_Z, 0)
+    zo = M.forward(M.inference_params(p, S, H), X, S, H)
+    np.testing.assert_allclose(z, zo, rtol=1e-5, atol=5e-5)
+    ens.resample()
+    n_occ = len(np.unique(M.bins_of(z, edges)))
+    assert ens.get(P.WE_OUT_COUNTS)[0] == 6 * n_occ
+    assert abs(ens.weights(0).sum() - 1.0) < 1e-12
