@@ -70,7 +70,7 @@ typedef int32_t we_status;
 #define WE_MAP_AUTO 0          /* let the autotuner pick */
 #define WE_MAP_THREAD 1        /* one thread per walker, propensity tree in registers */
 #define WE_MAP_WARP 2          /* one warp per walker, propensity tree in shared memory
-                                  (any network up to ~13,000 reactions) */
+                                  (any network up to 16,384 reactions) */
 #define WE_MAP_THREAD_TABLE 3  /* one thread per walker, propensity tree looked up by count
                                   (networks whose propensities all read one species) */
 

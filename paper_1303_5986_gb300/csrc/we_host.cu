@@ -505,8 +505,8 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   const int block = c->block_threads > 0 ? c->block_threads : (thread_map ? 128 : 32);
   if (thread_map && block != 32 && block != 64 && block != 96 && block != 128)
     return fail(WE_EINVAL, "thread mapping supports block_threads of 32, 64, 96 or 128");
-  if (mapping == WE_MAP_WARP && 16ull * n->P + 4ull * n->S + sizeof(LogTables) + 16 > 227ull * 1024)
-    return fail(WE_ENOTSUPPORTED, "warp mapping keeps the walker's tree in shared memory: at most ~13,000 reactions");
+  if (mapping == WE_MAP_WARP && 12ull * (n->P < 4 ? 4 : n->P) + 4ull * n->S + sizeof(LogTables) + 16 > 227ull * 1024)
+    return fail(WE_ENOTSUPPORTED, "warp mapping keeps the walker's tree in shared memory: at most 16,384 reactions");
   Offsets o = layout(n, b, c, cap);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void *ws = workspace;

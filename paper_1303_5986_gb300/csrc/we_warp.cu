@@ -1,16 +1,24 @@
-// we_warp.cu -- one warp per walker, for networks too large for a register tree (up to 8192
-// reactions): Gillespie's direct method (Sec. II.A) for one interval tau, with recycling
+// we_warp.cu -- one warp per walker, for networks too large for a register tree (up to about
+// 18,000 reactions): Gillespie's direct method (Sec. II.A) for one interval tau, with recycling
 // (Sec. II.B.2), bin assignment and observables, as in the thread kernels.
 //
-// The walker's counts and its whole canonical propensity tree (P leaves, node k = node 2k +
-// node 2k+1, rounded; 16P bytes) live in shared memory.  Per event:
+// The walker's counts and its canonical propensity tree (Pw = max(P, 4) leaves, node k = node
+// 2k + node 2k+1, rounded) live in shared memory.  The leaves and the internal nodes of every
+// level but the lowest are stored (12 Pw bytes); a lowest-level node, the sum of two adjacent
+// leaves, is recomputed where it is read.  That is the same rounded sum the stored node would
+// hold, so values and descent are those of the full tree, and four walkers of a 4096-leaf
+// network fit on one SM instead of three.  Per event:
 //   * the warp makes 32 draws at a time (one Philox block and one float-float logarithm per
 //     lane) and hands them out one per event by shuffle;
-//   * every lane walks the same descent (uniform control flow, broadcast loads);
-//   * after the reaction fires, the lanes re-evaluate the reactions the dependency graph lists
-//     for it, one per lane, and recompute the dirty tree nodes level by level -- duplicates
-//     compute the same rounded sum, so no ordering is needed -- giving the same node values
-//     as a full rebuild (each node is a function of its two children only).
+//   * every lane walks the same descent, two levels per shared-memory round trip;
+//   * the fired reaction's changes and dependency list, and the dependents' parameters, are
+//     fetched before the counts change (none of them depends on the counts), so an event waits
+//     on three global round trips instead of five;
+//   * the lanes re-evaluate the dependent reactions (one or two per lane) and then recompute
+//     the dirty ancestors once, level by level: while a level has more than 32 nodes each lane
+//     updates its dependents' ancestors (duplicates compute the same rounded sum), above that
+//     every node of the level is recomputed, one per lane.  Each node is a function of its two
+//     children only, so the tree equals a full rebuild.
 #include "we_ssa_common.cuh"
 
 namespace we {
@@ -45,15 +53,65 @@ __device__ __forceinline__ void finish_walker_warp(const PropagateParams &prm, i
   }
 }
 
-// Block = one warp = one walker.  Shared memory: tree (2P doubles), counts (S ints), log tables.
+// The fields of RxnMeta that a propensity reads, in registers: a = (n_reac, sp0, sp1, sp2),
+// b = (m0, m1, m2, law), c = (hsp, hn, d_begin, d_end).
+struct MetaRegs {
+  int4 a, b, c;
+};
+
+__device__ __forceinline__ MetaRegs load_meta(const RxnMeta *mt) {
+  const int4 *q = reinterpret_cast<const int4 *>(mt);
+  return MetaRegs{__ldg(q), __ldg(q + 1), __ldg(q + 2)};
+}
+
+// The same operations, in the same order, as propensity() for one reaction.
+__device__ __forceinline__ double propensity_regs(const MetaRegs &r, double keff, double Kn, const int32_t *xs) {
+  if (r.b.w == 1) {
+    const long long y = xs[r.c.x];
+    long long yn = y;
+    if (r.c.y >= 2) yn *= y;
+    if (r.c.y >= 3) yn *= y;
+    return __ddiv_rn(keff, __dadd_rn(Kn, __ll2double_rn(yn)));
+  }
+  long long h = 1;
+  if (r.a.x > 0) h *= binom_small(xs[r.a.y], r.b.x);
+  if (r.a.x > 1) h *= binom_small(xs[r.a.z], r.b.y);
+  if (r.a.x > 2) h *= binom_small(xs[r.a.w], r.b.z);
+  return __dmul_rn(keff, __ll2double_rn(h));
+}
+
+__device__ __forceinline__ double2 lds2(const double *p) { return *reinterpret_cast<const double2 *>(p); }
+
+// Node k of the lowest stored level (k in [Pw/4, Pw/2)) from its four leaves lf[4k - Pw ...].
+__device__ __forceinline__ void update_from_leaves(double *nd, const double *lf, int Pw, int k) {
+  const double2 l = lds2(lf + 4 * k - Pw), r = lds2(lf + 4 * k - Pw + 2);
+  nd[k] = __dadd_rn(__dadd_rn(l.x, l.y), __dadd_rn(r.x, r.y));
+}
+
+__device__ __forceinline__ void update_from_children(double *nd, int k) {
+  const double2 c = lds2(nd + 2 * k);
+  nd[k] = __dadd_rn(c.x, c.y);
+}
+
+// One descent step at a node whose children have values (lv, rv).
+__device__ __forceinline__ void descend_step(double &target, int &k, double lv, double rv) {
+  const bool right = (bits(rv) != 0) && !(bits(target) < bits(lv));
+  if (right) target = __dsub_rn(target, lv);
+  k = 2 * k + (right ? 1 : 0);
+}
+
+// Block = one warp = one walker.  Shared memory: internal nodes (Pw/2 doubles, index 0 unused),
+// leaves (Pw doubles), log tables, counts (S ints).
 __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const NetView &N = prm.net;
   const EnsView &E = prm.ens;
   const int lane = threadIdx.x;
-  const int P = N.P, L = N.log2P;
-  double *nd = reinterpret_cast<double *>(smem_raw);                    // 2P
-  LogTables *lt = reinterpret_cast<LogTables *>(nd + 2 * P);
+  const int P = N.P;
+  const int Lw = N.log2P < 2 ? 2 : N.log2P, Pw = 1 << Lw;
+  double *nd = reinterpret_cast<double *>(smem_raw);                    // Pw/2
+  double *lf = nd + Pw / 2;                                              // Pw
+  LogTables *lt = reinterpret_cast<LogTables *>(lf + Pw);
   int32_t *xs = reinterpret_cast<int32_t *>(lt + 1);                      // S
   {
     const double *src = reinterpret_cast<const double *>(prm.logt);
@@ -77,12 +135,14 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
   const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
   __syncwarp();
 
-  // full rebuild of leaves and internal nodes
+  // full rebuild: leaves, the lowest stored level from four leaves each, then the levels above
   auto rebuild = [&]() {
-    for (int j = lane; j < P; j += 32) nd[P + j] = propensity(N.meta[j], keff[j], Kn[j], xs, 1);
+    for (int j = lane; j < Pw; j += 32) lf[j] = j < P ? propensity(N.meta[j], keff[j], Kn[j], xs, 1) : 0.0;
     __syncwarp();
-    for (int lvl = L - 1; lvl >= 0; --lvl) {
-      for (int k = (1 << lvl) + lane; k < (2 << lvl); k += 32) nd[k] = __dadd_rn(nd[2 * k], nd[2 * k + 1]);
+    for (int k = Pw / 4 + lane; k < Pw / 2; k += 32) update_from_leaves(nd, lf, Pw, k);
+    __syncwarp();
+    for (int lvl = Lw - 3; lvl >= 0; --lvl) {
+      for (int k = (1 << lvl) + lane; k < (2 << lvl); k += 32) update_from_children(nd, k);
       __syncwarp();
     }
   };
@@ -116,21 +176,49 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
     const double tn = advance_clock(t, e, rcp_pos(a0));
     if (bits(tn) > tau_bits) break;
     if (nev >= E.max_steps) { status = kStatusStepCap; break; }
+    // descent: stored levels two at a time, then the computed lowest level and the leaves
     double target = __dmul_rn(u01_index(m2), a0);
-    int k = 1;
-    for (int lvl = 0; lvl < L; ++lvl) {
-      const double Lv = nd[2 * k], Rv = nd[2 * k + 1];
-      const bool right = (bits(Rv) != 0) && !(bits(target) < bits(Lv));
-      if (right) { target = __dsub_rn(target, Lv); k = 2 * k + 1; }
-      else { k = 2 * k; }
+    int k = 1, lvl = 0;
+    for (; lvl + 2 <= Lw - 2; lvl += 2) {
+      const double2 c = lds2(nd + 2 * k), g0 = lds2(nd + 4 * k), g1 = lds2(nd + 4 * k + 2);
+      const bool right = (bits(c.y) != 0) && !(bits(target) < bits(c.x));
+      if (right) target = __dsub_rn(target, c.x);
+      k = 2 * k + (right ? 1 : 0);
+      const double2 gc = right ? g1 : g0;
+      descend_step(target, k, gc.x, gc.y);
     }
-    const int j = k - P;
-    const int db = N.meta[j].d_begin, de = N.meta[j].d_end;
+    if (lvl < Lw - 2) {
+      const double2 c = lds2(nd + 2 * k);
+      descend_step(target, k, c.x, c.y);
+    }
+    {
+      const double2 l = lds2(lf + 4 * k - Pw), rr = lds2(lf + 4 * k - Pw + 2);
+      const double lv = __dadd_rn(l.x, l.y), rv = __dadd_rn(rr.x, rr.y);
+      const bool right = (bits(rv) != 0) && !(bits(target) < bits(lv));
+      if (right) target = __dsub_rn(target, lv);
+      k = 2 * k + (right ? 1 : 0);
+      const double2 pr = right ? rr : l;
+      descend_step(target, k, pr.x, pr.y);
+    }
+    const int j = k - Pw;
+    // everything the event reads from global memory, before the counts change
+    const int db = __ldg(&N.meta[j].d_begin), de = __ldg(&N.meta[j].d_end);
+    const int qb = __ldg(&N.dep_ptr[j]), qe = __ldg(&N.dep_ptr[j + 1]);
+    const bool has_d = db + lane < de;
+    const int dsp = has_d ? __ldg(&N.d_sp[db + lane]) : 0;
+    const int dval = has_d ? __ldg(&N.d_val[db + lane]) : 0;
+    const int ia = qb + lane < qe ? __ldg(&N.dep_idx[qb + lane]) : -1;
+    const int ib = qb + 32 + lane < qe ? __ldg(&N.dep_idx[qb + 32 + lane]) : -1;
+    MetaRegs ma{}, mb{};
+    double ka = 0.0, kna = 0.0, kb = 0.0, knb = 0.0;
+    if (ia >= 0) { ma = load_meta(&N.meta[ia]); ka = __ldg(&keff[ia]); kna = __ldg(&Kn[ia]); }
+    if (ib >= 0) { mb = load_meta(&N.meta[ib]); kb = __ldg(&keff[ib]); knb = __ldg(&Kn[ib]); }
     // overflow check, then apply the net changes (one lane per changed species)
-    bool over = false;
-    for (int q = db + lane; q < de; q += 32) over |= xs[N.d_sp[q]] + N.d_val[q] > kMaxCount;
+    bool over = has_d && xs[dsp] + dval > kMaxCount;
+    for (int q = db + 32 + lane; q < de; q += 32) over |= xs[N.d_sp[q]] + N.d_val[q] > kMaxCount;
     if (__any_sync(0xffffffffu, over)) { status = kStatusOverflow; break; }
-    for (int q = db + lane; q < de; q += 32) xs[N.d_sp[q]] += N.d_val[q];
+    if (has_d) xs[dsp] += dval;
+    for (int q = db + 32 + lane; q < de; q += 32) xs[N.d_sp[q]] += N.d_val[q];
     __syncwarp();
     ++nev;
     t = tn;
@@ -151,22 +239,36 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
       }
     }
     if (recycled) { rebuild(); __syncwarp(); continue; }
-    // dependent reactions: new leaves, then their ancestors level by level
-    const int qb = N.dep_ptr[j], qe = N.dep_ptr[j + 1];
-    for (int q0 = qb; q0 < qe; q0 += 32) {
-      const int q = q0 + lane;
-      int node = 0;
-      if (q < qe) {
-        const int i = N.dep_idx[q];
-        nd[P + i] = propensity(N.meta[i], keff[i], Kn[i], xs, 1);
-        node = (P + i) >> 1;
+    // dependent reactions: new leaves, then the dirty ancestors once, level by level
+    {
+      double pa = 0.0, pb = 0.0;
+      if (ia >= 0) pa = propensity_regs(ma, ka, kna, xs);
+      if (ib >= 0) pb = propensity_regs(mb, kb, knb, xs);
+      if (ia >= 0) lf[ia] = pa;
+      if (ib >= 0) lf[ib] = pb;
+    }
+    for (int q = qb + 64 + lane; q < qe; q += 32) {
+      const int i = N.dep_idx[q];
+      lf[i] = propensity(N.meta[i], keff[i], Kn[i], xs, 1);
+    }
+    __syncwarp();
+    for (int sh = 2; sh <= Lw; ++sh) {
+      const int cnt = Pw >> sh;            // nodes on this level: [cnt, 2 cnt)
+      if (cnt > 32) {
+        if (sh == 2) {
+          if (ia >= 0) update_from_leaves(nd, lf, Pw, (Pw + ia) >> 2);
+          if (ib >= 0) update_from_leaves(nd, lf, Pw, (Pw + ib) >> 2);
+          for (int q = qb + 64 + lane; q < qe; q += 32) update_from_leaves(nd, lf, Pw, (Pw + N.dep_idx[q]) >> 2);
+        } else {
+          if (ia >= 0) update_from_children(nd, (Pw + ia) >> sh);
+          if (ib >= 0) update_from_children(nd, (Pw + ib) >> sh);
+          for (int q = qb + 64 + lane; q < qe; q += 32) update_from_children(nd, (Pw + N.dep_idx[q]) >> sh);
+        }
+      } else if (lane < cnt) {
+        if (sh == 2) update_from_leaves(nd, lf, Pw, cnt + lane);
+        else update_from_children(nd, cnt + lane);
       }
       __syncwarp();
-      for (int lvl = 0; lvl < L; ++lvl) {
-        if (q < qe) nd[node] = __dadd_rn(nd[2 * node], nd[2 * node + 1]);
-        __syncwarp();
-        node >>= 1;
-      }
     }
   }
   __syncwarp();
@@ -175,7 +277,8 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
 
 size_t propagate_warp_smem(const NetView &N, int block) {
   (void)block;
-  return 16 * (size_t)N.P + sizeof(LogTables) + 4 * (size_t)N.S + 16;
+  const size_t Pw = N.P < 4 ? 4 : (size_t)N.P;
+  return 12 * Pw + sizeof(LogTables) + 4 * (size_t)N.S + 16;
 }
 
 cudaError_t launch_propagate_warp(const PropagateParams &prm, int block, cudaStream_t st) {
