@@ -328,7 +328,8 @@ struct Offsets {
   size_t flux, totw, nw, events, hist, pack;
   size_t logt, table, base;
   size_t lw1, lw2, lw3, lb, lz, zout;
-  int32_t table_len, table_lenB;
+  size_t wrec;
+  int32_t table_len, table_lenB, wrec_stride;
   size_t total;
 };
 
@@ -348,6 +349,62 @@ static int table_len_for(const we_network *n, int *lenB_out = nullptr) {
   if ((size_t)n->nps * L * L * row > budget) return 0;
   if (lenB_out) *lenB_out = L;
   return L;
+}
+
+static int choose_mapping(const we_network *n, const we_run_config *c) {
+  if (c->mapping == WE_MAP_THREAD || c->mapping == WE_MAP_WARP || c->mapping == WE_MAP_THREAD_TABLE)
+    return c->mapping;
+  if (table_len_for(n) > 0) return WE_MAP_THREAD_TABLE;
+  return (n->P <= kThreadMaxLeaves && n->S <= kThreadMaxSpecies) ? WE_MAP_THREAD : WE_MAP_WARP;
+}
+
+// Event records of the warp-per-walker kernel (layout documented at NetView::wrec).
+struct WarpRecords {
+  int32_t stride = 0, chg = 0, dep = 0;     // in 16-byte units; entries kept per record
+  std::vector<int32_t> words;               // P x stride x 4
+};
+
+static WarpRecords warp_records(const we_network *n) {
+  WarpRecords W;
+  const int P = n->P;
+  int maxc = 0, maxd = 0;
+  for (int j = 0; j < P; ++j) {
+    maxc = std::max(maxc, n->meta[j].d_end - n->meta[j].d_begin);
+    maxd = std::max(maxd, n->dep_ptr[j + 1] - n->dep_ptr[j]);
+  }
+  W.chg = std::min(maxc, 32);
+  W.dep = std::min(maxd, 96);
+  W.stride = 1 + (W.chg + 1) / 2 + 2 * W.dep;
+  W.words.assign((size_t)P * W.stride * 4, 0);
+  for (int j = 0; j < P; ++j) {
+    int32_t *r = W.words.data() + (size_t)j * W.stride * 4;
+    const RxnMeta &mt = n->meta[j];
+    const int nd = n->dep_ptr[j + 1] - n->dep_ptr[j];
+    r[0] = mt.d_end - mt.d_begin; r[1] = nd; r[2] = mt.d_begin; r[3] = n->dep_ptr[j];
+    int32_t *c = r + 4;
+    for (int q = 0; q < W.chg; ++q) {
+      const bool have = q < mt.d_end - mt.d_begin;
+      c[2 * q] = have ? n->d_sp[mt.d_begin + q] : -1;
+      c[2 * q + 1] = have ? n->d_val[mt.d_begin + q] : 0;
+    }
+    int32_t *d = r + 4 * (1 + (W.chg + 1) / 2);
+    for (int q = 0; q < W.dep; ++q) {
+      int32_t *e = d + 8 * q;
+      if (q >= nd) { e[0] = -1; continue; }
+      const int i = n->dep_idx[n->dep_ptr[j] + q];
+      const RxnMeta &mi = n->meta[i];
+      const int hill = mi.law == WE_HILL_REPRESSION ? 1 : 0;
+      const int packed = (mi.n_reac & 3) | hill << 2 | (mi.hn & 3) << 3 | (mi.m[0] & 3) << 5 |
+                         (mi.m[1] & 3) << 7 | (mi.m[2] & 3) << 9;
+      e[0] = i | packed << 20;
+      e[1] = hill ? mi.hsp : mi.sp[0];
+      e[2] = mi.sp[1];
+      e[3] = mi.sp[2];
+      const double kd[2] = {n->keff[i], n->Kn[i]};
+      std::memcpy(e + 4, kd, 16);
+    }
+  }
+  return W;
 }
 
 static Offsets layout(const we_network *n, const we_binmap *b, const we_run_config *c, int cap) {
@@ -374,6 +431,15 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
   o.d_val = L.take(4 * (n->d_val.size() + 1));
   o.dep_ptr = L.take(4 * n->dep_ptr.size());
   o.dep_idx = L.take(4 * (n->dep_idx.size() + 1));
+  if (choose_mapping(n, c) == WE_MAP_WARP) {
+    int maxc = 0, maxd = 0;
+    for (int j = 0; j < n->P; ++j) {
+      maxc = std::max(maxc, n->meta[j].d_end - n->meta[j].d_begin);
+      maxd = std::max(maxd, n->dep_ptr[j + 1] - n->dep_ptr[j]);
+    }
+    o.wrec_stride = 1 + (std::min(maxc, 32) + 1) / 2 + 2 * std::min(maxd, 96);
+    o.wrec = L.take(16 * (size_t)n->P * o.wrec_stride);
+  }
   o.edges = L.take(8 * b->edges.size());
   o.run_id = L.take(4 * R);
   o.param_set = L.take(4 * R);
@@ -479,12 +545,6 @@ extern "C" we_status we_ensemble_workspace_bytes(const we_network *n, const we_b
 template <typename T>
 static T *at(void *base, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(base) + off); }
 
-static int choose_mapping(const we_network *n, const we_run_config *c) {
-  if (c->mapping == WE_MAP_THREAD || c->mapping == WE_MAP_WARP || c->mapping == WE_MAP_THREAD_TABLE)
-    return c->mapping;
-  if (table_len_for(n) > 0) return WE_MAP_THREAD_TABLE;
-  return (n->P <= kThreadMaxLeaves && n->S <= kThreadMaxSpecies) ? WE_MAP_THREAD : WE_MAP_WARP;
-}
 
 
 
@@ -575,6 +635,12 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   e = e ? e : up(o.d_val, n->d_val.data(), 4 * n->d_val.size());
   e = e ? e : up(o.dep_ptr, n->dep_ptr.data(), 4 * n->dep_ptr.size());
   e = e ? e : up(o.dep_idx, n->dep_idx.data(), 4 * n->dep_idx.size());
+  WarpRecords wrec;                                                       // lives past the copies
+  if (mapping == WE_MAP_WARP) {
+    wrec = warp_records(n);
+    if (wrec.stride != o.wrec_stride) return cleanup(fail(WE_EINVAL, "event record layout mismatch"));
+    e = e ? e : up(o.wrec, wrec.words.data(), 4 * wrec.words.size());
+  }
   e = e ? e : up(o.edges, b->edges.data(), 8 * b->edges.size());
   e = e ? e : up(o.run_id, run_id.data(), 4 * R);
   e = e ? e : up(o.param_set, pset.data(), 4 * R);
@@ -614,6 +680,10 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   N.d_val = at<int32_t>(ws, o.d_val);
   N.dep_ptr = at<int32_t>(ws, o.dep_ptr);
   N.dep_idx = at<int32_t>(ws, o.dep_idx);
+  if (mapping == WE_MAP_WARP) {
+    N.wrec = at<int4>(ws, o.wrec);
+    N.wrec_stride = wrec.stride; N.wrec_chg = wrec.chg; N.wrec_dep = wrec.dep;
+  }
   BinView &Bv = E->prm.bins;
   Bv.ndim = b->ndim; Bv.n_bins = b->n_bins;
   for (int d = 0; d < kMaxBinDims; ++d) { Bv.species[d] = b->species[d]; Bv.nb[d] = b->nb[d]; Bv.edge_off[d] = b->edge_off[d]; }

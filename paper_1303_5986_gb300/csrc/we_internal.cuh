@@ -43,6 +43,19 @@ struct NetView {
   // dependency graph: reactions whose propensity reads a species changed by j (CSR over P)
   const int32_t *dep_ptr;      // P + 1
   const int32_t *dep_idx;
+  // Per-reaction event records for the warp-per-walker kernel (null for the other mappings):
+  // everything one event reads from global memory, at a fixed stride so that it is fetched in
+  // one round trip.  Record j, in 16-byte units:
+  //   [0]                      (n_changes, n_dependents, d_begin, dep_begin)
+  //   [1, 1 + (wrec_chg+1)/2)  the first wrec_chg net changes as int2 (species, change);
+  //                            unused entries have species -1
+  //   then wrec_dep entries of 32 bytes, one per dependent reaction i (dep_idx order):
+  //     int4 (i | packed << 20, sp0, sp1, sp2), double2 (keff, Kn) of parameter set 0;
+  //     packed = n_reac | hill << 2 | hn << 3 | m0 << 5 | m1 << 7 | m2 << 9 (sp0 = hsp for a
+  //     Hill term); unused entries have word 0 = -1.
+  // Changes and dependents past these counts are read from d_sp/d_val and dep_idx/meta.
+  const int4 *wrec;
+  int32_t wrec_stride, wrec_chg, wrec_dep;
 };
 
 // Learned progress coordinate: z = w3 . silu(W2 silu(W1 phi + b1) + b2) + b3 with

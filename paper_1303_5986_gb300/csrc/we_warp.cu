@@ -11,10 +11,11 @@
 //   * the warp makes 32 draws at a time (one Philox block and one float-float logarithm per
 //     lane) and hands them out one per event by shuffle;
 //   * every lane walks the same descent, two levels per shared-memory round trip;
-//   * the fired reaction's changes and dependency list, and the dependents' parameters, are
-//     fetched before the counts change (none of them depends on the counts), so an event waits
-//     on three global round trips instead of five;
-//   * the lanes re-evaluate the dependent reactions (one or two per lane) and then recompute
+//   * the fired reaction's event record (its net changes and its dependents' species,
+//     multiplicities and rate constants, at a fixed stride) is fetched in one round trip,
+//     requested before the clock arithmetic so that the two overlap; the descent runs before
+//     the clock too, as it has no side effects;
+//   * the lanes re-evaluate the dependent reactions (up to three per lane) and then recompute
 //     the dirty ancestors once, level by level: while a level has more than 32 nodes each lane
 //     updates its dependents' ancestors (duplicates compute the same rounded sum), above that
 //     every node of the level is recomputed, one per lane.  Each node is a function of its two
@@ -53,31 +54,42 @@ __device__ __forceinline__ void finish_walker_warp(const PropagateParams &prm, i
   }
 }
 
-// The fields of RxnMeta that a propensity reads, in registers: a = (n_reac, sp0, sp1, sp2),
-// b = (m0, m1, m2, law), c = (hsp, hn, d_begin, d_end).
-struct MetaRegs {
-  int4 a, b, c;
+// One dependent reaction from an event record (layout at NetView::wrec); w.x < 0: no entry.
+struct DepRec {
+  int4 w;
+  double keff, Kn;
 };
 
-__device__ __forceinline__ MetaRegs load_meta(const RxnMeta *mt) {
-  const int4 *q = reinterpret_cast<const int4 *>(mt);
-  return MetaRegs{__ldg(q), __ldg(q + 1), __ldg(q + 2)};
+__device__ __forceinline__ DepRec load_dep(const int4 *dr, int q, int n) {
+  DepRec d{make_int4(-1, 0, 0, 0), 0.0, 0.0};
+  if (q < n) {
+    d.w = __ldg(dr + 2 * q);
+    const double2 k = __ldg(reinterpret_cast<const double2 *>(dr + 2 * q + 1));
+    d.keff = k.x;
+    d.Kn = k.y;
+  }
+  return d;
 }
 
-// The same operations, in the same order, as propensity() for one reaction.
-__device__ __forceinline__ double propensity_regs(const MetaRegs &r, double keff, double Kn, const int32_t *xs) {
-  if (r.b.w == 1) {
-    const long long y = xs[r.c.x];
+__device__ __forceinline__ int dep_index(const DepRec &d) { return d.w.x & 0xFFFFF; }
+
+// The same operations, in the same order, as propensity() for the entry's reaction.
+__device__ __forceinline__ double propensity_rec(const DepRec &d, const int32_t *xs) {
+  const int pk = d.w.x >> 20;
+  if ((pk >> 2) & 1) {
+    const int hn = (pk >> 3) & 3;
+    const long long y = xs[d.w.y];
     long long yn = y;
-    if (r.c.y >= 2) yn *= y;
-    if (r.c.y >= 3) yn *= y;
-    return __ddiv_rn(keff, __dadd_rn(Kn, __ll2double_rn(yn)));
+    if (hn >= 2) yn *= y;
+    if (hn >= 3) yn *= y;
+    return __ddiv_rn(d.keff, __dadd_rn(d.Kn, __ll2double_rn(yn)));
   }
+  const int nr = pk & 3;
   long long h = 1;
-  if (r.a.x > 0) h *= binom_small(xs[r.a.y], r.b.x);
-  if (r.a.x > 1) h *= binom_small(xs[r.a.z], r.b.y);
-  if (r.a.x > 2) h *= binom_small(xs[r.a.w], r.b.z);
-  return __dmul_rn(keff, __ll2double_rn(h));
+  if (nr > 0) h *= binom_small(xs[d.w.y], (pk >> 5) & 3);
+  if (nr > 1) h *= binom_small(xs[d.w.z], (pk >> 7) & 3);
+  if (nr > 2) h *= binom_small(xs[d.w.w], (pk >> 9) & 3);
+  return __dmul_rn(d.keff, __ll2double_rn(h));
 }
 
 __device__ __forceinline__ double2 lds2(const double *p) { return *reinterpret_cast<const double2 *>(p); }
@@ -173,10 +185,8 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
     e.x = __shfl_sync(0xffffffffu, my_e.x, used);
     e.y = __shfl_sync(0xffffffffu, my_e.y, used);
     ++used;
-    const double tn = advance_clock(t, e, rcp_pos(a0));
-    if (bits(tn) > tau_bits) break;
-    if (nev >= E.max_steps) { status = kStatusStepCap; break; }
-    // descent: stored levels two at a time, then the computed lowest level and the leaves
+    // descent (no side effects, so it may run before the clock decides whether the event
+    // fires): stored levels two at a time, then the computed lowest level and the leaves
     double target = __dmul_rn(u01_index(m2), a0);
     int k = 1, lvl = 0;
     for (; lvl + 2 <= Lw - 2; lvl += 2) {
@@ -201,24 +211,32 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
       descend_step(target, k, pr.x, pr.y);
     }
     const int j = k - Pw;
-    // everything the event reads from global memory, before the counts change
-    const int db = __ldg(&N.meta[j].d_begin), de = __ldg(&N.meta[j].d_end);
-    const int qb = __ldg(&N.dep_ptr[j]), qe = __ldg(&N.dep_ptr[j + 1]);
-    const bool has_d = db + lane < de;
-    const int dsp = has_d ? __ldg(&N.d_sp[db + lane]) : 0;
-    const int dval = has_d ? __ldg(&N.d_val[db + lane]) : 0;
-    const int ia = qb + lane < qe ? __ldg(&N.dep_idx[qb + lane]) : -1;
-    const int ib = qb + 32 + lane < qe ? __ldg(&N.dep_idx[qb + 32 + lane]) : -1;
-    MetaRegs ma{}, mb{};
-    double ka = 0.0, kna = 0.0, kb = 0.0, knb = 0.0;
-    if (ia >= 0) { ma = load_meta(&N.meta[ia]); ka = __ldg(&keff[ia]); kna = __ldg(&Kn[ia]); }
-    if (ib >= 0) { mb = load_meta(&N.meta[ib]); kb = __ldg(&keff[ib]); knb = __ldg(&Kn[ib]); }
+    // the fired reaction's record -- net changes and the dependents' parameters, one round
+    // trip -- is requested before the clock arithmetic, which then overlaps the loads
+    const int4 *rec = N.wrec + (size_t)j * N.wrec_stride;
+    const int4 hdr = __ldg(rec);                       // n_changes, n_dependents, d_begin, dep_begin
+    int2 chg = make_int2(-1, 0);
+    if (lane < N.wrec_chg) chg = __ldg(reinterpret_cast<const int2 *>(rec + 1) + lane);
+    const int4 *dr = rec + 1 + (N.wrec_chg + 1) / 2;
+    DepRec da = load_dep(dr, lane, N.wrec_dep);
+    DepRec db = load_dep(dr, lane + 32, N.wrec_dep);
+    DepRec dc = load_dep(dr, lane + 64, N.wrec_dep);
+    const double tn = advance_clock(t, e, rcp_pos(a0));
+    if (bits(tn) > tau_bits) break;
+    if (nev >= E.max_steps) { status = kStatusStepCap; break; }
+    if (ps != 0) {                                      // the record holds parameter set 0
+      if (da.w.x >= 0) { da.keff = keff[dep_index(da)]; da.Kn = Kn[dep_index(da)]; }
+      if (db.w.x >= 0) { db.keff = keff[dep_index(db)]; db.Kn = Kn[dep_index(db)]; }
+      if (dc.w.x >= 0) { dc.keff = keff[dep_index(dc)]; dc.Kn = Kn[dep_index(dc)]; }
+    }
+    const int cb = hdr.z + N.wrec_chg, ce = hdr.z + hdr.x;      // changes past the record
+    const int qb = hdr.w + N.wrec_dep, qe = hdr.w + hdr.y;      // dependents past the record
     // overflow check, then apply the net changes (one lane per changed species)
-    bool over = has_d && xs[dsp] + dval > kMaxCount;
-    for (int q = db + 32 + lane; q < de; q += 32) over |= xs[N.d_sp[q]] + N.d_val[q] > kMaxCount;
+    bool over = chg.x >= 0 && xs[chg.x] + chg.y > kMaxCount;
+    for (int q = cb + lane; q < ce; q += 32) over |= xs[N.d_sp[q]] + N.d_val[q] > kMaxCount;
     if (__any_sync(0xffffffffu, over)) { status = kStatusOverflow; break; }
-    if (has_d) xs[dsp] += dval;
-    for (int q = db + 32 + lane; q < de; q += 32) xs[N.d_sp[q]] += N.d_val[q];
+    if (chg.x >= 0) xs[chg.x] += chg.y;
+    for (int q = cb + lane; q < ce; q += 32) xs[N.d_sp[q]] += N.d_val[q];
     __syncwarp();
     ++nev;
     t = tn;
@@ -241,13 +259,15 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
     if (recycled) { rebuild(); __syncwarp(); continue; }
     // dependent reactions: new leaves, then the dirty ancestors once, level by level
     {
-      double pa = 0.0, pb = 0.0;
-      if (ia >= 0) pa = propensity_regs(ma, ka, kna, xs);
-      if (ib >= 0) pb = propensity_regs(mb, kb, knb, xs);
-      if (ia >= 0) lf[ia] = pa;
-      if (ib >= 0) lf[ib] = pb;
+      double pa = 0.0, pb = 0.0, pc = 0.0;
+      if (da.w.x >= 0) pa = propensity_rec(da, xs);
+      if (db.w.x >= 0) pb = propensity_rec(db, xs);
+      if (dc.w.x >= 0) pc = propensity_rec(dc, xs);
+      if (da.w.x >= 0) lf[dep_index(da)] = pa;
+      if (db.w.x >= 0) lf[dep_index(db)] = pb;
+      if (dc.w.x >= 0) lf[dep_index(dc)] = pc;
     }
-    for (int q = qb + 64 + lane; q < qe; q += 32) {
+    for (int q = qb + lane; q < qe; q += 32) {
       const int i = N.dep_idx[q];
       lf[i] = propensity(N.meta[i], keff[i], Kn[i], xs, 1);
     }
@@ -256,13 +276,15 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
       const int cnt = Pw >> sh;            // nodes on this level: [cnt, 2 cnt)
       if (cnt > 32) {
         if (sh == 2) {
-          if (ia >= 0) update_from_leaves(nd, lf, Pw, (Pw + ia) >> 2);
-          if (ib >= 0) update_from_leaves(nd, lf, Pw, (Pw + ib) >> 2);
-          for (int q = qb + 64 + lane; q < qe; q += 32) update_from_leaves(nd, lf, Pw, (Pw + N.dep_idx[q]) >> 2);
+          if (da.w.x >= 0) update_from_leaves(nd, lf, Pw, (Pw + dep_index(da)) >> 2);
+          if (db.w.x >= 0) update_from_leaves(nd, lf, Pw, (Pw + dep_index(db)) >> 2);
+          if (dc.w.x >= 0) update_from_leaves(nd, lf, Pw, (Pw + dep_index(dc)) >> 2);
+          for (int q = qb + lane; q < qe; q += 32) update_from_leaves(nd, lf, Pw, (Pw + N.dep_idx[q]) >> 2);
         } else {
-          if (ia >= 0) update_from_children(nd, (Pw + ia) >> sh);
-          if (ib >= 0) update_from_children(nd, (Pw + ib) >> sh);
-          for (int q = qb + 64 + lane; q < qe; q += 32) update_from_children(nd, (Pw + N.dep_idx[q]) >> sh);
+          if (da.w.x >= 0) update_from_children(nd, (Pw + dep_index(da)) >> sh);
+          if (db.w.x >= 0) update_from_children(nd, (Pw + dep_index(db)) >> sh);
+          if (dc.w.x >= 0) update_from_children(nd, (Pw + dep_index(dc)) >> sh);
+          for (int q = qb + lane; q < qe; q += 32) update_from_children(nd, (Pw + N.dep_idx[q]) >> sh);
         }
       } else if (lane < cnt) {
         if (sh == 2) update_from_leaves(nd, lf, Pw, cnt + lane);

@@ -336,6 +336,34 @@ def test_warp_mapping_synthetic_354x3680():
     assert ev.min() > 1000                      # hundreds of events per walker per interval
 
 
+def _hub_network(n_x=40):
+    """A hub species H read by 102 reactions (H -> H + X_k for 100 rate constants, H -> 0 and
+    H -> X_0 + ... + X_39), so the reactions that change H have more dependents than an event
+    record holds (96), and H -> X_0 + ... + X_39 has 41 net changes (a record holds 32)."""
+    H = n_x
+    reactants, products, rate = [], [], []
+    for k in range(100):
+        reactants.append([(H, 1)]); products.append([(H, 1), (k % n_x, 1)]); rate.append(0.05 + 0.001 * k)
+    for k in range(n_x):
+        reactants.append([(k, 1)]); products.append([]); rate.append(1.0)
+    reactants.append([]); products.append([(H, 1)]); rate.append(5.0)
+    reactants.append([(H, 1)]); products.append([]); rate.append(1.0)
+    reactants.append([(H, 1)]); products.append([(k, 1) for k in range(n_x)]); rate.append(0.2)
+    return W.NetworkSpec(species=[f"X{k}" for k in range(n_x)] + ["H"], reactants=reactants,
+                         products=products, rate=[rate], name="hub")
+
+
+def test_warp_mapping_past_the_event_record():
+    """Dependents and net changes beyond what the warp kernel's per-reaction record holds are
+    read from the CSR arrays; trajectories stay bit-exact."""
+    net = _hub_network()
+    x0 = [0] * 40 + [5]
+    cfg = W.WEConfig(network=net, bins=W.GridBins([40], [W.uniform_edges(0, 1, 21)]), tau=2.0,
+                     m_targ=4, n_iters=6, x0=x0, hist_species=40, hist_len=22, name="hub")
+    ens = _parity(cfg, cfg.n_iters, mapping=P.WE_MAP_WARP)
+    assert ens.per_iter(P.WE_OUT_EVENTS, 0).min() > 100
+
+
 def test_warp_mapping_synthetic_plain_ssa_times():
     cfg = _small_synthetic(n_walkers=40, n_iters=2)
     ens = gpu_run(cfg, 2, resample=False, mapping=P.WE_MAP_WARP)
