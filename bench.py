@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--block", type=int, default=0, help="threads per block of the SSA kernel (0: auto)")
     ap.add_argument("--workload", choices=["schlogl", "toggle_learned", "toggle_batch", "synthetic_large"],
                     default="schlogl")
+    ap.add_argument("--batch-iters", type=int, default=0,
+                    help="toggle_batch / synthetic_large: WE iterations per step (0: 500 / 100)")
     ap.add_argument("--plain-iters", type=int, default=120000, help="toggle_learned: plain-binning iterations")
     ap.add_argument("--learned-iters", type=int, default=2000, help="toggle_learned: learned-binning iterations")
     return ap.parse_args()
@@ -392,17 +394,17 @@ def run_batch_workload(a):
 
     pbuild.build()
     if a.workload == "toggle_batch":
-        n_iters = 500
+        n_iters = a.batch_iters or 500
         mk = lambda seed: W.toggle_batch_we(n_runs=64, n_iters=n_iters, seed=seed)
         desc = ("batched two-gene toggle sweep: 64 runs, a_U, a_V uniform in [20,60], K=1, n=2, d=1; "
-                "30x30 bins of width 4 x 8 walkers, tau=0.1, 500 iterations, recycling into "
+                f"30x30 bins of width 4 x 8 walkers, tau=0.1, {n_iters} iterations, recycling into "
                 "{V>=a_V/2, U<=a_U/4}, one launch per phase for all runs")
     else:
-        n_iters = 100
+        n_iters = a.batch_iters or 100
         mk = lambda seed: W.synthetic_large_we(n_walkers=4096, n_iters=n_iters, seed=seed)
         desc = ("synthetic 354-species / 3680-reaction network (seed 7): 4096 walkers, counts "
                 "uniform in [0,200], 50 bins of width 4 on species 0 x 82 walkers, tau=0.01, "
-                "100 iterations, one warp per walker")
+                f"{n_iters} iterations, one warp per walker")
     base = mk(0)
     net = P.network_from_spec(base.network)
     bm = P.we_binmap_grid(base.bins.species, base.bins.edges)
