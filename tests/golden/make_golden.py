@@ -16,14 +16,16 @@ def main():
     b, d = E.schlogl_rates()
     bb, dd = E.birth_death_rates()
     out = {
-        "source": "oracle/exact.py (birth-death closed forms, truncated CME); see each entry",
+        "source": "oracle/exact.py (birth-death closed forms, truncated CME, uniformized futile-cycle CME); see each entry",
         "schlogl_mfpt_85_to_550_s": E.bd_mfpt(85, 550, b, d),
         "schlogl_mfpt_82_to_563_s": E.bd_mfpt(82, 563, b, d),
         "schlogl_p_ge_700_t5_from_82": float(E.bd_transient(b, d, 82, 5.0, 2000)[700:].sum()),
         "birth_death_mfpt_100_to_250": E.bd_mfpt(100, 250, bb, dd),
+        "futile_p_s1_gt_90_t100": float(E.futile_s1_law(100.0)[91:].sum()),
         "notes": {
             "schlogl_mfpt_82_to_563_s": "paper Sec. III.B.3 quotes approximately 5e4 s",
             "schlogl_p_ge_700_t5_from_82": "paper Sec. III.B.3 prints the CME value 1.148e-9",
+            "futile_p_s1_gt_90_t100": "paper Sec. III.A prints the CME value 2.72e-18 (from S1 = S2 = 50)",
         },
     }
     with open(os.path.join(HERE, "exact_values.json"), "w") as f:

@@ -298,6 +298,56 @@ def test_merge_ties_take_earliest():
     assert set(p2.tolist()) in ({0, 2, 3}, {1, 2, 3})
 
 
+# ---------------------------------------------------------------- futile-cycle CME -------------
+def test_futile_cme_matches_paper_and_invariants():
+    """The futile cycle's exact law (uniformized CME over its 400 states): P(S1 > 90, t = 100)
+    from S1 = S2 = 50 equals the 2.72e-18 printed in Sec. III.A; S1 and S2 have the same law
+    (the two half-cycles have the same rates), the law sums to 1, and it agrees with a dense
+    matrix exponential where that is accurate (the bulk)."""
+    law = E.futile_s1_law(100.0)
+    assert round(law[91:].sum(), 20) == pytest.approx(2.72e-18, abs=0.005e-18)
+    assert abs(law.sum() - 1.0) < 1e-10
+    from scipy.linalg import expm
+    st, idx, tr = E.futile_generator()
+    n = len(st)
+    assert n == 400
+    p0 = np.zeros(n)
+    p0[idx[(0, 0, 50)]] = 1.0
+    pt = E.uniformized_transient(n, tr, p0, 100.0)
+    s1_law, s2_law = np.zeros(101), np.zeros(101)
+    for k, (b1, b2, s1) in enumerate(st):
+        s1_law[s1] += pt[k]
+        s2_law[100 - s1 - b1 - b2] += pt[k]
+    np.testing.assert_allclose(s1_law, law, rtol=1e-12)
+    np.testing.assert_allclose(s1_law, s2_law, rtol=1e-9, atol=0)     # S1 <-> S2 symmetry
+    Q = np.zeros((n, n))
+    for a_, b_, r in tr:
+        Q[a_, b_] += r
+        Q[a_, a_] -= r
+    p = p0 @ expm(Q * 20.0)
+    dense = np.zeros(101)
+    for k, (b1, b2, s1) in enumerate(st):
+        dense[s1] += p[k]
+    short = E.futile_s1_law(20.0)
+    bulk = dense > 1e-6
+    np.testing.assert_allclose(short[bulk], dense[bulk], rtol=1e-9)
+
+
+def test_futile_cme_generator_against_the_oracle_network():
+    """Every CME transition out of a state equals the oracle's propensity of the reaction that
+    makes it (S1, S2, E1, E2, B1, B2 order), and the CME's total exit rate equals a0."""
+    net = O.Network(W.futile_cycle())
+    st, idx, tr = E.futile_generator()
+    out = {}
+    for a_, b_, r in tr:
+        out[a_] = out.get(a_, 0.0) + r
+    for k, (b1, b2, s1) in enumerate(st[::37]):
+        kk = idx[(b1, b2, s1)]
+        s2 = 100 - s1 - b1 - b2
+        a = net.propensities([s1, s2, 1 - b1, 1 - b2, b1, b2])
+        assert math.isclose(sum(a), out.get(kk, 0.0), rel_tol=1e-15)
+
+
 # ---------------------------------------------------------------- whole WE runs ------------------
 def _replicas(cfg, R, **kw):
     outs = []

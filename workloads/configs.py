@@ -12,7 +12,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .networks import NetworkSpec, birth_death, schlogl, synthetic_large, toggle_switch
+from .networks import NetworkSpec, birth_death, futile_cycle, schlogl, synthetic_large, toggle_switch
 
 OP_GE = 0
 OP_LE = 1
@@ -153,6 +153,15 @@ def schlogl_pdf_we(n_iters: int = 101, n_runs: int = 1, seed: int = 0, m_targ: i
     return WEConfig(network=net, bins=bins, tau=0.05, m_targ=m_targ, n_iters=n_iters,
                     x0=[x0, A, B], n_runs=n_runs, seed=seed, hist_species=0, hist_len=1201,
                     name="schlogl_pdf")
+
+
+def futile_pdf_we(n_iters: int = 100, n_runs: int = 1, seed: int = 0, m_targ: int = 100) -> WEConfig:
+    """Enzymatic futile cycle distribution (Sec. III.A): 101 unit-width bins on S1, 100 walkers
+    per bin, tau=1, 100 iterations, from S1 = S2 = 50 with both enzymes free."""
+    bins = GridBins(species=[0], edges=[uniform_edges(0, 1, 101)])
+    return WEConfig(network=futile_cycle(), bins=bins, tau=1.0, m_targ=m_targ, n_iters=n_iters,
+                    x0=[50, 50, 1, 1, 0, 0], n_runs=n_runs, seed=seed, hist_species=0,
+                    hist_len=102, name="futile_pdf")
 
 
 def toggle_params(n_runs: int = 64, seed: int = 0, lo: float = 20.0, hi: float = 60.0):
