@@ -199,6 +199,16 @@ typedef struct {
                                       mappings: 128 = one event warp fed by three draw warps
                                       per 32 walkers (default); 32, 64, 96 = every thread
                                       makes its own draws */
+  int32_t reweight_period;         /* 0: off.  > 0: steady-state reweighting (Sec. II.B.2,
+                                      Eq. "ss") after the split/merge of every
+                                      reweight_period-th iteration: the rates k_ij = F_ij / W_j
+                                      from the weight F_ij that moved from bin j to bin i over
+                                      all intervals so far (W_j = sum_i F_ij), the balance
+                                      equations over the bins with W_j > 0 solved by Gaussian
+                                      elimination, and the walkers of every bin that holds any
+                                      rescaled to the solved bin weights (their total kept).
+                                      Needs resample = 1 and at most 1024 bins; adds
+                                      16 * n_bins^2 bytes per run to the workspace */
 } we_run_config;
 
 /* ------------------------------------------------------------------------------------------
@@ -260,6 +270,8 @@ we_status we_ensemble_sync(we_ensemble *ens, void *stream);
  *   WE_OUT_Z         float[n_prev]                  learned coordinate of each walker at the end
  *                                                   of the last interval (learned bin maps)
  *   WE_OUT_NREC      int32[n_prev]                  recycles of each walker in the last interval
+ *   WE_OUT_RW        int32[iters x runs]            steady-state reweighting per iteration: 1 done,
+ *                                                   -1 attempted and skipped, 0 not scheduled
  * Per-iteration arrays hold the recorded iterations in order. */
 #define WE_OUT_COUNTS 1
 #define WE_OUT_STATES 2
@@ -276,6 +288,7 @@ we_status we_ensemble_sync(we_ensemble *ens, void *stream);
 #define WE_OUT_TLAST 13
 #define WE_OUT_Z 14
 #define WE_OUT_NREC 15
+#define WE_OUT_RW 16
 we_status we_ensemble_get(we_ensemble *ens, int32_t what, int32_t run, void *dst,
                           size_t dst_bytes, size_t *needed, void *stream);
 

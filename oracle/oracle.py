@@ -37,13 +37,15 @@ class WEConfigC(C.Structure):
                 ("n_clauses", C.c_int32), ("tgt_species", C.c_int32 * 4),
                 ("tgt_op", C.c_int32 * 4), ("tgt_threshold", C.c_int32 * 4),
                 ("recycle_state", _I32P), ("max_steps", C.c_int64), ("capacity", C.c_int32),
-                ("hist_species", C.c_int32), ("hist_len", C.c_int32), ("resample", C.c_int32)]
+                ("hist_species", C.c_int32), ("hist_len", C.c_int32), ("resample", C.c_int32),
+                ("reweight_period", C.c_int32)]
 
 
 class WEOut(C.Structure):
     _fields_ = [("flux_weight", _F64P), ("total_weight", _F64P), ("n_walkers", _I32P),
                 ("events", _I64P), ("hist", _F64P), ("states", _I32P), ("weights", _F64P),
-                ("parent", _I32P), ("t_last", _F64P), ("n_final", C.c_int32), ("status", C.c_int32)]
+                ("parent", _I32P), ("t_last", _F64P), ("n_final", C.c_int32), ("status", C.c_int32),
+                ("reweighted", _I32P)]
 
 
 _lib = None
@@ -77,6 +79,8 @@ def lib():
                                    C.c_int32, C.c_uint64, C.c_uint32, C.c_int32, _I32P, _F64P, _I32P]
         L.orc_resample.restype = C.c_int32
         L.orc_we_run.argtypes = [C.c_void_p, C.POINTER(WEConfigC), C.POINTER(WEOut)]
+        L.orc_rw_solve.argtypes = [C.c_int32, _F64P, _F64P, _F64P]
+        L.orc_rw_solve.restype = C.c_int32
         L.orc_we_run.restype = C.c_int
         _lib = L
     return _lib
@@ -189,6 +193,7 @@ def make_config(cfg, run: int = 0, n_iters: int | None = None, first_iter: int |
     c.hist_species = cfg.hist_species
     c.hist_len = cfg.hist_len
     c.resample = 1 if resample else 0
+    c.reweight_period = int(getattr(cfg, "reweight_period", 0) or 0)
     return c, keep
 
 
@@ -207,12 +212,13 @@ def we_run(cfg, run: int = 0, n_iters: int | None = None, first_iter: int | None
         "n_walkers": np.zeros(n, dtype=np.int32), "events": np.zeros(n, dtype=np.int64),
         "hist": np.zeros((n, max(cfg.hist_len, 1))), "states": np.zeros((cap, S), dtype=np.int32),
         "weights": np.zeros(cap), "parent": np.zeros(cap, dtype=np.int32), "t_last": np.zeros(cap),
+        "reweighted": np.zeros(n, dtype=np.int32),
     }
     out = WEOut(_p(o["flux_weight"], _F64P), _p(o["total_weight"], _F64P),
                 _p(o["n_walkers"], _I32P), _p(o["events"], _I64P),
                 _p(o["hist"], _F64P) if cfg.hist_len > 0 else None,
                 _p(o["states"], _I32P), _p(o["weights"], _F64P), _p(o["parent"], _I32P),
-                _p(o["t_last"], _F64P), 0, 0)
+                _p(o["t_last"], _F64P), 0, 0, _p(o["reweighted"], _I32P))
     lib().orc_we_run(net.h, C.byref(c), C.byref(out))
     nf = out.n_final
     o["t_last_prev"] = o["t_last"]
@@ -264,6 +270,17 @@ def resample(states, weights, bins, n_bins: int, m_targ: int, iteration: int, se
     if m < 0:
         raise RuntimeError(f"oracle resample failed: {STATUS.get(m, m)}")
     return os_[:m], ow[:m], op[:m]
+
+
+def rw_solve(F, cb):
+    """Steady-state reweighting factors per bin from accumulated transfers F[end, start] and the
+    current bin weights (Sec. II.B.2, Eq. "ss"); returns (status, factors)."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    nb = F.shape[0]
+    cb = np.ascontiguousarray(cb, dtype=np.float64)
+    fac = np.zeros(nb)
+    st = lib().orc_rw_solve(nb, _p(F, _F64P), _p(cb, _F64P), _p(fac, _F64P))
+    return st, fac
 
 
 def we_run_all(cfg, **kw) -> list:

@@ -416,6 +416,95 @@ int32_t orc_resample(int32_t n, int32_t S, const int32_t *states, const double *
 }
 
 /* ------------------------------------------------------------------------------------------
+ * Steady-state reweighting (Sec. II.B.2, Eq. "ss").  In steady state the weight flowing into
+ * each bin equals the weight flowing out: sum_j (k_ij w_j - k_ji w_i) = 0, with f_ij = k_ij w_j
+ * the flux into bin i from bin j.  The rates are estimated from the measured transfers,
+ * k_ij = F_ij / W_j, where F_ij is the weight that started an interval in bin j and ended it in
+ * bin i, and W_j = sum_i F_ij (ascending i) the weight that started in j, both summed over all
+ * intervals so far.  Only bins with W_j > 0 take part ("active"); transfers into other bins
+ * are left out (nothing is known about leaving them).  The balance equations over the active
+ * bins, with the last one replaced by sum_i w_i = 1, are solved by Gaussian elimination with
+ * partial pivoting (largest magnitude, ties to the lower row; every product and difference
+ * rounded on its own) and column-oriented back substitution.  Bins that hold walkers now take
+ * the solved weights, scaled so that their total is unchanged: the walkers of bin i are
+ * multiplied by (x_i q) / c_i with q = (sum of their current weights c) / (sum of their x).
+ * Nothing is changed when fewer than two bins are active, a pivot is zero, or a bin holding
+ * walkers gets a solved weight that is not positive.
+ * ------------------------------------------------------------------------------------------ */
+int32_t orc_rw_solve(int32_t nb, const double *F, const double *cb, double *fac) {
+  for (int32_t b = 0; b < nb; ++b) fac[b] = 0.0;
+  double *W = (double *)malloc(sizeof(double) * nb);
+  int32_t *A = (int32_t *)malloc(sizeof(int32_t) * nb);
+  if (!W || !A) { free(W); free(A); return -1; }
+  int32_t n = 0;
+  for (int32_t b = 0; b < nb; ++b) {
+    double s = 0.0;
+    for (int32_t e = 0; e < nb; ++e) s = s + F[(size_t)e * nb + b];
+    W[b] = s;
+    if (s > 0.0) A[n++] = b;
+  }
+  int32_t result = -1;
+  double *M = NULL, *rhs = NULL, *x = NULL;
+  if (n < 2) goto done;
+  M = (double *)malloc(sizeof(double) * (size_t)n * n);
+  rhs = (double *)malloc(sizeof(double) * n);
+  x = (double *)malloc(sizeof(double) * n);
+  if (!M || !rhs || !x) goto done;
+  /* k_ij off the diagonal; the diagonal is minus the column's other entries (rate out of j) */
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = 0; j < n; ++j)
+      M[(size_t)i * n + j] = i == j ? 0.0 : F[(size_t)A[i] * nb + A[j]] / W[A[j]];
+  for (int32_t j = 0; j < n; ++j) {
+    double out = 0.0;
+    for (int32_t i = 0; i < n; ++i)
+      if (i != j) out = out + M[(size_t)i * n + j];
+    M[(size_t)j * n + j] = -out;
+  }
+  for (int32_t j = 0; j < n; ++j) M[(size_t)(n - 1) * n + j] = 1.0;
+  for (int32_t i = 0; i < n; ++i) rhs[i] = i == n - 1 ? 1.0 : 0.0;
+  for (int32_t k = 0; k < n; ++k) {
+    int32_t p = k;
+    for (int32_t r = k + 1; r < n; ++r)
+      if (fabs(M[(size_t)r * n + k]) > fabs(M[(size_t)p * n + k])) p = r;
+    if (M[(size_t)p * n + k] == 0.0) goto done;
+    if (p != k) {
+      for (int32_t c = 0; c < n; ++c) {
+        double t = M[(size_t)k * n + c]; M[(size_t)k * n + c] = M[(size_t)p * n + c]; M[(size_t)p * n + c] = t;
+      }
+      double t = rhs[k]; rhs[k] = rhs[p]; rhs[p] = t;
+    }
+    for (int32_t r = k + 1; r < n; ++r) {
+      double l = M[(size_t)r * n + k] / M[(size_t)k * n + k];
+      for (int32_t c = k + 1; c < n; ++c) M[(size_t)r * n + c] = M[(size_t)r * n + c] - l * M[(size_t)k * n + c];
+      rhs[r] = rhs[r] - l * rhs[k];
+    }
+  }
+  for (int32_t k = n - 1; k >= 0; --k) {
+    x[k] = rhs[k] / M[(size_t)k * n + k];
+    for (int32_t r = 0; r < k; ++r) rhs[r] = rhs[r] - M[(size_t)r * n + k] * x[k];
+  }
+  {
+    double C = 0.0, T = 0.0;
+    int32_t held = 0;
+    for (int32_t i = 0; i < n; ++i) {
+      if (!(cb[A[i]] > 0.0)) continue;
+      if (!(x[i] > 0.0) || isinf(x[i])) goto done;
+      C = C + cb[A[i]];
+      T = T + x[i];
+      ++held;
+    }
+    if (held == 0 || !(T > 0.0) || isinf(T)) goto done;
+    const double q = C / T;
+    for (int32_t i = 0; i < n; ++i)
+      if (cb[A[i]] > 0.0) fac[A[i]] = (x[i] * q) / cb[A[i]];
+    result = 1;
+  }
+done:
+  free(W); free(A); free(M); free(rhs); free(x);
+  return result;
+}
+
+/* ------------------------------------------------------------------------------------------
  * The WE procedure (Sec. II.B, algorithm listing): for each iteration, propagate every walker for
  * tau, record the observables, then split/merge per bin.  Observables per iteration: the
  * recycled weight (its ratio to tau is the flux whose inverse is the MFPT, Eq. "mfpt"), the
@@ -442,6 +531,22 @@ int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
     free(st); free(st2); free(w); free(w2); free(par); free(bins); free(nrec);
     return out->status = ORC_ENOMEM;
   }
+  /* steady-state reweighting: start bin of every walker (-1: unknown, the initial walkers),
+   * accumulated transfers F, a per-bin accumulator and the current bin weights */
+  const int rw = cfg->reweight_period > 0 && cfg->resample;
+  int32_t *sbin = (int32_t *)malloc(sizeof(int32_t) * cap);
+  double *F = rw ? (double *)calloc((size_t)n_bins * n_bins, sizeof(double)) : NULL;
+  double *acc = rw ? (double *)calloc((size_t)n_bins, sizeof(double)) : NULL;
+  double *cb = rw ? (double *)calloc((size_t)n_bins, sizeof(double)) : NULL;
+  double *fac = rw ? (double *)calloc((size_t)n_bins, sizeof(double)) : NULL;
+  int32_t *mark = rw ? (int32_t *)malloc(sizeof(int32_t) * n_bins) : NULL;
+  if (!sbin || (rw && (!F || !acc || !cb || !fac || !mark))) {
+    free(st); free(st2); free(w); free(w2); free(par); free(bins); free(nrec);
+    free(sbin); free(F); free(acc); free(cb); free(fac); free(mark);
+    return out->status = ORC_ENOMEM;
+  }
+  for (int32_t i = 0; i < cap; ++i) sbin[i] = -1;
+  for (int32_t b = 0; rw && b < n_bins; ++b) mark[b] = -1;
   int32_t nw = cfg->n_init;
   memcpy(st, cfg->init_states, sizeof(int32_t) * (size_t)nw * S);
   memcpy(w, cfg->init_weights, sizeof(double) * nw);
@@ -473,12 +578,36 @@ int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
     if (status != ORC_OK) break;
     if (cfg->resample) {
       for (int32_t s = 0; s < nw; ++s) bins[s] = orc_bin_of(cfg, st + (size_t)s * S);
+      if (rw) {
+        /* transfers of this interval: the walkers of one start bin are consecutive slots in
+         * ascending order (the resampling's output order); each (end, start) pair is summed
+         * over them from 0, then added to F once */
+        int32_t s0 = 0;
+        while (s0 < nw) {
+          int32_t s1 = s0;
+          while (s1 < nw && sbin[s1] == sbin[s0]) ++s1;
+          if (sbin[s0] >= 0) {
+            const int32_t b = sbin[s0];
+            for (int32_t s = s0; s < s1; ++s) {
+              if (mark[bins[s]] != s0) { mark[bins[s]] = s0; acc[bins[s]] = 0.0; }
+              acc[bins[s]] = acc[bins[s]] + w[s];
+            }
+            for (int32_t s = s0; s < s1; ++s)
+              if (mark[bins[s]] == s0) {
+                F[(size_t)bins[s] * n_bins + b] = F[(size_t)bins[s] * n_bins + b] + acc[bins[s]];
+                mark[bins[s]] = -1;
+              }
+          }
+          s0 = s1;
+        }
+      }
       int32_t m = orc_resample(nw, S, st, w, bins, n_bins, cfg->m_targ, iter, cfg->seed,
                                cfg->run_id, cap, st2, w2, par);
       if (m < 0) { status = m; break; }
       nw = m;
       int32_t *ts = st; st = st2; st2 = ts;
       double *tw = w; w = w2; w2 = tw;
+      for (int32_t s = 0; s < nw; ++s) sbin[s] = bins[par[s]];
     } else {
       for (int32_t s = 0; s < nw; ++s) par[s] = s;
     }
@@ -486,6 +615,17 @@ int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
     for (int32_t s = 0; s < nw; ++s) tot = tot + w[s];
     out->total_weight[li] = tot;
     out->n_walkers[li] = nw;
+    if (out->reweighted) out->reweighted[li] = 0;
+    if (rw && (li + 1) % cfg->reweight_period == 0) {
+      /* current bin weights, each summed over its walkers in ascending slot order */
+      for (int32_t b = 0; b < n_bins; ++b) cb[b] = 0.0;
+      for (int32_t s = 0; s < nw; ++s) cb[sbin[s]] = cb[sbin[s]] + w[s];
+      const int32_t done = orc_rw_solve(n_bins, F, cb, fac);
+      if (done == 1)
+        for (int32_t s = 0; s < nw; ++s)
+          if (fac[sbin[s]] != 0.0) w[s] = w[s] * fac[sbin[s]];
+      if (out->reweighted) out->reweighted[li] = done;
+    }
   }
   memcpy(out->states, st, sizeof(int32_t) * (size_t)nw * S);
   memcpy(out->weights, w, sizeof(double) * nw);
@@ -493,5 +633,6 @@ int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
   out->n_final = nw;
   out->status = status;
   free(st); free(st2); free(w); free(w2); free(par); free(bins); free(nrec);
+  free(sbin); free(F); free(acc); free(cb); free(fac); free(mark);
   return status;
 }

@@ -77,6 +77,8 @@ typedef struct {
   int32_t capacity;                  /* walker slots */
   int32_t hist_species, hist_len;    /* weighted histogram of one species, last entry = overflow */
   int32_t resample;                  /* 0: plain propagation (no split/merge) */
+  int32_t reweight_period;           /* >0: steady-state reweighting (Eq. "ss") after the
+                                        resampling of every reweight_period-th iteration */
 } orc_we_config;
 
 typedef struct {
@@ -94,6 +96,8 @@ typedef struct {
                                         interval, by slot before resampling (may be NULL) */
   int32_t n_final;
   int32_t status;
+  int32_t *reweighted;               /* per iteration: 1 reweighted, -1 attempted and skipped,
+                                        0 not a reweighting iteration (may be NULL) */
 } orc_we_out;
 
 /* Philox-4x32-10 block function: out = philox(ctr, key). */
@@ -127,6 +131,12 @@ int32_t orc_resample(int32_t n, int32_t n_species, const int32_t *states, const 
                      const int32_t *bins, int32_t n_bins, int32_t m_targ, int32_t iter,
                      uint64_t seed, uint32_t run_id, int32_t capacity,
                      int32_t *out_states, double *out_weights, int32_t *out_parent);
+
+/* Steady-state reweighting (Sec. II.B.2, Eq. "ss").  F[e * n_bins + b] holds the weight that
+ * moved from bin b (start of an interval) to bin e (its end), summed over the intervals seen;
+ * cb[b] the current weight of bin b.  Writes fac[b] = the factor for the walkers of bin b
+ * (0: leave them as they are) and returns 1, or returns -1 when no reweighting is possible. */
+int32_t orc_rw_solve(int32_t n_bins, const double *F, const double *cb, double *fac);
 
 /* The whole WE run of the paper's algorithm listing (Sec. II.B). */
 int orc_we_run(const orc_net *net, const orc_we_config *cfg, orc_we_out *out);

@@ -42,6 +42,7 @@ WE_OUT_RECORDED = 12
 WE_OUT_TLAST = 13
 WE_OUT_Z = 14
 WE_OUT_NREC = 15
+WE_OUT_RW = 16
 
 _I32P = C.POINTER(C.c_int32)
 _U32P = C.POINTER(C.c_uint32)
@@ -59,7 +60,7 @@ class we_run_config(C.Structure):
         ("tgt_species", C.c_int32 * 4), ("tgt_op", C.c_int32 * 4), ("tgt_threshold", _I32P),
         ("recycle_state", _I32P), ("max_steps", C.c_int64), ("hist_species", C.c_int32),
         ("hist_len", C.c_int32), ("resample", C.c_int32), ("mapping", C.c_int32),
-        ("block_threads", C.c_int32),
+        ("block_threads", C.c_int32), ("reweight_period", C.c_int32),
     ]
 
 

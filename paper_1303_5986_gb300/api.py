@@ -111,7 +111,7 @@ def we_binmap_grid(species, edges) -> BinMap:
 def make_run_config(tau, m_targ, init_states, init_weights, *, n_runs=None, seed=0, run_ids=None,
                     param_set=None, first_iter=0, capacity=0, record_iters=1, target=None,
                     recycle_state=None, max_steps=0, hist_species=0, hist_len=0, resample=True,
-                    mapping=L.WE_MAP_AUTO, block_threads=0):
+                    mapping=L.WE_MAP_AUTO, block_threads=0, reweight_period=0):
     """Build a we_run_config.  init_states: (runs, n_init, S); init_weights: (runs, n_init);
     target: None or (species list, op list, thresholds (runs, clauses)).  Returns
     (config, keepalive) -- keep the second object alive while the config is used."""
@@ -154,6 +154,7 @@ def make_run_config(tau, m_targ, init_states, init_weights, *, n_runs=None, seed
     c.resample = 1 if resample else 0
     c.mapping = int(mapping)
     c.block_threads = int(block_threads)
+    c.reweight_period = int(reweight_period)
     return c, keep
 
 
@@ -174,7 +175,7 @@ def run_config_from(cfg, record_iters=None, resample=True, first_iter=None, init
         record_iters=cfg.n_iters if record_iters is None else record_iters, target=tgt,
         recycle_state=cfg.recycle_state, max_steps=cfg.max_steps if max_steps is None else max_steps,
         hist_species=cfg.hist_species, hist_len=cfg.hist_len, resample=resample, mapping=mapping,
-        block_threads=block_threads)
+        block_threads=block_threads, reweight_period=getattr(cfg, "reweight_period", 0) if resample else 0)
 
 
 _OUT_DTYPES = {
@@ -183,6 +184,7 @@ _OUT_DTYPES = {
     L.WE_OUT_NWALKERS: np.int32, L.WE_OUT_EVENTS: np.int64, L.WE_OUT_HIST: np.float64,
     L.WE_OUT_STATUS: np.int32, L.WE_OUT_ITER: np.int32, L.WE_OUT_RECORDED: np.int32,
     L.WE_OUT_TLAST: np.float64, L.WE_OUT_Z: np.float32, L.WE_OUT_NREC: np.int32,
+    L.WE_OUT_RW: np.int32,
 }
 
 

@@ -30,6 +30,8 @@ cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_pack_states(const EnsView &E, int r, int32_t *out, cudaStream_t st);
 cudaError_t launch_learned_bins(const PropagateParams &prm, cudaStream_t st);
+cudaError_t launch_rw_flux(const PropagateParams &prm, cudaStream_t st);
+cudaError_t launch_rw_solve_apply(const PropagateParams &prm, cudaStream_t st);
 }  // namespace we
 
 using namespace we;
@@ -329,6 +331,7 @@ struct Offsets {
   size_t logt, table, base;
   size_t lw1, lw2, lw3, lb, lz, zout;
   size_t wrec;
+  size_t rw_F, rw_M, rw_vec, rw_act, rw_obs;
   int32_t table_len, table_lenB, wrec_stride;
   size_t total;
 };
@@ -473,6 +476,14 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
   o.events = L.take(8 * rec * R);
   o.hist = L.take(8 * rec * R * (c->hist_len > 0 ? c->hist_len : 1));
   o.pack = L.take(4 * (size_t)R * cap * n->S);
+  if (c->reweight_period > 0) {
+    const size_t nb = b->n_bins;
+    o.rw_F = L.take(8 * R * nb * nb);
+    o.rw_M = L.take(8 * R * nb * nb);
+    o.rw_vec = L.take(8 * 5 * R * nb);
+    o.rw_act = L.take(4 * R * nb);
+    o.rw_obs = L.take(4 * rec * R);
+  }
   o.total = L.off;
   return o;
 }
@@ -519,6 +530,9 @@ static we_status check_config(const we_network *n, const we_binmap *b, const we_
   }
   if (c->hist_len < 0 || (c->hist_len > 0 && (c->hist_species < 0 || c->hist_species >= n->S)))
     return fail(WE_EINVAL, "bad histogram species/length");
+  if (c->reweight_period < 0) return fail(WE_EINVAL, "reweight_period must be >= 0");
+  if (c->reweight_period > 0 && (!c->resample || b->n_bins > 1024))
+    return fail(WE_EINVAL, "steady-state reweighting needs resample = 1 and at most 1024 bins");
   if (c->param_set)
     for (int r = 0; r < c->n_runs; ++r)
       if (c->param_set[r] < 0 || c->param_set[r] >= n->nps) return fail(WE_EINVAL, "run %d: parameter set out of range", r);
@@ -729,6 +743,18 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   V.obs_hist = at<double>(ws, o.hist);
   E->prm.resample = c->resample ? 1 : 0;
   E->prm.logt = at<LogTables>(ws, o.logt);
+  if (c->reweight_period > 0) {
+    RwView &rw = E->prm.rw;
+    const size_t nbR = (size_t)b->n_bins * R;
+    rw.period = c->reweight_period;
+    rw.nb = b->n_bins;
+    rw.F = at<double>(ws, o.rw_F);
+    rw.M = at<double>(ws, o.rw_M);
+    rw.W = at<double>(ws, o.rw_vec);
+    rw.cb = rw.W + nbR; rw.rhs = rw.cb + nbR; rw.x = rw.rhs + nbR; rw.fac = rw.x + nbR;
+    rw.act = at<int32_t>(ws, o.rw_act);
+    rw.obs = at<int32_t>(ws, o.rw_obs);
+  }
   E->prm.tab.species = -1;
   E->prm.tab.species2 = -1;
   E->prm.tab.lenB = 1;
@@ -781,9 +807,12 @@ static cudaError_t enqueue_propagate(we_ensemble *E, cudaStream_t s) {
 
 static cudaError_t enqueue_resample(we_ensemble *E, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (E->prm.resample) e = launch_resample_chain(E->prm, s);
-  if (e) return e;
-  return launch_gather_finalize(E->prm, s);
+  const bool rw = E->prm.resample && E->prm.rw.period > 0;
+  if (rw) e = launch_rw_flux(E->prm, s);           // before the split/merge replaces its tasks
+  if (!e && E->prm.resample) e = launch_resample_chain(E->prm, s);
+  if (!e) e = launch_gather_finalize(E->prm, s);
+  if (!e && rw) e = launch_rw_solve_apply(E->prm, s);
+  return e;
 }
 
 extern "C" we_status we_ensemble_propagate(we_ensemble *E, void *stream) {
@@ -1019,6 +1048,10 @@ extern "C" we_status we_ensemble_get(we_ensemble *E, int32_t what, int32_t run, 
                                          : (const void *)(V.nrec + (size_t)run * E->cap);
       if (bytes) WE_CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));
       return WE_OK;
+    }
+    case WE_OUT_RW: {
+      if (E->prm.rw.period <= 0) return fail(WE_EINVAL, "WE_OUT_RW needs reweight_period > 0");
+      return per_iter(E->prm.rw.obs, 4);
     }
     case WE_OUT_ITER: return scalar(&iter, 4);
     case WE_OUT_RECORDED: { int32_t v = rec; return scalar(&v, 4); }

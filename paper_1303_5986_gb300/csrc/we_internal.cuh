@@ -157,6 +157,19 @@ struct TableView {
   double clock_scale;          // 2^62 / tau, for rows evaluated on the fly
 };
 
+// Steady-state reweighting (Sec. II.B.2, Eq. "ss"): per run, the weight moved from bin b to
+// bin e summed over the intervals so far (F, nb x nb, row e), the solve's scratch (M, n x n
+// over the active bins), per-bin vectors and the per-iteration outcome.
+struct RwView {
+  int32_t period;              // 0: off; else reweight after every period-th iteration
+  int32_t nb;                  // bins
+  double *F;                   // R x nb x nb
+  double *M;                   // R x nb x nb
+  double *W, *cb, *rhs, *x, *fac;   // R x nb each
+  int32_t *act;                // R x nb: active bins, ascending
+  int32_t *obs;                // record_iters x R: 1 reweighted, -1 skipped, 0 not scheduled
+};
+
 struct PropagateParams {
   NetView net;
   BinView bins;
@@ -164,6 +177,7 @@ struct PropagateParams {
   TableView tab;
   const LogTables *logt;
   int32_t resample;            // 1: WE; 0: plain SSA (bookkeeping of parents is identity)
+  RwView rw;
 };
 
 }  // namespace we

@@ -305,6 +305,33 @@ def test_timed_step_matches_step_and_reports_kernel_times():
         assert np.array_equal(a.per_iter(P.WE_OUT_EVENTS, r), b.per_iter(P.WE_OUT_EVENTS, r))
 
 
+# ------------------------------------------------------------------ steady-state reweighting --
+@pytest.mark.parametrize("period", [1, 2, 5])
+def test_reweighting_parity_schlogl(period):
+    """Steady-state reweighting (Sec. II.B.2, Eq. "ss") on the Schloegl flux run, three runs in
+    one batch: the accumulated transfers, the Gaussian elimination and the rescaling give the
+    oracle's weights bit for bit, and the same iterations are reweighted or skipped."""
+    cfg = W.schlogl_flux_we(reweight_period=period, n_iters=24, n_runs=3, m_targ=6)
+    ens = _parity(cfg, 24)
+    rw = ens.per_iter(P.WE_OUT_RW)
+    for r in range(3):
+        o = oracle_run(cfg, r, n_iters=24)
+        assert np.array_equal(rw[:, r], o["reweighted"]), (period, r, rw[:, r], o["reweighted"])
+    assert (rw == 1).sum() >= 3 * (24 // period) // 2
+
+
+def test_reweighting_parity_toggle_2d():
+    """Reweighting over a 30 x 30 grid (900 bins) with Hill kinetics and one parameter set per
+    run."""
+    cfg = W.toggle_batch_we(n_runs=3, n_iters=12)
+    cfg.reweight_period = 3
+    ens = _parity(cfg, 12)
+    rw = ens.per_iter(P.WE_OUT_RW)
+    for r in range(3):
+        assert np.array_equal(rw[:, r], oracle_run(cfg, r, n_iters=12)["reweighted"])
+    assert (rw[[5, 8, 11]] == 1).all()
+
+
 # ------------------------------------------------------------------ warp per walker ----------
 @pytest.mark.parametrize("factory", ["schlogl", "toggle", "futile"])
 def test_warp_mapping_small_networks(factory):

@@ -443,3 +443,82 @@ def test_synthetic_network_homodimer_and_conservation():
             assert a[j] == spec.rate[0, j] * float(int(x[reac[0][0]]) * int(x[reac[1][0]]))
             seen_bi = True
     assert seen_dimer and seen_bi
+
+
+# ---------------------------------------------------------------- steady-state reweighting -----
+def _transfers(K, W):
+    """F[e, b] = P_eb W_b: the transfers over one interval of a chain whose moves b -> e (e != b)
+    have probabilities K[e, b]; the rest of the weight stays (P_bb = 1 - sum_e K[e, b]), so that
+    W_b = sum_e F[e, b] as in a WE run."""
+    P = K.copy()
+    np.fill_diagonal(P, 0.0)
+    np.fill_diagonal(P, 1.0 - P.sum(axis=0))
+    assert (P >= 0).all()
+    return P * W[None, :]
+
+
+def test_rw_solve_birth_death_chain_detailed_balance():
+    """Tridiagonal moves: the steady state is fixed by detailed balance,
+    pi_{i+1} / pi_i = up_i / down_{i+1}, with no linear solve.  The factors must give every bin
+    that holds walkers the weight pi_i scaled to the bins' current total."""
+    rng = np.random.default_rng(3)
+    n = 40
+    up = rng.uniform(0.02, 0.4, n)
+    down = rng.uniform(0.02, 0.4, n)
+    K = np.zeros((n, n))
+    for i in range(n - 1):
+        K[i + 1, i] = up[i]
+        K[i, i + 1] = down[i + 1]
+    W = rng.uniform(0.5, 3.0, n)
+    pi = np.ones(n)
+    for i in range(n - 1):
+        pi[i + 1] = pi[i] * up[i] / down[i + 1]
+    cb = rng.uniform(0.01, 1.0, n)
+    st, fac = O.rw_solve(_transfers(K, W), cb)
+    assert st == 1
+    new = fac * cb
+    np.testing.assert_allclose(new / new.sum(), pi / pi.sum(), rtol=1e-10)
+    assert abs(new.sum() - cb.sum()) < 1e-14 * cb.sum() * n
+
+
+def test_rw_solve_cycle_and_partial_occupancy():
+    """A one-way cycle 0 -> 1 -> 2 -> 0 with move probabilities a, b, c per interval has pi
+    proportional to (1/a, 1/b, 1/c) (inflow of each state = outflow).  A bin that holds no walkers keeps factor 0 and the others
+    share the current total in the solved proportions."""
+    a, b, c = 0.07, 0.25, 0.13
+    K = np.zeros((4, 4))
+    K[1, 0], K[2, 1], K[0, 2] = a, b, c
+    W = np.array([1.0, 2.0, 0.5, 0.0])                 # bin 3 never started an interval: inactive
+    cb = np.array([0.2, 0.0, 0.5, 0.3])                # bin 1 holds no walkers now
+    st, fac = O.rw_solve(_transfers(K, W), cb)
+    assert st == 1
+    pi = np.array([1 / a, 1 / b, 1 / c])
+    assert fac[1] == 0.0 and fac[3] == 0.0
+    held = fac[[0, 2]] * cb[[0, 2]]
+    np.testing.assert_allclose(held / held.sum(), pi[[0, 2]] / pi[[0, 2]].sum(), rtol=1e-12)
+    assert abs(held.sum() - (cb[0] + cb[2])) < 1e-15
+
+
+def test_rw_solve_refuses_degenerate_systems():
+    """One active bin, or two disconnected components (a zero pivot), leave everything as is."""
+    F = np.zeros((3, 3))
+    F[0, 0] = 1.0
+    st, fac = O.rw_solve(F, np.array([1.0, 0.0, 0.0]))
+    assert st == -1 and not fac.any()
+    K = np.zeros((4, 4))
+    K[1, 0], K[0, 1], K[3, 2], K[2, 3] = 0.1, 0.2, 0.1, 0.3
+    st, fac = O.rw_solve(_transfers(K, np.ones(4)), np.full(4, 0.25))
+    assert st == -1 and not fac.any()
+
+
+def test_we_with_reweighting_keeps_total_weight_and_schedule():
+    """Schloegl flux run with reweighting every 3 iterations: the schedule, the total weight
+    (1 to 1e-12 at every iteration) and the first reweighting only after transfers exist."""
+    cfg = W.schlogl_flux_we(reweight_period=3, n_iters=12, m_targ=4)
+    o = O.we_run(cfg, 0)
+    assert o["status"] == 0
+    rw = o["reweighted"]
+    assert list(np.nonzero(rw)[0]) == [2, 5, 8, 11]
+    assert (rw[[5, 8, 11]] == 1).all()
+    assert np.all(np.abs(o["total_weight"] - 1.0) < 1e-12)
+    assert abs(o["weights"].sum() - 1.0) < 1e-12

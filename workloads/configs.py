@@ -77,6 +77,7 @@ class WEConfig:
     capacity: int = 0
     max_steps: int = 0
     first_iter: int = 0
+    reweight_period: int = 0             # >0: steady-state reweighting every this many iterations
     name: str = ""
     notes: dict = field(default_factory=dict)
 
@@ -141,6 +142,19 @@ def schlogl_mfpt_we(n_iters: int = 1000, n_runs: int = 1, seed: int = 0, x0: int
     return WEConfig(network=net, bins=bins, tau=0.05, m_targ=m_targ, n_iters=n_iters,
                     x0=[x0, A, B], n_runs=n_runs, seed=seed, target=tgt, hist_species=0,
                     hist_len=1001, name="schlogl_mfpt")
+
+
+def schlogl_flux_we(reweight_period: int = 0, n_iters: int = 500, n_runs: int = 1, seed: int = 0,
+                    m_targ: int = 32) -> WEConfig:
+    """Schloegl flux run of Sec. III.B.2/3: 80 bins of width 10 on [0,800), 32 walkers per bin,
+    tau=0.1, 500 iterations from X0=82, recycling at X >= 563 back to 82; steady-state
+    reweighting every ``reweight_period`` iterations (the paper's RW-100, RW-5, RW-2)."""
+    cfg = schlogl_mfpt_we(n_iters=n_iters, n_runs=n_runs, seed=seed, x0=82, threshold=563,
+                          m_targ=m_targ)
+    cfg.tau = 0.1
+    cfg.reweight_period = reweight_period
+    cfg.name = "schlogl_flux"
+    return cfg
 
 
 def schlogl_pdf_we(n_iters: int = 101, n_runs: int = 1, seed: int = 0, m_targ: int = 100,
