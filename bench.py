@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the SSA kernel (0: auto)")
-    ap.add_argument("--workload", choices=["schlogl", "toggle_learned", "toggle_batch", "synthetic_large"],
+    ap.add_argument("--workload", choices=["schlogl", "toggle_learned", "toggle_batch", "synthetic_large",
+                                           "schlogl_flux"],
                     default="schlogl")
     ap.add_argument("--batch-iters", type=int, default=0,
                     help="toggle_batch / synthetic_large: WE iterations per step (0: 500 / 100)")
@@ -466,6 +467,86 @@ def run_batch_workload(a):
     print(json.dumps(line))
 
 
+def run_schlogl_flux(a):
+    """Steady-state reweighting (Sec. II.B.2, Eq. "ss") on the paper's Schloegl flux runs
+    (Sec. III.B.2/3: 80 bins of width 10, 32 walkers per bin, tau = 0.1, from X = 82 with
+    recycling at X >= 563, 500 iterations): the replica-mean flux into the target for
+    reweighting every 100, 5 and 2 iterations and none, against the exact flux 1 / MFPT; the
+    iterations (and GPU time) after which its 10-iteration moving average stays within 50 % and
+    20 % of it, and the GPU cost per iteration of each schedule."""
+    import numpy as np
+    import torch
+    import paper_1303_5986_gb300 as P
+    import workloads as W
+    from paper_1303_5986_gb300 import build as pbuild
+
+    pbuild.build()
+    with open(os.path.join(ROOT, "tests", "golden", "exact_values.json")) as f:
+        exact = 1.0 / json.load(f)["schlogl_mfpt_82_to_563_s"]
+    n_iters, R = a.batch_iters or 500, 16
+    base = W.schlogl_flux_we(n_iters=n_iters, n_runs=R)
+    net = P.network_from_spec(base.network)
+    bm = P.we_binmap_grid(base.bins.species, base.bins.edges)
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+
+    def settle(curve, tol):
+        ma = np.convolve(curve, np.ones(10) / 10, mode="valid")      # ma[k]: iterations k..k+9
+        ok = np.abs(ma / exact - 1.0) <= tol
+        bad = np.nonzero(~ok)[0]
+        if len(bad) == 0:
+            return 10
+        return None if bad[-1] == len(ma) - 1 else int(bad[-1] + 11)   # first iteration count after which it holds
+
+    out = {}
+    clocks.start()
+    for period in (0, 100, 5, 2):
+        for w in range(a.warmup + 1):                                  # warm-ups, then one timed run
+            cfg = W.schlogl_flux_we(reweight_period=period, n_iters=n_iters, n_runs=R, seed=7 + w)
+            c, keep = P.run_config_from(cfg, record_iters=n_iters)
+            ens = P.we_ensemble_create(net, bm, c, keep)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ens.step(n_iters)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        flux = ens.per_iter(P.WE_OUT_FLUX) / cfg.tau                  # iters x replicas
+        curve = flux.mean(axis=1)
+        rw = ens.per_iter(P.WE_OUT_RW) if period else np.zeros((n_iters, R), dtype=np.int32)
+        i50, i20 = settle(curve, 0.5), settle(curve, 0.2)
+        per_it = ms / n_iters
+        out[f"rw_{period}"] = {
+            "iters_to_50pct": i50, "iters_to_20pct": i20,
+            "gpu_s_to_50pct": None if i50 is None else i50 * per_it * 1e-3,
+            "ms_per_iteration": per_it,
+            "flux_over_exact_by_50_iterations": [round(float(curve[k:k + 50].mean() / exact), 3)
+                                                 for k in range(0, n_iters, 50)],
+            "reweightings": int((rw == 1).sum()), "skipped": int((rw == -1).sum()),
+            "status": sorted(set(int(x) for x in ens.status())),
+        }
+    clk = clocks.stop()
+    done = [k for k in ("rw_2", "rw_5", "rw_100") if out[k]["iters_to_50pct"] is not None]
+    pick = min(done, key=lambda k: out[k]["iters_to_50pct"]) if done else "rw_2"
+    best = out[pick]
+    line = {
+        "metric": "WE iterations until the Schloegl flux stays within 50% of exact (steady-state reweighting)",
+        "value": best["iters_to_50pct"], "value_schedule": pick,
+        "unit": "WE iterations (10-iteration moving average of 16 replicas)",
+        "n_gpus": 1, "steps": 1, "warmup": a.warmup, "ms_per_step": best["ms_per_iteration"] * n_iters,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Schloegl flux runs: 80 bins of width 10 x 32 walkers, tau=0.1, {n_iters} "
+                               "iterations from X=82, recycling at X>=563, 16 replicas per schedule; "
+                               "reweighting every 2, 5 or 100 iterations (value: the fastest of them, "
+                               "value_schedule) and never (the baseline, in schedules)",
+                   "exact_flux_per_s": exact},
+        "schedules": out, "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 # ------------------------------------------------------------------------------------------
 # ranks: every rank runs its own replicas (weak scaling, no data-path collective); the job's
 # figures are the slowest rank's time and the sum of every rank's work
@@ -504,6 +585,13 @@ def main():
                               "default Schloegl workload only"}))
             return
         run_batch_workload(a)
+        return
+    if a.workload == "schlogl_flux":
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reweighting comparison has no CPU "
+                              "oracle arm; its baseline is the schedule without reweighting on the same GPU"}))
+            return
+        run_schlogl_flux(a)
         return
     if a.workload == "toggle_learned":
         if a.impl == "reference":

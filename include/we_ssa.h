@@ -204,9 +204,12 @@ typedef struct {
                                       reweight_period-th iteration: the rates k_ij = F_ij / W_j
                                       from the weight F_ij that moved from bin j to bin i over
                                       all intervals so far (W_j = sum_i F_ij), the balance
-                                      equations over the bins with W_j > 0 solved by Gaussian
-                                      elimination, and the walkers of every bin that holds any
-                                      rescaled to the solved bin weights (their total kept).
+                                      equations solved on the largest strongly connected set
+                                      of bins with W_j > 0 (elimination of Grassmann, Taksar
+                                      and Heyman, which keeps every weight's relative
+                                      accuracy), and the walkers of each of its bins that
+                                      holds any rescaled to the solved bin weights (their
+                                      total kept); the outcome per iteration is WE_OUT_RW.
                                       Needs resample = 1 and at most 1024 bins; adds
                                       16 * n_bins^2 bytes per run to the workspace */
 } we_run_config;

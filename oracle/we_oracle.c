@@ -421,67 +421,129 @@ int32_t orc_resample(int32_t n, int32_t S, const int32_t *states, const double *
  * the flux into bin i from bin j.  The rates are estimated from the measured transfers,
  * k_ij = F_ij / W_j, where F_ij is the weight that started an interval in bin j and ended it in
  * bin i, and W_j = sum_i F_ij (ascending i) the weight that started in j, both summed over all
- * intervals so far.  Only bins with W_j > 0 take part ("active"); transfers into other bins
- * are left out (nothing is known about leaving them).  The balance equations over the active
- * bins, with the last one replaced by sum_i w_i = 1, are solved by Gaussian elimination with
- * partial pivoting (largest magnitude, ties to the lower row; every product and difference
- * rounded on its own) and column-oriented back substitution.  Bins that hold walkers now take
+ * intervals so far.  The bins taken are the largest strongly connected component of the
+ * observed transfers among the bins with W_j > 0 (so that the estimated chain on them is
+ * irreducible and its steady state unique and positive); transfers that leave that set are
+ * left out, and bins outside it keep their weights.  The balance equations on that set are
+ * solved by the elimination of Grassmann, Taksar and Heyman (GTH): states are removed from the
+ * last to the first, each one's exit rates folded into the rates among the remaining states,
+ * then the weights are rebuilt from the first state on.  It only adds, multiplies and divides
+ * non-negative numbers, so every weight keeps its relative accuracy -- steady-state bin weights
+ * in WE span many orders of magnitude, and Gaussian elimination with pivoting leaves the small
+ * ones with absolute errors of ~1e-17 that can make them negative.  Bins that hold walkers now take
  * the solved weights, scaled so that their total is unchanged: the walkers of bin i are
  * multiplied by (x_i q) / c_i with q = (sum of their current weights c) / (sum of their x).
- * Nothing is changed when fewer than two bins are active, a pivot is zero, or a bin holding
+ * Nothing is changed when the set has fewer than two bins, an eliminated state has no exit
+ * rate left (not possible for an irreducible chain unless rates underflow), or a bin holding
  * walkers gets a solved weight that is not positive.
  * ------------------------------------------------------------------------------------------ */
+/* The largest strongly connected component of the observed-transfer graph over the active bins
+ * act[0..n) (edge j -> i when i != j and F[i][j] > 0), written ascending to out; returns its
+ * size.  Largest by bin count, ties to the component with the lowest bin.  Components found by
+ * Kosaraju's two depth-first passes (finish order, then the transposed graph). */
+static int32_t largest_scc(int32_t n, const int32_t *act, const double *F, int32_t nb, int32_t *out) {
+  int32_t *seen = (int32_t *)calloc(n, sizeof(int32_t));
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * n);
+  int32_t *stk = (int32_t *)malloc(sizeof(int32_t) * n);
+  int32_t *nxt = (int32_t *)malloc(sizeof(int32_t) * n);
+  int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * n);
+  int32_t best_size = 0;
+  if (!seen || !order || !stk || !nxt || !comp) goto done;
+  {
+    int32_t no = 0;
+    for (int32_t s0 = 0; s0 < n; ++s0) {
+      if (seen[s0]) continue;
+      int32_t top = 0;
+      stk[0] = s0; nxt[0] = 0; seen[s0] = 1;
+      while (top >= 0) {
+        const int32_t j = stk[top];
+        int32_t i = nxt[top];
+        while (i < n && (i == j || seen[i] || !(F[(size_t)act[i] * nb + act[j]] > 0.0))) ++i;
+        if (i < n) {
+          nxt[top] = i + 1;
+          seen[i] = 1;
+          ++top; stk[top] = i; nxt[top] = 0;
+        } else {
+          order[no++] = j;
+          --top;
+        }
+      }
+    }
+    for (int32_t k = 0; k < n; ++k) comp[k] = -1;
+    int32_t nc = 0;
+    for (int32_t q = n - 1; q >= 0; --q) {
+      const int32_t s1 = order[q];
+      if (comp[s1] >= 0) continue;
+      int32_t top = 0;
+      stk[0] = s1; nxt[0] = 0; comp[s1] = nc;
+      while (top >= 0) {
+        const int32_t j = stk[top];
+        int32_t i = nxt[top];                     /* transposed: i -> j exists when F[j][i] > 0 */
+        while (i < n && (i == j || comp[i] >= 0 || !(F[(size_t)act[j] * nb + act[i]] > 0.0))) ++i;
+        if (i < n) {
+          nxt[top] = i + 1;
+          comp[i] = nc;
+          ++top; stk[top] = i; nxt[top] = 0;
+        } else {
+          --top;
+        }
+      }
+      ++nc;
+    }
+    int32_t best = -1, best_min = 0;
+    for (int32_t c = 0; c < nc; ++c) {
+      int32_t size = 0, mn = n;
+      for (int32_t k = 0; k < n; ++k)
+        if (comp[k] == c) { ++size; if (k < mn) mn = k; }
+      if (size > best_size || (size == best_size && mn < best_min)) { best = c; best_size = size; best_min = mn; }
+    }
+    int32_t m = 0;
+    for (int32_t k = 0; k < n; ++k)
+      if (comp[k] == best) out[m++] = act[k];
+  }
+done:
+  free(seen); free(order); free(stk); free(nxt); free(comp);
+  return best_size;
+}
+
 int32_t orc_rw_solve(int32_t nb, const double *F, const double *cb, double *fac) {
   for (int32_t b = 0; b < nb; ++b) fac[b] = 0.0;
   double *W = (double *)malloc(sizeof(double) * nb);
   int32_t *A = (int32_t *)malloc(sizeof(int32_t) * nb);
   if (!W || !A) { free(W); free(A); return -1; }
-  int32_t n = 0;
+  int32_t na = 0;
   for (int32_t b = 0; b < nb; ++b) {
     double s = 0.0;
     for (int32_t e = 0; e < nb; ++e) s = s + F[(size_t)e * nb + b];
     W[b] = s;
-    if (s > 0.0) A[n++] = b;
+    if (s > 0.0) A[na++] = b;
   }
   int32_t result = -1;
-  double *M = NULL, *rhs = NULL, *x = NULL;
+  double *M = NULL, *x = NULL;
+  int32_t n = na >= 2 ? largest_scc(na, A, F, nb, A) : 0;
   if (n < 2) goto done;
   M = (double *)malloc(sizeof(double) * (size_t)n * n);
-  rhs = (double *)malloc(sizeof(double) * n);
   x = (double *)malloc(sizeof(double) * n);
-  if (!M || !rhs || !x) goto done;
-  /* k_ij off the diagonal; the diagonal is minus the column's other entries (rate out of j) */
-  for (int32_t i = 0; i < n; ++i)
-    for (int32_t j = 0; j < n; ++j)
-      M[(size_t)i * n + j] = i == j ? 0.0 : F[(size_t)A[i] * nb + A[j]] / W[A[j]];
-  for (int32_t j = 0; j < n; ++j) {
+  if (!M || !x) goto done;
+  /* R[a][b]: rate from the a-th to the b-th bin of the set, k_ba = F[b][a] / W[a] */
+  for (int32_t a = 0; a < n; ++a)
+    for (int32_t b = 0; b < n; ++b)
+      M[(size_t)a * n + b] = a == b ? 0.0 : F[(size_t)A[b] * nb + A[a]] / W[A[a]];
+  /* GTH elimination, last state first: fold state k's exits into the others' rates */
+  for (int32_t k = n - 1; k >= 1; --k) {
     double out = 0.0;
-    for (int32_t i = 0; i < n; ++i)
-      if (i != j) out = out + M[(size_t)i * n + j];
-    M[(size_t)j * n + j] = -out;
+    for (int32_t j = 0; j < k; ++j) out = out + M[(size_t)k * n + j];
+    if (!(out > 0.0)) goto done;
+    for (int32_t i = 0; i < k; ++i) M[(size_t)i * n + k] = M[(size_t)i * n + k] / out;
+    for (int32_t i = 0; i < k; ++i)
+      for (int32_t j = 0; j < k; ++j)
+        if (i != j) M[(size_t)i * n + j] = M[(size_t)i * n + j] + M[(size_t)i * n + k] * M[(size_t)k * n + j];
   }
-  for (int32_t j = 0; j < n; ++j) M[(size_t)(n - 1) * n + j] = 1.0;
-  for (int32_t i = 0; i < n; ++i) rhs[i] = i == n - 1 ? 1.0 : 0.0;
-  for (int32_t k = 0; k < n; ++k) {
-    int32_t p = k;
-    for (int32_t r = k + 1; r < n; ++r)
-      if (fabs(M[(size_t)r * n + k]) > fabs(M[(size_t)p * n + k])) p = r;
-    if (M[(size_t)p * n + k] == 0.0) goto done;
-    if (p != k) {
-      for (int32_t c = 0; c < n; ++c) {
-        double t = M[(size_t)k * n + c]; M[(size_t)k * n + c] = M[(size_t)p * n + c]; M[(size_t)p * n + c] = t;
-      }
-      double t = rhs[k]; rhs[k] = rhs[p]; rhs[p] = t;
-    }
-    for (int32_t r = k + 1; r < n; ++r) {
-      double l = M[(size_t)r * n + k] / M[(size_t)k * n + k];
-      for (int32_t c = k + 1; c < n; ++c) M[(size_t)r * n + c] = M[(size_t)r * n + c] - l * M[(size_t)k * n + c];
-      rhs[r] = rhs[r] - l * rhs[k];
-    }
-  }
-  for (int32_t k = n - 1; k >= 0; --k) {
-    x[k] = rhs[k] / M[(size_t)k * n + k];
-    for (int32_t r = 0; r < k; ++r) rhs[r] = rhs[r] - M[(size_t)r * n + k] * x[k];
+  x[0] = 1.0;
+  for (int32_t k = 1; k < n; ++k) {
+    double v = 0.0;
+    for (int32_t i = 0; i < k; ++i) v = v + x[i] * M[(size_t)i * n + k];
+    x[k] = v;
   }
   {
     double C = 0.0, T = 0.0;
@@ -500,7 +562,7 @@ int32_t orc_rw_solve(int32_t nb, const double *F, const double *cb, double *fac)
     result = 1;
   }
 done:
-  free(W); free(A); free(M); free(rhs); free(x);
+  free(W); free(A); free(M); free(x);
   return result;
 }
 

@@ -331,7 +331,7 @@ struct Offsets {
   size_t logt, table, base;
   size_t lw1, lw2, lw3, lb, lz, zout;
   size_t wrec;
-  size_t rw_F, rw_M, rw_vec, rw_act, rw_obs;
+  size_t rw_F, rw_M, rw_vec, rw_act, rw_iscr, rw_obs;
   int32_t table_len, table_lenB, wrec_stride;
   size_t total;
 };
@@ -480,8 +480,9 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
     const size_t nb = b->n_bins;
     o.rw_F = L.take(8 * R * nb * nb);
     o.rw_M = L.take(8 * R * nb * nb);
-    o.rw_vec = L.take(8 * 5 * R * nb);
+    o.rw_vec = L.take(8 * 4 * R * nb);
     o.rw_act = L.take(4 * R * nb);
+    o.rw_iscr = L.take(16 * R * nb);
     o.rw_obs = L.take(4 * rec * R);
   }
   o.total = L.off;
@@ -751,8 +752,9 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
     rw.F = at<double>(ws, o.rw_F);
     rw.M = at<double>(ws, o.rw_M);
     rw.W = at<double>(ws, o.rw_vec);
-    rw.cb = rw.W + nbR; rw.rhs = rw.cb + nbR; rw.x = rw.rhs + nbR; rw.fac = rw.x + nbR;
+    rw.cb = rw.W + nbR; rw.x = rw.cb + nbR; rw.fac = rw.x + nbR;
     rw.act = at<int32_t>(ws, o.rw_act);
+    rw.iscr = at<int32_t>(ws, o.rw_iscr);
     rw.obs = at<int32_t>(ws, o.rw_obs);
   }
   E->prm.tab.species = -1;

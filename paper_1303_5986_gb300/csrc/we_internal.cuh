@@ -159,14 +159,15 @@ struct TableView {
 
 // Steady-state reweighting (Sec. II.B.2, Eq. "ss"): per run, the weight moved from bin b to
 // bin e summed over the intervals so far (F, nb x nb, row e), the solve's scratch (M, n x n
-// over the active bins), per-bin vectors and the per-iteration outcome.
+// over the bins solved for), per-bin vectors and the per-iteration outcome.
 struct RwView {
   int32_t period;              // 0: off; else reweight after every period-th iteration
   int32_t nb;                  // bins
   double *F;                   // R x nb x nb
   double *M;                   // R x nb x nb
-  double *W, *cb, *rhs, *x, *fac;   // R x nb each
-  int32_t *act;                // R x nb: active bins, ascending
+  double *W, *cb, *x, *fac;    // R x nb each
+  int32_t *act;                // R x nb: the bins solved for, ascending
+  int32_t *iscr;               // R x 4 nb: scratch of the strongly-connected-set search
   int32_t *obs;                // record_iters x R: 1 reweighted, -1 skipped, 0 not scheduled
 };
 

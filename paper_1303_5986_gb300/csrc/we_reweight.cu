@@ -4,17 +4,20 @@
 // f_ij = k_ij w_j the flux into bin i from bin j.  The rates come from the transfers measured
 // over every interval so far: F_ij = weight that started an interval in bin j and ended it in
 // bin i, W_j = sum_i F_ij, k_ij = F_ij / W_j.  Every reweight_period-th iteration, after the
-// split/merge, the balance equations over the bins with W_j > 0 (the last replaced by
-// sum_i w_i = 1) are solved, and the walkers of each bin that holds any are rescaled so that
-// the bins carry the solved weights (their total unchanged).
+// split/merge, the balance equations are solved on the largest strongly connected set of bins
+// with W_j > 0 (transfers leaving the set left out), and the walkers of each of its bins that
+// holds any are rescaled so that those bins carry the solved weights (their total unchanged).
 //
 //   k_rw_flux   (after the SSA, before the split/merge): one warp per bin of the previous
 //               split/merge, whose M_targ walkers are consecutive slots; lane 0 sums their
 //               weights by end bin in ascending slot order and adds each sum to F once.
-//   k_rw_solve  (after the split/merge; one block per run): Gaussian elimination with partial
-//               pivoting and column-oriented back substitution, every product and difference
-//               rounded on its own (no fused multiply-add), so the factors are the same bits
-//               as a sequential elimination in the same order.
+//   k_rw_solve  (after the split/merge; one block per run): the largest strongly connected
+//               set of bins (one thread, Kosaraju), then the elimination of Grassmann, Taksar
+//               and Heyman on it -- only sums and products of non-negative numbers, so every
+//               bin weight keeps its relative accuracy however small -- with the sums taken
+//               in a fixed order by one thread and the rank-one updates in parallel, each
+//               product and sum rounded on its own (no fused multiply-add): the factors are
+//               the same bits as the sequential elimination.
 //   k_rw_apply  multiplies each walker's weight by its bin's factor.
 #include "we_internal.cuh"
 
@@ -59,6 +62,67 @@ __device__ __forceinline__ bool rw_due(const EnsView &E, const RwView &rw, int &
   return li >= 0 && (li + 1) % rw.period == 0;
 }
 
+// The largest strongly connected component of the observed-transfer graph over the active bins
+// act[0..n) (edge j -> i when i != j and F[i][j] > 0), written ascending over act; returns its
+// size (largest by bin count, ties to the component with the lowest bin).  Kosaraju's two
+// iterative depth-first passes; one thread, scratch of 4 n ints.
+__device__ int rw_largest_scc(int n, int32_t *act, const double *F, int nb, int32_t *scr) {
+  int32_t *seen = scr, *order = scr + n, *stk = scr + 2 * n, *nxt = scr + 3 * n;
+  for (int k = 0; k < n; ++k) seen[k] = 0;
+  int no = 0;
+  for (int s0 = 0; s0 < n; ++s0) {
+    if (seen[s0]) continue;
+    int top = 0;
+    stk[0] = s0; nxt[0] = 0; seen[s0] = 1;
+    while (top >= 0) {
+      const int j = stk[top];
+      int i = nxt[top];
+      while (i < n && (i == j || seen[i] || !(F[(size_t)act[i] * nb + act[j]] > 0.0))) ++i;
+      if (i < n) {
+        nxt[top] = i + 1;
+        seen[i] = 1;
+        ++top; stk[top] = i; nxt[top] = 0;
+      } else {
+        order[no++] = j;
+        --top;
+      }
+    }
+  }
+  int32_t *comp = seen;                              // reused: component labels, -1 = none yet
+  for (int k = 0; k < n; ++k) comp[k] = -1;
+  int nc = 0;
+  for (int q = n - 1; q >= 0; --q) {
+    const int s1 = order[q];
+    if (comp[s1] >= 0) continue;
+    int top = 0;
+    stk[0] = s1; nxt[0] = 0; comp[s1] = nc;
+    while (top >= 0) {
+      const int j = stk[top];
+      int i = nxt[top];
+      while (i < n && (i == j || comp[i] >= 0 || !(F[(size_t)act[j] * nb + act[i]] > 0.0))) ++i;
+      if (i < n) {
+        nxt[top] = i + 1;
+        comp[i] = nc;
+        ++top; stk[top] = i; nxt[top] = 0;
+      } else {
+        --top;
+      }
+    }
+    ++nc;
+  }
+  int best = -1, best_size = 0, best_min = 0;
+  for (int c = 0; c < nc; ++c) {
+    int size = 0, mn = n;
+    for (int k = 0; k < n; ++k)
+      if (comp[k] == c) { ++size; if (k < mn) mn = k; }
+    if (size > best_size || (size == best_size && mn < best_min)) { best = c; best_size = size; best_min = mn; }
+  }
+  int m = 0;
+  for (int k = 0; k < n; ++k)
+    if (comp[k] == best) act[m++] = act[k];
+  return best_size;
+}
+
 __global__ void __launch_bounds__(256) k_rw_solve(EnsView E, RwView rw) {
   const int r = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
   const int nb = rw.nb;
@@ -71,12 +135,12 @@ __global__ void __launch_bounds__(256) k_rw_solve(EnsView E, RwView rw) {
   }
   const double *F = rw.F + (size_t)r * nb * nb;
   double *W = rw.W + (size_t)r * nb, *cb = rw.cb + (size_t)r * nb, *fac = rw.fac + (size_t)r * nb;
-  double *rhs = rw.rhs + (size_t)r * nb, *x = rw.x + (size_t)r * nb;
+  double *x = rw.x + (size_t)r * nb;
   double *M = rw.M + (size_t)r * nb * nb;
   int32_t *A = rw.act + (size_t)r * nb;
-  __shared__ int s_n, s_ok, s_p;
-  __shared__ double s_v[256];
-  __shared__ int s_i[256];
+  int32_t *scr = rw.iscr + (size_t)r * 4 * nb;
+  __shared__ int s_n, s_ok;
+  __shared__ double s_out;
   for (int b = tid; b < nb; b += B) {
     double s = 0.0;
     for (int e = 0; e < nb; ++e) s = __dadd_rn(s, F[(size_t)e * nb + b]);
@@ -96,86 +160,52 @@ __global__ void __launch_bounds__(256) k_rw_solve(EnsView E, RwView rw) {
     cb[tk.x] = s;
   }
   if (tid == 0) {
-    int n = 0;
+    int na = 0;
     for (int b = 0; b < nb; ++b)
-      if (W[b] > 0.0) A[n++] = b;
+      if (W[b] > 0.0) A[na++] = b;
+    const int n = na >= 2 ? rw_largest_scc(na, A, F, nb, scr) : 0;
     s_n = n;
     s_ok = n >= 2;
   }
   __syncthreads();
   const int n = s_n;
   if (s_ok) {
+    // R[a][b] = rate from the a-th to the b-th bin of the set, k_ba = F[b][a] / W[a]
     for (int idx = tid; idx < n * n; idx += B) {
-      const int i = idx / n, j = idx - i * n;
-      M[idx] = i == j ? 0.0 : __ddiv_rn(F[(size_t)A[i] * nb + A[j]], W[A[j]]);
+      const int a = idx / n, b = idx - a * n;
+      M[idx] = a == b ? 0.0 : __ddiv_rn(F[(size_t)A[b] * nb + A[a]], W[A[a]]);
     }
     __syncthreads();
-    for (int j = tid; j < n; j += B) {
-      double out = 0.0;
-      for (int i = 0; i < n; ++i)
-        if (i != j) out = __dadd_rn(out, M[(size_t)i * n + j]);
-      M[(size_t)j * n + j] = -out;
-    }
-    __syncthreads();
-    for (int j = tid; j < n; j += B) M[(size_t)(n - 1) * n + j] = 1.0;
-    for (int i = tid; i < n; i += B) rhs[i] = i == n - 1 ? 1.0 : 0.0;
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-      // pivot: the first row (from k) of largest magnitude in column k
-      double bv = -1.0;
-      int bi = n;
-      for (int rr = k + tid; rr < n; rr += B) {
-        const double v = fabs(M[(size_t)rr * n + k]);
-        if (v > bv) { bv = v; bi = rr; }
-      }
-      s_v[tid] = bv;
-      s_i[tid] = bi;
-      __syncthreads();
-      for (int h = B / 2; h > 0; h >>= 1) {
-        if (tid < h) {
-          const double ov = s_v[tid + h];
-          const int oi = s_i[tid + h];
-          if (ov > s_v[tid] || (ov == s_v[tid] && oi < s_i[tid])) { s_v[tid] = ov; s_i[tid] = oi; }
-        }
-        __syncthreads();
-      }
-      const int p = s_i[0];
-      if (M[(size_t)p * n + k] == 0.0) {
-        if (tid == 0) s_ok = 0;
-        break;                                       // uniform: every thread read the same p
-      }
-      if (p != k) {
-        for (int c = tid; c < n; c += B) {
-          const double a = M[(size_t)k * n + c];
-          M[(size_t)k * n + c] = M[(size_t)p * n + c];
-          M[(size_t)p * n + c] = a;
-        }
-        if (tid == 0) { const double a = rhs[k]; rhs[k] = rhs[p]; rhs[p] = a; }
+    // GTH elimination, last state first (non-negative arithmetic only)
+    for (int k = n - 1; k >= 1; --k) {
+      if (tid == 0) {
+        double out = 0.0;
+        for (int j = 0; j < k; ++j) out = __dadd_rn(out, M[(size_t)k * n + j]);
+        s_out = out;
+        if (!(out > 0.0)) s_ok = 0;
       }
       __syncthreads();
-      const int wdt = n - k;                         // columns k+1 .. n-1 and the right-hand side
-      for (int idx = tid; idx < (n - k - 1) * wdt; idx += B) {
-        const int rr = k + 1 + idx / wdt, c = k + 1 + idx % wdt;
-        const double l = __ddiv_rn(M[(size_t)rr * n + k], M[(size_t)k * n + k]);
-        if (c < n) M[(size_t)rr * n + c] = __dsub_rn(M[(size_t)rr * n + c], __dmul_rn(l, M[(size_t)k * n + c]));
-        else rhs[rr] = __dsub_rn(rhs[rr], __dmul_rn(l, rhs[k]));
+      if (!s_ok) break;                              // uniform: every thread read the same flag
+      const double out = s_out;
+      for (int i = tid; i < k; i += B) M[(size_t)i * n + k] = __ddiv_rn(M[(size_t)i * n + k], out);
+      __syncthreads();
+      for (int idx = tid; idx < k * k; idx += B) {
+        const int i = idx / k, j = idx - i * k;
+        if (i != j)
+          M[(size_t)i * n + j] = __dadd_rn(M[(size_t)i * n + j], __dmul_rn(M[(size_t)i * n + k], M[(size_t)k * n + j]));
       }
-      __syncthreads();
-    }
-    __syncthreads();
-  }
-  if (s_ok) {
-    for (int k = n - 1; k >= 0; --k) {
-      if (tid == 0) x[k] = __ddiv_rn(rhs[k], M[(size_t)k * n + k]);
-      __syncthreads();
-      const double xk = x[k];
-      for (int rr = tid; rr < k; rr += B) rhs[rr] = __dsub_rn(rhs[rr], __dmul_rn(M[(size_t)rr * n + k], xk));
       __syncthreads();
     }
   }
   if (tid == 0) {
     int outcome = -1;
     if (s_ok) {
+      x[0] = 1.0;
+      for (int k = 1; k < n; ++k) {
+        double v = 0.0;
+        for (int i = 0; i < k; ++i) v = __dadd_rn(v, __dmul_rn(x[i], M[(size_t)i * n + k]));
+        x[k] = v;
+      }
       double C = 0.0, T = 0.0;
       int held = 0;
       bool good = true;

@@ -460,11 +460,13 @@ def _transfers(K, W):
 def test_rw_solve_birth_death_chain_detailed_balance():
     """Tridiagonal moves: the steady state is fixed by detailed balance,
     pi_{i+1} / pi_i = up_i / down_{i+1}, with no linear solve.  The factors must give every bin
-    that holds walkers the weight pi_i scaled to the bins' current total."""
+    that holds walkers the weight pi_i scaled to the bins' current total -- to 1e-10 relative
+    even where pi is 1e-60 of its largest entry (the solve keeps relative accuracy)."""
     rng = np.random.default_rng(3)
     n = 40
     up = rng.uniform(0.02, 0.4, n)
     down = rng.uniform(0.02, 0.4, n)
+    up[:20] *= 1e-3                                               # a steep left tail
     K = np.zeros((n, n))
     for i in range(n - 1):
         K[i + 1, i] = up[i]
@@ -499,16 +501,33 @@ def test_rw_solve_cycle_and_partial_occupancy():
     assert abs(held.sum() - (cb[0] + cb[2])) < 1e-15
 
 
-def test_rw_solve_refuses_degenerate_systems():
-    """One active bin, or two disconnected components (a zero pivot), leave everything as is."""
+def test_rw_solve_takes_the_largest_strongly_connected_set():
+    """One active bin leaves everything as is.  Of two closed pairs {0, 1} and {2, 3} (equal
+    size) the one with the lower bin is reweighted (pi_0 / pi_1 = 0.2 / 0.1) and the other keeps
+    its weights.  A bin that was only ever seen staying (absorbing in the estimate) and a bin
+    that only feeds the chain are left out of a 4-bin cycle, which is solved alone."""
     F = np.zeros((3, 3))
     F[0, 0] = 1.0
     st, fac = O.rw_solve(F, np.array([1.0, 0.0, 0.0]))
     assert st == -1 and not fac.any()
     K = np.zeros((4, 4))
     K[1, 0], K[0, 1], K[3, 2], K[2, 3] = 0.1, 0.2, 0.1, 0.3
-    st, fac = O.rw_solve(_transfers(K, np.ones(4)), np.full(4, 0.25))
-    assert st == -1 and not fac.any()
+    cb = np.array([0.1, 0.3, 0.25, 0.35])
+    st, fac = O.rw_solve(_transfers(K, np.ones(4)), cb)
+    assert st == 1 and fac[2] == 0.0 and fac[3] == 0.0
+    new = fac[:2] * cb[:2]
+    assert new[0] / new[1] == pytest.approx(2.0, rel=1e-14)
+    assert new.sum() == pytest.approx(0.4, rel=1e-15)
+    K = np.zeros((6, 6))
+    K[1, 0], K[2, 1], K[3, 2], K[0, 3] = 0.1, 0.2, 0.3, 0.4     # cycle 0 -> 1 -> 2 -> 3 -> 0
+    K[4, 3] = 0.05                                              # 3 -> 4; 4 only stays
+    K[0, 5] = 0.2                                               # 5 -> 0 only
+    cb = np.full(6, 1.0 / 6)
+    st, fac = O.rw_solve(_transfers(K, np.ones(6)), cb)
+    assert st == 1 and fac[4] == 0.0 and fac[5] == 0.0
+    pi = 1.0 / np.array([0.1, 0.2, 0.3, 0.4])                   # moves within the set only
+    new = fac[:4] * cb[:4]
+    np.testing.assert_allclose(new / new.sum(), pi / pi.sum(), rtol=1e-12)
 
 
 def test_we_with_reweighting_keeps_total_weight_and_schedule():
@@ -522,3 +541,24 @@ def test_we_with_reweighting_keeps_total_weight_and_schedule():
     assert (rw[[5, 8, 11]] == 1).all()
     assert np.all(np.abs(o["total_weight"] - 1.0) < 1e-12)
     assert abs(o["weights"].sum() - 1.0) < 1e-12
+
+
+def test_we_reweighting_is_unbiased_with_state_resolved_bins():
+    """With one state per bin the bin-to-bin chain that reweighting estimates is the exact lumped
+    chain, so the steady-state flux it produces matches 1 / MFPT (birth-death 100 -> 140 with
+    recycling, unit bins, reweighting every 5 iterations; 8 replicas, iterations 100-300)."""
+    b, d = E.birth_death_rates()
+    exact = 1.0 / E.bd_mfpt(100, 140, b, d)
+    cfg = W.birth_death_we(n_iters=300, target=140)
+    cfg.bins = W.GridBins(species=[0], edges=[W.uniform_edges(0, 1, 150)])
+    cfg.capacity = cfg.m_targ * cfg.bins.n_bins
+    cfg.reweight_period = 5
+    m = []
+    for r in range(8):
+        cfg.run_ids = np.array([r], dtype=np.uint32)
+        o = O.we_run(cfg, 0)
+        assert o["status"] == 0 and (o["reweighted"][4::5] == 1).all()
+        m.append(o["flux_weight"][100:].mean() / cfg.tau / exact)
+    m = np.array(m)
+    se = m.std(ddof=1) / np.sqrt(len(m))
+    assert abs(m.mean() - 1.0) < 3 * se + 0.05, (m.mean(), se)
