@@ -482,7 +482,7 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
     o.rw_M = L.take(8 * R * nb * nb);
     o.rw_vec = L.take(8 * 4 * R * nb);
     o.rw_act = L.take(4 * R * nb);
-    o.rw_iscr = L.take(16 * R * nb);
+    o.rw_iscr = L.take(24 * R * nb);
     o.rw_obs = L.take(4 * rec * R);
   }
   o.total = L.off;

@@ -167,7 +167,7 @@ struct RwView {
   double *M;                   // R x nb x nb
   double *W, *cb, *x, *fac;    // R x nb each
   int32_t *act;                // R x nb: the bins solved for, ascending
-  int32_t *iscr;               // R x 4 nb: scratch of the strongly-connected-set search
+  int32_t *iscr;               // R x 6 nb: scratch of the strongly-connected-set search
   int32_t *obs;                // record_iters x R: 1 reweighted, -1 skipped, 0 not scheduled
 };
 

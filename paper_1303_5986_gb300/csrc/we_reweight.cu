@@ -12,7 +12,7 @@
 //               split/merge, whose M_targ walkers are consecutive slots; lane 0 sums their
 //               weights by end bin in ascending slot order and adds each sum to F once.
 //   k_rw_solve  (after the split/merge; one block per run): the largest strongly connected
-//               set of bins (one thread, Kosaraju), then the elimination of Grassmann, Taksar
+//               set of bins (one warp, Kosaraju), then the elimination of Grassmann, Taksar
 //               and Heyman on it -- only sums and products of non-negative numbers, so every
 //               bin weight keeps its relative accuracy however small -- with the sums taken
 //               in a fixed order by one thread and the rank-one updates in parallel, each
@@ -65,61 +65,96 @@ __device__ __forceinline__ bool rw_due(const EnsView &E, const RwView &rw, int &
 // The largest strongly connected component of the observed-transfer graph over the active bins
 // act[0..n) (edge j -> i when i != j and F[i][j] > 0), written ascending over act; returns its
 // size (largest by bin count, ties to the component with the lowest bin).  Kosaraju's two
-// iterative depth-first passes; one thread, scratch of 4 n ints.
-__device__ int rw_largest_scc(int n, int32_t *act, const double *F, int nb, int32_t *scr) {
+// iterative depth-first passes, run by one warp: every lane follows the same search, the next
+// neighbour is found 32 candidates at a time by ballot, and lane 0 writes the scratch (6 n
+// ints) that the lanes read after a warp barrier.
+// The next i >= from (i != j) with mark[i] == unmarked and an observed transfer j -> i (i -> j
+// when transposed), 32 candidates per ballot; n if there is none.  Called by a whole warp.
+__device__ __forceinline__ int rw_next_neighbour(int n, const int32_t *act, const double *F, int nb, int j,
+                                                 int from, const int32_t *mark, int unmarked, bool transposed) {
+  const int lane = threadIdx.x & 31;
+  for (int base = from; base < n; base += 32) {
+    const int i = base + lane;
+    bool ok = false;
+    if (i < n && i != j && mark[i] == unmarked) {
+      const double f = transposed ? F[(size_t)act[j] * nb + act[i]] : F[(size_t)act[i] * nb + act[j]];
+      ok = f > 0.0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    if (m) return base + __ffs(m) - 1;
+  }
+  return n;
+}
+
+__device__ __forceinline__ int rw_largest_scc(int n, int32_t *act, const double *F, int nb, int32_t *scr) {
+  const int lane = threadIdx.x & 31;
   int32_t *seen = scr, *order = scr + n, *stk = scr + 2 * n, *nxt = scr + 3 * n;
-  for (int k = 0; k < n; ++k) seen[k] = 0;
+  int32_t *csize = scr + 4 * n, *cfirst = scr + 5 * n;
+  for (int k = lane; k < n; k += 32) seen[k] = 0;
+  __syncwarp();
   int no = 0;
   for (int s0 = 0; s0 < n; ++s0) {
     if (seen[s0]) continue;
     int top = 0;
-    stk[0] = s0; nxt[0] = 0; seen[s0] = 1;
+    if (lane == 0) { stk[0] = s0; nxt[0] = 0; seen[s0] = 1; }
+    __syncwarp();
     while (top >= 0) {
       const int j = stk[top];
-      int i = nxt[top];
-      while (i < n && (i == j || seen[i] || !(F[(size_t)act[i] * nb + act[j]] > 0.0))) ++i;
+      const int i = rw_next_neighbour(n, act, F, nb, j, nxt[top], seen, 0, false);
       if (i < n) {
-        nxt[top] = i + 1;
-        seen[i] = 1;
-        ++top; stk[top] = i; nxt[top] = 0;
+        if (lane == 0) { nxt[top] = i + 1; seen[i] = 1; stk[top + 1] = i; nxt[top + 1] = 0; }
+        ++top;
       } else {
-        order[no++] = j;
+        if (lane == 0) order[no] = j;
+        ++no;
         --top;
       }
+      __syncwarp();
     }
   }
   int32_t *comp = seen;                              // reused: component labels, -1 = none yet
-  for (int k = 0; k < n; ++k) comp[k] = -1;
+  for (int k = lane; k < n; k += 32) comp[k] = -1;
+  __syncwarp();
   int nc = 0;
   for (int q = n - 1; q >= 0; --q) {
     const int s1 = order[q];
     if (comp[s1] >= 0) continue;
     int top = 0;
-    stk[0] = s1; nxt[0] = 0; comp[s1] = nc;
+    if (lane == 0) { stk[0] = s1; nxt[0] = 0; comp[s1] = nc; }
+    __syncwarp();
     while (top >= 0) {
       const int j = stk[top];
-      int i = nxt[top];
-      while (i < n && (i == j || comp[i] >= 0 || !(F[(size_t)act[j] * nb + act[i]] > 0.0))) ++i;
+      const int i = rw_next_neighbour(n, act, F, nb, j, nxt[top], comp, -1, true);
       if (i < n) {
-        nxt[top] = i + 1;
-        comp[i] = nc;
-        ++top; stk[top] = i; nxt[top] = 0;
+        if (lane == 0) { nxt[top] = i + 1; comp[i] = nc; stk[top + 1] = i; nxt[top + 1] = 0; }
+        ++top;
       } else {
         --top;
       }
+      __syncwarp();
     }
     ++nc;
   }
+  for (int c = lane; c < nc; c += 32) { csize[c] = 0; cfirst[c] = n; }
+  __syncwarp();
+  if (lane == 0)
+    for (int k = 0; k < n; ++k) {
+      const int c = comp[k];
+      if (csize[c] == 0) cfirst[c] = k;
+      ++csize[c];
+    }
+  __syncwarp();
   int best = -1, best_size = 0, best_min = 0;
-  for (int c = 0; c < nc; ++c) {
-    int size = 0, mn = n;
+  for (int c = 0; c < nc; ++c)
+    if (csize[c] > best_size || (csize[c] == best_size && cfirst[c] < best_min)) {
+      best = c; best_size = csize[c]; best_min = cfirst[c];
+    }
+  if (lane == 0) {
+    int m = 0;
     for (int k = 0; k < n; ++k)
-      if (comp[k] == c) { ++size; if (k < mn) mn = k; }
-    if (size > best_size || (size == best_size && mn < best_min)) { best = c; best_size = size; best_min = mn; }
+      if (comp[k] == best) act[m++] = act[k];
   }
-  int m = 0;
-  for (int k = 0; k < n; ++k)
-    if (comp[k] == best) act[m++] = act[k];
+  __syncwarp();
   return best_size;
 }
 
@@ -138,7 +173,7 @@ __global__ void __launch_bounds__(256) k_rw_solve(EnsView E, RwView rw) {
   double *x = rw.x + (size_t)r * nb;
   double *M = rw.M + (size_t)r * nb * nb;
   int32_t *A = rw.act + (size_t)r * nb;
-  int32_t *scr = rw.iscr + (size_t)r * 4 * nb;
+  int32_t *scr = rw.iscr + (size_t)r * 6 * nb;
   __shared__ int s_n, s_ok;
   __shared__ double s_out;
   for (int b = tid; b < nb; b += B) {
@@ -159,13 +194,19 @@ __global__ void __launch_bounds__(256) k_rw_solve(EnsView E, RwView rw) {
     for (int k = 0; k < n; ++k) s = __dadd_rn(s, w[k]);
     cb[tk.x] = s;
   }
-  if (tid == 0) {
+  __syncthreads();
+  if (tid < 32) {                                    // warp 0: the active list, then the set search
     int na = 0;
-    for (int b = 0; b < nb; ++b)
-      if (W[b] > 0.0) A[na++] = b;
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+      const int b = b0 + tid;
+      const bool act_b = b < nb && W[b] > 0.0;
+      const unsigned m = __ballot_sync(0xffffffffu, act_b);
+      if (act_b) A[na + __popc(m & ((1u << tid) - 1u))] = b;
+      na += __popc(m);
+    }
+    __syncwarp();
     const int n = na >= 2 ? rw_largest_scc(na, A, F, nb, scr) : 0;
-    s_n = n;
-    s_ok = n >= 2;
+    if (tid == 0) { s_n = n; s_ok = n >= 2; }
   }
   __syncthreads();
   const int n = s_n;

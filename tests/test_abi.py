@@ -42,6 +42,7 @@ def test_run_config_struct_layout_matches_header():
     c = P._lib.we_run_config
     assert c.tau.offset == 0 and c.seed.offset == 16 and c.init_states.offset == 48
     assert c.tgt_threshold.offset == 120 and c.max_steps.offset == 136
+    assert c.block_threads.offset == 160 and c.reweight_period.offset == 164
     assert ctypes.sizeof(c) == 168
 
 
@@ -106,3 +107,28 @@ def test_config_validation_without_gpu():
     c.m_targ = 0
     with pytest.raises(P.WEError):
         P.we_ensemble_workspace_bytes(net, bm, c)
+
+
+def test_reweighting_config_validation_without_gpu():
+    """Steady-state reweighting: a negative period, plain propagation, or more than 1024 bins
+    are refused before any device work; a valid period adds the per-run transfer matrix and
+    solve scratch (16 n_bins^2 bytes and more) to the workspace."""
+    cfg = W.schlogl_flux_we(reweight_period=0, n_iters=4, n_runs=3)
+    net = P.network_from_spec(cfg.network)
+    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+    c, keep = P.run_config_from(cfg)
+    base = P.we_ensemble_workspace_bytes(net, bm, c)
+    c.reweight_period = 5
+    grown = P.we_ensemble_workspace_bytes(net, bm, c)
+    assert grown - base >= 16 * 80 * 80 * 3
+    c.reweight_period = -1
+    with pytest.raises(P.WEError):
+        P.we_ensemble_workspace_bytes(net, bm, c)
+    c.reweight_period = 2
+    c.resample = 0
+    with pytest.raises(P.WEError):
+        P.we_ensemble_workspace_bytes(net, bm, c)
+    big = P.we_binmap_grid([0], [W.uniform_edges(0, 1, 1100)])
+    c.resample = 1
+    with pytest.raises(P.WEError):
+        P.we_ensemble_workspace_bytes(net, big, c)
