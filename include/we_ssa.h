@@ -144,10 +144,13 @@ int32_t we_binmap_n_bins(const we_binmap *bm);
  * we_mlp_gradient: the batch-mean loss and its gradient (device, n_params floats) over all n
  *   samples, without changing the weights (for gradient checks).
  * we_mlp_forward: z (device, n floats) of n states (device, n x n_in int32) from the FP32
- *   weights (bf16 = 0) or from their BF16 roundings (bf16 = 1: the same z as a learned bin map
- *   made from this MLP computes, bit for bit).
+ *   weights on the CUDA cores (bf16 = 0) or in the inference form (bf16 = 1): weights rounded
+ *   to BF16, the 64 x 64 layer on the tensor cores (tcgen05, FP32 accumulator, the FP32
+ *   activations split into three BF16 parts), the same z as a learned bin map made from this
+ *   MLP computes, bit for bit.
  * Training is FP32 with sums in sample order (deterministic).  Errors: WE_EINVAL, WE_ENOMEM,
- * WE_ECUDA.
+ * WE_ECUDA; WE_ENOTSUPPORTED when the inference form's shared memory (57 KB + 2 hidden
+ * (n_in + 1) bytes + biases) passes 227 KB.
  * ------------------------------------------------------------------------------------------ */
 typedef struct we_mlp we_mlp;
 we_status we_mlp_create(int32_t n_in, int32_t hidden, const float *params, we_mlp **out);
@@ -160,9 +163,10 @@ we_status we_mlp_gradient(const we_mlp *mlp, const int32_t *states, const float 
                           float *grad, float *loss, void *stream);
 we_status we_mlp_forward(const we_mlp *mlp, const int32_t *states, int32_t n, int32_t bf16, float *z,
                          void *stream);
-/* Bin map on the learned coordinate: a snapshot of the MLP's weights rounded to BF16 (inference
- * runs in FP32 on those weights), with n_bins intervals [edges[k], edges[k+1]) of z (values
- * outside fall in the end bins).  Binning runs in a kernel of its own after the SSA kernel. */
+/* Bin map on the learned coordinate: a snapshot of the MLP's weights rounded to BF16, with
+ * n_bins intervals [edges[k], edges[k+1]) of z (values outside fall in the end bins).  Binning
+ * runs in a kernel of its own after the SSA kernel, in tiles of 128 walkers, in the inference
+ * form of we_mlp_forward with bf16 = 1. */
 we_status we_binmap_learned(const we_mlp *mlp, int32_t n_bins, const float *edges, we_binmap **out);
 
 /* ------------------------------------------------------------------------------------------

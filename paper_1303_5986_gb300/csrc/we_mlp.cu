@@ -9,7 +9,13 @@
 //     k_mlp_reduce       one thread per parameter: the rows summed in block order
 //                        (deterministic), then an Adam step (or just the gradient, for checks)
 //   inference (BF16 weights, FP32 arithmetic), fused with bin assignment:
-//     k_learned_bins one thread per walker after the SSA kernel: z, its bin, bin counts
+//     k_learned_bins a block per tile of 128 walkers after the SSA kernel: the first layer on
+//                    the CUDA cores (one walker per thread), the 64 x 64 layer on the tensor
+//                    cores (tcgen05, accumulator in tensor memory), then z, its bin, bin counts
+//     k_mlp_forward_tc the same tile computation for given states (the standalone BF16 forward)
+//   The tensor cores take BF16 operands: each activation of the first layer is split into three
+//   BF16 parts (h = h0 + h1 + h2 to about 2^-26 relative) and each part is multiplied by the
+//   BF16 weights into the same FP32 accumulator, so the layer keeps FP32-level accuracy.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -18,6 +24,7 @@
 #include "../../include/we_ssa.h"
 #include "we_mlp.cuh"
 #include "we_ssa_common.cuh"
+#include "we_tc.cuh"
 
 namespace we {
 
@@ -186,14 +193,13 @@ __device__ __forceinline__ float bf16_round_dev(float f) {
   return __uint_as_float(u & 0xffff0000u);
 }
 
-// z of samples from the FP32 master weights, or from their BF16 roundings (BF16 = true), in the
-// operation order of mlp_coordinate, so that the BF16 form equals the binning kernel's z.
-template <bool BF16>
+// z of samples from the FP32 master weights, FP32 arithmetic on the CUDA cores (the reference
+// form of the trained network; the BF16 inference form is k_mlp_forward_tc).
 __global__ void k_mlp_forward(MlpShape sh, const float *p, const int32_t *states, int n, float *z) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n) return;
   const int H = sh.H, ni = sh.n_in;
-  auto wt = [](float w) { return BF16 ? bf16_round_dev(w) : w; };
+  auto wt = [](float w) { return w; };
   float h1[64];
 #pragma unroll
   for (int o = 0; o < 64; ++o) h1[o] = 0.0f;
@@ -217,50 +223,204 @@ __global__ void k_mlp_forward(MlpShape sh, const float *p, const int32_t *states
   z[b] = zz;
 }
 
-// z of every live walker after the SSA kernel, its bin and the bin counts (learned bin maps).
-__global__ void k_learned_bins(PropagateParams prm) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// ------------------------------------------------------------------------------------------
+// Tensor-core inference.  Dynamic shared memory of a 128-thread block:
+//   [0, 48 KB)     three A tiles (parts 0, 1, 2 of the activations): 128 samples x 64, BF16,
+//                  core-matrix layout, 16 KB each
+//   [48, 56 KB)    B tile: W2 (64 x 64, zero beyond H), BF16, core-matrix layout
+//   [56 KB, +16)   mbarrier, tensor-memory address
+//   [57 KB, ...)   W1 (H x n_in) and w3 (H) as BF16, then b1, b2 (H each) and b3 as FP32
+// ------------------------------------------------------------------------------------------
+constexpr int kTcTile = 128;
+constexpr size_t kTcWeightsOff = 57 * 1024;
+constexpr int kTcParts = 3;
+constexpr long kTcWaitLimit = 1l << 24;
+
+size_t tc_mlp_smem(int n_in, int H) {
+  return kTcWeightsOff + 2 * ((size_t)H * n_in + H) + 8 + 4 * (2 * (size_t)H + 1) + 16;
+}
+
+struct TcMlp {
+  unsigned char *a, *b;          // A tiles (kTcParts x 16 KB), B tile
+  uint64_t *mbar;
+  uint32_t *slot;
+  MlpView m;                     // weights and biases in shared memory
+};
+
+// Carve the shared memory, stage the BF16 weights (w1, w2, w3 given as BF16 bits) and biases,
+// fill the B tile, allocate 64 tensor-memory columns (warp 0) and initialise the mbarrier.
+__device__ TcMlp tc_mlp_setup(unsigned char *sm, int n_in, int H, const uint16_t *w1, const uint16_t *w2,
+                              const uint16_t *w3, const float *b1, const float *b2, const float *b3) {
+  TcMlp T;
+  T.a = sm;
+  T.b = sm + 49152;
+  T.mbar = reinterpret_cast<uint64_t *>(sm + 57344);
+  T.slot = reinterpret_cast<uint32_t *>(sm + 57352);
+  uint16_t *sw1 = reinterpret_cast<uint16_t *>(sm + kTcWeightsOff);
+  uint16_t *sw3 = sw1 + (size_t)H * n_in;
+  float *sb = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(sw3 + H + 3) & ~(uintptr_t)7);
+  for (int i = threadIdx.x; i < H * n_in; i += blockDim.x) sw1[i] = w1[i];
+  for (int i = threadIdx.x; i < H; i += blockDim.x) { sw3[i] = w3[i]; sb[i] = b1[i]; sb[H + i] = b2[i]; }
+  if (threadIdx.x == 0) sb[2 * H] = b3[0];
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    const int n = e >> 6, k = e & 63;
+    *reinterpret_cast<uint16_t *>(T.b + tc_tile_offset(n, k)) = (n < H && k < H) ? w2[n * H + k] : (uint16_t)0;
+  }
+  if (threadIdx.x == 0) tc_mbar_init(T.mbar, 1);
+  if (threadIdx.x < 32) tc_alloc(T.slot, 64);
+  tc_fence_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  T.m.n_in = n_in;
+  T.m.hidden = H;
+  T.m.w1 = sw1;
+  T.m.w2 = nullptr;
+  T.m.w3 = sw3;
+  T.m.b1 = sb;
+  T.m.b2 = sb + H;
+  T.m.b3 = sb + 2 * H;
+  return T;
+}
+
+__device__ __forceinline__ void tc_mlp_teardown(const TcMlp &T) {
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) tc_dealloc(*T.slot, 64);
+}
+
+// One tile: thread t holds sample t (valid or not).  First layer on the CUDA cores, activations
+// split into three BF16 parts in the A tiles (part p+1 = BF16 of what parts 0..p leave over),
+// thread 0 issues part_p . W2^T for p = 0, 1, 2 (K = 16 per instruction) into one 128 x 64
+// FP32 accumulator, every thread reads its accumulator row
+// and finishes z = b3 + sum_o w3_o silu(acc_o + b2_o).  `tile_no` counts this block's tiles
+// (mbarrier phase).  Returns false (for every thread) if the tensor core did not complete in
+// time; z is then NaN.
+__device__ bool tc_mlp_tile(const TcMlp &T, const int32_t *xs, int stride, bool valid, uint32_t tile_no, float &z) {
+  const int t = threadIdx.x;
+  const int H = T.m.hidden;
+  float h1[64];
+  mlp_layer1(T.m, xs, stride, valid, h1);
+#pragma unroll
+  for (int kg = 0; kg < 8; ++kg) {
+    uint32_t pw[kTcParts][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float ra = h1[kg * 8 + 2 * j], rb = h1[kg * 8 + 2 * j + 1];      // what is left to represent
+#pragma unroll
+      for (int q = 0; q < kTcParts; ++q) {
+        const float pa = bf16_round_dev(ra), pb = bf16_round_dev(rb);
+        pw[q][j] = (__float_as_uint(pa) >> 16) | (__float_as_uint(pb) & 0xffff0000u);
+        ra = __fsub_rn(ra, pa);                                       // exact
+        rb = __fsub_rn(rb, pb);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kTcParts; ++q)
+      *reinterpret_cast<uint4 *>(T.a + q * 16384 + tc_tile_offset(t, kg * 8)) =
+          make_uint4(pw[q][0], pw[q][1], pw[q][2], pw[q][3]);
+  }
+  tc_fence_smem();
+  __syncthreads();
+  const uint32_t taddr = *T.slot;
+  if (t == 0) {
+    tc_fence_after();
+    constexpr uint32_t idesc = tc_idesc_bf16(kTcTile, 64);
+    const uint32_t aa = tc_smem_addr(T.a), bb = tc_smem_addr(T.b);
+#pragma unroll
+    for (int part = 0; part < kTcParts; ++part)
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc)
+        tc_mma_bf16(taddr, tc_desc(aa + 16384 * part + 256 * kc, 128, 1024), tc_desc(bb + 256 * kc, 128, 1024),
+                    idesc, part > 0 || kc > 0);
+    tc_commit(T.mbar);
+  }
+  const bool done = __syncthreads_and(tc_mbar_wait(T.mbar, tile_no & 1u, kTcWaitLimit) ? 1 : 0) != 0;
+  tc_fence_after();
+  z = __int_as_float(0x7fc00000);
+  if (done) {
+    float acc[64];
+    tc_ld_row64(taddr, acc);
+    float zz = T.m.b3[0];
+#pragma unroll
+    for (int o = 0; o < 64; ++o)
+      if (o < H) zz = __fmaf_rn(bf16_to_f32(T.m.w3[o]), silu_f(__fadd_rn(acc[o], T.m.b2[o])), zz);
+    z = zz;
+  }
+  tc_fence_before();
+  __syncthreads();                                    // A tiles and the accumulator free again
+  return done;
+}
+
+// z of every live walker after the SSA kernel, its bin and the bin counts (learned bin maps):
+// tiles of 128 live walkers in run order, a persistent grid.
+__global__ void __launch_bounds__(128) k_learned_bins(PropagateParams prm) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   const EnsView &E = prm.ens;
   const BinView &bv = prm.bins;
   const MlpView &m = bv.mlp;
-  const int H = m.hidden, ni = m.n_in;
-  uint16_t *w1 = reinterpret_cast<uint16_t *>(smem_raw);
-  uint16_t *w2 = w1 + H * ni;
-  uint16_t *w3 = w2 + H * H;
-  float *bb = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(w3 + H + 1) & ~(uintptr_t)3);
-  for (int i = threadIdx.x; i < H * ni; i += blockDim.x) w1[i] = m.w1[i];
-  for (int i = threadIdx.x; i < H * H; i += blockDim.x) w2[i] = m.w2[i];
-  for (int i = threadIdx.x; i < H; i += blockDim.x) { w3[i] = m.w3[i]; bb[i] = m.b1[i]; bb[H + i] = m.b2[i]; }
-  if (threadIdx.x == 0) bb[2 * H] = m.b3[0];
-  __syncthreads();
-  MlpView ms = m;
-  ms.w1 = w1; ms.w2 = w2; ms.w3 = w3; ms.b1 = bb; ms.b2 = bb + H; ms.b3 = bb + 2 * H;
-  const int iter = *E.iter;
-  const int par = iter & 1;
+  TcMlp T = tc_mlp_setup(smem_raw, m.n_in, m.hidden, m.w1, m.w2, m.w3, m.b1, m.b2, m.b3);
+  const int par = (*E.iter) & 1;
   const int ld = E.R * E.cap;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ld; g += gridDim.x * blockDim.x) {
-    const int r = g / E.cap, w = g - r * E.cap;
-    if (w >= E.count[r]) continue;
-    const float z = mlp_coordinate(ms, E.x[par] + g, ld);
-    const int b = z_bin(bv, z);
+  const int total = E.run_off[E.R];
+  uint32_t tile_no = 0;
+  for (int base = blockIdx.x * kTcTile; base < total; base += gridDim.x * kTcTile, ++tile_no) {
+    const int f = base + (int)threadIdx.x;
+    const bool valid = f < total;
+    const int r = !valid ? 0 : (E.R == 1 ? 0 : find_run(E.run_off, E.R, f));
+    const int g = r * E.cap + (valid ? f - E.run_off[r] : 0);
+    float z;
+    const bool ok = tc_mlp_tile(T, E.x[par] + g, ld, valid, tile_no, z);
+    if (!valid) continue;
+    if (!ok) atomicCAS(&E.status[r], 0, WE_ETIMEOUT);
+    const int b = ok ? z_bin(bv, z) : 0;
     E.bin[g] = b;
     if (bv.zout) bv.zout[g] = z;
     if (prm.resample) atomicAdd(&E.bin_count[r * bv.n_bins + b], 1);
   }
+  tc_mlp_teardown(T);
 }
 
-size_t learned_bins_smem(int n_in, int H) { return 2 * ((size_t)H * n_in + H * H + H + 2) + 4 * (2 * H + 1) + 16; }
+// The standalone BF16 forward pass of given states (walker-major, n x n_in) from the FP32 master
+// weights rounded to BF16 here: the same tile computation, so z equals the binning kernel's.
+__global__ void __launch_bounds__(128) k_mlp_forward_tc(MlpShape sh, const float *p, const int32_t *states, int n,
+                                                        uint16_t *wbf, float *z) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int H = sh.H, ni = sh.n_in;
+  TcMlp T = tc_mlp_setup(smem_raw, ni, H, wbf, wbf + (size_t)H * ni, wbf + (size_t)H * ni + H * H,
+                         p + sh.o_b1(), p + sh.o_b2(), p + sh.o_b3());
+  uint32_t tile_no = 0;
+  for (int base = blockIdx.x * kTcTile; base < n; base += gridDim.x * kTcTile, ++tile_no) {
+    const int b = base + (int)threadIdx.x;
+    const bool valid = b < n;
+    float zz;
+    tc_mlp_tile(T, states + (size_t)(valid ? b : 0) * ni, 1, valid, tile_no, zz);
+    if (valid) z[b] = zz;
+  }
+  tc_mlp_teardown(T);
+}
+
+// BF16 bits of the weights W1, W2, w3 (round to nearest even), packed in that order.
+__global__ void k_mlp_weights_bf16(MlpShape sh, const float *p, uint16_t *out) {
+  const int H = sh.H, ni = sh.n_in;
+  const int n1 = H * ni, n2 = H * H;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + H; i += gridDim.x * blockDim.x) {
+    const float w = i < n1 ? p[sh.o_w1() + i] : (i < n1 + n2 ? p[sh.o_w2() + i - n1] : p[sh.o_w3() + i - n1 - n2]);
+    out[i] = (uint16_t)(__float_as_uint(bf16_round_dev(w)) >> 16);
+  }
+}
+
+size_t learned_bins_smem(int n_in, int H) { return tc_mlp_smem(n_in, H); }
 
 cudaError_t launch_learned_bins(const PropagateParams &prm, cudaStream_t st) {
   const size_t smem = learned_bins_smem(prm.bins.mlp.n_in, prm.bins.mlp.hidden);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_learned_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_learned_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   const int ld = prm.ens.R * prm.ens.cap;
-  int grid = (ld + 127) / 128;
-  if (grid > 152 * 4) grid = 152 * 4;
-  k_learned_bins<<<grid, 128, smem, st>>>(prm);
+  int grid = (ld + kTcTile - 1) / kTcTile;
+  if (grid > 152 * 2) grid = 152 * 2;
+  k_learned_bins<<<grid, kTcTile, smem, st>>>(prm);
   return cudaGetLastError();
 }
 
@@ -274,6 +434,7 @@ using namespace we;
 struct we_mlp {
   MlpShape sh{};
   float *p = nullptr, *m = nullptr, *v = nullptr;   // device: params, Adam moments
+  uint16_t *wbf = nullptr;                          // device: BF16 weights for the forward pass
   int step = 0;
 };
 
@@ -295,23 +456,30 @@ extern "C" we_status we_mlp_create(int32_t n_in, int32_t hidden, const float *pa
   M->sh.n_in = n_in;
   M->sh.H = hidden;
   const size_t np = (size_t)M->sh.n_params();
-  if (cudaMalloc(&M->p, 4 * np) || cudaMalloc(&M->m, 4 * np) || cudaMalloc(&M->v, 4 * np)) {
+  const size_t nw = (size_t)hidden * n_in + (size_t)hidden * hidden + hidden;
+  if (cudaMalloc(&M->p, 4 * np) || cudaMalloc(&M->m, 4 * np) || cudaMalloc(&M->v, 4 * np) ||
+      cudaMalloc(&M->wbf, 2 * nw)) {
     cudaGetLastError();
-    cudaFree(M->p); cudaFree(M->m); cudaFree(M->v);
+    cudaFree(M->p); cudaFree(M->m); cudaFree(M->v); cudaFree(M->wbf);
     delete M;
     return WE_ENOMEM;
   }
   cudaError_t e = cudaMemcpy(M->p, params, 4 * np, cudaMemcpyHostToDevice);
   e = e ? e : cudaMemset(M->m, 0, 4 * np);
   e = e ? e : cudaMemset(M->v, 0, 4 * np);
-  if (e) { cudaGetLastError(); cudaFree(M->p); cudaFree(M->m); cudaFree(M->v); delete M; return WE_ECUDA; }
+  if (e) {
+    cudaGetLastError();
+    cudaFree(M->p); cudaFree(M->m); cudaFree(M->v); cudaFree(M->wbf);
+    delete M;
+    return WE_ECUDA;
+  }
   *out = M;
   return WE_OK;
 }
 
 extern "C" void we_mlp_destroy(we_mlp *M) {
   if (!M) return;
-  cudaFree(M->p); cudaFree(M->m); cudaFree(M->v);
+  cudaFree(M->p); cudaFree(M->m); cudaFree(M->v); cudaFree(M->wbf);
   delete M;
 }
 
@@ -390,9 +558,19 @@ extern "C" we_status we_mlp_forward(const we_mlp *M, const int32_t *states, int3
   if (!M || n < 0 || (n > 0 && (!states || !z))) return WE_EINVAL;
   if (n == 0) return WE_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (bf16) k_mlp_forward<true><<<(n + 127) / 128, 128, 0, st>>>(M->sh, M->p, states, n, z);
-  else k_mlp_forward<false><<<(n + 127) / 128, 128, 0, st>>>(M->sh, M->p, states, n, z);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (bf16) {
+    const size_t smem = tc_mlp_smem(M->sh.n_in, M->sh.H);
+    if (smem > 227 * 1024) return WE_ENOTSUPPORTED;
+    k_mlp_weights_bf16<<<64, 256, 0, st>>>(M->sh, M->p, M->wbf);
+    e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = (n + kTcTile - 1) / kTcTile;
+    if (grid > 152 * 2) grid = 152 * 2;
+    if (!e) k_mlp_forward_tc<<<grid, kTcTile, smem, st>>>(M->sh, M->p, states, n, M->wbf, z);
+  } else {
+    k_mlp_forward<<<(n + 127) / 128, 128, 0, st>>>(M->sh, M->p, states, n, z);
+  }
+  e = e ? e : cudaGetLastError();
   e = e ? e : cudaStreamSynchronize(st);
   if (e) { cudaGetLastError(); return WE_ECUDA; }
   return WE_OK;

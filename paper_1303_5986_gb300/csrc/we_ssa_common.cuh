@@ -69,13 +69,14 @@ __device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_floa
 
 __device__ __forceinline__ float silu_f(float a) { return __fdiv_rn(a, __fadd_rn(1.0f, expf(-a))); }
 
-// The learned coordinate of one state (see MlpView): layer 1 is accumulated input by input so
-// that each log1p is taken once; layer 2 is folded output by output into the final dot product.
-// Hidden width at most 64.
-__device__ __forceinline__ float mlp_coordinate(const MlpView &m, const int32_t *xs, int stride) {
-  float h1[64];
+// First layer of the learned coordinate (see MlpView) for one state: h1 = silu(W1 phi + b1),
+// accumulated input by input so that each log1p is taken once; zero beyond the hidden width,
+// and all zero for an invalid sample (whose counts are not read).  Hidden width at most 64.
+__device__ __forceinline__ void mlp_layer1(const MlpView &m, const int32_t *xs, int stride, bool valid,
+                                           float (&h1)[64]) {
 #pragma unroll
   for (int o = 0; o < 64; ++o) h1[o] = 0.0f;
+  if (!valid) return;
   for (int i = 0; i < m.n_in; ++i) {
     const float phi = log1pf((float)xs[i * stride]);
 #pragma unroll
@@ -85,15 +86,6 @@ __device__ __forceinline__ float mlp_coordinate(const MlpView &m, const int32_t 
 #pragma unroll
   for (int o = 0; o < 64; ++o)
     if (o < m.hidden) h1[o] = silu_f(__fadd_rn(h1[o], m.b1[o]));
-  float z = m.b3[0];
-  for (int o = 0; o < m.hidden; ++o) {
-    float a = m.b2[o];
-#pragma unroll
-    for (int i = 0; i < 64; ++i)
-      if (i < m.hidden) a = __fmaf_rn(bf16_to_f32(m.w2[o * m.hidden + i]), h1[i], a);
-    z = __fmaf_rn(bf16_to_f32(m.w3[o]), silu_f(a), z);
-  }
-  return z;
 }
 
 // Bin of a z value among n_bins intervals [zedges[k], zedges[k+1]) (clamped at both ends).

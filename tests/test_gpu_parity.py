@@ -320,6 +320,15 @@ def test_reweighting_parity_schlogl(period):
     assert (rw == 1).sum() >= 3 * (24 // period) // 2
 
 
+@pytest.mark.parametrize("mapping", [P.WE_MAP_WARP, P.WE_MAP_THREAD])
+def test_reweighting_parity_other_mappings(mapping):
+    """The transfer accumulation reads the end bins that every SSA kernel writes: the same
+    reweighted weights with the warp-per-walker and the general thread kernels."""
+    cfg = W.schlogl_flux_we(reweight_period=3, n_iters=15, n_runs=2, m_targ=5)
+    ens = _parity(cfg, 15, mapping=mapping)
+    assert (ens.per_iter(P.WE_OUT_RW)[[5, 8, 11, 14]] == 1).all()
+
+
 def test_reweighting_parity_toggle_2d():
     """Reweighting over a 30 x 30 grid (900 bins) with Hill kinetics and one parameter set per
     run."""
