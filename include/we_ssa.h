@@ -249,9 +249,19 @@ we_status we_ensemble_resample(we_ensemble *ens, void *stream);
 we_status we_ensemble_step(we_ensemble *ens, int32_t n_iters, void *stream);
 /* The same n_iters iterations as we_ensemble_step, with the device time of every iteration's
  * SSA kernel measured by CUDA events recorded on `stream` on either side of it; synchronises
- * the stream and writes n_iters durations in milliseconds to propagate_ms (host array). */
+ * the stream and writes n_iters durations in milliseconds to propagate_ms (host array).  The
+ * events come from a per-device pool that the library creates on first need and keeps for the
+ * life of the process (2 per iteration), so nothing is created or destroyed while the launches
+ * run; timed calls on one device must not overlap in time.  n_iters = 0 only captures the
+ * timed graph (nothing runs), so that a later timed call launches at once. */
 we_status we_ensemble_step_timed(we_ensemble *ens, int32_t n_iters, void *stream,
                                  float *propagate_ms);
+/* we_ensemble_step_timed with only every `every`-th iteration (0, every, 2 every, ...) timed
+ * and the others replayed from the plain graph: ceil(n_iters / every) durations are written.
+ * The event-record nodes cost the timed iterations a few microseconds each; sampling keeps the
+ * timed run close to we_ensemble_step's. */
+we_status we_ensemble_step_timed_every(we_ensemble *ens, int32_t n_iters, int32_t every, void *stream,
+                                       float *propagate_ms);
 /* Synchronise the stream and return the first non-OK device status of any run (or WE_OK). */
 we_status we_ensemble_sync(we_ensemble *ens, void *stream);
 

@@ -86,6 +86,7 @@ SIGNATURES = [
     ("we_ensemble_resample", C.c_int32, [_VP, _VP]),
     ("we_ensemble_step", C.c_int32, [_VP, C.c_int32, _VP]),
     ("we_ensemble_step_timed", C.c_int32, [_VP, C.c_int32, _VP, C.POINTER(C.c_float)]),
+    ("we_ensemble_step_timed_every", C.c_int32, [_VP, C.c_int32, C.c_int32, _VP, C.POINTER(C.c_float)]),
     ("we_ensemble_sync", C.c_int32, [_VP, _VP]),
     ("we_ensemble_get", C.c_int32, [_VP, C.c_int32, C.c_int32, _VP, C.c_size_t,
                                     C.POINTER(C.c_size_t), _VP]),

@@ -215,12 +215,14 @@ class Ensemble:
     def step(self, n_iters: int, stream=None):
         check(lib().we_ensemble_step(self.h, int(n_iters), _stream_handle(stream)))
 
-    def step_timed(self, n_iters: int, stream=None) -> np.ndarray:
-        """step() with the SSA kernel of every iteration timed by CUDA events (ms)."""
-        ms = np.zeros(max(int(n_iters), 1), dtype=np.float32)
-        check(lib().we_ensemble_step_timed(self.h, int(n_iters), _stream_handle(stream),
-                                           ms.ctypes.data_as(C.POINTER(C.c_float))))
-        return ms[:int(n_iters)]
+    def step_timed(self, n_iters: int, stream=None, every: int = 1) -> np.ndarray:
+        """step() with the SSA kernel of every `every`-th iteration (0, every, ...) timed by CUDA
+        events (ms, one entry per timed iteration)."""
+        n_t = (int(n_iters) + every - 1) // every
+        ms = np.zeros(max(n_t, 1), dtype=np.float32)
+        check(lib().we_ensemble_step_timed_every(self.h, int(n_iters), int(every), _stream_handle(stream),
+                                                 ms.ctypes.data_as(C.POINTER(C.c_float))))
+        return ms[:n_t]
 
     def sync(self, stream=None):
         check(lib().we_ensemble_sync(self.h, _stream_handle(stream)))

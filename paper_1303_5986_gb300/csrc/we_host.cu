@@ -500,7 +500,7 @@ struct we_ensemble {
   int32_t iters_enqueued = 0;       // iterations recorded so far (host view)
   bool phase_propagated = false;
   cudaGraphExec_t graph = nullptr;
-  cudaGraphExec_t timed_graph = nullptr;
+  cudaGraphExec_t timed_graph = nullptr, timed_graph2 = nullptr;   // two instances, alternated
   cudaGraph_t timed_graph_src = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   cudaGraphNode_t ev_node_start = nullptr, ev_node_end = nullptr;
@@ -782,6 +782,7 @@ extern "C" we_status we_ensemble_destroy(we_ensemble *E) {
   if (!E) return WE_OK;
   if (E->graph) cudaGraphExecDestroy(E->graph);
   if (E->timed_graph) cudaGraphExecDestroy(E->timed_graph);
+  if (E->timed_graph2) cudaGraphExecDestroy(E->timed_graph2);
   if (E->timed_graph_src) cudaGraphDestroy(E->timed_graph_src);
   if (E->ev_a) cudaEventDestroy(E->ev_a);
   if (E->ev_b) cudaEventDestroy(E->ev_b);
@@ -837,6 +838,21 @@ extern "C" we_status we_ensemble_resample(we_ensemble *E, void *stream) {
   return WE_OK;
 }
 
+// The iteration graph (propagate + resample), captured once per ensemble.
+static we_status build_graph(we_ensemble *E) {
+  if (!E->cap_stream) WE_CUDA_TRY(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
+  WE_CUDA_TRY(cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e1 = enqueue_propagate(E, E->cap_stream);
+  cudaError_t e2 = e1 ? e1 : enqueue_resample(E, E->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(E->cap_stream, &g);
+  if (e2 || e3) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return cuda_fail(e2 ? e2 : e3, "graph capture"); }
+  cudaError_t e4 = cudaGraphInstantiate(&E->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e4) { E->graph = nullptr; return cuda_fail(e4, "graph instantiate"); }
+  return WE_OK;
+}
+
 extern "C" we_status we_ensemble_step(we_ensemble *E, int32_t n_iters, void *stream) {
   if (!E) return fail(WE_EINVAL, "ensemble is NULL");
   if (n_iters < 0) return fail(WE_EINVAL, "n_iters must be >= 0");
@@ -846,19 +862,31 @@ extern "C" we_status we_ensemble_step(we_ensemble *E, int32_t n_iters, void *str
   if (n_iters == 0) return WE_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!E->graph) {
-    WE_CUDA_TRY(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
-    WE_CUDA_TRY(cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = enqueue_propagate(E, E->cap_stream);
-    cudaError_t e2 = e1 ? e1 : enqueue_resample(E, E->cap_stream);
-    cudaGraph_t g = nullptr;
-    cudaError_t e3 = cudaStreamEndCapture(E->cap_stream, &g);
-    if (e2 || e3) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return cuda_fail(e2 ? e2 : e3, "graph capture"); }
-    cudaError_t e4 = cudaGraphInstantiate(&E->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e4) { E->graph = nullptr; return cuda_fail(e4, "graph instantiate"); }
+    we_status st = build_graph(E);
+    if (st) return st;
   }
   for (int i = 0; i < n_iters; ++i) WE_CUDA_TRY(cudaGraphLaunch(E->graph, s));
   E->iters_enqueued += n_iters;
+  return WE_OK;
+}
+
+// Events for timed replays, per device: grown on demand, kept for the life of the process.
+// Calls that overlap in time on one device must not share them; timed replays of different
+// ensembles are meant to run one after another (they synchronise before returning).
+static std::mutex g_ev_mu;
+static std::vector<cudaEvent_t> g_ev_pool[256];
+
+static we_status timing_events(size_t n, cudaEvent_t **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) { cudaGetLastError(); return fail(WE_ECUDA, "current device"); }
+  std::lock_guard<std::mutex> lk(g_ev_mu);
+  std::vector<cudaEvent_t> &pool = g_ev_pool[dev];
+  while (pool.size() < n) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return fail(WE_ECUDA, "event creation"); }
+    pool.push_back(e);
+  }
+  *out = pool.data();
   return WE_OK;
 }
 
@@ -896,46 +924,75 @@ static we_status build_timed_graph(we_ensemble *E) {
     cudaGraphDestroy(g);
     return fail(WE_ECUDA, "timed graph: event-record nodes not found in the capture");
   }
+  // two executable instances, launched alternately: retargeting the event nodes of one while
+  // the other runs keeps the host from waiting on the launch in flight
   cudaError_t e3 = cudaGraphInstantiate(&E->timed_graph, g, 0);
-  if (e3) { cudaGraphDestroy(g); E->timed_graph = nullptr; return cuda_fail(e3, "timed graph instantiate"); }
+  e3 = e3 ? e3 : cudaGraphInstantiate(&E->timed_graph2, g, 0);
+  if (e3) {
+    if (E->timed_graph) cudaGraphExecDestroy(E->timed_graph);
+    cudaGraphDestroy(g);
+    E->timed_graph = E->timed_graph2 = nullptr;
+    return cuda_fail(e3, "timed graph instantiate");
+  }
   // the event-record node handles used to retarget the executable graph belong to this graph,
   // so it lives as long as the ensemble
   E->timed_graph_src = g;
   return WE_OK;
 }
 
-extern "C" we_status we_ensemble_step_timed(we_ensemble *E, int32_t n_iters, void *stream,
-                                            float *propagate_ms) {
+extern "C" we_status we_ensemble_step_timed_every(we_ensemble *E, int32_t n_iters, int32_t every, void *stream,
+                                                 float *propagate_ms) {
   if (!E || !propagate_ms) return fail(WE_EINVAL, "ensemble and propagate_ms are required");
   if (n_iters < 0) return fail(WE_EINVAL, "n_iters must be >= 0");
+  if (every < 1) return fail(WE_EINVAL, "every must be >= 1");
   if (E->phase_propagated) return fail(WE_EINVAL, "step called between propagate and resample");
   if (E->iters_enqueued + n_iters > E->cfg.record_iters)
     return fail(WE_EOVERFLOW, "%d more iterations would exceed record_iters (%d)", n_iters, E->cfg.record_iters);
-  if (n_iters == 0) return WE_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (!E->timed_graph) {
+  if (!E->timed_graph) {                                 // n_iters = 0: capture only
     we_status st = build_timed_graph(E);
     if (st) return st;
   }
-  std::vector<cudaEvent_t> ev(2 * (size_t)n_iters, nullptr);
-  auto release = [&]() { for (auto e : ev) if (e) cudaEventDestroy(e); };
-  for (auto &e : ev)
-    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); release(); return fail(WE_ECUDA, "event creation"); }
+  if (every > 1 && !E->graph) {
+    we_status st = build_graph(E);
+    if (st) return st;
+  }
+  if (n_iters == 0) return WE_OK;
+  const int n_timed = (n_iters + every - 1) / every;
+  // per-iteration events from a process-wide pool (per device), created once and reused, so
+  // that no event is created or destroyed between the launches being timed
+  cudaEvent_t *ev = nullptr;
+  {
+    we_status st = timing_events(2 * (size_t)n_timed, &ev);
+    if (st) return st;
+  }
   for (int i = 0; i < n_iters; ++i) {
-    cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(E->timed_graph, E->ev_node_start, ev[2 * i]);
-    e = e ? e : cudaGraphExecEventRecordNodeSetEvent(E->timed_graph, E->ev_node_end, ev[2 * i + 1]);
-    e = e ? e : cudaGraphLaunch(E->timed_graph, s);
-    if (e) { cudaGetLastError(); release(); return cuda_fail(e, "timed graph launch"); }
+    cudaError_t e;
+    if (i % every == 0) {
+      const int k = i / every;
+      cudaGraphExec_t gx = (k & 1) ? E->timed_graph2 : E->timed_graph;
+      e = cudaGraphExecEventRecordNodeSetEvent(gx, E->ev_node_start, ev[2 * k]);
+      e = e ? e : cudaGraphExecEventRecordNodeSetEvent(gx, E->ev_node_end, ev[2 * k + 1]);
+      e = e ? e : cudaGraphLaunch(gx, s);
+    } else {
+      e = cudaGraphLaunch(E->graph, s);
+    }
+    if (e) { cudaGetLastError(); return cuda_fail(e, "timed graph launch"); }
   }
   E->iters_enqueued += n_iters;
-  cudaError_t e = cudaEventSynchronize(ev[2 * (size_t)n_iters - 1]);
-  for (int i = 0; i < n_iters && !e; ++i) e = cudaEventElapsedTime(&propagate_ms[i], ev[2 * i], ev[2 * i + 1]);
-  // point the nodes back at the ensemble's own events before the per-iteration ones go away
-  cudaGraphExecEventRecordNodeSetEvent(E->timed_graph, E->ev_node_start, E->ev_a);
-  cudaGraphExecEventRecordNodeSetEvent(E->timed_graph, E->ev_node_end, E->ev_b);
-  release();
+  cudaError_t e = cudaStreamSynchronize(s);
+  for (int k = 0; k < n_timed && !e; ++k) e = cudaEventElapsedTime(&propagate_ms[k], ev[2 * k], ev[2 * k + 1]);
+  // point the nodes back at the ensemble's own events
+  for (cudaGraphExec_t gx : {E->timed_graph, E->timed_graph2}) {
+    cudaGraphExecEventRecordNodeSetEvent(gx, E->ev_node_start, E->ev_a);
+    cudaGraphExecEventRecordNodeSetEvent(gx, E->ev_node_end, E->ev_b);
+  }
   if (e) return cuda_fail(e, "event timing");
   return WE_OK;
+}
+
+extern "C" we_status we_ensemble_step_timed(we_ensemble *E, int32_t n_iters, void *stream, float *propagate_ms) {
+  return we_ensemble_step_timed_every(E, n_iters, 1, stream, propagate_ms);
 }
 
 extern "C" we_status we_ensemble_sync(we_ensemble *E, void *stream) {

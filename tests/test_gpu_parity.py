@@ -305,6 +305,23 @@ def test_timed_step_matches_step_and_reports_kernel_times():
         assert np.array_equal(a.per_iter(P.WE_OUT_EVENTS, r), b.per_iter(P.WE_OUT_EVENTS, r))
 
 
+def test_sampled_timed_step_matches_step():
+    """Every 5th iteration timed (0, 5, 10), the others from the plain graph, across two calls
+    (the second after a capture-only call): the same trajectories as untimed steps."""
+    cfg = W.schlogl_mfpt_we(n_iters=24, n_runs=2)
+    a = gpu_run(cfg, 24)
+    b = gpu_run(cfg, 0, record_iters=24)
+    assert b.step_timed(0, every=5).shape == (0,)
+    ms1 = b.step_timed(12, every=5)
+    ms2 = b.step_timed(12, every=5)
+    b.sync()
+    assert ms1.shape == (3,) and ms2.shape == (3,) and np.all(ms1 > 0) and np.all(ms2 > 0)
+    for r in range(2):
+        assert np.array_equal(a.states(r), b.states(r))
+        assert np.array_equal(a.weights(r).view(np.int64), b.weights(r).view(np.int64))
+        assert np.array_equal(a.per_iter(P.WE_OUT_EVENTS, r), b.per_iter(P.WE_OUT_EVENTS, r))
+
+
 # ------------------------------------------------------------------ steady-state reweighting --
 @pytest.mark.parametrize("period", [1, 2, 5])
 def test_reweighting_parity_schlogl(period):
