@@ -501,6 +501,25 @@ def test_rw_solve_cycle_and_partial_occupancy():
     assert abs(held.sum() - (cb[0] + cb[2])) < 1e-15
 
 
+def test_rw_solve_matches_a_null_space_on_dense_chains():
+    """Random dense chains (every move possible): the solved bin weights are the null vector of
+    the rate matrix (singular value decomposition), to 1e-10 relative."""
+    rng = np.random.default_rng(11)
+    for n in (3, 7, 20, 45):
+        K = rng.uniform(0.0, 0.5 / n, (n, n))
+        W = rng.uniform(0.2, 2.0, n)
+        F = _transfers(K, W)
+        cb = rng.uniform(0.1, 1.0, n)
+        st, fac = O.rw_solve(F, cb)
+        assert st == 1
+        P_ = F / F.sum(axis=0)[None, :]                  # column-stochastic move matrix
+        G = P_ - np.eye(n)
+        _, _, vt = np.linalg.svd(G)
+        pi = np.abs(vt[-1])
+        new = fac * cb
+        np.testing.assert_allclose(new / new.sum(), pi / pi.sum(), rtol=1e-10)
+
+
 def test_rw_solve_takes_the_largest_strongly_connected_set():
     """One active bin leaves everything as is.  Of two closed pairs {0, 1} and {2, 3} (equal
     size) the one with the lower bin is reweighted (pi_0 / pi_1 = 0.2 / 0.1) and the other keeps
