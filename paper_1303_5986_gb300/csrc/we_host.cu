@@ -30,6 +30,7 @@ cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_pack_states(const EnsView &E, int r, int32_t *out, cudaStream_t st);
 cudaError_t launch_learned_bins(const PropagateParams &prm, cudaStream_t st);
+size_t learned_bins_smem(int n_in, int H);
 cudaError_t launch_rw_flux(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_rw_solve_apply(const PropagateParams &prm, cudaStream_t st);
 }  // namespace we
@@ -519,6 +520,9 @@ static we_status check_config(const we_network *n, const we_binmap *b, const we_
     if (b->species[d] >= n->S) return fail(WE_EINVAL, "bin dimension %d names species %d >= S", d, b->species[d]);
   if (b->learned && b->lb.n_in != n->S)
     return fail(WE_EINVAL, "learned bin map reads %d species, the network has %d", b->lb.n_in, n->S);
+  if (b->learned && learned_bins_smem(b->lb.n_in, b->lb.H) > 227 * 1024)
+    return fail(WE_ENOTSUPPORTED, "learned bin map: %d inputs x %d hidden do not fit the binning kernel's shared memory",
+                b->lb.n_in, b->lb.H);
   long long cap = c->capacity > 0 ? c->capacity : std::max<long long>((long long)c->m_targ * b->n_bins, c->n_init);
   if (cap < c->n_init) return fail(WE_EINVAL, "capacity %lld < n_init %d", cap, c->n_init);
   if (cap * c->n_runs > (1ll << 30)) return fail(WE_EINVAL, "runs x capacity too large");
