@@ -326,7 +326,7 @@ def test_sampled_timed_step_matches_step():
 @pytest.mark.parametrize("period", [1, 2, 5])
 def test_reweighting_parity_schlogl(period):
     """Steady-state reweighting (Sec. II.B.2, Eq. "ss") on the Schloegl flux run, three runs in
-    one batch: the accumulated transfers, the Gaussian elimination and the rescaling give the
+    one batch: the accumulated transfers, the GTH elimination and the rescaling give the
     oracle's weights bit for bit, and the same iterations are reweighted or skipped."""
     cfg = W.schlogl_flux_we(reweight_period=period, n_iters=24, n_runs=3, m_targ=6)
     ens = _parity(cfg, 24)
