@@ -1,5 +1,5 @@
-// we_warp.cu -- one warp per walker, for networks too large for a register tree (up to about
-// 18,000 reactions): Gillespie's direct method (Sec. II.A) for one interval tau, with recycling
+// we_warp.cu -- one warp per walker, for networks too large for a register tree (up to 16,384
+// reactions): Gillespie's direct method (Sec. II.A) for one interval tau, with recycling
 // (Sec. II.B.2), bin assignment and observables, as in the thread kernels.
 //
 // The walker's counts and its canonical propensity tree (Pw = max(P, 4) leaves, node k = node
