@@ -204,8 +204,10 @@ typedef struct {
                                       per 32 walkers (default); 32, 64, 96 = every thread
                                       makes its own draws */
   int32_t reweight_period;         /* 0: off.  > 0: steady-state reweighting (Sec. II.B.2,
-                                      Eq. "ss") after the split/merge of every
-                                      reweight_period-th iteration: the rates k_ij = F_ij / W_j
+                                      Eq. "ss") after the split/merge of iterations period-1,
+                                      2 period-1, ... (iteration indices counted from 0 for
+                                      the run, so a resumed run keeps the schedule): the rates
+                                      k_ij = F_ij / W_j
                                       from the weight F_ij that moved from bin j to bin i over
                                       all intervals so far (W_j = sum_i F_ij), the balance
                                       equations solved on the largest strongly connected set
@@ -216,6 +218,9 @@ typedef struct {
                                       total kept); the outcome per iteration is WE_OUT_RW.
                                       Needs resample = 1 and at most 1024 bins; adds
                                       16 * n_bins^2 bytes per run to the workspace */
+  const int32_t *n_init_per_run;   /* n_runs initial walker counts, each 1..n_init (NULL: n_init
+                                      for every run); run r uses the first n_init_per_run[r]
+                                      walkers of its n_init rows of init_states/init_weights */
 } we_run_config;
 
 /* ------------------------------------------------------------------------------------------
@@ -262,6 +267,27 @@ we_status we_ensemble_step_timed(we_ensemble *ens, int32_t n_iters, void *stream
  * timed run close to we_ensemble_step's. */
 we_status we_ensemble_step_timed_every(we_ensemble *ens, int32_t n_iters, int32_t every, void *stream,
                                        float *propagate_ms);
+
+/* Checkpoint of an ensemble between iterations: every run's live walkers (counts and weights,
+ * in slot order), the next iteration index, and, with steady-state reweighting on, the
+ * accumulated transfers and the bin layout of the last split/merge.  Synchronises the stream.
+ * dst (host) may be NULL to query the size (*needed).  The walkers and the counter-based
+ * random numbers are the whole state of the dynamics, so a resumed ensemble continues exactly
+ * as the original would have.  Errors: WE_EINVAL (between propagate and resample, or dst too
+ * small), WE_ECUDA. */
+we_status we_ensemble_checkpoint(we_ensemble *ens, void *dst, size_t dst_bytes, size_t *needed,
+                                 void *stream);
+/* A new ensemble continuing from a checkpoint: cfg gives everything but the walkers, their
+ * per-run counts and the first iteration, which come from the checkpoint (cfg's n_init,
+ * init_states, init_weights, n_init_per_run and first_iter are ignored; give recycle_state
+ * explicitly for feedback runs -- its default, the first initial walker, would be the
+ * checkpoint's).  The checkpoint must have cfg's run count and the network's species count;
+ * reweighting data is restored when cfg reweights over the same bins (and is otherwise
+ * refused).  Device memory is allocated by the library.  Errors: WE_EINVAL (malformed or
+ * mismatched checkpoint), and those of we_ensemble_create. */
+we_status we_ensemble_resume(const we_network *net, const we_binmap *bins, const we_run_config *cfg,
+                             const void *checkpoint, size_t checkpoint_bytes, void *stream,
+                             we_ensemble **out);
 /* Synchronise the stream and return the first non-OK device status of any run (or WE_OK). */
 we_status we_ensemble_sync(we_ensemble *ens, void *stream);
 

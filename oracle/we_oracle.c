@@ -678,7 +678,7 @@ int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
     out->total_weight[li] = tot;
     out->n_walkers[li] = nw;
     if (out->reweighted) out->reweighted[li] = 0;
-    if (rw && (li + 1) % cfg->reweight_period == 0) {
+    if (rw && (iter + 1) % cfg->reweight_period == 0) {      /* after iterations period-1, 2 period-1, ... */
       /* current bin weights, each summed over its walkers in ascending slot order */
       for (int32_t b = 0; b < n_bins; ++b) cb[b] = 0.0;
       for (int32_t s = 0; s < nw; ++s) cb[sbin[s]] = cb[sbin[s]] + w[s];

@@ -78,7 +78,7 @@ typedef struct {
   int32_t hist_species, hist_len;    /* weighted histogram of one species, last entry = overflow */
   int32_t resample;                  /* 0: plain propagation (no split/merge) */
   int32_t reweight_period;           /* >0: steady-state reweighting (Eq. "ss") after the
-                                        resampling of every reweight_period-th iteration */
+                                        resampling of iterations period-1, 2 period-1, ... */
 } orc_we_config;
 
 typedef struct {

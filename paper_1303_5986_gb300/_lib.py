@@ -60,7 +60,7 @@ class we_run_config(C.Structure):
         ("tgt_species", C.c_int32 * 4), ("tgt_op", C.c_int32 * 4), ("tgt_threshold", _I32P),
         ("recycle_state", _I32P), ("max_steps", C.c_int64), ("hist_species", C.c_int32),
         ("hist_len", C.c_int32), ("resample", C.c_int32), ("mapping", C.c_int32),
-        ("block_threads", C.c_int32), ("reweight_period", C.c_int32),
+        ("block_threads", C.c_int32), ("reweight_period", C.c_int32), ("n_init_per_run", _I32P),
     ]
 
 
@@ -87,6 +87,9 @@ SIGNATURES = [
     ("we_ensemble_step", C.c_int32, [_VP, C.c_int32, _VP]),
     ("we_ensemble_step_timed", C.c_int32, [_VP, C.c_int32, _VP, C.POINTER(C.c_float)]),
     ("we_ensemble_step_timed_every", C.c_int32, [_VP, C.c_int32, C.c_int32, _VP, C.POINTER(C.c_float)]),
+    ("we_ensemble_checkpoint", C.c_int32, [_VP, _VP, C.c_size_t, C.POINTER(C.c_size_t), _VP]),
+    ("we_ensemble_resume", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, C.c_size_t, _VP,
+                                       C.POINTER(_VP)]),
     ("we_ensemble_sync", C.c_int32, [_VP, _VP]),
     ("we_ensemble_get", C.c_int32, [_VP, C.c_int32, C.c_int32, _VP, C.c_size_t,
                                     C.POINTER(C.c_size_t), _VP]),

@@ -227,6 +227,15 @@ class Ensemble:
     def sync(self, stream=None):
         check(lib().we_ensemble_sync(self.h, _stream_handle(stream)))
 
+    def checkpoint(self, stream=None) -> np.ndarray:
+        """The ensemble's state between iterations as bytes (see we_ensemble_checkpoint)."""
+        n = C.c_size_t()
+        check(lib().we_ensemble_checkpoint(self.h, None, 0, C.byref(n), _stream_handle(stream)))
+        buf = np.zeros(n.value, dtype=np.uint8)
+        check(lib().we_ensemble_checkpoint(self.h, C.c_void_p(buf.ctypes.data), buf.nbytes, C.byref(n),
+                                           _stream_handle(stream)))
+        return buf
+
     def nbytes(self, what: int, run: int = -1, stream=None) -> int:
         n = C.c_size_t()
         check(lib().we_ensemble_get(self.h, what, run, None, 0, C.byref(n), _stream_handle(stream)))
@@ -295,6 +304,17 @@ def we_ensemble_create(net: Network, bins: BinMap, cfg, keep=None, workspace="to
                                    C.byref(h)))
     hl = cfg.hist_len if cfg.hist_len > 0 else 1
     return Ensemble(h, ws, keep, cfg.n_runs, net.n_species, hl)
+
+
+def we_ensemble_resume(net: Network, bins: BinMap, cfg, checkpoint, keep=None, stream=None) -> Ensemble:
+    """A new ensemble continuing from Ensemble.checkpoint() bytes; cfg supplies everything else
+    (its initial walkers and first iteration are replaced by the checkpoint's)."""
+    blob = np.ascontiguousarray(checkpoint, dtype=np.uint8)
+    h = C.c_void_p()
+    check(lib().we_ensemble_resume(net.h, bins.h, C.byref(cfg), C.c_void_p(blob.ctypes.data), blob.nbytes,
+                                   _stream_handle(stream), C.byref(h)))
+    hl = cfg.hist_len if cfg.hist_len > 0 else 1
+    return Ensemble(h, None, keep, cfg.n_runs, net.n_species, hl)
 
 
 def we_run(net: Network, bins: BinMap, cfg, keep=None, stream=None) -> Ensemble:

@@ -536,6 +536,10 @@ static we_status check_config(const we_network *n, const we_binmap *b, const we_
   if (c->hist_len < 0 || (c->hist_len > 0 && (c->hist_species < 0 || c->hist_species >= n->S)))
     return fail(WE_EINVAL, "bad histogram species/length");
   if (c->reweight_period < 0) return fail(WE_EINVAL, "reweight_period must be >= 0");
+  if (c->n_init_per_run)
+    for (int r = 0; r < c->n_runs; ++r)
+      if (c->n_init_per_run[r] < 1 || c->n_init_per_run[r] > c->n_init)
+        return fail(WE_EINVAL, "run %d: n_init_per_run must be 1..n_init", r);
   if (c->reweight_period > 0 && (!c->resample || b->n_bins > 1024))
     return fail(WE_EINVAL, "steady-state reweighting needs resample = 1 and at most 1024 bins");
   if (c->param_set)
@@ -630,13 +634,16 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   const int par0 = c->first_iter & 1;
   std::vector<int32_t> xh((size_t)S * RC, 0), ph(RC, -1), cnt(R, c->n_init), roff(R + 1);
   std::vector<double> wh(RC, 0.0);
+  if (c->n_init_per_run)
+    for (int r = 0; r < R; ++r) cnt[r] = c->n_init_per_run[r];
   for (int r = 0; r < R; ++r)
-    for (int w = 0; w < c->n_init; ++w) {
+    for (int w = 0; w < cnt[r]; ++w) {
       const size_t g = (size_t)r * cap + w;
       for (int sp = 0; sp < S; ++sp) xh[(size_t)sp * RC + g] = c->init_states[((size_t)r * c->n_init + w) * S + sp];
       wh[g] = c->init_weights[(size_t)r * c->n_init + w];
     }
-  for (int r = 0; r <= R; ++r) roff[r] = r * c->n_init;
+  roff[0] = 0;
+  for (int r = 0; r < R; ++r) roff[r + 1] = roff[r] + cnt[r];
   int32_t it0 = c->first_iter;
   auto up = [&](size_t offs, const void *src, size_t bytes) -> cudaError_t {
     if (!bytes) return cudaSuccess;
@@ -1007,6 +1014,118 @@ extern "C" we_status we_ensemble_sync(we_ensemble *E, void *stream) {
   WE_CUDA_TRY(cudaMemcpy(st.data(), E->prm.ens.status, 4 * st.size(), cudaMemcpyDeviceToHost));
   for (int r = 0; r < E->cfg.n_runs; ++r)
     if (st[r]) return fail(st[r], "run %d reported %s on the device", r, we_status_string(st[r]));
+  return WE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// checkpoint / resume
+// ------------------------------------------------------------------------------------------
+// Byte layout: int32 header[8] = {magic, version, runs, species, next iteration, bins of the
+// reweighting data (0: none), m_targ, 0}; int32 counts[runs]; per run: int32 states[count x S]
+// (walker-major) then double weights[count]; with reweighting data: int32 n_tasks[runs],
+// int4 tasks[runs x bins], double transfers[runs x bins x bins].
+constexpr int32_t kCkptMagic = 0x31434557;   // "WEC1"
+constexpr int32_t kCkptVersion = 1;
+
+extern "C" we_status we_ensemble_checkpoint(we_ensemble *E, void *dst, size_t dst_bytes, size_t *needed,
+                                            void *stream) {
+  if (!E) return fail(WE_EINVAL, "ensemble is NULL");
+  if (E->phase_propagated) return fail(WE_EINVAL, "checkpoint called between propagate and resample");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WE_CUDA_TRY(cudaStreamSynchronize(s));
+  const int R = E->cfg.n_runs, S = E->S;
+  const EnsView &V = E->prm.ens;
+  const RwView &rw = E->prm.rw;
+  std::vector<int32_t> cnt(R);
+  int32_t iter = 0;
+  WE_CUDA_TRY(cudaMemcpy(cnt.data(), V.count, 4 * (size_t)R, cudaMemcpyDeviceToHost));
+  WE_CUDA_TRY(cudaMemcpy(&iter, V.iter, 4, cudaMemcpyDeviceToHost));
+  const int nb = rw.period > 0 ? rw.nb : 0;
+  size_t bytes = 32 + 4 * (size_t)R;
+  for (int r = 0; r < R; ++r) bytes += (size_t)cnt[r] * (4 * (size_t)S + 8);
+  if (nb) bytes += 4 * (size_t)R + 16 * (size_t)R * nb + 8 * (size_t)R * nb * nb;
+  if (needed) *needed = bytes;
+  if (!dst) return WE_OK;
+  if (dst_bytes < bytes) return fail(WE_EINVAL, "dst too small (%zu < %zu)", dst_bytes, bytes);
+  char *o = static_cast<char *>(dst);
+  const int32_t hdr[8] = {kCkptMagic, kCkptVersion, R, S, iter, nb, E->cfg.m_targ, 0};
+  std::memcpy(o, hdr, 32); o += 32;
+  std::memcpy(o, cnt.data(), 4 * (size_t)R); o += 4 * (size_t)R;
+  for (int r = 0; r < R; ++r) {
+    const size_t ns = (size_t)cnt[r] * S * 4, nw = (size_t)cnt[r] * 8;
+    size_t got = 0;
+    we_status st = we_ensemble_get(E, WE_OUT_STATES, r, o, ns, &got, stream);
+    if (st) return st;
+    o += ns;
+    st = we_ensemble_get(E, WE_OUT_WEIGHTS, r, o, nw, &got, stream);
+    if (st) return st;
+    o += nw;
+  }
+  if (nb) {
+    WE_CUDA_TRY(cudaMemcpy(o, V.n_tasks, 4 * (size_t)R, cudaMemcpyDeviceToHost)); o += 4 * (size_t)R;
+    WE_CUDA_TRY(cudaMemcpy(o, V.tasks, 16 * (size_t)R * nb, cudaMemcpyDeviceToHost)); o += 16 * (size_t)R * nb;
+    WE_CUDA_TRY(cudaMemcpy(o, rw.F, 8 * (size_t)R * nb * nb, cudaMemcpyDeviceToHost)); o += 8 * (size_t)R * nb * nb;
+  }
+  return WE_OK;
+}
+
+extern "C" we_status we_ensemble_resume(const we_network *n, const we_binmap *b, const we_run_config *c,
+                                        const void *ckpt, size_t bytes, void *stream, we_ensemble **out) {
+  if (!out) return fail(WE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!n || !b || !c || !ckpt) return fail(WE_EINVAL, "network, bins, config and checkpoint are required");
+  const char *p = static_cast<const char *>(ckpt);
+  if (bytes < 32) return fail(WE_EINVAL, "checkpoint too short");
+  int32_t hdr[8];
+  std::memcpy(hdr, p, 32);
+  const int R = hdr[2], S = hdr[3], nb = hdr[5];
+  if (hdr[0] != kCkptMagic || hdr[1] != kCkptVersion) return fail(WE_EINVAL, "not a checkpoint of this version");
+  if (R != c->n_runs || S != n->S) return fail(WE_EINVAL, "checkpoint has %d runs x %d species, expected %d x %d", R, S, c->n_runs, n->S);
+  if (hdr[4] < 0 || hdr[6] < 1) return fail(WE_EINVAL, "checkpoint header is inconsistent");
+  const bool rw_cfg = c->reweight_period > 0;
+  if (nb != 0 && (!rw_cfg || nb != b->n_bins)) return fail(WE_EINVAL, "checkpoint's reweighting data does not match the configuration");
+  size_t need = 32 + 4 * (size_t)R;
+  if (bytes < need) return fail(WE_EINVAL, "checkpoint too short");
+  std::vector<int32_t> cnt(R);
+  std::memcpy(cnt.data(), p + 32, 4 * (size_t)R);
+  int mx = 1;
+  for (int r = 0; r < R; ++r) {
+    if (cnt[r] < 1) return fail(WE_EINVAL, "checkpoint run %d has no walkers", r);
+    mx = std::max(mx, cnt[r]);
+    need += (size_t)cnt[r] * (4 * (size_t)S + 8);
+  }
+  if (nb) need += 4 * (size_t)R + 16 * (size_t)R * nb + 8 * (size_t)R * nb * nb;
+  if (bytes < need) return fail(WE_EINVAL, "checkpoint too short (%zu < %zu)", bytes, need);
+  std::vector<int32_t> xs((size_t)R * mx * S, 0);
+  std::vector<double> ws((size_t)R * mx, 0.0);
+  const char *q = p + 32 + 4 * (size_t)R;
+  for (int r = 0; r < R; ++r) {
+    std::memcpy(xs.data() + (size_t)r * mx * S, q, (size_t)cnt[r] * S * 4); q += (size_t)cnt[r] * S * 4;
+    std::memcpy(ws.data() + (size_t)r * mx, q, (size_t)cnt[r] * 8); q += (size_t)cnt[r] * 8;
+  }
+  we_run_config c2 = *c;
+  c2.n_init = mx;
+  c2.init_states = xs.data();
+  c2.init_weights = ws.data();
+  c2.n_init_per_run = cnt.data();
+  c2.first_iter = hdr[4];
+  we_ensemble *E = nullptr;
+  we_status st = we_ensemble_create(n, b, &c2, nullptr, 0, stream, &E);
+  if (st) return st;
+  E->cfg.n_init_per_run = nullptr;       // the host arrays above do not outlive this call
+  E->cfg.init_states = nullptr;
+  E->cfg.init_weights = nullptr;
+  if (nb) {
+    const EnsView &V = E->prm.ens;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(V.n_tasks, q, 4 * (size_t)R, cudaMemcpyHostToDevice, s); q += 4 * (size_t)R;
+    e = e ? e : cudaMemcpyAsync(V.tasks, q, 16 * (size_t)R * nb, cudaMemcpyHostToDevice, s); q += 16 * (size_t)R * nb;
+    e = e ? e : cudaMemcpyAsync(E->prm.rw.F, q, 8 * (size_t)R * nb * nb, cudaMemcpyHostToDevice, s);
+    e = e ? e : cudaStreamSynchronize(s);
+    if (e) { cudaGetLastError(); we_ensemble_destroy(E); return cuda_fail(e, "checkpoint upload"); }
+    E->prm.rw.start_known = 1;
+  }
+  *out = E;
   return WE_OK;
 }
 

@@ -163,6 +163,7 @@ struct TableView {
 struct RwView {
   int32_t period;              // 0: off; else reweight after every period-th iteration
   int32_t nb;                  // bins
+  int32_t start_known;         // 1: the first interval's start bins are known (resumed ensemble)
   double *F;                   // R x nb x nb
   double *M;                   // R x nb x nb
   double *W, *cb, *x, *fac;    // R x nb each

@@ -30,7 +30,7 @@ __global__ void k_rw_flux(EnsView E, RwView rw) {
   int32_t *mark = reinterpret_cast<int32_t *>(acc + nb);
   const int r = blockIdx.y, t = blockIdx.x, lane = threadIdx.x;
   const int iter = *E.iter;
-  if (iter <= E.first_iter) return;                 // the initial walkers' start bins are unknown
+  if (iter <= E.first_iter && !rw.start_known) return;   // the initial walkers' start bins are unknown
   if (t >= E.n_tasks[r]) return;
   for (int e = lane; e < nb; e += 32) mark[e] = 0;
   __syncwarp();
@@ -56,10 +56,13 @@ __global__ void k_rw_flux(EnsView E, RwView rw) {
   }
 }
 
-// The iteration that just finished (k_finalize has advanced E.iter) and whether it reweights.
+// The iteration that just finished (k_finalize has advanced E.iter), as an index into the
+// recorded iterations, and whether it reweights: after iterations period-1, 2 period-1, ... of
+// the run counted from 0, whatever iteration this ensemble started at.
 __device__ __forceinline__ bool rw_due(const EnsView &E, const RwView &rw, int &li) {
-  li = *E.iter - 1 - E.first_iter;
-  return li >= 0 && (li + 1) % rw.period == 0;
+  const int it = *E.iter - 1;
+  li = it - E.first_iter;
+  return li >= 0 && (it + 1) % rw.period == 0;
 }
 
 // The largest strongly connected component of the observed-transfer graph over the active bins

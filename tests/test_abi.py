@@ -43,7 +43,8 @@ def test_run_config_struct_layout_matches_header():
     assert c.tau.offset == 0 and c.seed.offset == 16 and c.init_states.offset == 48
     assert c.tgt_threshold.offset == 120 and c.max_steps.offset == 136
     assert c.block_threads.offset == 160 and c.reweight_period.offset == 164
-    assert ctypes.sizeof(c) == 168
+    assert c.n_init_per_run.offset == 168
+    assert ctypes.sizeof(c) == 176
 
 
 def test_status_strings_and_last_error():
@@ -132,3 +133,29 @@ def test_reweighting_config_validation_without_gpu():
     c.resample = 1
     with pytest.raises(P.WEError):
         P.we_ensemble_workspace_bytes(net, big, c)
+
+
+def test_resume_refuses_malformed_checkpoints_without_gpu():
+    """The checkpoint is validated on the host before any device work: wrong magic, wrong run or
+    species count, truncation, and reweighting data the configuration does not use."""
+    cfg = W.schlogl_mfpt_we(n_iters=4, n_runs=2)
+    net = P.network_from_spec(cfg.network)
+    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+    c, keep = P.run_config_from(cfg)
+    S = cfg.network.n_species
+
+    def blob(magic=0x31434557, runs=2, species=S, nb=0, counts=(3, 2), cut=0):
+        hdr = np.array([magic, 1, runs, species, 7, nb, cfg.m_targ, 0], dtype=np.int32).tobytes()
+        body = np.array(counts, dtype=np.int32).tobytes()
+        for k in counts:
+            body += np.zeros(k * species, dtype=np.int32).tobytes() + np.full(k, 0.1).tobytes()
+        b = hdr + body
+        return np.frombuffer(b[:len(b) - cut], dtype=np.uint8)
+
+    L = P._lib.lib()
+    for bad in (blob(magic=1), blob(runs=3, counts=(1, 1, 1)), blob(species=S + 1), blob(cut=4),
+                blob(nb=80), blob(counts=(0, 2))):
+        h = ctypes.c_void_p()
+        st = L.we_ensemble_resume(net.h, bm.h, ctypes.byref(c), ctypes.c_void_p(bad.ctypes.data), bad.nbytes,
+                                  None, ctypes.byref(h))
+        assert st == -1 and h.value is None, st

@@ -252,6 +252,39 @@ def test_checkpoint_resume_is_bit_identical():
     assert n > 0
 
 
+@pytest.mark.parametrize("case", ["schlogl", "toggle", "reweighted"])
+def test_checkpoint_and_resume_a_batch(case):
+    """we_ensemble_checkpoint after 12 iterations, we_ensemble_resume, 12 more: every run of the
+    batch (uneven walker counts) ends bit-identical to 24 uninterrupted iterations, including
+    the steady-state reweighting state (transfers and the last split/merge's bin layout)."""
+    if case == "schlogl":
+        mk = lambda n: W.schlogl_mfpt_we(n_iters=n, n_runs=3)
+    elif case == "toggle":
+        mk = lambda n: W.toggle_batch_we(n_runs=4, n_iters=n)
+    else:
+        mk = lambda n: W.schlogl_flux_we(reweight_period=3, n_iters=n, n_runs=2, m_targ=6)
+    cfg = mk(24)
+    full = gpu_run(cfg, 24)
+    full.sync()
+    first = gpu_run(cfg, 12, record_iters=24)
+    first.sync()
+    blob = first.checkpoint()
+    c2 = mk(12)
+    net = P.network_from_spec(c2.network)
+    bm = P.we_binmap_grid(c2.bins.species, c2.bins.edges)
+    conf, keep = P.run_config_from(c2, record_iters=12)
+    ens = P.we_ensemble_resume(net, bm, conf, blob, keep)
+    ens.step(12)
+    ens.sync()
+    assert int(ens.get(P.WE_OUT_ITER)[0]) == 24
+    for r in range(cfg.n_runs):
+        assert np.array_equal(ens.states(r), full.states(r)), r
+        assert np.array_equal(ens.weights(r).view(np.int64), full.weights(r).view(np.int64)), r
+        assert np.array_equal(ens.per_iter(P.WE_OUT_EVENTS, r), full.per_iter(P.WE_OUT_EVENTS, r)[12:]), r
+    if case == "reweighted":
+        assert np.array_equal(ens.per_iter(P.WE_OUT_RW), full.per_iter(P.WE_OUT_RW)[12:])
+
+
 def test_repeat_runs_are_identical():
     cfg = W.toggle_batch_we(n_runs=4, n_iters=20)
     a = gpu_run(cfg, 20)
