@@ -77,6 +77,11 @@ typedef int32_t we_status;
 const char *we_status_string(we_status s);
 /* Message of the last failing call on this thread ("" if none).  Valid until the next call. */
 const char *we_last_error(void);
+/* Fault injection for tests: the nth device allocation the library makes from now on fails as
+ * if the device were out of memory (its caller then returns WE_ENOMEM and frees what it had
+ * allocated); 0 disarms.  Allocations: a library-owned ensemble workspace (1), an MLP (4), an
+ * MLP training or gradient call (1).  Process-wide. */
+we_status we_debug_fail_allocation(int32_t nth);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int32_t we_version(void);
 

@@ -68,6 +68,7 @@ class we_run_config(C.Structure):
 SIGNATURES = [
     ("we_status_string", C.c_char_p, [C.c_int32]),
     ("we_last_error", C.c_char_p, []),
+    ("we_debug_fail_allocation", C.c_int32, [C.c_int32]),
     ("we_version", C.c_int32, []),
     ("we_network_create", C.c_int32, [C.c_int32, C.c_int32, _I32P, _I32P, _I32P, _I32P, _I32P, _I32P,
                                       C.c_int32, _F64P, _I32P, _I32P, C.c_int32, _F64P, _I32P, _I32P,

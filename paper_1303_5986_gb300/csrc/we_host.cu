@@ -2,6 +2,7 @@
 // compilation (constant folding, net changes, dependency graph), device workspace layout,
 // kernel launches and CUDA-graph replay of whole WE iterations.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -77,6 +78,29 @@ extern "C" const char *we_status_string(we_status s) {
 }
 
 extern "C" const char *we_last_error(void) { return g_last_error.c_str(); }
+
+// Fault injection for tests: the n-th device allocation from now on fails (0: none).
+static std::atomic<int> g_fail_alloc{0};
+
+extern "C" we_status we_debug_fail_allocation(int32_t nth) {
+  if (nth < 0) return fail(WE_EINVAL, "nth must be >= 0");
+  g_fail_alloc.store(nth);
+  return WE_OK;
+}
+
+namespace we {
+cudaError_t device_alloc(void **p, size_t bytes) {
+  *p = nullptr;
+  int n = g_fail_alloc.load();
+  while (n > 0) {
+    if (g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+      if (n == 1) return cudaErrorMemoryAllocation;        // the armed allocation
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+}  // namespace we
 extern "C" int32_t we_version(void) { return 100; }
 
 // ------------------------------------------------------------------------------------------
@@ -598,7 +622,7 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
     if (workspace_bytes < o.total) return fail(WE_ENOMEM, "workspace of %zu bytes < %zu needed", workspace_bytes, o.total);
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(WE_EINVAL, "workspace must be 256-byte aligned");
   } else {
-    cudaError_t e = cudaMalloc(&ws, o.total);
+    cudaError_t e = device_alloc(&ws, o.total);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(WE_ENOMEM, "cudaMalloc(%zu): %s", o.total, cudaGetErrorString(e)); }
     owns = true;
   }

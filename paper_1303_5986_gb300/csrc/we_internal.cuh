@@ -172,6 +172,10 @@ struct RwView {
   int32_t *obs;                // record_iters x R: 1 reweighted, -1 skipped, 0 not scheduled
 };
 
+// Every device allocation of the library goes through here, so that a test can make the n-th
+// one fail as if the device were out of memory (we_debug_fail_allocation).
+cudaError_t device_alloc(void **p, size_t bytes);
+
 struct PropagateParams {
   NetView net;
   BinView bins;

@@ -457,8 +457,8 @@ extern "C" we_status we_mlp_create(int32_t n_in, int32_t hidden, const float *pa
   M->sh.H = hidden;
   const size_t np = (size_t)M->sh.n_params();
   const size_t nw = (size_t)hidden * n_in + (size_t)hidden * hidden + hidden;
-  if (cudaMalloc(&M->p, 4 * np) || cudaMalloc(&M->m, 4 * np) || cudaMalloc(&M->v, 4 * np) ||
-      cudaMalloc(&M->wbf, 2 * nw)) {
+  if (device_alloc((void **)&M->p, 4 * np) || device_alloc((void **)&M->m, 4 * np) ||
+      device_alloc((void **)&M->v, 4 * np) || device_alloc((void **)&M->wbf, 2 * nw)) {
     cudaGetLastError();
     cudaFree(M->p); cudaFree(M->m); cudaFree(M->v); cudaFree(M->wbf);
     delete M;
@@ -538,7 +538,7 @@ extern "C" we_status we_mlp_gradient(const we_mlp *M, const int32_t *states, con
   const TrainPlan tp = plan_training(M->sh, n);
   const int np = M->sh.n_params();
   float *part = nullptr;
-  if (cudaMalloc(&part, 4 * ((size_t)tp.grid * (np + 1) + 1))) { cudaGetLastError(); return WE_ENOMEM; }
+  if (device_alloc((void **)&part, 4 * ((size_t)tp.grid * (np + 1) + 1))) { cudaGetLastError(); return WE_ENOMEM; }
   float *dloss = part + (size_t)tp.grid * (np + 1);
   cudaError_t e = launch_train_tiles(tp, M->sh, M->p, states, labels, n, 0, n, part, st);
   if (!e) {
@@ -585,7 +585,7 @@ extern "C" we_status we_mlp_train(we_mlp *M, const int32_t *states, const float 
   const TrainPlan tp = plan_training(M->sh, batch);
   const int np = M->sh.n_params();
   float *part = nullptr;
-  if (cudaMalloc(&part, 4 * ((size_t)tp.grid * (np + 1) + (size_t)(steps > 0 ? steps : 1)))) {
+  if (device_alloc((void **)&part, 4 * ((size_t)tp.grid * (np + 1) + (size_t)(steps > 0 ? steps : 1)))) {
     cudaGetLastError();
     return WE_ENOMEM;
   }

@@ -285,6 +285,38 @@ def test_checkpoint_and_resume_a_batch(case):
         assert np.array_equal(ens.per_iter(P.WE_OUT_RW), full.per_iter(P.WE_OUT_RW)[12:])
 
 
+def test_failed_device_allocations_are_reported_and_undone():
+    """Host-side fault injection: the k-th device allocation of an MLP (4 of them) or of a
+    library-owned ensemble workspace fails; the call returns WE_ENOMEM, frees what it had
+    allocated, and the same call succeeds once disarmed."""
+    import torch
+    L = P._lib.lib()
+    p = W.mlp_init_params(2, 64, seed=3)
+    cfg = W.schlogl_mfpt_we(n_iters=2, n_runs=1)
+    net = P.network_from_spec(cfg.network)
+    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    try:
+        for k in (1, 2, 3, 4):
+            assert L.we_debug_fail_allocation(k) == 0
+            with pytest.raises(P.WEError) as ei:
+                P.we_mlp_create(2, 64, p)
+            assert ei.value.status == -2, ei.value
+        assert L.we_debug_fail_allocation(1) == 0
+        with pytest.raises(P.WEError) as ei:
+            P.we_run(net, bm, P.run_config_from(cfg)[0])
+        assert ei.value.status == -2
+    finally:
+        L.we_debug_fail_allocation(0)
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20)
+    mlp = P.we_mlp_create(2, 64, p)
+    assert mlp.params().shape[0] == len(p)
+    ens = P.we_run(net, bm, P.run_config_from(cfg)[0])
+    ens.sync()
+
+
 def test_repeat_runs_are_identical():
     cfg = W.toggle_batch_we(n_runs=4, n_iters=20)
     a = gpu_run(cfg, 20)
