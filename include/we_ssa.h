@@ -376,9 +376,15 @@ we_status we_resample_static(int32_t n, const int32_t *bins, const double *weigh
 
 /* Autotuner: time the SSA kernel mappings and block sizes on a short probe of this
  * configuration and return the fastest (mapping, block_threads).  Results are cached per
- * (S, M, walkers, device) for the life of the process. */
+ * (device name, S, M, walker slots, initial walkers) for the life of the process; the cache
+ * can be saved to and merged from a text file (one entry per line: device S M walker_slots
+ * n_init mapping block_threads) and cleared.  Errors of the file calls: WE_EINVAL (unreadable
+ * or unwritable file, malformed line; entries before a malformed line are kept). */
 we_status we_autotune(const we_network *net, const we_binmap *bins, const we_run_config *cfg,
                       void *stream, int32_t *mapping, int32_t *block_threads);
+we_status we_autotune_cache_save(const char *path);
+we_status we_autotune_cache_load(const char *path);
+void we_autotune_cache_clear(void);
 
 #ifdef __cplusplus
 }

@@ -96,6 +96,9 @@ SIGNATURES = [
                                     C.POINTER(C.c_size_t), _VP]),
     ("we_run", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, C.POINTER(_VP)]),
     ("we_autotune", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, _I32P, _I32P]),
+    ("we_autotune_cache_save", C.c_int32, [C.c_char_p]),
+    ("we_autotune_cache_load", C.c_int32, [C.c_char_p]),
+    ("we_autotune_cache_clear", None, []),
     ("we_mlp_create", C.c_int32, [C.c_int32, C.c_int32, _F32P, C.POINTER(_VP)]),
     ("we_mlp_destroy", None, [_VP]),
     ("we_mlp_n_params", C.c_int32, [_VP]),

@@ -336,6 +336,20 @@ def we_autotune(net: Network, bins: BinMap, cfg, stream=None):
     return m.value, b.value
 
 
+def autotune_cache_save(path: str):
+    """Write the autotuner's cached choices to a text file."""
+    check(lib().we_autotune_cache_save(str(path).encode()))
+
+
+def autotune_cache_load(path: str):
+    """Merge cached choices from a file written by autotune_cache_save."""
+    check(lib().we_autotune_cache_load(str(path).encode()))
+
+
+def autotune_cache_clear():
+    lib().we_autotune_cache_clear()
+
+
 def we_resample_static(bins, weights, n_bins: int, m_targ: int, iteration: int, seed: int,
                        run_id: int, out_weights, out_parent, out_count, stream=None):
     """Split/merge of one run held in device tensors, with no allocation by the library

@@ -1283,7 +1283,62 @@ extern "C" we_status we_run(const we_network *n, const we_binmap *b, const we_ru
 // autotuner: time every supported (mapping, block) on a short probe, cache per shape
 // ------------------------------------------------------------------------------------------
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+// (device name, S, M, walker slots, initial walkers) -> (mapping, block_threads)
+using TuneKey = std::tuple<std::string, int, int, int, int>;
+static std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+static std::string device_name() {
+  int dev = 0;
+  cudaDeviceProp pr;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string nm(pr.name);
+  for (auto &ch : nm) if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+  return nm;
+}
+
+// One line per entry: device S M walker_slots n_init mapping block_threads
+extern "C" we_status we_autotune_cache_save(const char *path) {
+  if (!path) return fail(WE_EINVAL, "path is NULL");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE *f = std::fopen(path, "w");
+  if (!f) return fail(WE_EINVAL, "cannot write %s", path);
+  for (const auto &kv : g_tune_cache)
+    std::fprintf(f, "%s %d %d %d %d %d %d\n", std::get<0>(kv.first).c_str(), std::get<1>(kv.first),
+                 std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), kv.second.first, kv.second.second);
+  const bool ok = std::fclose(f) == 0;
+  return ok ? WE_OK : fail(WE_EINVAL, "cannot write %s", path);
+}
+
+extern "C" we_status we_autotune_cache_load(const char *path) {
+  if (!path) return fail(WE_EINVAL, "path is NULL");
+  FILE *f = std::fopen(path, "r");
+  if (!f) return fail(WE_EINVAL, "cannot read %s", path);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  char name[256];
+  int S, M, W, n0, map, bt, line = 0;
+  we_status st = WE_OK;
+  for (;;) {
+    const int got = std::fscanf(f, "%255s %d %d %d %d %d %d", name, &S, &M, &W, &n0, &map, &bt);
+    if (got == EOF) break;
+    ++line;
+    if (got != 7 || S < 1 || M < 1 || W < 1 || n0 < 1 ||
+        (map != WE_MAP_THREAD && map != WE_MAP_WARP && map != WE_MAP_THREAD_TABLE) || bt < 32 || bt > 1024) {
+      st = fail(WE_EINVAL, "%s: line %d is not a tuning entry", path, line);
+      break;
+    }
+    g_tune_cache[TuneKey(name, S, M, W, n0)] = {map, bt};
+  }
+  std::fclose(f);
+  return st;
+}
+
+extern "C" void we_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
+}
 
 extern "C" we_status we_autotune(const we_network *n, const we_binmap *b, const we_run_config *c,
                                  void *stream, int32_t *mapping, int32_t *block_threads) {
@@ -1291,9 +1346,7 @@ extern "C" we_status we_autotune(const we_network *n, const we_binmap *b, const 
   int cap = 0;
   we_status st = check_config(n, b, c, &cap);
   if (st) return st;
-  int dev = 0;
-  WE_CUDA_TRY(cudaGetDevice(&dev));
-  auto key = std::make_tuple(n->S, n->M, c->n_runs * cap, dev, c->n_init);
+  const TuneKey key(device_name(), n->S, n->M, c->n_runs * cap, c->n_init);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);

@@ -159,3 +159,24 @@ def test_resume_refuses_malformed_checkpoints_without_gpu():
         st = L.we_ensemble_resume(net.h, bm.h, ctypes.byref(c), ctypes.c_void_p(bad.ctypes.data), bad.nbytes,
                                   None, ctypes.byref(h))
         assert st == -1 and h.value is None, st
+
+
+def test_autotune_cache_file_round_trip_without_gpu(tmp_path):
+    """The autotuner's cache as a text file: entries load, save back unchanged (sorted), and a
+    malformed line is refused."""
+    src = tmp_path / "tune.txt"
+    src.write_text("NVIDIA_GB300 1 4 16000 20 3 128\nNVIDIA_GB300 2 6 57600 8 1 64\n")
+    P.autotune_cache_clear()
+    P.autotune_cache_load(src)
+    out = tmp_path / "out.txt"
+    P.autotune_cache_save(out)
+    assert sorted(out.read_text().splitlines()) == sorted(src.read_text().splitlines())
+    bad = tmp_path / "bad.txt"
+    bad.write_text("NVIDIA_GB300 1 4 16000 20 9 128\n")
+    with pytest.raises(P.WEError):
+        P.autotune_cache_load(bad)
+    with pytest.raises(P.WEError):
+        P.autotune_cache_load(tmp_path / "missing.txt")
+    P.autotune_cache_clear()
+    P.autotune_cache_save(out)
+    assert out.read_text() == ""

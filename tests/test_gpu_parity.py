@@ -317,6 +317,38 @@ def test_failed_device_allocations_are_reported_and_undone():
     ens.sync()
 
 
+def test_autotuner_choice_and_cache(tmp_path):
+    """The autotuner picks a valid (mapping, block) for a one-species, a two-species Hill and
+    a large network; the trajectories do not depend on the pick; its cache survives a save,
+    clear and load (the second call returns the same pick from the cache)."""
+    cases = [W.schlogl_mfpt_we(n_iters=6, n_runs=2), W.toggle_batch_we(n_runs=2, n_iters=6),
+             _small_synthetic(n_walkers=24, n_iters=2)]
+    P.autotune_cache_clear()
+    picks = []
+    for cfg in cases:
+        net = P.network_from_spec(cfg.network)
+        bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+        c, keep = P.run_config_from(cfg)
+        mapping, block = P.we_autotune(net, bm, c)
+        assert mapping in (P.WE_MAP_THREAD, P.WE_MAP_WARP, P.WE_MAP_THREAD_TABLE) and block in (32, 64, 96, 128)
+        picks.append((mapping, block))
+        a = gpu_run(cfg, cfg.n_iters)
+        b = gpu_run(cfg, cfg.n_iters, mapping=mapping, block_threads=block)
+        for r in range(cfg.n_runs):
+            assert np.array_equal(a.states(r), b.states(r))
+            assert np.array_equal(a.weights(r).view(np.int64), b.weights(r).view(np.int64))
+    path = tmp_path / "tune.txt"
+    P.autotune_cache_save(path)
+    assert len(path.read_text().splitlines()) == len(cases)
+    P.autotune_cache_clear()
+    P.autotune_cache_load(path)
+    for cfg, pick in zip(cases, picks):
+        net = P.network_from_spec(cfg.network)
+        bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+        c, keep = P.run_config_from(cfg)
+        assert P.we_autotune(net, bm, c) == pick
+
+
 def test_repeat_runs_are_identical():
     cfg = W.toggle_batch_we(n_runs=4, n_iters=20)
     a = gpu_run(cfg, 20)
