@@ -165,6 +165,42 @@ def toggle_mfpt(a_u: float, a_v: float, start, in_target, d=1.0, K=1.0, n=2, b0=
     return float(T[idx(*start)])
 
 
+def epigenetic_mfpt(start, in_target, a1=156.0, a2=30.0, n=3, m=1, K1=1.0, K2=1.0, k0=1.0,
+                    G1: int = 400, G2: int = 120) -> float:
+    """MFPT of the epigenetic switch of Sec. III.C from ``start`` into ``in_target(g1, g2)``:
+    0 -> g1 at a1/(1+(g2/K2)^n), 0 -> g2 at a2/(1+(g1/K1)^m), g1 -> 0 and g2 -> 0 at k0 per
+    molecule, written out again from the model's equations.  Solves sum_y Q(x,y) T(y) = -1 off
+    the target, T = 0 on it, on [0,G1] x [0,G2] (no production out of the box)."""
+    n1, n2 = G1 + 1, G2 + 1
+    idx = lambda u, v: u * n2 + v
+    rows, cols, vals = [], [], []
+    rhs = np.zeros(n1 * n2)
+    for u in range(n1):
+        for v in range(n2):
+            i = idx(u, v)
+            if in_target(u, v):
+                rows.append(i); cols.append(i); vals.append(1.0)
+                continue
+            rhs[i] = -1.0
+            out = 0.0
+            moves = []
+            if u < G1:
+                moves.append((idx(u + 1, v), a1 / (1.0 + (v / K2) ** n)))
+            if v < G2:
+                moves.append((idx(u, v + 1), a2 / (1.0 + (u / K1) ** m)))
+            if u > 0:
+                moves.append((idx(u - 1, v), k0 * u))
+            if v > 0:
+                moves.append((idx(u, v - 1), k0 * v))
+            for j, r in moves:
+                rows.append(i); cols.append(j); vals.append(r)
+                out += r
+            rows.append(i); cols.append(i); vals.append(-out)
+    A = sparse.csr_matrix((vals, (rows, cols)), shape=(n1 * n2, n1 * n2))
+    T = spsolve(A.tocsc(), rhs)
+    return float(T[idx(*start)])
+
+
 # ----------------------------------------------------------------------------------------------
 # enzymatic futile cycle (Eq. "futile", Sec. III.A): truncation-free CME by uniformization
 # ----------------------------------------------------------------------------------------------

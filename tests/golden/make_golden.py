@@ -22,10 +22,12 @@ def main():
         "schlogl_p_ge_700_t5_from_82": float(E.bd_transient(b, d, 82, 5.0, 2000)[700:].sum()),
         "birth_death_mfpt_100_to_250": E.bd_mfpt(100, 250, bb, dd),
         "futile_p_s1_gt_90_t100": float(E.futile_s1_law(100.0)[91:].sum()),
+        "epigenetic_mfpt_0_30_to_g1_ge_50_s": E.epigenetic_mfpt((0, 30), lambda u, v: u >= 50),
         "notes": {
             "schlogl_mfpt_82_to_563_s": "paper Sec. III.B.3 quotes approximately 5e4 s",
             "schlogl_p_ge_700_t5_from_82": "paper Sec. III.B.3 prints the CME value 1.148e-9",
             "futile_p_s1_gt_90_t100": "paper Sec. III.A prints the CME value 2.72e-18 (from S1 = S2 = 50)",
+            "epigenetic_mfpt_0_30_to_g1_ge_50_s": "paper Sec. III.C prints 1.3e6 s (WE and brute-force MLE); source and target read as the g2-high state and the last g1 bin",
         },
     }
     with open(os.path.join(HERE, "exact_values.json"), "w") as f:

@@ -443,6 +443,16 @@ def test_reweighting_parity_other_mappings(mapping):
     assert (ens.per_iter(P.WE_OUT_RW)[[5, 8, 11, 14]] == 1).all()
 
 
+def test_epigenetic_switch_parity():
+    """The epigenetic switch with the paper's non-uniform 2-D bins (15 x 31), Hill exponents 3
+    and 1, recycling into the last g1 bin and reweighting every 5 iterations: bit-exact."""
+    cfg = W.epigenetic_mfpt_we(n_iters=20, n_runs=2, reweight_period=5)
+    ens = _parity(cfg, 20)
+    rw = ens.per_iter(P.WE_OUT_RW)
+    for r in range(2):
+        assert np.array_equal(rw[:, r], oracle_run(cfg, r, n_iters=20)["reweighted"])
+
+
 def test_reweighting_parity_toggle_2d():
     """Reweighting over a 30 x 30 grid (900 bins) with Hill kinetics and one parameter set per
     run."""

@@ -114,6 +114,25 @@ def test_reweighting_unbiased_with_state_resolved_bins():
     assert abs(m.mean() - 1.0) < 3 * se + 0.05, (m.mean(), se)
 
 
+def test_epigenetic_switch_mfpt_matches_paper():
+    """The epigenetic switch MFPT runs of Sec. III.C (15 x 31 non-uniform 2-D bins, 16 walkers
+    per bin, tau = 0.1, 500 iterations, reweighting every 100, from (g1, g2) = (0, 30) with
+    recycling at g1 >= 50), 32 replicas: MFPT = 1/flux over iterations 100-499 against the
+    exact 1.32e6 s (the paper prints 1.3e6 s) within 3 standard errors."""
+    exact = GOLDEN["epigenetic_mfpt_0_30_to_g1_ge_50_s"]
+    assert round(exact, -5) == 1.3e6
+    cfg = W.epigenetic_mfpt_we(n_runs=32)
+    ens = gpu_run(cfg, 500)
+    ens.sync()
+    assert np.all(ens.status() == 0)
+    assert (ens.per_iter(P.WE_OUT_RW)[99::100] == 1).all()
+    flux = ens.per_iter(P.WE_OUT_FLUX)[100:].mean(axis=0) / cfg.tau     # per replica
+    se = flux.std(ddof=1) / np.sqrt(len(flux))
+    assert abs(flux.mean() - 1.0 / exact) < 3 * se + 0.05 / exact, (1 / flux.mean(), exact, se * exact)
+    tot = ens.per_iter(P.WE_OUT_TOTAL_W)
+    assert np.all(np.abs(tot - 1.0) < 1e-12)
+
+
 def test_schlogl_mfpt_matches_closed_form():
     """Steady-state WE with recycling at X >= 550 from X0 = 85 (80 bins of width 10, 20 walkers
     per bin, tau = 0.05): MFPT = 1/flux (Eq. "mfpt") against the birth-death closed form

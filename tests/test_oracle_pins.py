@@ -298,6 +298,18 @@ def test_merge_ties_take_earliest():
     assert set(p2.tolist()) in ({0, 2, 3}, {1, 2, 3})
 
 
+# ---------------------------------------------------------------- epigenetic switch -----------
+def test_epigenetic_switch_mfpt_matches_paper():
+    """The exact MFPT of the epigenetic switch (Sec. III.C) from the g2-high state (0, 30) into
+    the last g1 bin (g1 >= 50), by a sparse solve of the truncated master equation, is the
+    1.3e6 s the paper prints (its WE and brute-force estimates); the truncation is converged,
+    and the opposite transition is four orders of magnitude faster."""
+    T = E.epigenetic_mfpt((0, 30), lambda u, v: u >= 50)
+    assert round(T, -5) == 1.3e6
+    assert abs(E.epigenetic_mfpt((0, 30), lambda u, v: u >= 50, G1=300, G2=90) - T) < 1e-6 * T
+    assert E.epigenetic_mfpt((156, 0), lambda u, v: v >= 30) < 1e4
+
+
 # ---------------------------------------------------------------- futile-cycle CME -------------
 def test_futile_cme_matches_paper_and_invariants():
     """The futile cycle's exact law (uniformized CME over its 400 states): P(S1 > 90, t = 100)

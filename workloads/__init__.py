@@ -8,12 +8,12 @@ fed identical bytes.
 from .networks import (NetworkSpec, birth_death, schlogl, toggle_switch, epigenetic_switch,
                        futile_cycle, synthetic_large)
 from .mlp_init import mlp_init_params, mlp_n_params, logit_edges
-from .configs import (WEConfig, GridBins, Target, birth_death_we, schlogl_mfpt_we, schlogl_flux_we, schlogl_pdf_we, futile_pdf_we,
+from .configs import (WEConfig, GridBins, Target, birth_death_we, schlogl_mfpt_we, schlogl_flux_we, schlogl_pdf_we, futile_pdf_we, epigenetic_mfpt_we,
                       toggle_batch_we, synthetic_large_we, uniform_edges)
 
 __all__ = [
     "NetworkSpec", "birth_death", "schlogl", "toggle_switch", "epigenetic_switch", "futile_cycle",
     "synthetic_large", "WEConfig", "GridBins", "Target", "birth_death_we", "schlogl_mfpt_we",
-    "schlogl_flux_we", "schlogl_pdf_we", "futile_pdf_we", "toggle_batch_we", "synthetic_large_we", "uniform_edges", "mlp_init_params",
+    "schlogl_flux_we", "schlogl_pdf_we", "futile_pdf_we", "epigenetic_mfpt_we", "toggle_batch_we", "synthetic_large_we", "uniform_edges", "mlp_init_params",
     "mlp_n_params", "logit_edges",
 ]

@@ -12,7 +12,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .networks import NetworkSpec, birth_death, futile_cycle, schlogl, synthetic_large, toggle_switch
+from .networks import (NetworkSpec, birth_death, epigenetic_switch, futile_cycle, schlogl, synthetic_large,
+                       toggle_switch)
 
 OP_GE = 0
 OP_LE = 1
@@ -176,6 +177,22 @@ def futile_pdf_we(n_iters: int = 100, n_runs: int = 1, seed: int = 0, m_targ: in
     return WEConfig(network=futile_cycle(), bins=bins, tau=1.0, m_targ=m_targ, n_iters=n_iters,
                     x0=[50, 50, 1, 1, 0, 0], n_runs=n_runs, seed=seed, hist_species=0,
                     hist_len=102, name="futile_pdf")
+
+
+def epigenetic_mfpt_we(n_iters: int = 500, n_runs: int = 6, seed: int = 0, m_targ: int = 16,
+                       reweight_period: int = 100) -> WEConfig:
+    """Epigenetic switch MFPT runs (Sec. III.C): 15 x 31 bins -- g1 unit-width on [0,10], width
+    10 on [10,50], one bin [50,inf); g2 unit-width on [0,30], one bin [30,inf) -- 16 walkers per
+    bin, tau = 0.1, 500 iterations, reweighting every 100; from the g2-high state (g1, g2) =
+    (0, 30), recycling on reaching g1 >= 50 (the last g1 bin)."""
+    net = epigenetic_switch()
+    e1 = np.concatenate([np.arange(0, 10, dtype=np.float64), np.arange(10, 51, 10, dtype=np.float64), [np.inf]])
+    e2 = uniform_edges(0, 1, 30, overflow=True)
+    bins = GridBins(species=[0, 1], edges=[e1, e2])
+    tgt = Target(species=[0], op=[OP_GE], threshold=np.full((n_runs, 1), 50, dtype=np.int32))
+    return WEConfig(network=net, bins=bins, tau=0.1, m_targ=m_targ, n_iters=n_iters, x0=[0, 30],
+                    n_runs=n_runs, seed=seed, target=tgt, hist_species=0, hist_len=101,
+                    reweight_period=reweight_period, name="epigenetic_mfpt")
 
 
 def toggle_params(n_runs: int = 64, seed: int = 0, lo: float = 20.0, hi: float = 60.0):
