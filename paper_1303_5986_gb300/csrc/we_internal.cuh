@@ -130,10 +130,10 @@ struct EnsView {
 };
 
 // Tables of the waiting-time logarithm (see neg_log_u01), each value as an unevaluated sum
-// of two floats (hi, lo): 1/c_j, -log(c_j / 2), i ln 2.
+// of two floats (hi, lo): cb[j] = (1/c_j, -log(c_j / 2)) side by side, so that a draw fetches
+// both with one 16-byte shared-memory load; n_ln2[i] = i ln 2.
 struct LogTables {
-  float2 inv_c[128];
-  float2 b[128];
+  float4 cb[128];
   float2 n_ln2[64];
 };
 

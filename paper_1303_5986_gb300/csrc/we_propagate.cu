@@ -29,8 +29,8 @@ __global__ void k_init_log_tables(LogTables *T) {
   const int i = threadIdx.x;
   if (i < 128) {
     const double c = 1.0 + (double)(2 * i + 1) / 256.0;
-    T->inv_c[i] = split_ff(__ddiv_rn(1.0, c));
-    T->b[i] = split_ff(-log(c * 0.5));
+    const float2 ic = split_ff(__ddiv_rn(1.0, c)), nb = split_ff(-log(c * 0.5));
+    T->cb[i] = make_float4(ic.x, ic.y, nb.x, nb.y);
   }
   if (i < 64) T->n_ln2[i] = split_ff(log(ldexp(1.0, i)));
 }

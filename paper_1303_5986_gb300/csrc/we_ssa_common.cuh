@@ -206,7 +206,8 @@ __device__ __forceinline__ float2 neg_log_u01(uint32_t hi, uint32_t lo, const Lo
   const float fh = __fsub_rn(__int_as_float(0x4B400000 + dh), 12582912.0f);   // 1.5 * 2^23
   const float fl = __fsub_rn(__int_as_float(0x4B000000 | dl), 8388608.0f);    // 2^23
   const float2 d = ff_fast_two_sum(__fmul_rn(fh, 0x1p-30f), __fmul_rn(fl, 0x1p-52f));
-  const float2 r = ff_mul(d, T.inv_c[j]);
+  const float4 cb = T.cb[j];                                  // (1/c_j, -log(c_j / 2))
+  const float2 r = ff_mul(d, make_float2(cb.x, cb.y));
   const float2 r2 = ff_mul(r, r);
   const float rh = r.x;
   // r^3/3 - r^4/4 + r^5/5 - r^6/6 in float
@@ -215,7 +216,7 @@ __device__ __forceinline__ float2 neg_log_u01(uint32_t hi, uint32_t lo, const Lo
                                          1.0f / 3.0f));
   float2 p = ff_add(r, make_float2(-0.5f * r2.x, -0.5f * r2.y));
   p = ff_add(p, make_float2(tail, 0.0f));                     // log1p(r)
-  float2 e = ff_add(T.n_ln2[52 - k], T.b[j]);
+  float2 e = ff_add(T.n_ln2[52 - k], make_float2(cb.z, cb.w));
   return ff_add(e, make_float2(-p.x, -p.y));
 }
 
