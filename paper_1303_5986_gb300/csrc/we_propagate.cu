@@ -902,14 +902,15 @@ static cudaError_t launch_k(K kern, const PropagateParams &prm, int grid, int bl
 // Rows of the table a block of the warp-specialised kernel may stage: as many as fit while
 // every block of the launch stays resident at once (up to the kernel's register limit of
 // blocks per SM), and no more than the table has.
-static int num_sms() {
-  int dev = 0, n = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+static int device_attr(cudaDeviceAttr a, int fallback) {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, a, dev) != cudaSuccess) {
     cudaGetLastError();
-    return 1;
+    return fallback;
   }
-  return n > 0 ? n : 1;
+  return v;
 }
+static int num_sms() { return std::max(1, device_attr(cudaDevAttrMultiProcessorCount, 1)); }
 
 template <typename K>
 static int pipe_table_rows(K kern, const PropagateParams &prm, int grid) {
@@ -919,7 +920,14 @@ static int pipe_table_rows(K kern, const PropagateParams &prm, int grid) {
   const int by_regs = std::max(1, 65536 / std::max(1, fa.numRegs * 128));
   const int sms = num_sms();
   const int per_sm = std::min(by_regs, std::max(1, (grid + sms - 1) / sms));
-  const size_t budget = (size_t)(227 * 1024) / per_sm - 1024;
+  // an SM's shared memory, shared by per_sm blocks, each of which also holds the reserved
+  // bytes per block and the kernel's static shared variables; a block's own limit on top
+  const size_t sm_bytes = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerMultiprocessor, 228 * 1024);
+  const size_t reserved = (size_t)device_attr(cudaDevAttrReservedSharedMemoryPerBlock, 1024);
+  const size_t block_max = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, 227 * 1024);
+  const size_t per_block = sm_bytes / per_sm;
+  if (per_block <= reserved + fa.sharedSizeBytes || block_max <= fa.sharedSizeBytes) return 0;
+  const size_t budget = std::min(per_block - reserved, block_max) - fa.sharedSizeBytes;
   const size_t base = propagate_pipe_smem(prm.net, 0);
   if (base >= budget) return 0;
   const size_t rows = (budget - base) / ((size_t)prm.net.P * sizeof(unsigned long long));
@@ -944,6 +952,10 @@ static cudaError_t launch_pipe(K kern, const PropagateParams &prm_in, int groups
   PropagateParams prm = prm_in;
   const int grid = persistent_grid(kern, groups);
   prm.tab.smem_rows = pipe_table_rows(kern, prm, grid);
+  // the window is sized to fill the SM's shared memory: ask for the largest carveout
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return launch_k(kern, prm, grid, 128, propagate_pipe_smem(prm.net, prm.tab.smem_rows), st);
 }
 
