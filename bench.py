@@ -49,8 +49,9 @@ DISCARD = 300              # iterations before the flux average (steady state, S
 OPS_PER_EVENT = 210
 ISSUE_PEAK_GOPS = 152 * 4 * 32 * 2.07
 KERNELS_PER_ITER = 6       # SSA, bin scan, placement, split/merge, gather, finalize
-# DRAM bytes (read + write) of one SSA launch on this workload, from the ncu capture summarised
-# in profiles/schlogl_mfpt_ssa_kernel.md (mean of two 16,000-walker launches, as in every timed launch)
+# DRAM bytes (read + write) of one SSA launch on this workload, from an ncu capture of the
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum, mean of two 16,000-walker launches, as
+# in every timed launch)
 SSA_TRAFFIC_BYTES = 397440
 
 

@@ -21,8 +21,8 @@
  *     algorithm listing), and the per-iteration observables the paper reads off: bin-free
  *     weighted histograms of a species (Sec. II.B.1) and the recycled flux (Eq. "mfpt").
  *
- * Readings of points the paper leaves open are fixed here and listed in the design doc; the ones
- * that matter for bit-exact comparison are stated beside the code that implements them.
+ * Points the paper leaves open are fixed by one reading each; every reading is stated beside
+ * the code that implements it (in this header or in we_oracle.c).
  */
 #ifndef WE_ORACLE_H
 #define WE_ORACLE_H
