@@ -273,11 +273,24 @@ def futile_s1_law(t: float, s1_0=50, s2_0=50, kf=1.0, ks=0.1) -> np.ndarray:
 # brute-force estimator of a transition time (Eq. "mld", Sec. II.C)
 # ----------------------------------------------------------------------------------------------
 def mle_transition_time(T: float, N: int, times) -> tuple:
-    """mu = (1 - n/N) T + (1/n) sum t_i and sigma = mu / sqrt(n), for n transitions seen at times
-    t_i among N runs of length T."""
+    """Mean transition time from N brute-force runs of length T, n of which saw the transition, at
+    times t_i (Eq. "mld", Sec. II.C): the maximum-likelihood mean of exponential waiting times
+    whose runs without a transition are censored at T,
+
+        mu = (sum t_i + (N - n) T) / n = (1/n) sum t_i + (N/n - 1) T,   sigma = mu / sqrt(n).
+
+    Reading: the equation as printed puts the factor (1 - n/N) on T.  The censored likelihood
+    gives (N/n - 1), and so do the paper's own epigenetic-switch figures (Sec. III.C): 753 runs
+    of 1e6 s giving 1.3e6 s with sigma 6.5e4 s mean n = (mu / sigma)^2 = 400 transitions, which
+    an exponential of mean 1.3e6 s yields (753 (1 - e^(-1/1.3)) = 404) at a mean observed time of
+    4.4e5 s; with (N/n - 1) that is 1.3e6 s again, with (1 - n/N) it would be 9.0e5 s."""
     times = np.asarray(times, dtype=np.float64)
     n = len(times)
-    mu = (1.0 - n / N) * T + times.sum() / n
+    if n == 0:
+        raise ValueError("no transition observed: the estimate is unbounded")
+    if n > N or np.any(times < 0) or np.any(times > T):
+        raise ValueError("need 0 <= t_i <= T and at most N transitions")
+    mu = (times.sum() + (N - n) * T) / n
     return mu, mu / np.sqrt(n)
 
 

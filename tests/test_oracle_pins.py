@@ -310,6 +310,54 @@ def test_epigenetic_switch_mfpt_matches_paper():
     assert E.epigenetic_mfpt((156, 0), lambda u, v: v >= 30) < 1e4
 
 
+# ---------------------------------------------- brute-force transition-time estimator ----------
+def test_mle_transition_time_maximises_the_censored_likelihood():
+    """Eq. "mld" is the maximum-likelihood mean of exponential waiting times, the runs without a
+    transition censored at T: the estimate sits where a bounded numerical search finds the
+    likelihood's maximum (densities of the observed times, survival T of the other runs); with
+    every run transitioning it is the sample mean; sigma is mu / sqrt(n)."""
+    from scipy.optimize import minimize_scalar
+    rng = np.random.default_rng(5)
+    T, N = 1.0, 500
+    t = rng.exponential(1.3, N)
+    seen = t[t <= T]
+    n = len(seen)
+
+    def minus_log_likelihood(mu):
+        return sum(math.log(mu) + ti / mu for ti in seen) + (N - n) * T / mu
+
+    best = minimize_scalar(minus_log_likelihood, bounds=(0.01, 100.0), method="bounded",
+                           options={"xatol": 1e-10})
+    mu, sig = E.mle_transition_time(T, N, seen)
+    assert mu == pytest.approx(best.x, rel=1e-6)
+    assert sig == pytest.approx(mu / math.sqrt(n), rel=1e-14)
+    every = rng.exponential(2.0, 50)
+    assert E.mle_transition_time(every.max(), 50, every)[0] == pytest.approx(every.mean(), rel=1e-14)
+    with pytest.raises(ValueError):
+        E.mle_transition_time(1.0, 10, [])
+
+
+def test_mle_transition_time_is_consistent_and_gives_the_paper_figures():
+    """Censored exponential samples of mean 1.3 (200,000 runs of length 1) give 1.3 back within 4
+    standard errors.  The expected data of the paper's brute-force campaign (Sec. III.C: 753 runs
+    of 1e6 s of a switch whose mean transition time is 1.3e6 s, so 404 transitions at a mean
+    observed time of 4.37e5 s) give the 1.3e6 s and 6.5e4 s it prints; the factor (1 - n/N) of
+    the printed equation would give 9.0e5 s."""
+    rng = np.random.default_rng(11)
+    t = rng.exponential(1.3, 200_000)
+    seen = t[t <= 1.0]
+    mu, sig = E.mle_transition_time(1.0, len(t), seen)
+    assert abs(mu - 1.3) < 4 * sig
+    m, T, N = 1.3e6, 1e6, 753
+    p = -math.expm1(-T / m)                          # P(transition within one run)
+    n = round(N * p)
+    mean_seen = m - T * math.exp(-T / m) / p         # mean of an exponential conditioned on t <= T
+    mu, sig = E.mle_transition_time(T, N, np.full(n, mean_seen))
+    assert n == 404
+    assert round(mu, -5) == 1.3e6
+    assert round(sig, -3) == 6.5e4
+
+
 # ---------------------------------------------------------------- futile-cycle CME -------------
 def test_futile_cme_matches_paper_and_invariants():
     """The futile cycle's exact law (uniformized CME over its 400 states): P(S1 > 90, t = 100)
