@@ -641,3 +641,54 @@ def test_we_reweighting_is_unbiased_with_state_resolved_bins():
     m = np.array(m)
     se = m.std(ddof=1) / np.sqrt(len(m))
     assert abs(m.mean() - 1.0) < 3 * se + 0.05, (m.mean(), se)
+
+
+# ---------------------------------------------------------------- grid bins ----------------------
+def test_grid_bins_match_a_library_search():
+    """Grid bin assignment (Sec. II.B: non-overlapping bins on a 1-D or 2-D grid): per dimension
+    the bin whose half-open interval [e_k, e_k+1) holds the count, clamped into the first and last
+    bins, the flat index row-major with the last dimension fastest.  WE stays unbiased under any
+    binning, so whole-run statistics cannot see a wrong bin map; here every count of the paper's
+    grids (Schloegl, toggle with an overflow edge at infinity, the epigenetic switch's non-uniform
+    2-D grid) and of random uneven 3-D grids goes against numpy's searchsorted and
+    ravel_multi_index."""
+    def by_library(cfg, x):
+        idx = []
+        for sp, e in zip(cfg.bins.species, cfg.bins.edges):
+            e = np.asarray(e, dtype=np.float64)
+            k = int(np.searchsorted(e, float(x[sp]), side="right")) - 1
+            idx.append(min(max(k, 0), len(e) - 2))
+        dims = [len(e) - 1 for e in cfg.bins.edges]
+        return int(np.ravel_multi_index(tuple(idx), tuple(dims)))
+
+    rng = np.random.default_rng(3)
+    cfgs = [W.schlogl_mfpt_we(n_iters=1), W.toggle_batch_we(n_runs=1, n_iters=1), W.epigenetic_mfpt_we(n_iters=1)]
+    for cfg in cfgs:
+        S = len(cfg.network.fixed_count)
+        hi = [int(np.max(np.where(np.isfinite(e), e, 0))) + 20 for e in cfg.bins.edges]
+        for _ in range(400):
+            x = np.zeros(S, np.int32)
+            for sp, h in zip(cfg.bins.species, hi):
+                x[sp] = rng.integers(0, h + 1)
+            assert O.bin_of(cfg, x) == by_library(cfg, x), (cfg.name, x)
+        # every edge and its neighbours along each dimension
+        for d, (sp, e) in enumerate(zip(cfg.bins.species, cfg.bins.edges)):
+            for v in np.asarray(e)[np.isfinite(e)]:
+                for dv in (-1, 0, 1):
+                    x = np.zeros(S, np.int32)
+                    x[sp] = max(int(v) + dv, 0)
+                    assert O.bin_of(cfg, x) == by_library(cfg, x), (cfg.name, d, x)
+    cfg = W.futile_pdf_we(n_iters=1)                  # six species: room for 3-D grids
+    S = len(cfg.network.fixed_count)
+    assert S >= 3
+    for trial in range(20):
+        ndim = 3
+        sp = list(rng.choice(S, size=ndim, replace=False))
+        edges = [np.concatenate([[0.0], np.cumsum(rng.integers(1, 9, size=rng.integers(1, 7))).astype(np.float64)])
+                 for _ in range(ndim)]
+        if trial % 2:
+            edges[-1] = np.append(edges[-1], np.inf)
+        cfg.bins = W.GridBins(species=[int(s) for s in sp], edges=edges)
+        for _ in range(200):
+            x = rng.integers(0, 60, size=S).astype(np.int32)
+            assert O.bin_of(cfg, x) == by_library(cfg, x), (trial, x)
