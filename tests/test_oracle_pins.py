@@ -692,3 +692,26 @@ def test_grid_bins_match_a_library_search():
         for _ in range(200):
             x = rng.integers(0, 60, size=S).astype(np.int32)
             assert O.bin_of(cfg, x) == by_library(cfg, x), (trial, x)
+
+
+# ------------------------------------------------------- exact birth-death tools -------------------
+def test_birth_death_exact_tools_agree_with_independent_forms():
+    """The exact tools that other tests take as expected values, each against an independent
+    computation: the truncated-CME transient (matrix exponential) of immigration-death against
+    its Binomial-Poisson closed form, the stationary law against Poisson(kb/kd), and the
+    first-passage-time sum against a sparse solve of the first-passage equations Q_sub T = -1 on
+    the states below the target (Schloegl and birth-death)."""
+    from scipy.sparse.linalg import spsolve
+    kb, kd = 10.0, 0.1
+    b, d = E.birth_death_rates(kb, kd)
+    for t in (0.5, 2.0, 20.0):
+        p = E.bd_transient(b, d, 100, t, 400)
+        q = E.immigration_death_pmf(100, kb, kd, t, 400)
+        assert np.max(np.abs(p - q)) < 1e-10, t
+    pi = E.bd_stationary(b, d, 400)
+    assert np.max(np.abs(pi - np.exp(E.log_poisson_pmf(np.arange(401), kb / kd)))) < 1e-12
+    for (rates, a, target) in ((E.birth_death_rates(), 100, 140), (E.schlogl_rates(), 85, 550),
+                               (E.schlogl_rates(), 0, 300)):
+        Q = E.bd_generator(*rates, target).tocsc()[:target, :target]     # exit to the target removed
+        T = spsolve(Q, -np.ones(target))
+        assert E.bd_mfpt(a, target, *rates) == pytest.approx(T[a], rel=1e-9), (a, target)
