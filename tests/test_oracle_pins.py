@@ -715,3 +715,25 @@ def test_birth_death_exact_tools_agree_with_independent_forms():
         Q = E.bd_generator(*rates, target).tocsc()[:target, :target]     # exit to the target removed
         T = spsolve(Q, -np.ones(target))
         assert E.bd_mfpt(a, target, *rates) == pytest.approx(T[a], rel=1e-9), (a, target)
+
+
+def test_two_species_mfpt_solvers_reduce_to_known_cases():
+    """The 2-D master-equation solvers behind the toggle and epigenetic-switch expected values:
+    with the repression switched off (K far above any count) the species entering the target
+    is an immigration-death process of its own, so the MFPT is the 1-D first-passage sum; with
+    equal Hill exponents and unit constants the two models are the same chain, so the two
+    solvers (each written from its own model's equations) agree; and the toggle's MFPT is
+    unchanged when the two genes swap roles."""
+    ind = lambda a: (lambda x: np.full(np.shape(x), a, dtype=np.float64))
+    lin = lambda x: 1.0 * np.asarray(x, dtype=np.float64)
+    t = E.toggle_mfpt(30.0, 12.0, (30, 0), lambda u, v: v >= 20, K=1e30, Umax=70, Vmax=40)
+    assert t == pytest.approx(E.bd_mfpt(0, 20, ind(12.0), lin), rel=1e-9)
+    g = E.epigenetic_mfpt((0, 30), lambda u, v: u >= 50, K1=1e30, K2=1e30, G1=90, G2=70)
+    assert g == pytest.approx(E.bd_mfpt(0, 50, ind(156.0), lin), rel=1e-9)
+    target = lambda u, v: v >= 10 and u <= 5
+    a = E.toggle_mfpt(20.0, 20.0, (20, 0), target, n=2, Umax=60, Vmax=60)
+    b = E.epigenetic_mfpt((20, 0), target, a1=20.0, a2=20.0, n=2, m=2, G1=60, G2=60)
+    assert a == pytest.approx(b, rel=1e-10)
+    swapped = E.toggle_mfpt(20.0, 20.0, (0, 20), lambda u, v: target(v, u), n=2, Umax=60, Vmax=60)
+    assert a == pytest.approx(swapped, rel=1e-10)
+    assert 10.0 < a < 1e6
