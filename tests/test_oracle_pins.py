@@ -737,3 +737,29 @@ def test_two_species_mfpt_solvers_reduce_to_known_cases():
     swapped = E.toggle_mfpt(20.0, 20.0, (0, 20), lambda u, v: target(v, u), n=2, Umax=60, Vmax=60)
     assert a == pytest.approx(swapped, rel=1e-10)
     assert 10.0 < a < 1e6
+
+
+def test_stored_golden_values_are_the_oracles():
+    """tests/golden/exact_values.json holds exactly what tests/golden/make_golden.py computes from
+    oracle/ today (a stale file, or one written by anything else, fails here), and its entries
+    agree with the values the paper prints: P(X >= 700, t = 5 | X0 = 82) = 1.148e-9 and an MFPT
+    of about 5e4 s between the Schloegl modes (Sec. III.B.3), P(S1 > 90, t = 100) = 2.72e-18
+    (Sec. III.A), the epigenetic switch's 1.3e6 s (Sec. III.C)."""
+    import importlib.util
+    import json
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    fresh = mg.compute()
+    stored = json.load(open(os.path.join(here, "exact_values.json")))
+    assert set(fresh) == set(stored)
+    for k, v in fresh.items():
+        if isinstance(v, float):
+            assert stored[k] == pytest.approx(v, rel=1e-9), k
+        else:
+            assert stored[k] == v, k
+    assert round(stored["schlogl_p_ge_700_t5_from_82"], 12) == 1.148e-9
+    assert round(stored["schlogl_mfpt_82_to_563_s"], -4) == 5e4
+    assert round(stored["futile_p_s1_gt_90_t100"], 20) == 2.72e-18
+    assert round(stored["epigenetic_mfpt_0_30_to_g1_ge_50_s"], -5) == 1.3e6
