@@ -458,7 +458,7 @@ def test_we_mfpt_matches_closed_form():
     outs = _replicas(cfg, 8)
     bb, dd = E.birth_death_rates()
     exact = 1.0 / E.bd_mfpt(100, 140, bb, dd)
-    est = np.array([o["flux_weight"][150:].mean() / cfg.tau for o in outs])
+    est = np.array([1.0 / O.mfpt_from_flux(o["flux_weight"], cfg.tau, discard=150) for o in outs])
     se = est.std(ddof=1) / np.sqrt(len(est))
     assert abs(est.mean() - exact) < 4 * se + 0.05 * exact, (est.mean(), exact, se)
     for o in outs:
