@@ -180,3 +180,30 @@ def test_autotune_cache_file_round_trip_without_gpu(tmp_path):
     P.autotune_cache_clear()
     P.autotune_cache_save(out)
     assert out.read_text() == ""
+
+
+def test_run_config_marshalling_reads_back():
+    """run_config_from writes a run description into the C struct field by field: scalars,
+    the per-run arrays behind its pointers (initial walkers and weights, target thresholds,
+    parameter sets), the target clauses, and the reweighting period, which plain propagation
+    (resample off) forces to 0."""
+    cfg = W.toggle_batch_we(n_runs=4, n_iters=7, seed=123)
+    cfg.reweight_period = 3
+    c, keep = P.run_config_from(cfg)
+    assert (c.tau, c.m_targ, c.n_runs, c.seed, c.record_iters) == (0.1, 8, 4, 123, 7)
+    assert (c.hist_species, c.hist_len, c.reweight_period) == (cfg.hist_species, cfg.hist_len, 3)
+    ist, iw = np.asarray(cfg.init_states), np.asarray(cfg.init_weights)
+    assert c.n_init == ist.shape[1]
+    n_st = ist.size
+    assert np.array_equal(np.ctypeslib.as_array(c.init_states, shape=(n_st,)), ist.ravel())
+    assert np.array_equal(np.ctypeslib.as_array(c.init_weights, shape=(iw.size,)), iw.ravel())
+    assert c.feedback == 1 and c.n_clauses == 2
+    assert [c.tgt_species[k] for k in range(2)] == list(cfg.target.species)
+    assert [c.tgt_op[k] for k in range(2)] == list(cfg.target.op)
+    thr = np.asarray(cfg.target.threshold)
+    assert np.array_equal(np.ctypeslib.as_array(c.tgt_threshold, shape=(thr.size,)), thr.ravel())
+    if cfg.param_set is not None:
+        ps = np.asarray(cfg.param_set)
+        assert np.array_equal(np.ctypeslib.as_array(c.param_set, shape=(ps.size,)), ps)
+    plain, keep2 = P.run_config_from(cfg, resample=False)
+    assert plain.reweight_period == 0 and plain.resample == 0
