@@ -1,0 +1,68 @@
+"""GPU path against the CPU oracle at the benchmark's full size, in the launch configuration the
+benchmark times (collected last: it is the longest GPU test).
+
+The Schloegl MFPT workload with 10 replicas of 1,600 walker slots each (80 bins x 20 walkers,
+tau = 0.05, recycling at X >= 550 back to X = 85; default mapping and block shape) runs 600
+iterations on the GPU, into the regime the benchmark spends its time in: walkers spread up to
+the high state and recycle every interval (~1,060 walkers and ~1.8e5 SSA events per run and
+iteration).  Three more iterations then run on the GPU and, from the GPU's own populations at
+iteration 600 (first iteration 600, so the same counter-based random numbers), on the oracle:
+every run's walkers, weights, parents, event counts, fluxes and histograms must agree (bit for
+bit; observables summed by device atomics within 1e-12 relative)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+from gpu_helpers import assert_run_parity, gpu_outputs, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1303_5986_gb300 import build
+    build.build()
+
+
+def test_schlogl_benchmark_configuration_at_full_size():
+    k, m, R = 600, 3, 10
+    cfg = W.schlogl_mfpt_we(n_iters=k + m, n_runs=R)
+    ens = gpu_run(cfg, k, record_iters=k + m)
+    ens.sync()
+    states = [ens.states(r) for r in range(R)]
+    weights = [ens.weights(r) for r in range(R)]
+    ens.step(m)
+    ens.sync()
+    recycled, events = 0.0, 0
+    for r in range(R):
+        g = gpu_outputs(ens, r)
+        for key in ("flux_weight", "total_weight", "n_walkers", "events", "hist"):
+            g[key] = g[key][k:]
+        o = oracle_run(cfg, r, n_iters=m, init_states=states, init_weights=weights, first_iter=k)
+        assert_run_parity(g, o, label=f"benchmark configuration, run {r}")
+        recycled += float(g["flux_weight"].sum())
+        events += int(g["events"].sum())
+    assert recycled > 0.0
+    assert events > R * m * 100_000
+
+
+def test_synthetic_354x3680_first_interval_at_full_size_sampled():
+    """The 354-species / 3680-reaction network at the benchmark's full size (4,096 walkers with
+    counts uniform in [0, 200], one warp per walker as the benchmark launches it): the first
+    interval (~3.9e4 events per walker) on the GPU, then eight sampled walkers (both ends of
+    the population and six between) replayed one by one on the oracle from the same initial
+    counts and random-number counters: their counts after the interval agree bit for bit."""
+    from oracle import oracle as O
+    cfg = W.synthetic_large_we(n_walkers=4096, n_iters=1)
+    ens = gpu_run(cfg, 0, record_iters=1)
+    ens.propagate()
+    ens.sync()
+    after = ens.states(0)
+    assert after.shape == (4096, 354)
+    x0 = np.asarray(cfg.init_states)[0]
+    net = O.Network(cfg.network, 0)
+    for s in (0, 1, 1000, 2047, 2048, 3000, 4094, 4095):
+        x, ev, rec, rc = O.propagate_one(cfg, x0[s], 0, s, run=0, net=net)
+        assert rc == 0 and ev > 10_000, (s, rc, ev)
+        assert np.array_equal(after[s], x), s
