@@ -1,5 +1,6 @@
-"""GPU path against the CPU oracle at the benchmark's full size, in the launch configuration the
-benchmark times (collected last: it is the longest GPU test).
+"""GPU path against the CPU oracle at the benchmarks' full sizes, in the launch configurations
+the benchmarks time (collected last: these are the longest GPU tests): the Schloegl MFPT
+workload, the 64-run toggle sweep in full, and sampled walkers of the 354 x 3680 network.
 
 The Schloegl MFPT workload with 10 replicas of 1,600 walker slots each (80 bins x 20 walkers,
 tau = 0.05, recycling at X >= 550 back to X = 85; default mapping and block shape) runs 600
@@ -66,3 +67,16 @@ def test_synthetic_354x3680_first_interval_at_full_size_sampled():
         x, ev, rec, rc = O.propagate_one(cfg, x0[s], 0, s, run=0, net=net)
         assert rc == 0 and ev > 10_000, (s, rc, ev)
         assert np.array_equal(after[s], x), s
+
+
+def test_toggle_sweep_at_full_size():
+    """The batched toggle sweep as the benchmark runs it: 64 runs, each with its own production
+    rates, 500 iterations, every phase one launch for all runs; every run's walkers, weights,
+    parents, event counts, fluxes and histograms against the oracle's."""
+    cfg = W.toggle_batch_we()
+    assert (cfg.n_runs, cfg.n_iters) == (64, 500)
+    ens = gpu_run(cfg, cfg.n_iters)
+    ens.sync()
+    for r in range(cfg.n_runs):
+        assert_run_parity(gpu_outputs(ens, r), oracle_run(cfg, r, n_iters=cfg.n_iters),
+                          label=f"toggle sweep, run {r}")
