@@ -80,3 +80,15 @@ def test_toggle_sweep_at_full_size():
     for r in range(cfg.n_runs):
         assert_run_parity(gpu_outputs(ens, r), oracle_run(cfg, r, n_iters=cfg.n_iters),
                           label=f"toggle sweep, run {r}")
+
+
+@pytest.mark.parametrize("target", [None, 250])
+def test_birth_death_at_full_size(target):
+    """The 1-D birth-death configuration in full: 60 bins of width 5 plus an overflow bin,
+    10 walkers per bin, tau = 0.1, 200 iterations, with and without recycling at X >= 250."""
+    cfg = W.birth_death_we(target=target)
+    assert cfg.n_iters == 200
+    ens = gpu_run(cfg, cfg.n_iters)
+    ens.sync()
+    assert_run_parity(gpu_outputs(ens, 0), oracle_run(cfg, 0, n_iters=cfg.n_iters),
+                      label=f"birth-death, target {target}")
