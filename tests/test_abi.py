@@ -207,3 +207,59 @@ def test_run_config_marshalling_reads_back():
         assert np.array_equal(np.ctypeslib.as_array(c.param_set, shape=(ps.size,)), ps)
     plain, keep2 = P.run_config_from(cfg, resample=False)
     assert plain.reweight_period == 0 and plain.resample == 0
+
+
+def test_every_run_description_check_is_made_on_the_host():
+    """Each malformed field of a run description is refused with WE_EINVAL before any device
+    work (through the host-only workspace-size call, so no GPU is needed): an empty initial
+    population, capacity below it, record slots, negative first iteration, target clauses
+    (count, species, operator), histogram species, per-run initial counts, parameter sets,
+    initial counts and weights out of range."""
+    import ctypes as C
+    cfg = W.toggle_batch_we(n_runs=2, n_iters=4)
+    net = P.network_from_spec(cfg.network)
+    bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+
+    def fresh():                       # the config's arrays may be the description's own
+        import copy
+        cc = copy.deepcopy(cfg)
+        c, keep = P.run_config_from(cc)
+        keep["cfg"] = cc
+        return c, keep
+
+    c, keep = fresh()
+    assert P.we_ensemble_workspace_bytes(net, bm, c) > 0
+    assert c.n_init == 8                # eight initial walkers per run
+    S = len(cfg.network.fixed_count)
+    cases = {
+        "n_init 0": lambda c, k: setattr(c, "n_init", 0),
+        "capacity below n_init": lambda c, k: setattr(c, "capacity", c.n_init - 1),
+        "record_iters 0": lambda c, k: setattr(c, "record_iters", 0),
+        "first_iter < 0": lambda c, k: setattr(c, "first_iter", -1),
+        "no clauses": lambda c, k: setattr(c, "n_clauses", 0),
+        "too many clauses": lambda c, k: setattr(c, "n_clauses", 5),
+        "clause species": lambda c, k: c.tgt_species.__setitem__(0, S),
+        "clause operator": lambda c, k: c.tgt_op.__setitem__(0, 7),
+        "histogram species": lambda c, k: setattr(c, "hist_species", S),
+        "param set": lambda c, k: k["ps"].__setitem__(0, 99),
+        "negative count": lambda c, k: k["ist"].__setitem__((0, 0, 0), -1),
+        "count too large": lambda c, k: k["ist"].__setitem__((0, 0, 0), 1 << 30),
+        "negative weight": lambda c, k: k["iw"].__setitem__((0, 0), -1.0),
+        "NaN weight": lambda c, k: k["iw"].__setitem__((0, 0), float("nan")),
+        "infinite weight": lambda c, k: k["iw"].__setitem__((0, 0), float("inf")),
+    }
+    for name, mutate in cases.items():
+        c, keep = fresh()
+        mutate(c, keep)
+        with pytest.raises(P.WEError) as e:
+            P.we_ensemble_workspace_bytes(net, bm, c)
+        assert e.value.status == -1, name
+    # per-run initial counts, given through the raw field
+    c, keep = fresh()
+    bad = np.array([0, 1], dtype=np.int32)
+    c.n_init_per_run = bad.ctypes.data_as(C.POINTER(C.c_int32))
+    with pytest.raises(P.WEError):
+        P.we_ensemble_workspace_bytes(net, bm, c)
+    ok = np.array([1, c.n_init], dtype=np.int32)
+    c.n_init_per_run = ok.ctypes.data_as(C.POINTER(C.c_int32))
+    assert P.we_ensemble_workspace_bytes(net, bm, c) > 0
