@@ -45,7 +45,7 @@ class WEOut(C.Structure):
     _fields_ = [("flux_weight", _F64P), ("total_weight", _F64P), ("n_walkers", _I32P),
                 ("events", _I64P), ("hist", _F64P), ("states", _I32P), ("weights", _F64P),
                 ("parent", _I32P), ("t_last", _F64P), ("n_final", C.c_int32), ("status", C.c_int32),
-                ("reweighted", _I32P)]
+                ("first_passage", _F64P), ("reweighted", _I32P)]
 
 
 _lib = None
@@ -181,7 +181,7 @@ def make_config(cfg, run: int = 0, n_iters: int | None = None, first_iter: int |
         c.bin_nbins[d] = cfg.bins.n_bins_per_dim[d]
     c.bin_edges = _p(keep["edges"], _F64P)
     if cfg.target is not None:
-        c.feedback = 1
+        c.feedback = 2 if getattr(cfg, "absorb", False) else 1
         c.n_clauses = len(cfg.target.species)
         for i in range(c.n_clauses):
             c.tgt_species[i] = cfg.target.species[i]
@@ -212,19 +212,20 @@ def we_run(cfg, run: int = 0, n_iters: int | None = None, first_iter: int | None
         "n_walkers": np.zeros(n, dtype=np.int32), "events": np.zeros(n, dtype=np.int64),
         "hist": np.zeros((n, max(cfg.hist_len, 1))), "states": np.zeros((cap, S), dtype=np.int32),
         "weights": np.zeros(cap), "parent": np.zeros(cap, dtype=np.int32), "t_last": np.zeros(cap),
-        "reweighted": np.zeros(n, dtype=np.int32),
+        "reweighted": np.zeros(n, dtype=np.int32), "first_passage": np.zeros(cap),
     }
     out = WEOut(_p(o["flux_weight"], _F64P), _p(o["total_weight"], _F64P),
                 _p(o["n_walkers"], _I32P), _p(o["events"], _I64P),
                 _p(o["hist"], _F64P) if cfg.hist_len > 0 else None,
                 _p(o["states"], _I32P), _p(o["weights"], _F64P), _p(o["parent"], _I32P),
-                _p(o["t_last"], _F64P), 0, 0, _p(o["reweighted"], _I32P))
+                _p(o["t_last"], _F64P), 0, 0, _p(o["first_passage"], _F64P), _p(o["reweighted"], _I32P))
     lib().orc_we_run(net.h, C.byref(c), C.byref(out))
     nf = out.n_final
     o["t_last_prev"] = o["t_last"]
     o["states"] = o["states"][:nf]
     o["weights"] = o["weights"][:nf]
     o["parent"] = o["parent"][:nf]
+    o["first_passage"] = o["first_passage"][:nf]
     o["n_final"] = nf
     o["status"] = out.status
     return o

@@ -260,6 +260,9 @@ static int in_target(const orc_we_config *cfg, const int32_t *x) {
  * is discarded, which leaves the process exact because the exponential clock is memoryless.
  * With feedback on, a walker that enters B is put back in the recycle state at once and keeps
  * running for the rest of the interval (first passage is detected at the event that crosses).
+ * With absorbing feedback (the brute-force runs of Sec. II.C, which record the time of the
+ * first transition), a walker stops at the event that enters B and stays there; one that starts
+ * the interval inside B fires nothing.
  * ------------------------------------------------------------------------------------------ */
 int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int32_t slot,
                   int32_t *x, int64_t *n_ev, int32_t *n_rec, double *t_last) {
@@ -276,6 +279,7 @@ int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int3
   int status = ORC_OK;
   orc_propensities(n, x, a);
   for (;;) {
+    if (cfg->feedback == 2 && in_target(cfg, x)) break;      /* absorbed: nothing more fires */
     double a0 = orc_tree_total(M, a);
     if (!(a0 > 0.0)) break;                     /* nothing can fire: idle to the end of tau */
     uint32_t ctr[4] = {draw, (uint32_t)iter, (uint32_t)slot, 0u}, r[4];
@@ -303,6 +307,7 @@ int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int3
     t = tn;
     if (cfg->feedback && in_target(cfg, x)) {
       ++rec;
+      if (cfg->feedback == 2) break;                          /* first passage: stop here */
       memcpy(x, cfg->recycle_state, sizeof(int32_t) * S);
     }
     orc_propensities(n, x, a);
@@ -613,14 +618,24 @@ int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
   memcpy(st, cfg->init_states, sizeof(int32_t) * (size_t)nw * S);
   memcpy(w, cfg->init_weights, sizeof(double) * nw);
   for (int32_t i = 0; i < nw; ++i) par[i] = -1;
+  if (out->first_passage)
+    for (int32_t i = 0; i < cap; ++i) out->first_passage[i] = -1.0;
+  const int absorb = cfg->feedback == 2 && !cfg->resample;
   int status = ORC_OK;
   for (int32_t li = 0; li < cfg->n_iters && status == ORC_OK; ++li) {
     int32_t iter = cfg->first_iter + li;
     int64_t events = 0;
     for (int32_t s = 0; s < nw; ++s) {
       int64_t ev = 0;
-      int32_t rc = orc_propagate(n, cfg, iter, s, st + (size_t)s * S, &ev, &nrec[s],
-                                 out->t_last ? &out->t_last[s] : NULL);
+      double tl = 0.0;
+      /* brute-force runs: a walker found inside B at the start of an interval entered it at
+       * that time at the latest (only the initial walkers can be found there unrecorded) */
+      if (absorb && out->first_passage && out->first_passage[s] < 0.0 && in_target(cfg, st + (size_t)s * S))
+        out->first_passage[s] = (double)iter * cfg->tau;
+      int32_t rc = orc_propagate(n, cfg, iter, s, st + (size_t)s * S, &ev, &nrec[s], &tl);
+      if (out->t_last) out->t_last[s] = tl;
+      if (absorb && out->first_passage && nrec[s] > 0 && out->first_passage[s] < 0.0)
+        out->first_passage[s] = (double)iter * cfg->tau + tl;
       events += ev;
       if (rc != ORC_OK && status == ORC_OK) status = rc;
     }

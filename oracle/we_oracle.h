@@ -69,7 +69,10 @@ typedef struct {
   int32_t bin_nbins[4];
   const double *bin_edges;           /* concatenated */
   /* optional per-walker bin override (learned bins are assigned outside and passed per call) */
-  int32_t feedback;                  /* 0/1: recycle walkers entering the target set */
+  int32_t feedback;                  /* 0: none; 1: recycle walkers entering the target set
+                                        (Sec. II.B.2); 2: absorb them -- a walker stops at its
+                                        first entrance and stays there (the brute-force
+                                        transition-time runs of Sec. II.C; resample = 0 only) */
   int32_t n_clauses;                 /* target set = AND of clauses  x[species] op threshold */
   int32_t tgt_species[4], tgt_op[4], tgt_threshold[4];
   const int32_t *recycle_state;      /* S */
@@ -96,6 +99,13 @@ typedef struct {
                                         interval, by slot before resampling (may be NULL) */
   int32_t n_final;
   int32_t status;
+  double *first_passage;             /* capacity, may be NULL; plain runs (resample = 0) with
+                                        feedback = 2: time from the run's start (iteration 0)
+                                        at which the walker of each slot first entered the
+                                        target set, fl(fl(iter * tau) + t) for an entrance at
+                                        time t of interval iter (fl(iter * tau) for a walker
+                                        found inside at the start of an interval); -1 if it
+                                        has not entered */
   int32_t *reweighted;               /* per iteration: 1 reweighted, -1 attempted and skipped,
                                         0 not a reweighting iteration (may be NULL) */
 } orc_we_out;
@@ -118,8 +128,9 @@ double orc_tree_total(int32_t n, const double *a);
 /* Reaction selected by a tree descent on target in [0, total). */
 int32_t orc_tree_select(int32_t n, const double *a, double target);
 
-/* One walker for one interval; returns status.  *n_rec = recycles, *n_ev = events fired,
- * *t_last = time of the last event fired in the interval (0 if none; may be NULL). */
+/* One walker for one interval; returns status.  *n_rec = recycles (feedback 2: 1 if the walker
+ * entered the target set in this interval), *n_ev = events fired, *t_last = time of the last
+ * event fired in the interval (0 if none; may be NULL). */
 int orc_propagate(const orc_net *net, const orc_we_config *cfg, int32_t iter, int32_t slot,
                   int32_t *x, int64_t *n_ev, int32_t *n_rec, double *t_last);
 int32_t orc_bin_of(const orc_we_config *cfg, const int32_t *x);

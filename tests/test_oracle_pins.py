@@ -358,6 +358,60 @@ def test_mle_transition_time_is_consistent_and_gives_the_paper_figures():
     assert round(sig, -3) == 6.5e4
 
 
+# --------------------------------------- brute-force runs with an absorbing target --------------
+def test_absorbing_runs_give_erlang_first_passage_times():
+    """Pure birth at rate 2 (the birth-death network with kd = 0) from 100, absorbed at X >= 130:
+    the first-passage time is the sum of 30 exponential waits, Erlang(30, 2) (mean 15, variance
+    7.5).  Intervals of 0.25 put each passage ~60 intervals in, so a time recorded without its
+    interval's start fl(i tau), or one interval off, or the time of the event before the
+    entrance, fails; so does a walker that keeps firing after its entrance."""
+    net = W.networks.NetworkSpec(species=["X"], reactants=[[], [(0, 1)]], products=[[(0, 1)], []],
+                                 rate=[[2.0, 0.0]], name="pure_birth")
+    tgt = W.Target(species=[0], op=[W.configs.OP_GE], threshold=np.full((1, 1), 130, dtype=np.int32))
+    cfg = W.bruteforce_fpt(net, [100], tgt, n_walkers=1500, tau=0.25, n_iters=160)
+    o = O.we_run(cfg, 0, resample=False)
+    fp = o["first_passage"]
+    assert o["status"] == 0 and np.all(fp > 0) and np.all(o["states"][:, 0] == 130)
+    assert np.all(fp <= 160 * 0.25)
+    assert int(o["events"].sum()) == 30 * 1500                       # nothing fires after absorption
+    se = fp.std(ddof=1) / np.sqrt(len(fp))
+    assert abs(fp.mean() - 15.0) < 3 * se, (fp.mean(), se)
+    assert stats.kstest(fp, stats.gamma(30, scale=0.5).cdf).pvalue > 0.01
+    n = len(fp)                                   # sd of s^2 / sigma^2: 2/(n-1) + excess kurtosis 6/30 over n
+    assert abs(fp.var(ddof=1) / 7.5 - 1.0) < 3 * np.sqrt(2.0 / (n - 1) + 0.2 / n)
+
+
+def test_absorbing_runs_mean_first_passage_matches_closed_form():
+    """Birth-death (kb = 10, kd = 0.1) from 100, absorbed at X >= 110, runs of 400 s in intervals
+    of 1 s (every run passes): the mean first-passage time equals the closed form
+    sum_k (sum_{j<=k} pi_j) / (lambda_k pi_k) = 20.91 within 3 standard errors, and the
+    censored-exponential MLE of Eq. "mld" with no censored run is the sample mean."""
+    b, d = E.birth_death_rates()
+    exact = E.bd_mfpt(100, 110, b, d)
+    cfg = W.birth_death_bruteforce(n_walkers=1200, tau=1.0, n_iters=400, threshold=110)
+    o = O.we_run(cfg, 0, resample=False)
+    fp = o["first_passage"]
+    assert o["status"] == 0 and np.all(fp > 0)
+    se = fp.std(ddof=1) / np.sqrt(len(fp))
+    assert abs(fp.mean() - exact) < 3 * se, (fp.mean(), exact, se)
+    mu, sig = E.mle_transition_time(400.0, len(fp), fp)
+    assert mu == pytest.approx(fp.mean(), rel=1e-12)
+
+
+def test_absorbing_walker_starting_inside_fires_nothing():
+    """A walker that starts inside the absorbing set fires no event and its first passage is the
+    start of the run; walkers outside are unaffected by it (their draws are keyed by slot)."""
+    cfg = W.birth_death_bruteforce(n_walkers=4, tau=1.0, n_iters=30, threshold=105)
+    cfg.init_states[0, 1, 0] = 107
+    o = O.we_run(cfg, 0, resample=False)
+    assert o["first_passage"][1] == 0.0 and o["states"][1, 0] == 107
+    cfg2 = W.birth_death_bruteforce(n_walkers=4, tau=1.0, n_iters=30, threshold=105)
+    o2 = O.we_run(cfg2, 0, resample=False)
+    keep = [0, 2, 3]
+    assert np.array_equal(o["first_passage"][keep], o2["first_passage"][keep])
+    assert np.array_equal(o["states"][keep], o2["states"][keep])
+
+
 # ---------------------------------------------------------------- futile-cycle CME -------------
 def test_futile_cme_matches_paper_and_invariants():
     """The futile cycle's exact law (uniformized CME over its 400 states): P(S1 > 90, t = 100)

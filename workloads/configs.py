@@ -79,6 +79,8 @@ class WEConfig:
     max_steps: int = 0
     first_iter: int = 0
     reweight_period: int = 0             # >0: steady-state reweighting every this many iterations
+    absorb: bool = False                 # with a target: walkers stop at their first entrance
+                                         # (brute-force first-passage runs, no resampling)
     name: str = ""
     notes: dict = field(default_factory=dict)
 
@@ -193,6 +195,42 @@ def epigenetic_mfpt_we(n_iters: int = 500, n_runs: int = 6, seed: int = 0, m_tar
     return WEConfig(network=net, bins=bins, tau=0.1, m_targ=m_targ, n_iters=n_iters, x0=[0, 30],
                     n_runs=n_runs, seed=seed, target=tgt, hist_species=0, hist_len=101,
                     reweight_period=reweight_period, name="epigenetic_mfpt")
+
+
+def bruteforce_fpt(network: NetworkSpec, x0, target: Target, n_walkers: int, tau: float, n_iters: int,
+                   n_runs: int = 1, seed: int = 0, name: str = "bruteforce") -> WEConfig:
+    """Brute-force transition-time campaign (Sec. II.C): n_walkers unweighted SSA runs per run id
+    from x0, each stopped at its first entrance into the target set; tau is only the length of
+    the intervals the runs are advanced by (n_iters of them: runs of length T = n_iters tau).
+    Run without resampling; one bin."""
+    S = network.n_species
+    x0 = np.asarray(x0, dtype=np.int32).reshape(-1, S)
+    if x0.shape[0] == 1:
+        x0 = np.repeat(x0, n_runs, axis=0)
+    init = np.repeat(x0[:, None, :], n_walkers, axis=1)
+    bins = GridBins(species=[0], edges=[np.array([0.0, np.inf])])
+    return WEConfig(network=network, bins=bins, tau=tau, m_targ=1, n_iters=n_iters, x0=x0,
+                    n_runs=n_runs, seed=seed, init_states=init,
+                    init_weights=np.full((n_runs, n_walkers), 1.0 / n_walkers), target=target,
+                    capacity=n_walkers, absorb=True, name=name)
+
+
+def schlogl_bruteforce(n_walkers: int = 1024, tau: float = 10.0, n_iters: int = 100, n_runs: int = 1,
+                       seed: int = 0, x0: int = 85, threshold: int = 550) -> WEConfig:
+    """Brute-force Schloegl transition runs (Sec. III.B.3's E50% comparison): walkers from X0 = 85
+    absorbed at X >= 550, runs of length n_iters * tau."""
+    net = schlogl()
+    A, B = int(net.fixed_count[1]), int(net.fixed_count[2])
+    tgt = Target(species=[0], op=[OP_GE], threshold=np.full((n_runs, 1), threshold, dtype=np.int32))
+    return bruteforce_fpt(net, [x0, A, B], tgt, n_walkers, tau, n_iters, n_runs, seed, "schlogl_bruteforce")
+
+
+def birth_death_bruteforce(n_walkers: int = 256, tau: float = 1.0, n_iters: int = 100, n_runs: int = 1,
+                           seed: int = 0, x0: int = 100, threshold: int = 130) -> WEConfig:
+    """Brute-force birth-death first passages 100 -> X >= threshold (kb = 10, kd = 0.1)."""
+    tgt = Target(species=[0], op=[OP_GE], threshold=np.full((n_runs, 1), threshold, dtype=np.int32))
+    return bruteforce_fpt(birth_death(), [x0], tgt, n_walkers, tau, n_iters, n_runs, seed,
+                          "birth_death_bruteforce")
 
 
 def toggle_params(n_runs: int = 64, seed: int = 0, lo: float = 20.0, hi: float = 60.0):
