@@ -62,6 +62,10 @@ typedef int32_t we_status;
 #define WE_MASS_ACTION 0
 #define WE_HILL_REPRESSION 1
 
+/* Feedback modes of we_run_config.feedback. */
+#define WE_FEEDBACK_RECYCLE 1
+#define WE_FEEDBACK_ABSORB 2
+
 /* Target-set clause operators: x[species] >= threshold, x[species] <= threshold. */
 #define WE_OP_GE 0
 #define WE_OP_LE 1
@@ -192,7 +196,14 @@ typedef struct {
   int32_t first_iter;              /* index of the first WE iteration (resume) */
   int32_t capacity;                /* walker slots per run (0: max(m_targ * n_bins, n_init)) */
   int32_t record_iters;            /* iterations of observables kept on the device (>= 1) */
-  int32_t feedback;                /* 1: recycle walkers that enter the target set */
+  int32_t feedback;                /* 0: none.  WE_FEEDBACK_RECYCLE (1): a walker that enters
+                                      the target set is put back in the recycle state at once
+                                      and its weight counted as flux (Sec. II.B.2).
+                                      WE_FEEDBACK_ABSORB (2): the target set is absorbing --
+                                      a walker stops at the event that enters it and stays
+                                      there, and the time of that first passage is kept per
+                                      walker (WE_OUT_FPT): the brute-force transition-time runs
+                                      of Sec. II.C; needs resample = 0 */
   int32_t n_clauses;               /* target set B = AND of clauses (1..4 when feedback) */
   int32_t tgt_species[4];
   int32_t tgt_op[4];               /* WE_OP_GE / WE_OP_LE */
@@ -320,6 +331,12 @@ we_status we_ensemble_sync(we_ensemble *ens, void *stream);
  *   WE_OUT_NREC      int32[n_prev]                  recycles of each walker in the last interval
  *   WE_OUT_RW        int32[iters x runs]            steady-state reweighting per iteration: 1 done,
  *                                                   -1 attempted and skipped, 0 not scheduled
+ *   WE_OUT_FPT       double[n_live]                 absorbing runs: each walker's first-passage
+ *                                                   time into the target set, counted from the
+ *                                                   run's start (iteration 0): fl(fl(i tau) + t)
+ *                                                   for an entrance at time t of interval i, or
+ *                                                   fl(i tau) for a walker found inside at the
+ *                                                   start of interval i; -1 if not (yet) entered
  * Per-iteration arrays hold the recorded iterations in order. */
 #define WE_OUT_COUNTS 1
 #define WE_OUT_STATES 2
@@ -337,8 +354,23 @@ we_status we_ensemble_sync(we_ensemble *ens, void *stream);
 #define WE_OUT_Z 14
 #define WE_OUT_NREC 15
 #define WE_OUT_RW 16
+#define WE_OUT_FPT 17
 we_status we_ensemble_get(we_ensemble *ens, int32_t what, int32_t run, void *dst,
                           size_t dst_bytes, size_t *needed, void *stream);
+
+/* Maximum-likelihood transition time of a brute-force campaign (Sec. II.C, Eq. "mld"), per run
+ * of an absorbing ensemble (feedback = WE_FEEDBACK_ABSORB): the run's N live walkers are N
+ * independent SSA runs of length T from the initial state; the n of them whose first-passage
+ * time t_i (WE_OUT_FPT) lies in [0, T] transitioned, the others are censored at T.  Under an
+ * exponential law of transition times the likelihood is maximal at
+ *     mu = (sum_i t_i + (N - n) T) / n,    with standard error sigma = mu / sqrt(n)
+ * (the printed factor (1 - n/N) on T is read as (N/n - 1): only this form reproduces the
+ * paper's own brute-force figures of Sec. III.C).  T <= 0 takes the time simulated so far,
+ * (next iteration index) x tau.  Writes runs x 5 doubles (N, n, sum t_i, mu, sigma; mu and
+ * sigma are +inf when n = 0) to dst (host or device, dst_bytes >= 40 runs); the sums run on
+ * the device in slot order; synchronises the stream.  Errors: WE_EINVAL (not an absorbing
+ * ensemble, dst too small, between propagate and resample), WE_ECUDA. */
+we_status we_ensemble_fpt_mle(we_ensemble *ens, double T, void *dst, size_t dst_bytes, void *stream);
 
 /* Whole WE procedure in one call (Sec. II.B): create an ensemble in library-owned memory,
  * run cfg->record_iters iterations, synchronise, and return the ensemble for we_ensemble_get.

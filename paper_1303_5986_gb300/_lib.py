@@ -43,6 +43,9 @@ WE_OUT_TLAST = 13
 WE_OUT_Z = 14
 WE_OUT_NREC = 15
 WE_OUT_RW = 16
+WE_OUT_FPT = 17
+WE_FEEDBACK_RECYCLE = 1
+WE_FEEDBACK_ABSORB = 2
 
 _I32P = C.POINTER(C.c_int32)
 _U32P = C.POINTER(C.c_uint32)
@@ -94,6 +97,7 @@ SIGNATURES = [
     ("we_ensemble_sync", C.c_int32, [_VP, _VP]),
     ("we_ensemble_get", C.c_int32, [_VP, C.c_int32, C.c_int32, _VP, C.c_size_t,
                                     C.POINTER(C.c_size_t), _VP]),
+    ("we_ensemble_fpt_mle", C.c_int32, [_VP, C.c_double, _VP, C.c_size_t, _VP]),
     ("we_run", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, C.POINTER(_VP)]),
     ("we_autotune", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, _I32P, _I32P]),
     ("we_autotune_cache_save", C.c_int32, [C.c_char_p]),

@@ -111,9 +111,10 @@ def we_binmap_grid(species, edges) -> BinMap:
 def make_run_config(tau, m_targ, init_states, init_weights, *, n_runs=None, seed=0, run_ids=None,
                     param_set=None, first_iter=0, capacity=0, record_iters=1, target=None,
                     recycle_state=None, max_steps=0, hist_species=0, hist_len=0, resample=True,
-                    mapping=L.WE_MAP_AUTO, block_threads=0, reweight_period=0):
+                    mapping=L.WE_MAP_AUTO, block_threads=0, reweight_period=0, absorb=False):
     """Build a we_run_config.  init_states: (runs, n_init, S); init_weights: (runs, n_init);
-    target: None or (species list, op list, thresholds (runs, clauses)).  Returns
+    target: None or (species list, op list, thresholds (runs, clauses)); absorb: the target set
+    is absorbing (brute-force first-passage runs, needs resample=False) instead of recycling.  Returns
     (config, keepalive) -- keep the second object alive while the config is used."""
     ist = _i32(init_states)
     iw = _f64(init_weights)
@@ -139,7 +140,7 @@ def make_run_config(tau, m_targ, init_states, init_weights, *, n_runs=None, seed
     if target is not None:
         sp, ops, thr = target
         keep["thr"] = _i32(thr).reshape(R, len(sp))
-        c.feedback = 1
+        c.feedback = L.WE_FEEDBACK_ABSORB if absorb else L.WE_FEEDBACK_RECYCLE
         c.n_clauses = len(sp)
         for k in range(len(sp)):
             c.tgt_species[k] = int(sp[k])
@@ -175,7 +176,8 @@ def run_config_from(cfg, record_iters=None, resample=True, first_iter=None, init
         record_iters=cfg.n_iters if record_iters is None else record_iters, target=tgt,
         recycle_state=cfg.recycle_state, max_steps=cfg.max_steps if max_steps is None else max_steps,
         hist_species=cfg.hist_species, hist_len=cfg.hist_len, resample=resample, mapping=mapping,
-        block_threads=block_threads, reweight_period=getattr(cfg, "reweight_period", 0) if resample else 0)
+        block_threads=block_threads, reweight_period=getattr(cfg, "reweight_period", 0) if resample else 0,
+        absorb=bool(getattr(cfg, "absorb", False)))
 
 
 _OUT_DTYPES = {
@@ -184,7 +186,7 @@ _OUT_DTYPES = {
     L.WE_OUT_NWALKERS: np.int32, L.WE_OUT_EVENTS: np.int64, L.WE_OUT_HIST: np.float64,
     L.WE_OUT_STATUS: np.int32, L.WE_OUT_ITER: np.int32, L.WE_OUT_RECORDED: np.int32,
     L.WE_OUT_TLAST: np.float64, L.WE_OUT_Z: np.float32, L.WE_OUT_NREC: np.int32,
-    L.WE_OUT_RW: np.int32,
+    L.WE_OUT_RW: np.int32, L.WE_OUT_FPT: np.float64,
 }
 
 
@@ -278,6 +280,18 @@ class Ensemble:
     def iteration(self) -> int:
         return int(self.get(L.WE_OUT_ITER)[0])
 
+    def first_passage(self, run: int = 0):
+        """Absorbing ensembles: each walker's first-passage time from the run's start (-1: none)."""
+        return self.get(L.WE_OUT_FPT, run)
+
+    def fpt_mle(self, T: float = 0.0, stream=None) -> np.ndarray:
+        """Brute-force transition time of every run (Sec. II.C, Eq. "mld") from the first-passage
+        times in [0, T] (T <= 0: the time simulated so far): rows (N, n, sum t_i, mu, sigma)."""
+        out = np.zeros((self.n_runs, 5))
+        check(lib().we_ensemble_fpt_mle(self.h, float(T), C.c_void_p(out.ctypes.data), out.nbytes,
+                                        _stream_handle(stream)))
+        return out
+
 
 def we_ensemble_workspace_bytes(net: Network, bins: BinMap, cfg) -> int:
     n = C.c_size_t()
@@ -350,16 +364,45 @@ def autotune_cache_clear():
     lib().we_autotune_cache_clear()
 
 
+def _require_cuda_tensor(t, dtype, min_numel: int, name: str, device=None):
+    """Raise WEError(WE_EINVAL) unless t is a contiguous CUDA tensor of `dtype` with at least
+    `min_numel` elements (on `device` when given).  The C entry points take raw device pointers
+    and cannot check any of this themselves."""
+    import torch
+    ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+          and t.numel() >= min_numel and (device is None or t.device == device))
+    if not ok:
+        desc = (f"{getattr(t, 'dtype', type(t).__name__)} on {getattr(t, 'device', '?')}, "
+                f"{getattr(t, 'numel', lambda: '?')()} elements")
+        raise L.WEError(L.WE_EINVAL, f"{name} must be a contiguous CUDA {dtype} tensor with at "
+                                     f"least {min_numel} elements on {device or 'a CUDA device'} ({desc})")
+
+
 def we_resample_static(bins, weights, n_bins: int, m_targ: int, iteration: int, seed: int,
                        run_id: int, out_weights, out_parent, out_count, stream=None):
     """Split/merge of one run held in device tensors, with no allocation by the library
-    (for callers that may not allocate device memory).  Arguments are CUDA tensors: bins int32,
-    weights float64, out_weights float64 and out_parent int32 of the same capacity, out_count
-    int32[1] (new count, or a negative status)."""
+    (for callers that may not allocate device memory).  Arguments are contiguous CUDA tensors on
+    the current device: bins int32 and weights float64 of n entries; out_weights float64 and
+    out_parent int32 with the same capacity (out_weights.numel()); out_count int32[>= 1], which
+    receives the new count or a negative status.  Anything else raises WEError(WE_EINVAL) before
+    the library is called."""
+    import torch
+    _require_cuda_tensor(bins, torch.int32, 1, "bins")
+    dev = bins.device
+    if dev.index != torch.cuda.current_device():
+        raise L.WEError(L.WE_EINVAL, f"bins is on {dev}, not on the current device "
+                                     f"cuda:{torch.cuda.current_device()}")
     n = int(bins.numel())
+    _require_cuda_tensor(weights, torch.float64, n, "weights", dev)
+    if weights.numel() != n:
+        raise L.WEError(L.WE_EINVAL, f"weights has {weights.numel()} entries for {n} bins")
+    _require_cuda_tensor(out_weights, torch.float64, 1, "out_weights", dev)
+    cap = int(out_weights.numel())
+    _require_cuda_tensor(out_parent, torch.int32, cap, "out_parent", dev)
+    _require_cuda_tensor(out_count, torch.int32, 1, "out_count", dev)
     check(lib().we_resample_static(n, C.c_void_p(bins.data_ptr()), C.c_void_p(weights.data_ptr()),
                                    int(n_bins), int(m_targ), int(iteration), int(seed), int(run_id),
-                                   int(out_weights.numel()), C.c_void_p(out_weights.data_ptr()),
+                                   cap, C.c_void_p(out_weights.data_ptr()),
                                    C.c_void_p(out_parent.data_ptr()), C.c_void_p(out_count.data_ptr()),
                                    _stream_handle(stream)))
 

@@ -29,6 +29,7 @@ cudaError_t launch_build_table(const NetView &N, const int32_t *base, int specie
 size_t propagate_warp_smem(const NetView &N, int block);
 cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st);
+cudaError_t launch_fpt_mle(const EnsView &E, double T, double *out, cudaStream_t st);
 cudaError_t launch_pack_states(const EnsView &E, int r, int32_t *out, cudaStream_t st);
 cudaError_t launch_learned_bins(const PropagateParams &prm, cudaStream_t st);
 size_t learned_bins_smem(int n_in, int H);
@@ -350,7 +351,7 @@ struct Layout {
 struct Offsets {
   size_t meta, keff, Kn, d_sp, d_val, dep_ptr, dep_idx, edges;
   size_t run_id, param_set, tgt_thr, recycle;
-  size_t x0, x1, w0, w1, p0, p1, bin, nrec, tlast;
+  size_t x0, x1, w0, w1, p0, p1, bin, nrec, tlast, fpt, mle;
   size_t count, prev_count, run_off, status, iter, bin_count, n_tasks, tasks, cursor, sorted_slot, sorted_w, alive, div_magic;
   size_t flux, totw, nw, events, hist, pack;
   size_t logt, table, base;
@@ -482,6 +483,8 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
   o.bin = L.take(4 * RC);
   o.nrec = L.take(4 * RC);
   o.tlast = L.take(8 * RC);
+  o.fpt = c->feedback == WE_FEEDBACK_ABSORB ? L.take(8 * RC) : 0;
+  o.mle = c->feedback == WE_FEEDBACK_ABSORB ? L.take(8 * 5 * R) : 0;
   o.count = L.take(4 * R);
   o.prev_count = L.take(4 * R);
   o.run_off = L.take(4 * (R + 1));
@@ -550,6 +553,10 @@ static we_status check_config(const we_network *n, const we_binmap *b, const we_
   long long cap = c->capacity > 0 ? c->capacity : std::max<long long>((long long)c->m_targ * b->n_bins, c->n_init);
   if (cap < c->n_init) return fail(WE_EINVAL, "capacity %lld < n_init %d", cap, c->n_init);
   if (cap * c->n_runs > (1ll << 30)) return fail(WE_EINVAL, "runs x capacity too large");
+  if (c->feedback < 0 || c->feedback > WE_FEEDBACK_ABSORB)
+    return fail(WE_EINVAL, "feedback must be 0, WE_FEEDBACK_RECYCLE or WE_FEEDBACK_ABSORB");
+  if (c->feedback == WE_FEEDBACK_ABSORB && c->resample)
+    return fail(WE_EINVAL, "an absorbing target (brute-force runs) needs resample = 0");
   if (c->feedback) {
     if (c->n_clauses < 1 || c->n_clauses > kMaxClauses || !c->tgt_threshold) return fail(WE_EINVAL, "feedback needs 1..4 target clauses with thresholds");
     for (int k = 0; k < c->n_clauses; ++k) {
@@ -646,7 +653,7 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
     for (int sp = 0; sp < S; ++sp)
       rec[(size_t)r * S + sp] = c->recycle_state ? c->recycle_state[(size_t)r * S + sp] : c->init_states[(size_t)r * c->n_init * S + sp];
   }
-  if (c->feedback)
+  if (c->feedback == WE_FEEDBACK_RECYCLE)
     for (int r = 0; r < R; ++r) {
       bool in = true;
       for (int k = 0; k < c->n_clauses; ++k) {
@@ -703,6 +710,8 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   e = e ? e : up(o.prev_count, cnt.data(), 4 * R);
   e = e ? e : up(o.run_off, roff.data(), 4 * (R + 1));
   e = e ? e : up(o.iter, &it0, 4);
+  std::vector<double> fpt0(c->feedback == WE_FEEDBACK_ABSORB ? RC : 0, -1.0);   // no first passage yet
+  e = e ? e : up(o.fpt, fpt0.data(), 8 * fpt0.size());
   std::vector<int32_t> base(S, 0);
   for (int sp = 0; sp < S; ++sp) base[sp] = n->fixed[sp] >= 0 ? n->fixed[sp] : 0;
   e = e ? e : up(o.base, base.data(), 4 * S);
@@ -754,7 +763,7 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   EnsView &V = E->prm.ens;
   V.R = R; V.cap = cap; V.S = S; V.m_targ = c->m_targ; V.record_iters = c->record_iters;
   V.first_iter = c->first_iter; V.hist_species = c->hist_species; V.hist_len = c->hist_len;
-  V.feedback = c->feedback ? 1 : 0; V.n_clauses = c->feedback ? c->n_clauses : 0;
+  V.feedback = c->feedback; V.n_clauses = c->feedback ? c->n_clauses : 0;
   for (int k = 0; k < kMaxClauses; ++k) { V.tgt_species[k] = c->tgt_species[k]; V.tgt_op[k] = c->tgt_op[k]; }
   V.max_steps = c->max_steps > 0 ? c->max_steps : WE_DEFAULT_MAX_STEPS;
   V.tau = c->tau; V.seed = c->seed;
@@ -766,6 +775,7 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   V.w[0] = at<double>(ws, o.w0); V.w[1] = at<double>(ws, o.w1);
   V.parent[0] = at<int32_t>(ws, o.p0); V.parent[1] = at<int32_t>(ws, o.p1);
   V.bin = at<int32_t>(ws, o.bin); V.nrec = at<int32_t>(ws, o.nrec); V.tlast = at<double>(ws, o.tlast);
+  V.fpt = c->feedback == WE_FEEDBACK_ABSORB ? at<double>(ws, o.fpt) : nullptr;
   V.count = at<int32_t>(ws, o.count); V.prev_count = at<int32_t>(ws, o.prev_count);
   V.run_off = at<int32_t>(ws, o.run_off);
   V.status = at<int32_t>(ws, o.status); V.iter = at<int32_t>(ws, o.iter);
@@ -1055,6 +1065,8 @@ extern "C" we_status we_ensemble_checkpoint(we_ensemble *E, void *dst, size_t ds
                                             void *stream) {
   if (!E) return fail(WE_EINVAL, "ensemble is NULL");
   if (E->phase_propagated) return fail(WE_EINVAL, "checkpoint called between propagate and resample");
+  if (E->cfg.feedback == WE_FEEDBACK_ABSORB)
+    return fail(WE_ENOTSUPPORTED, "checkpoints do not carry the first-passage times of an absorbing ensemble");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   WE_CUDA_TRY(cudaStreamSynchronize(s));
   const int R = E->cfg.n_runs, S = E->S;
@@ -1259,10 +1271,30 @@ extern "C" we_status we_ensemble_get(we_ensemble *E, int32_t what, int32_t run, 
       if (E->prm.rw.period <= 0) return fail(WE_EINVAL, "WE_OUT_RW needs reweight_period > 0");
       return per_iter(E->prm.rw.obs, 4);
     }
+    case WE_OUT_FPT: {
+      if (!V.fpt) return fail(WE_EINVAL, "WE_OUT_FPT needs feedback = WE_FEEDBACK_ABSORB");
+      return per_walker(V.fpt, 8);
+    }
     case WE_OUT_ITER: return scalar(&iter, 4);
     case WE_OUT_RECORDED: { int32_t v = rec; return scalar(&v, 4); }
     default: return fail(WE_EINVAL, "unknown output selector %d", what);
   }
+}
+
+extern "C" we_status we_ensemble_fpt_mle(we_ensemble *E, double T, void *dst, size_t dst_bytes, void *stream) {
+  if (!E) return fail(WE_EINVAL, "ensemble is NULL");
+  if (!E->prm.ens.fpt) return fail(WE_EINVAL, "the MLE needs an absorbing ensemble (feedback = WE_FEEDBACK_ABSORB)");
+  if (E->phase_propagated) return fail(WE_EINVAL, "fpt_mle called between propagate and resample");
+  const int R = E->cfg.n_runs;
+  if (!dst || dst_bytes < (size_t)R * 5 * sizeof(double)) return fail(WE_EINVAL, "dst must hold runs x 5 doubles");
+  if (std::isnan(T) || std::isinf(T)) return fail(WE_EINVAL, "T must be finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *res = at<double>(E->ws, E->off.mle);
+  cudaError_t e = launch_fpt_mle(E->prm.ens, T, res, s);
+  if (e) return cuda_fail(e, "fpt_mle launch");
+  WE_CUDA_TRY(cudaStreamSynchronize(s));
+  WE_CUDA_TRY(cudaMemcpy(dst, res, (size_t)R * 5 * sizeof(double), cudaMemcpyDefault));
+  return WE_OK;
 }
 
 extern "C" we_status we_run(const we_network *n, const we_binmap *b, const we_run_config *c,

@@ -89,7 +89,7 @@ struct EnsView {
   int32_t record_iters;
   int32_t first_iter;
   int32_t hist_species, hist_len;
-  int32_t feedback, n_clauses;
+  int32_t feedback, n_clauses;  // feedback: 0 none, 1 recycle, 2 absorb
   int32_t tgt_species[kMaxClauses];
   int32_t tgt_op[kMaxClauses];
   int64_t max_steps;
@@ -107,6 +107,8 @@ struct EnsView {
   int32_t *bin;                // R*cap  bin of each walker after propagation
   int32_t *nrec;               // R*cap  recycles of each walker in the last interval
   double *tlast;               // R*cap  time of each walker's last event in the last interval
+  double *fpt;                 // R*cap  absorbing runs: first-passage time from the run's start
+                               //        (-1: none yet); null unless feedback = 2
   // per-run bookkeeping
   int32_t *count;              // R      live walkers
   int32_t *prev_count;         // R      walkers propagated in the last interval

@@ -498,6 +498,49 @@ cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st) 
   return cudaGetLastError();
 }
 
+// Brute-force transition time (Sec. II.C, Eq. "mld") of every run of an absorbing ensemble:
+// one block per run.  Thread t sums the first-passage times t_i in [0, T] of slots t, t + 256,
+// ... in slot order, then the 256 partial sums are added in a fixed pairwise order, so the
+// result does not depend on timing.  out[5 r ..] = (N, n, sum t_i, mu, sigma) with
+// mu = (sum t_i + (N - n) T) / n and sigma = mu / sqrt(n) (+inf for both when n = 0).
+__global__ void __launch_bounds__(256) k_fpt_mle(EnsView E, double T, double *out) {
+  __shared__ double s_sum[256];
+  __shared__ int s_n[256];
+  const int r = blockIdx.x, t = threadIdx.x;
+  const int N = E.count[r];
+  const double Tr = T > 0.0 ? T : __dmul_rn((double)*E.iter, E.tau);
+  const double *f = E.fpt + (size_t)r * E.cap;
+  double sum = 0.0;
+  int n = 0;
+  for (int w = t; w < N; w += 256) {
+    const double v = f[w];
+    if (v >= 0.0 && v <= Tr) { sum = __dadd_rn(sum, v); ++n; }
+  }
+  s_sum[t] = sum;
+  s_n[t] = n;
+  __syncthreads();
+  for (int h = 128; h >= 1; h >>= 1) {
+    if (t < h) { s_sum[t] = __dadd_rn(s_sum[t], s_sum[t + h]); s_n[t] += s_n[t + h]; }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const int nn = s_n[0];
+    const double st = s_sum[0];
+    double mu = __longlong_as_double(0x7ff0000000000000ll), sg = mu;
+    if (nn > 0) {
+      mu = __ddiv_rn(__dadd_rn(st, __dmul_rn((double)(N - nn), Tr)), (double)nn);
+      sg = __ddiv_rn(mu, __dsqrt_rn((double)nn));
+    }
+    double *o = out + 5 * (size_t)r;
+    o[0] = (double)N; o[1] = (double)nn; o[2] = st; o[3] = mu; o[4] = sg;
+  }
+}
+
+cudaError_t launch_fpt_mle(const EnsView &E, double T, double *out, cudaStream_t st) {
+  k_fpt_mle<<<E.R, 256, 0, st>>>(E, T, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack_states(const EnsView &E, int r, int32_t *out, cudaStream_t st) {
   k_pack_states<<<152, 256, 0, st>>>(E, r, out);
   return cudaGetLastError();

@@ -196,6 +196,7 @@ __device__ __forceinline__ void finish_walker(const PropagateParams &prm, int r,
   for (int s = 0; s < E.S; ++s) X[(size_t)s * ld + g] = xme[s * B];
   E.nrec[g] = nrec;
   E.tlast[g] = t;
+  if (E.fpt) record_first_passage(E, r, g, xme, B, nrec, t);
   if (status) atomicCAS(&E.status[r], 0, status);
   if (!prm.bins.learned) {
     const int b = bin_of(prm.bins, xme, B);
@@ -261,7 +262,8 @@ __global__ void __launch_bounds__(128) k_propagate_direct(PropagateParams prm) {
   int nrec = 0, status = 0;
   DrawQueue dq;
   dq.init((uint32_t)iter, (uint32_t)w, k0, k1, *sm.logt);
-  for (;;) {
+  const bool absorbed = E.feedback == 2 && in_target(E, r, xme, B);
+  for (; !absorbed;) {
     const double a0 = nd[1];
     if (bits(a0) == 0) break;                        // nothing can fire: idle to tau
     unsigned long long m2;
@@ -292,6 +294,7 @@ __global__ void __launch_bounds__(128) k_propagate_direct(PropagateParams prm) {
     t = tn;
     if (E.feedback && in_target(E, r, xme, B)) {
       ++nrec;
+      if (E.feedback == 2) break;                    // absorbed at its first passage
       for (int s = 0; s < E.S; ++s) xme[s * B] = E.recycle[r * E.S + s];
     }
     rebuild();
@@ -358,7 +361,8 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
   int nrec = 0, status = 0;
   DrawQueue dq;
   dq.init((uint32_t)iter, (uint32_t)w, k0, k1, *sm.logt);
-  for (;;) {
+  const bool absorbed = E.feedback == 2 && in_target(E, r, xme, B);
+  for (; !absorbed;) {
     if (row.idle()) break;                           // nothing can fire: idle to tau
     unsigned long long m2;
     float2 e;
@@ -377,6 +381,7 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
     clk += dt;
     if (E.feedback && in_target(E, r, xme, B)) {
       ++nrec;
+      if (E.feedback == 2) break;                    // absorbed at its first passage
       for (int s = 0; s < E.S; ++s) xme[s * B] = E.recycle[r * E.S + s];
       x = xme[sx * B];
       y = sy >= 0 ? xme[sy * B] : 0;
@@ -460,6 +465,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
   if (warp == 0 && live) {
     for (int s = 0; s < E.S; ++s) xme[s * W] = E.x[par][(size_t)s * ld + g];
     rebuild();
+    if (E.feedback == 2 && in_target(E, r, xme, W)) done = true;   // already absorbed
   }
 
   for (int round = 0;; ++round) {
@@ -495,6 +501,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
         t = tn;
         if (E.feedback && in_target(E, r, xme, W)) {
           ++nrec;
+          if (E.feedback == 2) { done = true; break; }             // absorbed at its first passage
           for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
         }
         rebuild();
@@ -634,8 +641,18 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
     }
   };
   produce(0, 0u, warp, 4);                               // round 0: all four warps
+  // absorbing target: a walker that starts the interval inside it fires nothing
+  bool absorbed0 = false;
+  if (warp == 1 && live && E.feedback == 2) {
+    absorbed0 = true;
+    for (int c = 0; c < E.n_clauses; ++c) {
+      const int v = E.x[par][(size_t)E.tgt_species[c] * ld + g];
+      const int thr = E.tgt_thr[r * E.n_clauses + c];
+      absorbed0 = absorbed0 && (E.tgt_op[c] == 0 ? v >= thr : v <= thr);
+    }
+  }
   if (warp == 1) {
-    s_done[1][lane] = !live;
+    s_done[1][lane] = !live || absorbed0;
     if (lane == 0) s_more[1] = 1;
   }
 
@@ -668,7 +685,7 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
   unsigned long long clk = 0;                           // clock units of tau / 2^62
   long long nev = 0;
   int xc = 0, yc = 0, nrec = 0, status = 0;
-  bool done = !live, recycled = false;
+  bool done = !live || absorbed0, recycled = false;
   if (live && warp <= 1) {
     if (warp == 0)
       for (int s = 0; s < E.S; ++s) xme[s * W] = E.x[par][(size_t)s * ld + g];
@@ -721,7 +738,8 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
           int nx = x + dx, ny = D == 2 ? y + dy : 0;
           if (nx > kMaxCount || ny > kMaxCount) { ovf_m |= 1u << k; nx = x; ny = y; }
           if (E.feedback && ok && nx >= xlo && nx <= xhi && (D == 1 || (ny >= ylo && ny <= yhi))) {
-            rec_m |= 1u << k; nx = xrec; ny = yrec; ok = ok_rec;
+            rec_m |= 1u << k;
+            if (E.feedback == 1) { nx = xrec; ny = yrec; ok = ok_rec; }   // absorbing: stays inside
           }
           sx[(sb * K + k) * W + lane] = nx;
           if (D == 2) sy[(sb * K + k) * W + lane] = ny;
@@ -793,7 +811,9 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
           const uint32_t rec_m = sfl[(pb * 3 + 2) * W + lane];
           const long long room = E.max_steps - nev;       // draws that may still fire
           const uint32_t cap_m = room >= K ? 0u : ((0xffffu << (int)room) & 0xffffu);
-          const uint32_t quiet_m = idle_m | far_m | over_m;
+          // absorbing target: nothing fires after the draw that enters it
+          const uint32_t absorb_m = E.feedback == 2 ? ((rec_m << 1) & 0xffffu) : 0u;
+          const uint32_t quiet_m = idle_m | far_m | over_m | absorb_m;
           const uint32_t stop_m = (quiet_m | cap_m | ovf_m) & 0xffffu;
           const int kstop = stop_m ? __ffs(stop_m) - 1 : K;
           const uint32_t fired = (1u << kstop) - 1u;
@@ -804,6 +824,7 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
           nev += kstop;
           nrec += __popc(rec_m & fired);
           recycled = recycled || (rec_m & fired) != 0u;
+          if (E.feedback == 2 && (rec_m & fired)) done = true;
           if (kstop > 0) {
             xc = sx[(pb * K + kstop - 1) * W + lane];
             if (D == 2) yc = sy[(pb * K + kstop - 1) * W + lane];
@@ -828,7 +849,7 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
     if (!s_more[p & 1]) break;
   }
   if (warp == 1 && live) {
-    if (recycled)                                        // the other species take the recycle state
+    if (recycled && E.feedback == 1)                     // the other species take the recycle state
       for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
     xme[TV.species * W] = xc;
     if (D == 2) xme[TV.species2 * W] = yc;

@@ -126,6 +126,18 @@ __device__ __forceinline__ bool in_target(const EnsView &E, int r, const int32_t
   return in;
 }
 
+// Absorbing runs (feedback 2; the brute-force transition-time runs of Sec. II.C): the first-
+// passage time of the walker in slot g from the run's start, fl(fl(iter tau) + t) for an
+// entrance at time t of this interval.  A walker inside the target set that did not enter it in
+// this interval was inside at the interval's start: its time is the start, fl(iter tau).
+__device__ __forceinline__ void record_first_passage(const EnsView &E, int r, int g, const int32_t *xs,
+                                                     int stride, int nrec, double t) {
+  if (!(E.fpt[g] < 0.0)) return;
+  const double t0 = __dmul_rn((double)*E.iter, E.tau);
+  if (nrec) E.fpt[g] = __dadd_rn(t0, t);
+  else if (in_target(E, r, xs, stride)) E.fpt[g] = t0;
+}
+
 __device__ __forceinline__ int find_run(const int32_t *run_off, int R, int f) {
   int lo = 0, hi = R;
   while (hi - lo > 1) {

@@ -33,6 +33,7 @@ __device__ __forceinline__ void finish_walker_warp(const PropagateParams &prm, i
   if (lane != 0) return;
   E.nrec[g] = nrec;
   E.tlast[g] = t;
+  if (E.fpt) record_first_passage(E, r, g, xs, 1, nrec, t);
   if (status) atomicCAS(&E.status[r], 0, status);
   if (!prm.bins.learned) {
     const int b = bin_of(prm.bins, xs, 1);
@@ -172,7 +173,9 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
   float2 my_e = make_float2(0.f, 0.f);
   ssa_draw((uint32_t)lane, (uint32_t)iter, (uint32_t)w, k0, k1, T, my_m, my_e);
   int used = 0;
-  for (;;) {
+  // absorbing target: a walker that starts the interval inside it fires nothing
+  const bool absorbed = E.feedback == 2 && in_target(E, r, xs, 1);
+  for (; !absorbed;) {
     const double a0 = nd[1];
     if (bits(a0) == 0) break;
     if (used == 32) {
@@ -250,6 +253,7 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
       }
       if (in) {
         ++nrec;
+        if (E.feedback == 2) break;                     // absorbed at its first passage
         recycled = true;
         __syncwarp();
         for (int s = lane; s < E.S; s += 32) xs[s] = E.recycle[r * E.S + s];
