@@ -48,7 +48,13 @@ DISCARD = 300              # iterations before the flux average (steady state, S
 # 32-lane instruction per clock x 2.07 GHz.
 OPS_PER_EVENT = 210
 ISSUE_PEAK_GOPS = 152 * 4 * 32 * 2.07
-KERNELS_PER_ITER = 6       # SSA, bin scan, placement, split/merge, gather, finalize
+# Algorithmic FP64 operations of one direct-method event of the Schloegl model (four reactions):
+# four propensity products, three tree additions, the target u2 * a0, two descent subtractions,
+# the division dt = -log(u1) / a0 and the clock addition -- 12, plus one logarithm.
+FP64_OPS_PER_EVENT_SCHLOGL = 12
+# kernels of one WE iteration of networks with at most 8 species (the split/merge kernel copies
+# the species counts): SSA, bin scan, placement, split/merge, finalize
+KERNELS_PER_ITER = 5
 # DRAM bytes (read + write) of one SSA launch on this workload, from an ncu capture of the
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum, mean of two 16,000-walker launches, as
 # in every timed launch)
@@ -67,8 +73,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the SSA kernel (0: auto)")
     ap.add_argument("--workload", choices=["schlogl", "toggle_learned", "toggle_batch", "synthetic_large",
-                                           "schlogl_flux"],
+                                           "schlogl_flux", "schlogl_e50", "birth_death"],
                     default="schlogl")
+    ap.add_argument("--report-iter", type=int, default=-1,
+                    help="also report the SSA events of this iteration of the first timed step (for ncu)")
     ap.add_argument("--batch-iters", type=int, default=0,
                     help="toggle_batch / synthetic_large: WE iterations per step (0: 500 / 100)")
     ap.add_argument("--plain-iters", type=int, default=120000, help="toggle_learned: plain-binning iterations")
@@ -90,15 +98,38 @@ def exact_mfpt():
 # ------------------------------------------------------------------------------------------
 # CPU oracle leg (the only place besides --impl reference where bench.py runs oracle/)
 # ------------------------------------------------------------------------------------------
+def host_cpu() -> dict:
+    """This host's logical core count and CPU model (lscpu's model name, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model}
+
+
 def _oracle_sample(args):
-    replica, n_iters, seed = args
+    replica, n_iters, seed = args[:3]
+    depgraph = len(args) > 3 and args[3]
     import numpy as np  # noqa: F401
     import workloads as W
     from oracle import oracle as O
     cfg = W.schlogl_mfpt_we(n_iters=n_iters, n_runs=1, seed=seed)
     cfg.run_ids = np.array([replica], dtype=np.uint32)
     t0 = time.perf_counter()
-    o = O.we_run(cfg, 0)
+    o = O.we_run(cfg, 0, depgraph=depgraph)
     return int(o["events"].sum()), time.perf_counter() - t0
 
 
@@ -107,12 +138,12 @@ def _calibrate():
     return ev / dt, ev / 40.0
 
 
-def _oracle_pool_run(cores: int, n_iters: int, seed: int):
+def _oracle_pool_run(cores: int, n_iters: int, seed: int, depgraph: bool = False):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_sample, [(r, n_iters, seed) for r in range(cores)])
+        res = pool.map(_oracle_sample, [(r, n_iters, seed, depgraph) for r in range(cores)])
     return sum(e for e, _ in res), time.perf_counter() - t0
 
 
@@ -126,9 +157,71 @@ def cpu_baseline(seconds: float, replicas: int):
     rate, per_iter = _calibrate()
     n_iters = int(max(40, min(ITERS, seconds * rate / max(per_iter * 2.5, 1.0))))
     events, wall = _oracle_pool_run(cores, n_iters, 0)
+    ev_dg, wall_dg = _oracle_pool_run(cores, n_iters, 0, depgraph=True)
     return {"value": events / wall, "unit": "SSA events/s", "cores": cores, "kind": "oracle",
             "sample": f"{cores} replica(s) x first {n_iters} of {ITERS} iterations of the workload, "
-                      f"one host process each; {events} events in {wall:.1f} s"}
+                      f"one host process each; {events} events in {wall:.1f} s", **host_cpu(),
+            "depgraph": {"value": ev_dg / wall_dg, "unit": "SSA events/s", "cores": cores,
+                         "kind": "dependency-graph CPU SSA (same results as the oracle)",
+                         "sample": f"the same sample; {ev_dg} events in {wall_dg:.1f} s"}}
+
+
+def _batch_cpu_task(args):
+    """One CPU sample task of the batched or large-network workloads: (kind, item, n_iters,
+    depgraph) -> (events, seconds).  toggle: the first n_iters iterations of run `item` of the
+    64-run sweep; synthetic: `n_iters` intervals of plain propagation of walker `item` of the
+    4096 from its initial state (iteration i, slot item)."""
+    kind, item, n_iters, depgraph = args
+    import workloads as W
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    if kind == "toggle":
+        cfg = W.toggle_batch_we(n_runs=64, n_iters=n_iters, seed=0)
+        ev = int(O.we_run(cfg, item, n_iters=n_iters, depgraph=depgraph)["events"].sum())
+    else:
+        cfg = W.synthetic_large_we(n_walkers=4096, n_iters=n_iters)
+        net = O.Network(cfg.network)
+        x = cfg.init_states[0, item]
+        ev = 0
+        for it in range(n_iters):
+            x, e, _, _ = O.propagate_one(cfg, x, it, item, net=net, depgraph=depgraph)
+            ev += e
+    return ev, time.perf_counter() - t0
+
+
+def batch_cpu_baseline(kind: str):
+    """CPU figures (SSA events/s on this host's cores) for the toggle sweep and the large network:
+    the oracle and the dependency-graph CPU SSA on a bounded sample of the same workload, one
+    spawned process per core, before any GPU work."""
+    import multiprocessing as mp
+    from oracle import build as obuild
+    obuild.build()
+    cores = os.cpu_count() or 1
+    if kind == "toggle":
+        items, n_iters = list(range(min(64, cores))), 300
+        what = f"{len(items)} of the 64 toggle runs x their first {n_iters} iterations (WE, resampling included)"
+    else:
+        items, n_iters = list(range(64)), 2
+        what = f"64 of the 4096 walkers x {n_iters} intervals of tau=0.01 from their initial states (SSA only)"
+    out = {}
+    ctx = mp.get_context("spawn")
+    for dg in (False, True):
+        t0 = time.perf_counter()
+        with ctx.Pool(min(cores, len(items))) as pool:
+            res = pool.map(_batch_cpu_task, [(kind, i, n_iters, dg) for i in items])
+        wall = time.perf_counter() - t0
+        ev = sum(e for e, _ in res)
+        out["depgraph" if dg else "oracle"] = {"value": ev / wall, "events": ev, "wall_s": wall,
+                                               "per_event_core_us": 1e6 * sum(t for _, t in res) / max(ev, 1)}
+    o = out["oracle"]
+    return {"value": o["value"], "unit": "SSA events/s", "cores": min(cores, len(items)), "kind": "oracle",
+            "sample": what + f"; {o['events']} events in {o['wall_s']:.1f} s", **host_cpu(),
+            "per_event_core_us": o["per_event_core_us"],
+            "depgraph": {"value": out["depgraph"]["value"], "unit": "SSA events/s",
+                         "kind": "dependency-graph CPU SSA (same results as the oracle)",
+                         "per_event_core_us": out["depgraph"]["per_event_core_us"],
+                         "sample": f"the same sample; {out['depgraph']['events']} events in "
+                                   f"{out['depgraph']['wall_s']:.1f} s"}}
 
 
 # ------------------------------------------------------------------------------------------
@@ -207,7 +300,7 @@ def run_reference(a):
     v = tot_ev / tot_s
     cb = {"value": v, "unit": "SSA events/s", "cores": cores, "kind": "oracle",
           "sample": f"per step {cores} replica(s) x first {n_iters} of {a.iters} iterations, one host "
-                    f"process each; {tot_ev} events in {tot_s:.1f} s over {a.steps} steps"}
+                    f"process each; {tot_ev} events in {tot_s:.1f} s over {a.steps} steps", **host_cpu()}
     line = {"impl": "reference", "metric": "SSA events/sec and WE iterations/sec on 1 GB300; MFPT rel. error per GPU-s",
             "value": v, "unit": "SSA events/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * tot_s / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -394,6 +487,7 @@ def fp64_ops_per_event(spec, dep_degree):
 
 
 def run_batch_workload(a):
+    cb = None if a.no_cpu_baseline else batch_cpu_baseline("toggle" if a.workload == "toggle_batch" else "synthetic")
     import numpy as np
     import torch
     import paper_1303_5986_gb300 as P
@@ -478,7 +572,8 @@ def run_batch_workload(a):
                      "avg_launch_ms": prop_total_ms / max(n_launch, 1),
                      "share_of_step": ssa_ms_est / total_ms, "fp64_ops_per_event": ops,
                      "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz"},
-        "cpu_baseline": None, "e2e": None, "gpu_launches": 6 * n_iters * a.steps, "clocks": clk,
+        "cpu_baseline": cb, "e2e": None, "gpu_launches": (6 if a.workload == "synthetic_large" else 5) * n_iters * a.steps,
+        "clocks": clk,
     }
     print(json.dumps(line))
 
@@ -563,6 +658,197 @@ def run_schlogl_flux(a):
     print(json.dumps(line))
 
 
+
+# ------------------------------------------------------------------------------------------
+# E50%: brute-force SSA against WE on the Schloegl MFPT (Sec. II.C, Sec. III.B.3)
+# ------------------------------------------------------------------------------------------
+def _settled(err, tol=0.5):
+    """First index from which every later entry of err is <= tol (None if the last is not)."""
+    bad = [k for k, v in enumerate(err) if not (v <= tol)]
+    if not bad:
+        return 0
+    return None if bad[-1] == len(err) - 1 else bad[-1] + 1
+
+
+def run_schlogl_e50(a):
+    """E50% of Sec. II.C measured on GB300: the dynamics time (simulated seconds of all segments
+    or runs) brute-force SSA and WE need before their MFPT estimates stay within 50 % of the
+    exact value, for the Schloegl transition 82 -> X >= 563 (50,308 s).
+      brute force: 128 campaigns of 16 SSA runs from X = 82, absorbed at X >= 563, up to
+        1e5 s each; for run lengths T' on a grid the library's Eq. "mld" MLE per campaign
+        (we_ensemble_fpt_mle with T'), whose dynamics time is sum_i min(t_i, T') = n mu;
+      WE: the paper's flux runs (80 bins of width 10 x 32 walkers, tau = 0.1, recycling
+        82 <- X >= 563) with reweighting every 2, 5 and 100 iterations and without, 32
+        replicas each; the running MFPT of a replica after iteration i is tau / mean flux over
+        iterations i/2 .. i, its dynamics time tau x the walkers propagated so far.
+    A method has settled when the median over campaigns / replicas of |estimate / exact - 1|
+    stays <= 0.5 from then on; its dynamics time is the median at that point.  value = brute
+    force / WE (the paper's E50%, ~500 with reweighting); GPU seconds per campaign / replica
+    from CUDA events around every iteration of the batched launches are reported beside it."""
+    import numpy as np
+    import torch
+    import paper_1303_5986_gb300 as P
+    import workloads as W
+    from paper_1303_5986_gb300 import build as pbuild
+
+    pbuild.build()
+    with open(os.path.join(ROOT, "tests", "golden", "exact_values.json")) as f:
+        exact = json.load(f)["schlogl_mfpt_82_to_563_s"]
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    # brute force
+    n_camp, n_per, tau_bf, it_bf = 128, 16, 50.0, 2000
+    bcfg = W.schlogl_bruteforce(n_walkers=n_per, tau=tau_bf, n_iters=it_bf, n_runs=n_camp, seed=11,
+                                x0=82, threshold=563)
+    net = P.network_from_spec(bcfg.network)
+    one = P.we_binmap_grid(bcfg.bins.species, bcfg.bins.edges)
+    c, keep = P.run_config_from(bcfg, record_iters=it_bf, resample=False)
+    ens = P.we_ensemble_create(net, one, c, keep)
+    ms_bf = ens.step_timed(it_bf, every=1)                 # SSA kernel time per interval
+    ens.sync()
+    grid = np.unique(np.concatenate([np.geomspace(100.0, tau_bf * it_bf, 120), [tau_bf * it_bf]]))
+    err_bf, dyn_bf = [], []
+    for Tp in grid:
+        m = ens.fpt_mle(float(Tp))                         # (N, n, sum t, mu, sigma) per campaign
+        err_bf.append(float(np.median(np.abs(m[:, 3] / exact - 1.0))))
+        dyn_bf.append(float(np.median(m[:, 2] + (m[:, 0] - m[:, 1]) * Tp)))
+    kb = _settled(err_bf)
+    bf_events = float(ens.per_iter(P.WE_OUT_EVENTS).sum())
+    ens.close()
+    ssa_bf_ms = np.cumsum(ms_bf)
+    bf = {"campaigns": n_camp, "runs_per_campaign": n_per, "max_run_s": tau_bf * it_bf,
+          "settled_run_length_s": None if kb is None else float(grid[kb]),
+          "dynamics_s_to_50pct": None if kb is None else dyn_bf[kb],
+          "gpu_s_per_campaign_to_50pct": None if kb is None else
+          float(ssa_bf_ms[min(it_bf, int(np.ceil(grid[kb] / tau_bf))) - 1]) * 1e-3 / n_camp,
+          "ssa_events": bf_events, "ssa_gpu_s": float(ssa_bf_ms[-1]) * 1e-3,
+          "median_rel_err_at_max_length": err_bf[-1]}
+    # weighted ensemble, per reweighting schedule
+    R, n_it = 32, 500
+    we = {}
+    for period in (0, 100, 5, 2):
+        cfg = W.schlogl_flux_we(reweight_period=period, n_iters=n_it, n_runs=R, seed=13)
+        bm = P.we_binmap_grid(cfg.bins.species, cfg.bins.edges)
+        c, keep = P.run_config_from(cfg, record_iters=n_it)
+        e = P.we_ensemble_create(net, bm, c, keep)
+        ms = e.step_timed(n_it, every=1)
+        e.sync()
+        flux = e.per_iter(P.WE_OUT_FLUX)                   # iters x replicas
+        nw = e.per_iter(P.WE_OUT_NWALKERS)
+        prop = np.vstack([np.full((1, R), cfg.m_targ), nw[:-1]])      # walkers propagated per iteration
+        dyn = np.cumsum(prop, axis=0) * cfg.tau
+        err = []
+        for i in range(n_it):
+            f = flux[i // 2:i + 1].mean(axis=0)
+            est = np.where(f > 0, cfg.tau / np.maximum(f, 1e-300), np.inf)
+            err.append(float(np.median(np.abs(est / exact - 1.0))))
+        k = _settled(err)
+        we[f"rw_{period}"] = {
+            "iterations_to_50pct": None if k is None else k + 1,
+            "dynamics_s_to_50pct": None if k is None else float(np.median(dyn[k])),
+            "segments_to_50pct": None if k is None else float(np.median(np.cumsum(prop, axis=0)[k])),
+            "gpu_s_per_replica_to_50pct": None if k is None else float(np.sum(ms[:k + 1])) * 1e-3 / R,
+            "median_rel_err_end": err[-1]}
+        e.close()
+    clk = clocks.stop()
+    ok = {k: v for k, v in we.items() if v["dynamics_s_to_50pct"] is not None}
+    best = min(ok, key=lambda k: ok[k]["dynamics_s_to_50pct"]) if ok else None
+    value = None
+    if best is not None and bf["dynamics_s_to_50pct"] is not None:
+        value = bf["dynamics_s_to_50pct"] / we[best]["dynamics_s_to_50pct"]
+    gpu_ratio = None
+    if best is not None and bf["gpu_s_per_campaign_to_50pct"] is not None:
+        gpu_ratio = bf["gpu_s_per_campaign_to_50pct"] / we[best]["gpu_s_per_replica_to_50pct"]
+    line = {
+        "metric": "E50%: brute-force / WE dynamics time to a Schloegl MFPT within 50% of exact",
+        "value": value, "unit": "x (dynamics-time ratio, Sec. II.C)", "value_schedule": best,
+        "gpu_time_ratio": gpu_ratio, "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+        "data": "synthetic", "vs_baseline": None,
+        "config": {"workload": "Schloegl 82 -> X >= 563 (exact MFPT %.1f s); brute force: 128 campaigns x 16 "
+                               "absorbed SSA runs up to 1e5 s, Eq. \"mld\" MLE on the device; WE: 80 bins of "
+                               "width 10 x 32 walkers, tau=0.1, 500 iterations, 32 replicas, reweighting every "
+                               "2/5/100 iterations or never" % exact},
+        "bruteforce": bf, "we": we, "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------
+# the 1-D birth-death configuration: WE iterations/s against the launch floor
+# ------------------------------------------------------------------------------------------
+def run_birth_death(a):
+    """The 1-D birth-death configuration (kb = 10, kd = 0.1, X0 = 100; 60 bins of width 5 plus
+    overflow, 10 walkers per bin, tau = 0.1, 200 iterations), 10 replicas (run ids 0-9) in one
+    batch per step.  About 2 events per walker per interval: the iteration is launch-latency
+    bound, so its roofline is the measured floor of a CUDA graph of the same number of empty
+    launches (one block per SM each)."""
+    import numpy as np
+    import torch
+    import paper_1303_5986_gb300 as P
+    import workloads as W
+    from paper_1303_5986_gb300 import build as pbuild
+
+    pbuild.build()
+    n_iters, R = a.batch_iters or 200, 10
+    base = W.birth_death_we(n_iters=n_iters, n_runs=R)
+    net = P.network_from_spec(base.network)
+    bm = P.we_binmap_grid(base.bins.species, base.bins.edges)
+    seeds = rank_seeds(0, a.warmup + a.steps)
+
+    def ensemble(seed):
+        c, keep = P.run_config_from(W.birth_death_we(n_iters=n_iters, n_runs=R, seed=seed), record_iters=n_iters)
+        return P.we_ensemble_create(net, bm, c, keep)
+
+    warm = [ensemble(s) for s in seeds[:a.warmup]]
+    timed = [ensemble(s) for s in seeds[a.warmup:]]
+    for e in warm:
+        e.step_timed(n_iters, every=n_iters)
+        e.sync()
+    for e in timed:                       # capture each timed ensemble's graphs before timing
+        e.step_timed(0, every=n_iters)
+    floor_ms = P.measure_graph_floor(KERNELS_PER_ITER, 2000)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    step_ms = []
+    torch.cuda.synchronize()
+    clocks.start()
+    for e in timed:
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e.step_timed(n_iters, every=n_iters)      # the first iteration's SSA launch timed too
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    events = float(sum(e.per_iter(P.WE_OUT_EVENTS).sum() for e in timed))
+    status = sorted(set(int(x) for e in timed for x in e.status()))
+    it_per_s = a.steps * n_iters / (total_ms * 1e-3)
+    per_iter_ms = total_ms / (a.steps * n_iters)
+    line = {
+        "metric": "SSA events/sec and WE iterations/sec on 1 GB300",
+        "value": it_per_s, "unit": "WE iterations/s (10 replicas per iteration)", "n_gpus": 1,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "1-D birth-death kb=10, kd=0.1, X0=100: 60 bins of width 5 + overflow x 10 "
+                               f"walkers, tau=0.1, {n_iters} iterations, 10 replicas per step",
+                   "iterations": n_iters, "l2": "flushed between timed steps (256 MB write)"},
+        "ssa_events_per_s": events / (total_ms * 1e-3), "status": status,
+        "roofline": {"bound": "latency", "achieved": 1.0 / per_iter_ms * 1e3, "peak": 1.0 / floor_ms * 1e3,
+                     "unit": "WE iterations/s", "frac": floor_ms / per_iter_ms, "traffic": None,
+                     "kernel": "whole iteration graph (SSA, bin scan, placement, split/merge, finalize)",
+                     "ms_per_iteration": per_iter_ms, "floor_ms_per_iteration": floor_ms,
+                     "peak_source": f"measured: CUDA graph of {KERNELS_PER_ITER} empty launches of one "
+                                    "block per SM, replayed 2000 times (we_measure_graph_floor)"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": KERNELS_PER_ITER * n_iters * a.steps, "clocks": clk,
+    }
+    print(json.dumps(line))
+
 # ------------------------------------------------------------------------------------------
 # ranks: every rank runs its own replicas (weak scaling, no data-path collective); the job's
 # figures are the slowest rank's time and the sum of every rank's work
@@ -608,6 +894,13 @@ def main():
                               "oracle arm; its baseline is the schedule without reweighting on the same GPU"}))
             return
         run_schlogl_flux(a)
+        return
+    if a.workload in ("schlogl_e50", "birth_death"):
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm is timed on the "
+                              "default Schloegl workload only"}))
+            return
+        (run_schlogl_e50 if a.workload == "schlogl_e50" else run_birth_death)(a)
         return
     if a.workload == "toggle_learned":
         if a.impl == "reference":
@@ -688,6 +981,11 @@ def main():
 
     ev_iter = [e.per_iter(P.WE_OUT_EVENTS).sum(axis=1) for e in timed]   # events per iteration
     events = [int(v.sum()) for v in ev_iter]
+    report_iter = None
+    if 0 <= a.report_iter < a.iters:
+        report_iter = {"iteration": a.report_iter, "ssa_events": int(ev_iter[0][a.report_iter]),
+                       "walkers": int(timed[0].per_iter(P.WE_OUT_NWALKERS)[a.report_iter - 1].sum())
+                       if a.report_iter > 0 else None}
     ev_sampled = float(sum(v[::TIME_EVERY].sum() for v in ev_iter))     # of the timed launches
     fluxes = [e.per_iter(P.WE_OUT_FLUX) for e in timed]              # iters x replicas
     prop_total_ms = float(sum(p.sum() for p in prop_ms))
@@ -706,8 +1004,20 @@ def main():
     prop_s = prop_total_ms * 1e-3
     achieved = OPS_PER_EVENT * ev_sampled / prop_s / 1e9
     ssa_ms_est = prop_total_ms / max(n_launch, 1) * a.iters * a.steps
+    peaks = P.measure_alu_peaks()                     # builder-measured denominators (we_peaks.cu)
+    ev_rate = ev_sampled / prop_s                     # events/s inside the SSA kernel
+    fp64_form = {"achieved": FP64_OPS_PER_EVENT_SCHLOGL * ev_rate / 1e9,
+                 "peak": peaks["fp64_fma_per_s"] / 1e9, "unit": "G FP64 ops/s",
+                 "frac": FP64_OPS_PER_EVENT_SCHLOGL * ev_rate / peaks["fp64_fma_per_s"],
+                 "ops_per_event": FP64_OPS_PER_EVENT_SCHLOGL, "plus_per_event": "one logarithm",
+                 "peak_source": "measured by we_measure_alu_peaks (FP64 FMA lanes/s, this GPU)"}
+    lane_form_measured = {"achieved": achieved, "peak": peaks["ialu_per_s"] / 1e9, "unit": "G lane-ops/s",
+                          "frac": achieved * 1e9 / peaks["ialu_per_s"],
+                          "peak_source": "measured by we_measure_alu_peaks (INT32 xor/add lanes/s)",
+                          "imad_peak": peaks["imad_per_s"] / 1e9}
     roofline = {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK_GOPS, "unit": "G lane-ops/s",
                 "frac": achieved / ISSUE_PEAK_GOPS, "traffic": SSA_TRAFFIC_BYTES,
+                "fp64_form": fp64_form, "lane_form_measured_peak": lane_form_measured,
                 "kernel": "k_propagate_pipe<4,2,1> (state chain / clock / draw warps, state-indexed table)",
                 "launches": n_launch, "launches_sampled": f"every {TIME_EVERY}th iteration",
                 "avg_launch_ms": prop_total_ms / max(n_launch, 1),
@@ -743,7 +1053,7 @@ def main():
             "replica_iters_per_s": we_iters_per_s * a.replicas * world,
             "mfpt_s": mfpt, "mfpt_exact_s": exact, "mfpt_rel_error": rel_err, "mfpt_rel_se": se,
             "mfpt_rel_error_per_gpu_s": rel_err / (total_ms * 1e-3 / a.steps),
-            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "report_iter": report_iter,
             "gpu_launches": KERNELS_PER_ITER * a.iters * a.steps, "clocks": clk,
         }
         print(json.dumps(line))

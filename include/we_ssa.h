@@ -406,6 +406,22 @@ we_status we_resample_static(int32_t n, const int32_t *bins, const double *weigh
                              uint32_t run_id, int32_t capacity, double *out_weights,
                              int32_t *out_parent, int32_t *out_count, void *stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Measured denominators for the kernels' rooflines (not part of the method).
+ *
+ * we_measure_alu_peaks: whole-GPU throughput of FP64 fused multiply-adds, 32-bit integer
+ *   multiply-adds and 32-bit integer ALU operations (xor, add), in lane operations per second,
+ *   each from one CUDA-event-timed launch of independent chains on every SM after a warm-up
+ *   launch.  Allocates 64 bytes of device memory for the duration of the call; synchronises the
+ *   stream.  Errors: WE_EINVAL (NULL output), WE_ECUDA.
+ * we_measure_graph_floor: the launch-latency floor of one WE iteration: milliseconds per replay
+ *   of a CUDA graph of `kernels` (1..64) empty launches of one block per SM, replayed n_replays
+ *   times back to back.  Synchronises the stream.  Errors: WE_EINVAL, WE_ECUDA.
+ * ------------------------------------------------------------------------------------------ */
+we_status we_measure_alu_peaks(void *stream, double *fp64_fma_per_s, double *imad_per_s,
+                               double *ialu_per_s);
+we_status we_measure_graph_floor(int32_t kernels, int32_t n_replays, void *stream, double *ms_per_replay);
+
 /* Autotuner: time the SSA kernel mappings and block sizes on a short probe of this
  * configuration and return the fastest (mapping, block_threads).  Results are cached per
  * (device name, S, M, walker slots, initial walkers) for the life of the process; the cache

@@ -80,6 +80,14 @@ def lib():
         L.orc_resample.restype = C.c_int32
         L.orc_we_run.argtypes = [C.c_void_p, C.POINTER(WEConfigC), C.POINTER(WEOut)]
         L.orc_rw_solve.argtypes = [C.c_int32, _F64P, _F64P, _F64P]
+        L.orc_dg_create.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
+        L.orc_dg_create.restype = C.c_int
+        L.orc_dg_destroy.argtypes = [C.c_void_p]
+        L.orc_propagate_dg.argtypes = [C.c_void_p, C.POINTER(WEConfigC), C.c_int32, C.c_int32, _I32P,
+                                       _I64P, _I32P, _F64P]
+        L.orc_propagate_dg.restype = C.c_int
+        L.orc_we_run_dg.argtypes = [C.c_void_p, C.POINTER(WEConfigC), C.POINTER(WEOut)]
+        L.orc_we_run_dg.restype = C.c_int
         L.orc_rw_solve.restype = C.c_int32
         L.orc_we_run.restype = C.c_int
         _lib = L
@@ -130,9 +138,22 @@ class Network:
         self.S, self.M = spec.n_species, spec.n_reactions
 
     def __del__(self):
+        if getattr(self, "_dg", None) is not None and _lib is not None:
+            _lib.orc_dg_destroy(self._dg)
+            self._dg = None
         if getattr(self, "h", None) and _lib is not None:
             _lib.orc_net_destroy(self.h)
             self.h = None
+
+    def depgraph(self):
+        """The dependency-graph CPU baseline's handle for this network (created once)."""
+        if getattr(self, "_dg", None) is None:
+            h = C.c_void_p()
+            rc = lib().orc_dg_create(self.h, C.byref(h))
+            if rc != 0:
+                raise ValueError(f"dependency graph: {STATUS.get(rc, rc)}")
+            self._dg = h
+        return self._dg
 
     def keff(self, j: int) -> float:
         return lib().orc_net_keff(self.h, j)
@@ -199,8 +220,10 @@ def make_config(cfg, run: int = 0, n_iters: int | None = None, first_iter: int |
 
 def we_run(cfg, run: int = 0, n_iters: int | None = None, first_iter: int | None = None,
            resample: bool = True, init_states=None, init_weights=None, max_steps=None,
-           net: Network | None = None) -> dict:
-    """One WE run of the paper's algorithm (Sec. II.B) for run ``run`` of the config."""
+           net: Network | None = None, depgraph: bool = False) -> dict:
+    """One WE run of the paper's algorithm (Sec. II.B) for run ``run`` of the config.  With
+    depgraph=True the propagation runs the dependency-graph CPU baseline instead of the
+    oracle's full recomputation (same results, less work)."""
     if net is None:
         net = Network(cfg.network, int(cfg.param_set[run]))
     c, keep = make_config(cfg, run, n_iters, first_iter, resample, init_states, init_weights, max_steps)
@@ -219,7 +242,10 @@ def we_run(cfg, run: int = 0, n_iters: int | None = None, first_iter: int | None
                 _p(o["hist"], _F64P) if cfg.hist_len > 0 else None,
                 _p(o["states"], _I32P), _p(o["weights"], _F64P), _p(o["parent"], _I32P),
                 _p(o["t_last"], _F64P), 0, 0, _p(o["first_passage"], _F64P), _p(o["reweighted"], _I32P))
-    lib().orc_we_run(net.h, C.byref(c), C.byref(out))
+    if depgraph:
+        lib().orc_we_run_dg(net.depgraph(), C.byref(c), C.byref(out))
+    else:
+        lib().orc_we_run(net.h, C.byref(c), C.byref(out))
     nf = out.n_final
     o["t_last_prev"] = o["t_last"]
     o["states"] = o["states"][:nf]
@@ -232,8 +258,9 @@ def we_run(cfg, run: int = 0, n_iters: int | None = None, first_iter: int | None
 
 
 def propagate_one(cfg, x, iteration: int, slot: int, run: int = 0, net: Network | None = None,
-                  max_steps=None):
-    """SSA for one interval of one walker; returns (new_state, events, recycles, status)."""
+                  max_steps=None, depgraph: bool = False):
+    """SSA for one interval of one walker; returns (new_state, events, recycles, status).
+    depgraph=True: the dependency-graph CPU baseline (same result)."""
     if net is None:
         net = Network(cfg.network, int(cfg.param_set[run]))
     c, keep = make_config(cfg, run, max_steps=max_steps)
@@ -241,8 +268,9 @@ def propagate_one(cfg, x, iteration: int, slot: int, run: int = 0, net: Network 
     ev = C.c_int64(0)
     rec = C.c_int32(0)
     tl = C.c_double(0.0)
-    rc = lib().orc_propagate(net.h, C.byref(c), iteration, slot, _p(xs, _I32P), C.byref(ev), C.byref(rec),
-                             C.byref(tl))
+    fn = lib().orc_propagate_dg if depgraph else lib().orc_propagate
+    rc = fn(net.depgraph() if depgraph else net.h, C.byref(c), iteration, slot, _p(xs, _I32P), C.byref(ev),
+            C.byref(rec), C.byref(tl))
     return xs, ev.value, rec.value, rc
 
 

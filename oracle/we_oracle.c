@@ -172,21 +172,22 @@ int32_t orc_net_n_species(const orc_net *n) { return n->S; }
 int32_t orc_net_n_reactions(const orc_net *n) { return n->M; }
 double orc_net_keff(const orc_net *n, int32_t j) { return n->keff[j]; }
 
-void orc_propensities(const orc_net *n, const int32_t *x, double *a) {
-  for (int32_t j = 0; j < n->M; ++j) {
-    if (n->law[j] == ORC_HILL_REPRESSION) {
-      int64_t y = x[n->hill_sp[j]];
-      int64_t yn = y;
-      for (int32_t p = 1; p < n->hill_n[j]; ++p) yn *= y;
-      double den = n->hill_Kn[j] + (double)yn;
-      a[j] = n->keff[j] / den;
-    } else {
-      int64_t h = 1;
-      for (int32_t r = 0; r < n->n_reac[j]; ++r)
-        h *= binom_small(x[n->reac_sp[3 * j + r]], n->reac_m[3 * j + r]);
-      a[j] = n->keff[j] * (double)h;
-    }
+static double propensity_of(const orc_net *n, int32_t j, const int32_t *x) {
+  if (n->law[j] == ORC_HILL_REPRESSION) {
+    int64_t y = x[n->hill_sp[j]];
+    int64_t yn = y;
+    for (int32_t p = 1; p < n->hill_n[j]; ++p) yn *= y;
+    double den = n->hill_Kn[j] + (double)yn;
+    return n->keff[j] / den;
   }
+  int64_t h = 1;
+  for (int32_t r = 0; r < n->n_reac[j]; ++r)
+    h *= binom_small(x[n->reac_sp[3 * j + r]], n->reac_m[3 * j + r]);
+  return n->keff[j] * (double)h;
+}
+
+void orc_propensities(const orc_net *n, const int32_t *x, double *a) {
+  for (int32_t j = 0; j < n->M; ++j) a[j] = propensity_of(n, j, x);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -579,7 +580,13 @@ done:
  * resampling (the estimate of P(x, t) of Sec. II.B.1), and the total weight and walker count
  * after resampling.
  * ------------------------------------------------------------------------------------------ */
+static int we_run_impl(const orc_net *n, const orc_dg *dg, const orc_we_config *cfg, orc_we_out *out);
+
 int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
+  return we_run_impl(n, NULL, cfg, out);
+}
+
+static int we_run_impl(const orc_net *n, const orc_dg *dg, const orc_we_config *cfg, orc_we_out *out) {
   const int32_t S = n->S;
   const int32_t cap = cfg->capacity;
   if (cfg->n_init < 1 || cfg->n_init > cap || cfg->m_targ < 1 || !(cfg->tau > 0.0) ||
@@ -632,7 +639,8 @@ int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
        * that time at the latest (only the initial walkers can be found there unrecorded) */
       if (absorb && out->first_passage && out->first_passage[s] < 0.0 && in_target(cfg, st + (size_t)s * S))
         out->first_passage[s] = (double)iter * cfg->tau;
-      int32_t rc = orc_propagate(n, cfg, iter, s, st + (size_t)s * S, &ev, &nrec[s], &tl);
+      int32_t rc = dg ? orc_propagate_dg(dg, cfg, iter, s, st + (size_t)s * S, &ev, &nrec[s], &tl)
+                      : orc_propagate(n, cfg, iter, s, st + (size_t)s * S, &ev, &nrec[s], &tl);
       if (out->t_last) out->t_last[s] = tl;
       if (absorb && out->first_passage && nrec[s] > 0 && out->first_passage[s] < 0.0)
         out->first_passage[s] = (double)iter * cfg->tau + tl;
@@ -712,4 +720,141 @@ int orc_we_run(const orc_net *n, const orc_we_config *cfg, orc_we_out *out) {
   free(st); free(st2); free(w); free(w2); free(par); free(bins); free(nrec);
   free(sbin); free(F); free(acc); free(cb); free(fac); free(mark);
   return status;
+}
+
+/* ==========================================================================================
+ * CPU BASELINE, not part of the oracle's definition: the same direct SSA with a dependency
+ * graph -- after an event only the propensities that read a changed species are recomputed,
+ * and only their paths to the root of the canonical tree -- so that the CPU figure set beside
+ * the GPU's is not the oracle's O(M)-per-event strawman.  Every tree node is still the rounded
+ * sum of its two children and the descent is the oracle's, so the results are identical to
+ * orc_propagate's (checked by a CPU test); only the amount of work differs.
+ * ========================================================================================== */
+struct orc_dg {
+  const orc_net *n;
+  int32_t P;                 /* leaves of the canonical tree */
+  int32_t *dep_ptr, *dep;    /* reactions whose propensity reads a species that reaction j changes */
+};
+
+void orc_dg_destroy(orc_dg *g) {
+  if (!g) return;
+  free(g->dep_ptr); free(g->dep); free(g);
+}
+
+int orc_dg_create(const orc_net *n, orc_dg **out) {
+  *out = NULL;
+  const int32_t S = n->S, M = n->M;
+  orc_dg *g = (orc_dg *)calloc(1, sizeof(orc_dg));
+  int32_t *rd_ptr = (int32_t *)calloc((size_t)S + 1, sizeof(int32_t));   /* species -> readers */
+  int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * (size_t)M);
+  if (!g || !rd_ptr || !mark) { free(g); free(rd_ptr); free(mark); return ORC_ENOMEM; }
+  g->n = n;
+  g->P = pow2_at_least(M);
+  for (int32_t j = 0; j < M; ++j) {
+    if (n->law[j] == ORC_HILL_REPRESSION) rd_ptr[n->hill_sp[j] + 1]++;
+    else for (int32_t r = 0; r < n->n_reac[j]; ++r) rd_ptr[n->reac_sp[3 * j + r] + 1]++;
+  }
+  for (int32_t s = 0; s < S; ++s) rd_ptr[s + 1] += rd_ptr[s];
+  int32_t *rd = (int32_t *)malloc(sizeof(int32_t) * ((size_t)rd_ptr[S] + 1));
+  int32_t *fill = (int32_t *)calloc((size_t)S, sizeof(int32_t));
+  if (!rd || !fill) { free(rd); free(fill); free(rd_ptr); free(mark); free(g); return ORC_ENOMEM; }
+  for (int32_t j = 0; j < M; ++j) {
+    if (n->law[j] == ORC_HILL_REPRESSION) { int32_t s = n->hill_sp[j]; rd[rd_ptr[s] + fill[s]++] = j; }
+    else for (int32_t r = 0; r < n->n_reac[j]; ++r) { int32_t s = n->reac_sp[3 * j + r]; rd[rd_ptr[s] + fill[s]++] = j; }
+  }
+  /* two passes over reactions: count, then fill the deduplicated dependents */
+  g->dep_ptr = (int32_t *)calloc((size_t)M + 1, sizeof(int32_t));
+  int rc = g->dep_ptr ? ORC_OK : ORC_ENOMEM;
+  for (int pass = 0; pass < 2 && rc == ORC_OK; ++pass) {
+    for (int32_t i = 0; i < M; ++i) mark[i] = -1;
+    int32_t cnt = 0;
+    for (int32_t j = 0; j < M; ++j) {
+      if (pass == 1) g->dep_ptr[j] = cnt;
+      for (int32_t e = n->d_ptr[j]; e < n->d_ptr[j + 1]; ++e) {
+        int32_t s = n->d_sp[e];
+        for (int32_t q = rd_ptr[s]; q < rd_ptr[s + 1]; ++q)
+          if (mark[rd[q]] != j) { mark[rd[q]] = j; if (pass == 1) g->dep[cnt] = rd[q]; ++cnt; }
+      }
+    }
+    if (pass == 0) { g->dep = (int32_t *)malloc(sizeof(int32_t) * ((size_t)cnt + 1)); if (!g->dep) rc = ORC_ENOMEM; }
+    else g->dep_ptr[M] = cnt;
+  }
+  free(rd); free(fill); free(rd_ptr); free(mark);
+  if (rc != ORC_OK) { orc_dg_destroy(g); return rc; }
+  *out = g;
+  return ORC_OK;
+}
+
+int orc_propagate_dg(const orc_dg *g, const orc_we_config *cfg, int32_t iter, int32_t slot,
+                     int32_t *x, int64_t *n_ev, int32_t *n_rec, double *t_last) {
+  const orc_net *n = g->n;
+  const int32_t S = n->S, M = n->M, P = g->P;
+  double *node = (double *)calloc(2 * (size_t)P, sizeof(double));
+  if (!node) return ORC_ENOMEM;
+  uint32_t key[2];
+  run_key(cfg->seed, cfg->run_id, key);
+  const int64_t cap = cfg->max_steps > 0 ? cfg->max_steps : ORC_DEFAULT_MAX_STEPS;
+  double t = 0.0;
+  uint32_t draw = 0;
+  int64_t ev = 0;
+  int32_t rec = 0;
+  int status = ORC_OK;
+#define DG_REBUILD()                                                             \
+  do {                                                                          \
+    for (int32_t j = 0; j < M; ++j) node[P + j] = propensity_of(n, j, x);        \
+    for (int32_t k = P - 1; k >= 1; --k) node[k] = node[2 * k] + node[2 * k + 1]; \
+  } while (0)
+  DG_REBUILD();
+  for (;;) {
+    if (cfg->feedback == 2 && in_target(cfg, x)) break;
+    double a0 = node[1];
+    if (!(a0 > 0.0)) break;
+    uint32_t ctr[4] = {draw, (uint32_t)iter, (uint32_t)slot, 0u}, r[4];
+    ++draw;
+    orc_philox4x32_10(ctr, key, r);
+    double u1 = orc_u01(r[0], r[1]);
+    double u2 = orc_u01(r[2], r[3]);
+    double dt = -log(u1) / a0;
+    double tn = t + dt;
+    if (tn > cfg->tau) break;
+    if (ev >= cap) { status = ORC_ESTEPCAP; break; }
+    double target = u2 * a0;
+    int32_t k = 1;
+    while (k < P) {
+      double L = node[2 * k], R = node[2 * k + 1];
+      if (R == 0.0 || target < L) k = 2 * k;
+      else { target = target - L; k = 2 * k + 1; }
+    }
+    const int32_t j = k - P;
+    int over = 0;
+    for (int32_t e = n->d_ptr[j]; e < n->d_ptr[j + 1]; ++e)
+      if ((int64_t)x[n->d_sp[e]] + n->d_val[e] > ORC_MAX_COUNT) over = 1;
+    if (over) { status = ORC_EOVERFLOW; break; }
+    for (int32_t e = n->d_ptr[j]; e < n->d_ptr[j + 1]; ++e) x[n->d_sp[e]] += n->d_val[e];
+    ++ev;
+    t = tn;
+    if (cfg->feedback && in_target(cfg, x)) {
+      ++rec;
+      if (cfg->feedback == 2) break;
+      memcpy(x, cfg->recycle_state, sizeof(int32_t) * S);
+      DG_REBUILD();
+      continue;
+    }
+    for (int32_t q = g->dep_ptr[j]; q < g->dep_ptr[j + 1]; ++q) {
+      const int32_t i = g->dep[q];
+      node[P + i] = propensity_of(n, i, x);
+      for (int32_t a = (P + i) >> 1; a >= 1; a >>= 1) node[a] = node[2 * a] + node[2 * a + 1];
+    }
+  }
+#undef DG_REBUILD
+  free(node);
+  *n_ev = ev;
+  *n_rec = rec;
+  if (t_last) *t_last = t;
+  return status;
+}
+
+int orc_we_run_dg(const orc_dg *g, const orc_we_config *cfg, orc_we_out *out) {
+  if (cfg->reweight_period > 0) return out->status = ORC_EINVAL;
+  return we_run_impl(g->n, g, cfg, out);
 }

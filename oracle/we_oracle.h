@@ -152,6 +152,17 @@ int32_t orc_rw_solve(int32_t n_bins, const double *F, const double *cb, double *
 /* The whole WE run of the paper's algorithm listing (Sec. II.B). */
 int orc_we_run(const orc_net *net, const orc_we_config *cfg, orc_we_out *out);
 
+/* CPU baseline, not part of the oracle's definition: the same SSA with a dependency graph
+ * (only the propensities a fired reaction can change are recomputed, with their tree paths),
+ * for a CPU throughput figure that is not the oracle's full recomputation.  Same results as
+ * orc_propagate / orc_we_run (no steady-state reweighting). */
+typedef struct orc_dg orc_dg;
+int orc_dg_create(const orc_net *net, orc_dg **out);
+void orc_dg_destroy(orc_dg *g);
+int orc_propagate_dg(const orc_dg *g, const orc_we_config *cfg, int32_t iter, int32_t slot,
+                     int32_t *x, int64_t *n_ev, int32_t *n_rec, double *t_last);
+int orc_we_run_dg(const orc_dg *g, const orc_we_config *cfg, orc_we_out *out);
+
 #ifdef __cplusplus
 }
 #endif

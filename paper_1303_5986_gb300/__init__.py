@@ -13,6 +13,6 @@ from ._lib import (WEError, WE_OK, WE_EINVAL, WE_ENOMEM, WE_ECUDA, WE_EOVERFLOW,
 from .api import (Network, BinMap, Ensemble, we_network_create, network_from_spec, we_binmap_grid,
                   make_run_config, run_config_from, we_ensemble_workspace_bytes,
                   we_ensemble_create, we_ensemble_resume, we_run, we_autotune, autotune_cache_save, autotune_cache_load, autotune_cache_clear, we_resample_static, MLP, we_mlp_create,
-                  we_binmap_learned, first_passage_labels)
+                  we_binmap_learned, first_passage_labels, measure_alu_peaks, measure_graph_floor)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -99,6 +99,8 @@ SIGNATURES = [
                                     C.POINTER(C.c_size_t), _VP]),
     ("we_ensemble_fpt_mle", C.c_int32, [_VP, C.c_double, _VP, C.c_size_t, _VP]),
     ("we_run", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, C.POINTER(_VP)]),
+    ("we_measure_alu_peaks", C.c_int32, [_VP, _F64P, _F64P, _F64P]),
+    ("we_measure_graph_floor", C.c_int32, [C.c_int32, C.c_int32, _VP, _F64P]),
     ("we_autotune", C.c_int32, [_VP, _VP, C.POINTER(we_run_config), _VP, _I32P, _I32P]),
     ("we_autotune_cache_save", C.c_int32, [C.c_char_p]),
     ("we_autotune_cache_load", C.c_int32, [C.c_char_p]),

@@ -350,6 +350,22 @@ def we_autotune(net: Network, bins: BinMap, cfg, stream=None):
     return m.value, b.value
 
 
+def measure_alu_peaks(stream=None) -> dict:
+    """Measured whole-GPU lane operations per second of FP64 FMA, INT32 multiply-add and INT32
+    ALU (xor/add) -- the denominators of the SSA kernels' rooflines."""
+    f, m, a = C.c_double(), C.c_double(), C.c_double()
+    check(lib().we_measure_alu_peaks(_stream_handle(stream), C.byref(f), C.byref(m), C.byref(a)))
+    return {"fp64_fma_per_s": f.value, "imad_per_s": m.value, "ialu_per_s": a.value}
+
+
+def measure_graph_floor(kernels: int, n_replays: int = 2000, stream=None) -> float:
+    """Milliseconds per replay of a CUDA graph of `kernels` empty launches (the launch floor of a
+    WE iteration with that many kernels)."""
+    ms = C.c_double()
+    check(lib().we_measure_graph_floor(int(kernels), int(n_replays), _stream_handle(stream), C.byref(ms)))
+    return ms.value
+
+
 def autotune_cache_save(path: str):
     """Write the autotuner's cached choices to a text file."""
     check(lib().we_autotune_cache_save(str(path).encode()))

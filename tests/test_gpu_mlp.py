@@ -199,15 +199,16 @@ def test_first_passage_labels():
     exact = E.small_generator_expm(Q, p0, 2.0)[130]
     est = lab[:n].mean()
     se = np.sqrt(exact * (1 - exact) / n)
-    assert abs(est - exact) < 4 * se, (est, exact, se)
+    assert abs(est - exact) < 3 * se, (est, exact, se)
     assert lab.dtype == np.float32
 
 
 def test_we_with_learned_bins_is_unbiased():
     """Immigration-death chain (kb = 10, kd = 0.1, X0 = 100), tau = 0.1, 200 intervals, 10 walkers
     per bin on 100 bins of a coordinate trained on soft labels sigmoid((x - 130)/8): the weighted
-    tail P(X >= k, t = 20) against the exact transient distribution over 16 replicas -- and the
-    same for the plain species-count grid (60 bins of width 5 plus overflow) as the control."""
+    tail P(X >= k, t = 20) against the exact transient distribution within 3 standard errors over
+    64 replicas -- and the same for the plain species-count grid (60 bins of width 5 plus
+    overflow) as the control."""
     n_in, H = 1, 64
     xs = np.arange(0, 301, dtype=np.int32).reshape(-1, 1)
     ys = (1.0 / (1.0 + np.exp(-(xs[:, 0] - 130.0) / 8.0))).astype(np.float32)
@@ -219,7 +220,7 @@ def test_we_with_learned_bins_is_unbiased():
     edges = W.logit_edges(100, -10.0, 12.0)
     exact = E.immigration_death_pmf(100, 10.0, 0.1, 20.0, 400)
     for learned in (True, False):
-        cfg = W.birth_death_we(n_iters=200, n_runs=16, seed=5)
+        cfg = W.birth_death_we(n_iters=200, n_runs=64, seed=5)
         bm = P.we_binmap_learned(mlp, edges) if learned else None
         ens = gpu_run(cfg, 200, bins=bm, capacity=10 * 100 + 64)
         ens.sync()
@@ -228,7 +229,7 @@ def test_we_with_learned_bins_is_unbiased():
             est = Hh[199, :, k:].sum(axis=1)
             ex = exact[k:].sum()
             se = est.std(ddof=1) / np.sqrt(len(est))
-            assert abs(est.mean() - ex) < 3 * se + 0.05 * ex, (learned, k, est.mean(), ex, se)
+            assert abs(est.mean() - ex) < 3 * se, (learned, k, est.mean(), ex, se)
         tot = ens.per_iter(P.WE_OUT_TOTAL_W)
         assert np.all(np.abs(tot - 1.0) < 1e-12)
 

@@ -1,5 +1,13 @@
 """WE observables of the GPU path against the mathematics and the paper's printed values,
-within 3 standard errors over independent replicas (the replicate protocol of Sec. III.B.3)."""
+within 3 standard errors over independent replicas (the replicate protocol of Sec. III.B.3),
+with no tolerance beyond that.
+
+Deep-tail WE estimates are unbiased but right-skewed: per replica they spread over decades, and
+with too few replicas their sample mean falls below the exact value while the sample standard
+error understates its spread.  Each check therefore either uses enough replicas for the sample
+to cover the skew (10,000 for the futile cycle's 1e-18 tail) or stays where the replicas'
+log-spread sigma_ln is at most 1.5 (asserted), the range in which the standard error is a fair
+measure."""
 import json
 import os
 
@@ -24,48 +32,64 @@ def built():
     build.build()
 
 
+def _within_3se(est, exact, label):
+    se = est.std(ddof=1) / np.sqrt(len(est))
+    assert abs(est.mean() - exact) < 3 * se, (label, est.mean(), exact, se)
+    return (est.mean() - exact) / se
+
+
+def _log_spread(est):
+    return float(np.log(est[est > 0]).std(ddof=1))
+
+
 def test_schlogl_tail_probability_matches_paper():
     """Paper-scale Schloegl PDF run (802 unit bins, 100 walkers per bin, tau = 0.05, 101
     iterations from X = 82; Sec. III.B.2): P(X >= 700, t = 5) against the CME value printed in
-    Sec. III.B.3, 1.148e-9, over 10 replicas."""
-    cfg = W.schlogl_pdf_we(n_iters=101, n_runs=10)
+    Sec. III.B.3, 1.148e-9, over 40 replicas (~80,200 walkers each)."""
+    cfg = W.schlogl_pdf_we(n_iters=101, n_runs=40)
     ens = gpu_run(cfg, 101)
     ens.sync()
     H = ens.per_iter(P.WE_OUT_HIST)              # iters x runs x len; iteration 99 ends at t = 5
     est = H[99, :, 700:].sum(axis=1)
     exact = GOLDEN["schlogl_p_ge_700_t5_from_82"]   # truncated CME, written by make_golden.py
     assert abs(exact - 1.148e-9) < 0.001e-9      # the paper's CME value
-    se = est.std(ddof=1) / np.sqrt(len(est))
-    assert abs(est.mean() - exact) < 3 * se + 0.02 * exact, (est.mean(), exact, se)
+    _within_3se(est, exact, "P(X >= 700, t = 5)")
     tot = ens.per_iter(P.WE_OUT_TOTAL_W)
     assert np.all(np.abs(tot - 1.0) < 1e-12)
 
 
 def test_futile_cycle_tails_at_paper_scale():
-    """Futile-cycle distribution run at the paper's scale (101 unit bins on S1, 100 walkers per
-    bin, tau = 1, 100 iterations from S1 = S2 = 50; Sec. III.A), 10 replicas, against the
-    uniformized CME: P(S1 >= x, t = 100) within 3 standard errors for x = 60, 70, 75 (8.7e-3,
-    3.0e-6, 1.4e-8).  The paper's own observable, P(S1 > 90, t = 100) = 2.72e-18 (CME value
-    printed there; pinned on the CPU), is estimated and must be positive in every replica, but
-    is not compared: the tail front reaches S1 > 90 only after ~30 iterations, and over 10
-    replicas the estimate at t = 100 is too skewed to resolve (it spans 1e-23 to 2e-18)."""
-    cfg = W.futile_pdf_we(n_iters=100, n_runs=10)
-    ens = gpu_run(cfg, 100)
-    ens.sync()
-    assert np.all(ens.status() == 0)
-    H = ens.per_iter(P.WE_OUT_HIST)              # iters x runs x len; iteration 99 ends at t = 100
+    """Futile-cycle distribution runs at the paper's scale (101 unit bins on S1, 100 walkers per
+    bin, tau = 1, 100 iterations from S1 = S2 = 50; Sec. III.A), 10,000 replicas in batches of
+    200, against the uniformized CME: P(S1 >= x, t = 100) within 3 standard errors for x = 60 ...
+    85 and the paper's own observable P(S1 > 90, t = 100) = 2.72e-18 (the CME value printed
+    there).  Per-replica estimates of that tail spread over ~4 decades (sigma_ln ~4.3): 1,000
+    replicas still give a sample mean near a quarter of the exact value, 10,000 cover the skew.
+    Each run propagates ~0.81 M one-second segments (the paper: 840,000)."""
     law = E.futile_s1_law(100.0)
-    for x in (60, 70, 75):
-        est = H[99, :, x:].sum(axis=1)
-        exact = law[x:].sum()
-        se = est.std(ddof=1) / np.sqrt(len(est))
-        assert abs(est.mean() - exact) < 3 * se + 0.02 * exact, (x, est.mean(), exact, se)
+    H, segs = [], []
+    for batch in range(50):
+        cfg = W.futile_pdf_we(n_iters=100, n_runs=200, seed=batch)
+        ens = gpu_run(cfg, 100)
+        ens.sync()
+        assert np.all(ens.status() == 0)
+        H.append(ens.per_iter(P.WE_OUT_HIST)[99])        # runs x len; iteration 99 ends at t = 100
+        nw = ens.per_iter(P.WE_OUT_NWALKERS)              # walkers after each resampling
+        segs.append(nw[:-1].sum(axis=0) + cfg.m_targ)     # propagated in iterations 0 .. 99
+        if batch == 0:
+            tot = ens.per_iter(P.WE_OUT_TOTAL_W)
+            assert np.all(np.abs(tot - 1.0) < 1e-12)
+        ens.close()
+    H = np.concatenate(H)
+    segs = np.concatenate(segs)
+    assert 0.75e6 < segs.mean() < 0.9e6, segs.mean()
+    for x in (60, 70, 75, 80, 85):
+        _within_3se(H[:, x:].sum(axis=1), law[x:].sum(), f"P(S1 >= {x})")
     exact90 = GOLDEN["futile_p_s1_gt_90_t100"]   # uniformized CME, written by make_golden.py
     assert abs(exact90 - 2.72e-18) < 0.005e-18   # the paper's CME value
-    tail = H[99, :, 91:].sum(axis=1)
-    assert np.all(tail > 0) and np.all(tail < 1e-12)
-    tot = ens.per_iter(P.WE_OUT_TOTAL_W)
-    assert np.all(np.abs(tot - 1.0) < 1e-12)
+    tail = H[:, 91:].sum(axis=1)
+    assert np.all(tail > 0)
+    _within_3se(tail, exact90, "P(S1 > 90)")
 
 
 def test_reweighting_reaches_the_schlogl_flux_sooner():
@@ -91,17 +115,21 @@ def test_reweighting_reaches_the_schlogl_flux_sooner():
             early = flux[30:100].mean() / exact
     m = mean[2]
     se = m.std(ddof=1) / np.sqrt(len(m))
+    # reweighting every 2 iterations with bins 10 counts wide settles slightly high (the
+    # estimated bin-to-bin rates depend on the within-bin distributions); this checks how soon
+    # the flux arrives, with 5 % allowed for that, not unbiasedness (the state-resolved test
+    # below does)
     assert abs(m.mean() - 1.0) < 3 * se + 0.05, (m, se)
     assert early < 0.6, early
 
 
 def test_reweighting_unbiased_with_state_resolved_bins():
     """Birth-death 100 -> 140 with recycling, one state per bin, reweighting every 5 iterations,
-    32 replicas: the steady-state flux matches 1 / MFPT (with bins of one state the estimated
-    bin-to-bin chain is the exact lumped chain)."""
+    128 replicas: the steady-state flux matches 1 / MFPT within 3 standard errors (with bins of
+    one state the estimated bin-to-bin chain is the exact lumped chain)."""
     b, d = E.birth_death_rates()
     exact = 1.0 / E.bd_mfpt(100, 140, b, d)
-    cfg = W.birth_death_we(n_iters=300, target=140, n_runs=32)
+    cfg = W.birth_death_we(n_iters=300, target=140, n_runs=128)
     cfg.bins = W.GridBins(species=[0], edges=[W.uniform_edges(0, 1, 150)])
     cfg.capacity = cfg.m_targ * cfg.bins.n_bins
     cfg.reweight_period = 5
@@ -110,8 +138,7 @@ def test_reweighting_unbiased_with_state_resolved_bins():
     assert np.all(ens.status() == 0)
     assert (ens.per_iter(P.WE_OUT_RW)[4::5] == 1).all()
     m = ens.per_iter(P.WE_OUT_FLUX)[100:].mean(axis=0) / cfg.tau / exact
-    se = m.std(ddof=1) / np.sqrt(len(m))
-    assert abs(m.mean() - 1.0) < 3 * se + 0.05, (m.mean(), se)
+    _within_3se(m, 1.0, "state-resolved reweighting flux")
 
 
 def test_epigenetic_switch_mfpt_matches_paper():
@@ -127,8 +154,7 @@ def test_epigenetic_switch_mfpt_matches_paper():
     assert np.all(ens.status() == 0)
     assert (ens.per_iter(P.WE_OUT_RW)[99::100] == 1).all()
     flux = ens.per_iter(P.WE_OUT_FLUX)[100:].mean(axis=0) / cfg.tau     # per replica
-    se = flux.std(ddof=1) / np.sqrt(len(flux))
-    assert abs(flux.mean() - 1.0 / exact) < 3 * se + 0.05 / exact, (1 / flux.mean(), exact, se * exact)
+    _within_3se(flux, 1.0 / exact, "epigenetic flux")
     tot = ens.per_iter(P.WE_OUT_TOTAL_W)
     assert np.all(np.abs(tot - 1.0) < 1e-12)
 
@@ -136,15 +162,100 @@ def test_epigenetic_switch_mfpt_matches_paper():
 def test_schlogl_mfpt_matches_closed_form():
     """Steady-state WE with recycling at X >= 550 from X0 = 85 (80 bins of width 10, 20 walkers
     per bin, tau = 0.05): MFPT = 1/flux (Eq. "mfpt") against the birth-death closed form
-    (50,307 s; the paper quotes about 5e4 s for 82 -> 563), over 10 replicas."""
-    cfg = W.schlogl_mfpt_we(n_iters=1000, n_runs=10)
+    (50,307 s; the paper quotes about 5e4 s for 82 -> 563), over 100 replicas."""
+    cfg = W.schlogl_mfpt_we(n_iters=1000, n_runs=100)
     ens = gpu_run(cfg, 1000)
     ens.sync()
     flux = ens.per_iter(P.WE_OUT_FLUX)          # iters x runs
     per_run = flux[300:].mean(axis=0) / cfg.tau
     b, d = E.schlogl_rates()
     exact = 1.0 / E.bd_mfpt(85, 550, b, d)
-    se = per_run.std(ddof=1) / np.sqrt(len(per_run))
-    assert abs(per_run.mean() - exact) < 3 * se + 0.05 * exact, (1 / per_run.mean(), 1 / exact, se / exact)
+    _within_3se(per_run, exact, "Schloegl flux 85 -> 550")
     tot = ens.per_iter(P.WE_OUT_TOTAL_W)
     assert np.all(np.abs(tot - 1.0) < 1e-12)
+
+
+# ------------------------------------------------------------------ the 1-D birth-death process
+def test_birth_death_transient_tails_at_t20():
+    """The birth-death configuration as given (60 bins of width 5 plus overflow, 10 walkers per
+    bin, tau = 0.1, 200 iterations from X = 100), 200 replicas: P(X, t = 20) against the exact
+    transient law Binomial(100, e^-2) * Poisson(100 (1 - e^-2)) (Sec. II.B.1 reads P(x, t) off
+    the weights) within 3 standard errors where the estimates' log-spread is at most 1.5.
+    Deeper, where this configuration places walkers but resolves little (sigma_ln 2 to 12 from
+    1e-6 down), every replica still holds weight at X >= 150."""
+    cfg = W.birth_death_we(n_iters=200, n_runs=200)
+    ens = gpu_run(cfg, 200)
+    ens.sync()
+    h = ens.per_iter(P.WE_OUT_HIST)[199]                 # runs x len; iteration 199 ends at t = 20
+    law = E.immigration_death_pmf(100, 10.0, 0.1, 20.0, 400)
+    for sel, lab in ((slice(None, 71), "<= 70"), (slice(130, None), ">= 130"), (slice(140, None), ">= 140")):
+        est = h[:, sel].sum(axis=1)
+        assert _log_spread(est) <= 1.5, lab
+        _within_3se(est, law[sel].sum(), f"P(X {lab}, t = 20)")
+    assert np.all(h[:, 150:].sum(axis=1) > 0)
+
+
+def test_birth_death_stationary_tails_to_1e_30():
+    """Stationary birth-death law Poisson(100) from WE down to 1e-30 and below in both tails
+    (the depth asked of the 1-D configuration), with unit-width bins on [0, 300) plus overflow,
+    10 walkers per bin, tau = 0.1, steady-state reweighting every 5 iterations (Sec. II.B.2;
+    exact for bins of one state), 64 replicas of 4000 iterations, the weighted histogram
+    averaged over iterations 2000-3999: P(X <= 5), P(X <= 10), P(X <= 20), P(X <= 40),
+    P(X >= 180, 200, 220, 235, 250) -- 3.3e-36 to 4.1e-13 -- within 3 standard errors.  (Bins 5
+    counts wide resolve the stationary tails only to ~1e-13, and without reweighting unit bins
+    reach ~1e-19: the per-replica estimates' spread grows with depth.)"""
+    R, n = 64, 4000
+    cfg = W.birth_death_we(n_iters=n, n_runs=R)
+    cfg.bins = W.GridBins(species=[0], edges=[W.uniform_edges(0, 1, 300, overflow=True)])
+    cfg.capacity = cfg.m_targ * cfg.bins.n_bins
+    cfg.reweight_period = 5
+    ens = gpu_run(cfg, n)
+    ens.sync()
+    assert np.all(ens.status() == 0)
+    acc = ens.per_iter(P.WE_OUT_HIST)[2000:].mean(axis=0)          # runs x len
+    pois = np.exp(E.log_poisson_pmf(np.arange(401), 100.0))
+    for sel, lab in ((slice(None, 6), "<= 5"), (slice(None, 11), "<= 10"), (slice(None, 21), "<= 20"),
+                     (slice(None, 41), "<= 40"), (slice(180, None), ">= 180"), (slice(200, None), ">= 200"),
+                     (slice(220, None), ">= 220"), (slice(235, None), ">= 235"), (slice(250, None), ">= 250")):
+        est = acc[:, sel].sum(axis=1)
+        assert np.all(est > 0), lab
+        _within_3se(est, pois[sel].sum(), f"stationary P(X {lab})")
+    tot = ens.per_iter(P.WE_OUT_TOTAL_W)
+    assert np.all(np.abs(tot - 1.0) < 1e-12)
+
+
+def test_birth_death_mfpt_to_250():
+    """MFPT 100 -> X >= 250 of the birth-death chain, 5.8198e34 s by the closed form
+    sum_k (sum_{j<=k} pi_j) / (lambda_k pi_k): steady-state WE with recycling to X = 100, unit
+    bins on [0, 250) plus overflow, 10 walkers per bin, tau = 0.1, reweighting every 2
+    iterations, 128 replicas of 6000 iterations, flux averaged over iterations 1000-5999
+    (Eq. "mfpt": MFPT = 1 / flux), within 3 standard errors.  Without reweighting the flux
+    stays orders of magnitude low for thousands of iterations."""
+    exact = GOLDEN["birth_death_mfpt_100_to_250"]
+    R, n = 128, 6000
+    cfg = W.birth_death_we(n_iters=n, n_runs=R, target=250)
+    cfg.bins = W.GridBins(species=[0], edges=[W.uniform_edges(0, 1, 250, overflow=True)])
+    cfg.capacity = cfg.m_targ * cfg.bins.n_bins
+    cfg.reweight_period = 2
+    ens = gpu_run(cfg, n)
+    ens.sync()
+    assert np.all(ens.status() == 0)
+    flux = ens.per_iter(P.WE_OUT_FLUX)[1000:].mean(axis=0) / cfg.tau * exact   # flux x MFPT per replica
+    assert np.all(flux > 0)
+    _within_3se(flux, 1.0, "birth-death flux into X >= 250 (units of 1/MFPT)")
+
+
+# ------------------------------------------------------------------ brute force (Sec. II.C)
+def test_schlogl_bruteforce_mle_matches_closed_form():
+    """Brute-force transition runs (Sec. II.C): 4096 Schloegl SSA runs of 4000 s from X = 85,
+    absorbed at X >= 550; the censored-exponential MLE of Eq. "mld" (computed by the library
+    from the first-passage times) against the closed-form MFPT 50,307 s within 3 of its
+    standard errors mu / sqrt(n)."""
+    exact = GOLDEN["schlogl_mfpt_85_to_550_s"]
+    cfg = W.schlogl_bruteforce(n_walkers=4096, tau=10.0, n_iters=400)
+    ens = gpu_run(cfg, 400, resample=False)
+    ens.sync()
+    assert np.all(ens.status() == 0)
+    N, n, st, mu, sig = ens.fpt_mle()[0]
+    assert N == 4096 and 200 < n < 400
+    assert abs(mu - exact) < 3 * sig, (mu, exact, sig)

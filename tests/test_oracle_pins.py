@@ -215,7 +215,7 @@ def test_recycling_rate_is_inverse_mfpt():
     mfpt = E.bd_mfpt(100, 115, bb, dd)
     rate = hits[200:].sum() / (n_w * (n_it - 200) * cfg.tau)
     se = np.sqrt(hits[200:].sum()) / (n_w * (n_it - 200) * cfg.tau)
-    assert abs(rate - 1.0 / mfpt) < 4 * se + 0.02 / mfpt
+    assert abs(rate - 1.0 / mfpt) < 3 * se, (rate, 1.0 / mfpt, se)
 
 
 def test_step_cap_and_overflow_statuses():
@@ -358,6 +358,39 @@ def test_mle_transition_time_is_consistent_and_gives_the_paper_figures():
     assert round(sig, -3) == 6.5e4
 
 
+# ----------------------------- the dependency-graph CPU baseline equals the oracle --------------
+@pytest.mark.parametrize("case", ["schlogl", "toggle", "futile", "absorbing"])
+def test_dependency_graph_cpu_baseline_equals_oracle(case):
+    """The CPU baseline with a dependency graph (incremental tree updates) gives the oracle's
+    runs bit for bit: it only skips recomputing propensities that cannot have changed."""
+    if case == "schlogl":
+        cfg = W.schlogl_mfpt_we(n_iters=30)
+    elif case == "toggle":
+        cfg = W.toggle_batch_we(n_runs=2, n_iters=20)
+    elif case == "futile":
+        cfg = W.futile_pdf_we(n_iters=8, m_targ=10)
+    else:
+        cfg = W.birth_death_bruteforce(n_walkers=64, tau=1.0, n_iters=30, threshold=112)
+    resample = case != "absorbing"
+    for r in range(cfg.n_runs):
+        a = O.we_run(cfg, r, resample=resample)
+        b = O.we_run(cfg, r, resample=resample, depgraph=True)
+        for k in ("states", "weights", "parent", "events", "flux_weight", "hist", "first_passage", "n_walkers"):
+            assert np.array_equal(a[k], b[k]), (case, r, k)
+
+
+def test_dependency_graph_cpu_baseline_on_the_large_network():
+    """The 354 x 3680 network: one interval of eight walkers, propagated by the oracle (all 3680
+    propensities and the whole tree after every event) and by the dependency-graph baseline."""
+    cfg = W.synthetic_large_we(n_walkers=8, n_iters=1)
+    cfg.tau = 1e-4
+    net = O.Network(cfg.network)
+    for i in range(8):
+        a = O.propagate_one(cfg, cfg.init_states[0, i], 0, i, net=net)
+        b = O.propagate_one(cfg, cfg.init_states[0, i], 0, i, net=net, depgraph=True)
+        assert np.array_equal(a[0], b[0]) and a[1:] == b[1:] and a[1] > 100
+
+
 # --------------------------------------- brute-force runs with an absorbing target --------------
 def test_absorbing_runs_give_erlang_first_passage_times():
     """Pure birth at rate 2 (the birth-death network with kd = 0) from 100, absorbed at X >= 130:
@@ -473,18 +506,20 @@ def _replicas(cfg, R, **kw):
 
 def test_we_schlogl_tail_matches_cme():
     """WE estimate of P(X >= x, t = 1) for the Schloegl model from X=82 (unit-width bins as in
-    Sec. III.B.2, 10 walkers per bin) against the truncated CME, within 4 standard errors over
-    independent replicas (the protocol of Sec. III.B.3).  Transient WE tail estimates are
-    unbiased but skewed, so the check stays where 16 replicas resolve them."""
+    Sec. III.B.2, 10 walkers per bin) against the truncated CME, within 3 standard errors over
+    48 independent replicas (the protocol of Sec. III.B.3).  Transient WE tail estimates are
+    unbiased but right-skewed; the checks stay where the replicas' log-spread is below 1.5, so
+    that their standard error is a fair measure."""
     cfg = W.schlogl_pdf_we(n_iters=20, m_targ=10, n_unit_bins=400)
-    outs = _replicas(cfg, 16)
+    outs = _replicas(cfg, 48)
     b, d = E.schlogl_rates()
     p = E.bd_transient(b, d, 82, 1.0, 1500)
     for thr in (120, 150):
         est = np.array([o["hist"][-1, thr:].sum() for o in outs])
         exact = p[thr:].sum()
         se = est.std(ddof=1) / np.sqrt(len(est))
-        assert abs(est.mean() - exact) < 4 * se + 0.1 * exact, (thr, est.mean(), exact, se)
+        assert np.log(est).std(ddof=1) < 1.5, thr
+        assert abs(est.mean() - exact) < 3 * se, (thr, est.mean(), exact, se)
     for o in outs:
         assert np.all(np.abs(o["total_weight"] - 1.0) < 1e-12)
 
@@ -492,9 +527,9 @@ def test_we_schlogl_tail_matches_cme():
 def test_we_birth_death_stationary_tails_match_poisson():
     """Stationary WE of the birth-death process (kb=10, kd=0.1; 61 bins, 10 walkers per bin):
     the time-averaged weighted histogram reproduces the Poisson(100) law in both tails
-    (P(X >= 150) ~ 1.9e-6, P(X <= 50) ~ 2.4e-8), within 4 standard errors over replicas."""
+    (P(X >= 150) ~ 1.9e-6, P(X <= 50) ~ 2.4e-8), within 3 standard errors over 32 replicas."""
     cfg = W.birth_death_we(n_iters=1500)
-    outs = _replicas(cfg, 16)
+    outs = _replicas(cfg, 32)
     x = np.arange(401)
     pois = np.exp(E.log_poisson_pmf(x, 100.0))
     H = np.array([o["hist"][375:].mean(0) for o in outs])
@@ -502,19 +537,20 @@ def test_we_birth_death_stationary_tails_match_poisson():
         est = H[:, sel].sum(1)
         exact = pois[sel].sum()
         se = est.std(ddof=1) / np.sqrt(len(est))
-        assert abs(est.mean() - exact) < 4 * se + 0.1 * exact, (sel, est.mean(), exact, se)
+        assert abs(est.mean() - exact) < 3 * se, (sel, est.mean(), exact, se)
 
 
 def test_we_mfpt_matches_closed_form():
     """Steady-state WE with recycling: MFPT = 1/flux (Eq. "mfpt") for the rare passage
-    100 -> 140 of the birth-death chain (closed form ~9.8e3), 4 standard errors."""
+    100 -> 140 of the birth-death chain (closed form ~9.8e3), 3 standard errors over 32
+    replicas."""
     cfg = W.birth_death_we(n_iters=400, target=140)
-    outs = _replicas(cfg, 8)
+    outs = _replicas(cfg, 32)
     bb, dd = E.birth_death_rates()
     exact = 1.0 / E.bd_mfpt(100, 140, bb, dd)
     est = np.array([1.0 / O.mfpt_from_flux(o["flux_weight"], cfg.tau, discard=150) for o in outs])
     se = est.std(ddof=1) / np.sqrt(len(est))
-    assert abs(est.mean() - exact) < 4 * se + 0.05 * exact, (est.mean(), exact, se)
+    assert abs(est.mean() - exact) < 3 * se, (est.mean(), exact, se)
     for o in outs:
         assert np.all(np.abs(o["total_weight"] - 1.0) < 1e-12)
 
@@ -537,7 +573,7 @@ def test_toggle_recycling_rate_matches_master_equation():
     span = n_w * (n_it - 300) * cfg.tau
     rate = hits[300:].sum() / span
     se = np.sqrt(hits[300:].sum()) / span
-    assert abs(rate - 1.0 / mfpt) < 4 * se + 0.02 / mfpt, (rate, 1.0 / mfpt, se)
+    assert abs(rate - 1.0 / mfpt) < 3 * se, (rate, 1.0 / mfpt, se)
 
 
 def test_synthetic_network_homodimer_and_conservation():
@@ -679,7 +715,8 @@ def test_we_with_reweighting_keeps_total_weight_and_schedule():
 def test_we_reweighting_is_unbiased_with_state_resolved_bins():
     """With one state per bin the bin-to-bin chain that reweighting estimates is the exact lumped
     chain, so the steady-state flux it produces matches 1 / MFPT (birth-death 100 -> 140 with
-    recycling, unit bins, reweighting every 5 iterations; 8 replicas, iterations 100-300)."""
+    recycling, unit bins, reweighting every 5 iterations; 16 replicas, iterations 100-300), within
+    3 standard errors."""
     b, d = E.birth_death_rates()
     exact = 1.0 / E.bd_mfpt(100, 140, b, d)
     cfg = W.birth_death_we(n_iters=300, target=140)
@@ -687,14 +724,14 @@ def test_we_reweighting_is_unbiased_with_state_resolved_bins():
     cfg.capacity = cfg.m_targ * cfg.bins.n_bins
     cfg.reweight_period = 5
     m = []
-    for r in range(8):
+    for r in range(16):
         cfg.run_ids = np.array([r], dtype=np.uint32)
         o = O.we_run(cfg, 0)
         assert o["status"] == 0 and (o["reweighted"][4::5] == 1).all()
         m.append(o["flux_weight"][100:].mean() / cfg.tau / exact)
     m = np.array(m)
     se = m.std(ddof=1) / np.sqrt(len(m))
-    assert abs(m.mean() - 1.0) < 3 * se + 0.05, (m.mean(), se)
+    assert abs(m.mean() - 1.0) < 3 * se, (m.mean(), se)
 
 
 # ---------------------------------------------------------------- grid bins ----------------------
