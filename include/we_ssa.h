@@ -172,6 +172,19 @@ we_status we_mlp_gradient(const we_mlp *mlp, const int32_t *states, const float 
                           float *grad, float *loss, void *stream);
 we_status we_mlp_forward(const we_mlp *mlp, const int32_t *states, int32_t n, int32_t bf16, float *z,
                          void *stream);
+/* we_mlp_create_init: a new MLP with the library's own initial weights: W1, W2 and w3 uniform
+ *   in [-1/sqrt(fan_in), 1/sqrt(fan_in)) from a splitmix64 stream started at `seed` (in that
+ *   order, row-major), zero biases.
+ * we_mlp_coordinate_edges: n_bins equal intervals of the learned coordinate for bin placement:
+ *   z of the n given states (device, n x n_in int32) in the inference form (bf16 = 1, the z a
+ *   learned bin map computes), then lo = the floor(lo_q (n - 1))-th smallest z (0-based) and
+ *   hi = the largest, both found on the device by radix selection, and edges[i] =
+ *   fl32(lo + (hi - lo) i / n_bins) in double for i = 0..n_bins (hi = lo + 1 when hi <= lo).
+ *   edges: n_bins + 1 floats, host or device.  Allocates its scratch; synchronises the stream.
+ *   Errors: WE_EINVAL, WE_ENOMEM, WE_ECUDA, WE_ENOTSUPPORTED (as we_mlp_forward). */
+we_status we_mlp_create_init(int32_t n_in, int32_t hidden, uint64_t seed, we_mlp **out);
+we_status we_mlp_coordinate_edges(const we_mlp *mlp, const int32_t *states, int32_t n, int32_t n_bins,
+                                  double lo_q, float *edges, void *stream);
 /* Bin map on the learned coordinate: a snapshot of the MLP's weights rounded to BF16, with
  * n_bins intervals [edges[k], edges[k+1]) of z (values outside fall in the end bins).  Binning
  * runs in a kernel of its own after the SSA kernel, in tiles of 128 walkers, in the inference
@@ -331,6 +344,13 @@ we_status we_ensemble_sync(we_ensemble *ens, void *stream);
  *   WE_OUT_NREC      int32[n_prev]                  recycles of each walker in the last interval
  *   WE_OUT_RW        int32[iters x runs]            steady-state reweighting per iteration: 1 done,
  *                                                   -1 attempted and skipped, 0 not scheduled
+ *   WE_OUT_NEAR_TAU  int32[iters x runs]            walkers whose interval ended near tau: the
+ *                                                   last fired event or the first draw past tau
+ *                                                   within 2^-40 tau of tau.  The waiting times
+ *                                                   are computed to ~1e-14 relative (float-float
+ *                                                   logarithm), so such a stop decision may differ
+ *                                                   from one taken in other arithmetic; 0 means no
+ *                                                   walker was that close
  *   WE_OUT_FPT       double[n_live]                 absorbing runs: each walker's first-passage
  *                                                   time into the target set, counted from the
  *                                                   run's start (iteration 0): fl(fl(i tau) + t)
@@ -355,6 +375,7 @@ we_status we_ensemble_sync(we_ensemble *ens, void *stream);
 #define WE_OUT_NREC 15
 #define WE_OUT_RW 16
 #define WE_OUT_FPT 17
+#define WE_OUT_NEAR_TAU 18
 we_status we_ensemble_get(we_ensemble *ens, int32_t what, int32_t run, void *dst,
                           size_t dst_bytes, size_t *needed, void *stream);
 

@@ -44,6 +44,7 @@ WE_OUT_Z = 14
 WE_OUT_NREC = 15
 WE_OUT_RW = 16
 WE_OUT_FPT = 17
+WE_OUT_NEAR_TAU = 18
 WE_FEEDBACK_RECYCLE = 1
 WE_FEEDBACK_ABSORB = 2
 
@@ -113,6 +114,8 @@ SIGNATURES = [
     ("we_mlp_gradient", C.c_int32, [_VP, _VP, _VP, C.c_int32, _VP, _F32P, _VP]),
     ("we_mlp_forward", C.c_int32, [_VP, _VP, C.c_int32, C.c_int32, _VP, _VP]),
     ("we_binmap_learned", C.c_int32, [_VP, C.c_int32, _F32P, C.POINTER(_VP)]),
+    ("we_mlp_create_init", C.c_int32, [C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_VP)]),
+    ("we_mlp_coordinate_edges", C.c_int32, [_VP, _VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP]),
     ("we_resample_static", C.c_int32, [C.c_int32, _VP, _VP, C.c_int32, C.c_int32, C.c_int32,
                                        C.c_uint64, C.c_uint32, C.c_int32, _VP, _VP, _VP, _VP]),
 ]

@@ -186,7 +186,7 @@ _OUT_DTYPES = {
     L.WE_OUT_NWALKERS: np.int32, L.WE_OUT_EVENTS: np.int64, L.WE_OUT_HIST: np.float64,
     L.WE_OUT_STATUS: np.int32, L.WE_OUT_ITER: np.int32, L.WE_OUT_RECORDED: np.int32,
     L.WE_OUT_TLAST: np.float64, L.WE_OUT_Z: np.float32, L.WE_OUT_NREC: np.int32,
-    L.WE_OUT_RW: np.int32, L.WE_OUT_FPT: np.float64,
+    L.WE_OUT_RW: np.int32, L.WE_OUT_FPT: np.float64, L.WE_OUT_NEAR_TAU: np.int32,
 }
 
 
@@ -480,6 +480,22 @@ def we_mlp_create(n_in: int, hidden: int, params) -> MLP:
     h = C.c_void_p()
     check(lib().we_mlp_create(int(n_in), int(hidden), p.ctypes.data_as(_F32P), C.byref(h)))
     return MLP(h, n_in, hidden)
+
+
+def we_mlp_create_init(n_in: int, hidden: int, seed: int = 0) -> MLP:
+    """A new MLP with the library's own seeded initial weights (uniform +-1/sqrt(fan_in))."""
+    h = C.c_void_p()
+    check(lib().we_mlp_create_init(int(n_in), int(hidden), int(seed), C.byref(h)))
+    return MLP(h, n_in, hidden)
+
+
+def we_mlp_coordinate_edges(mlp: MLP, states, n_bins: int, lo_q: float = 0.001, stream=None) -> np.ndarray:
+    """Bin edges on the learned coordinate, computed by the library: n_bins equal intervals from
+    the floor(lo_q (n-1))-th smallest z of the device states (n x n_in int32) to the largest."""
+    edges = np.zeros(int(n_bins) + 1, dtype=np.float32)
+    check(lib().we_mlp_coordinate_edges(mlp.h, C.c_void_p(states.data_ptr()), int(states.shape[0]), int(n_bins),
+                                        float(lo_q), C.c_void_p(edges.ctypes.data), _stream_handle(stream)))
+    return edges
 
 
 def we_binmap_learned(mlp: MLP, edges) -> BinMap:

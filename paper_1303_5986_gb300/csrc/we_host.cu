@@ -353,7 +353,7 @@ struct Offsets {
   size_t run_id, param_set, tgt_thr, recycle;
   size_t x0, x1, w0, w1, p0, p1, bin, nrec, tlast, fpt, mle;
   size_t count, prev_count, run_off, status, iter, bin_count, n_tasks, tasks, cursor, sorted_slot, sorted_w, alive, div_magic;
-  size_t flux, totw, nw, events, hist, pack;
+  size_t flux, totw, nw, events, hist, pack, near;
   size_t logt, table, base;
   size_t lw1, lw2, lw3, lb, lz, zout;
   size_t wrec;
@@ -503,6 +503,7 @@ static Offsets layout(const we_network *n, const we_binmap *b, const we_run_conf
   o.nw = L.take(4 * rec * R);
   o.events = L.take(8 * rec * R);
   o.hist = L.take(8 * rec * R * (c->hist_len > 0 ? c->hist_len : 1));
+  o.near = L.take(4 * rec * R);
   o.pack = L.take(4 * (size_t)R * cap * n->S);
   if (c->reweight_period > 0) {
     const size_t nb = b->n_bins;
@@ -787,6 +788,7 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   V.obs_flux = at<double>(ws, o.flux); V.obs_totw = at<double>(ws, o.totw);
   V.obs_nw = at<int32_t>(ws, o.nw); V.obs_events = at<unsigned long long>(ws, o.events);
   V.obs_hist = at<double>(ws, o.hist);
+  V.obs_near = at<int32_t>(ws, o.near);
   E->prm.resample = c->resample ? 1 : 0;
   E->prm.logt = at<LogTables>(ws, o.logt);
   if (c->reweight_period > 0) {
@@ -1271,6 +1273,7 @@ extern "C" we_status we_ensemble_get(we_ensemble *E, int32_t what, int32_t run, 
       if (E->prm.rw.period <= 0) return fail(WE_EINVAL, "WE_OUT_RW needs reweight_period > 0");
       return per_iter(E->prm.rw.obs, 4);
     }
+    case WE_OUT_NEAR_TAU: return per_iter(V.obs_near, 4);
     case WE_OUT_FPT: {
       if (!V.fpt) return fail(WE_EINVAL, "WE_OUT_FPT needs feedback = WE_FEEDBACK_ABSORB");
       return per_walker(V.fpt, 8);

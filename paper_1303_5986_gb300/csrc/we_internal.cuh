@@ -129,6 +129,7 @@ struct EnsView {
   int32_t *obs_nw;
   unsigned long long *obs_events;
   double *obs_hist;
+  int32_t *obs_near;           // walkers whose interval ended within 2^-40 tau of an event
 };
 
 // Tables of the waiting-time logarithm (see neg_log_u01), each value as an unevaluated sum

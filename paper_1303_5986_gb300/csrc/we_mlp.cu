@@ -424,6 +424,56 @@ cudaError_t launch_learned_bins(const PropagateParams &prm, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------
+// Order statistics of z (bin edges of a learned coordinate): radix select on order-preserving
+// 32-bit keys of the floats, one 8-bit digit per pass from the top.  State: {prefix, mask, k}.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t float_key(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void k_radix_hist(const float *z, int n, const uint32_t *state, int shift, uint32_t *hist) {
+  __shared__ uint32_t h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const uint32_t prefix = state[0], mask = state[1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t k = float_key(z[i]);
+    if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// One thread: the digit holding the k-th key among those matching the prefix; clears hist.
+__global__ void k_radix_pick(uint32_t *state, int shift, uint32_t *hist) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t k = state[2], cum = 0;
+  int d = 255;
+  for (int i = 0; i < 256; ++i) {
+    if (cum + hist[i] > k) { d = i; break; }
+    cum += hist[i];
+  }
+  state[0] |= (uint32_t)d << shift;
+  state[1] |= 255u << shift;
+  state[2] = k - cum;
+  for (int i = 0; i < 256; ++i) hist[i] = 0;
+}
+
+// edges[i] = lo + (hi - lo) i / n_bins in double, rounded to float (hi = lo + 1 when hi <= lo)
+__global__ void k_coordinate_edges(const uint32_t *st_lo, const uint32_t *st_hi, int n_bins, float *edges) {
+  const double lo = (double)key_float(st_lo[0]);
+  double hi = (double)key_float(st_hi[0]);
+  if (!(hi > lo)) hi = lo + 1.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n_bins; i += gridDim.x * blockDim.x)
+    edges[i] = (float)(lo + (hi - lo) * (double)i / (double)n_bins);
+}
+
 }  // namespace we
 
 using namespace we;
@@ -474,6 +524,77 @@ extern "C" we_status we_mlp_create(int32_t n_in, int32_t hidden, const float *pa
     return WE_ECUDA;
   }
   *out = M;
+  return WE_OK;
+}
+
+// splitmix64 (Steele, Lea & Flood, OOPSLA 2014): the library's own initial weights
+static uint64_t splitmix64(uint64_t &s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+extern "C" we_status we_mlp_create_init(int32_t n_in, int32_t hidden, uint64_t seed, we_mlp **out) {
+  if (!out) return WE_EINVAL;
+  *out = nullptr;
+  if (n_in < 1 || n_in > 4096 || hidden < 1 || hidden > 64) return WE_EINVAL;
+  MlpShape sh{};
+  sh.n_in = n_in;
+  sh.H = hidden;
+  std::vector<float> p((size_t)sh.n_params(), 0.0f);
+  uint64_t s = seed;
+  auto fill = [&](int off, int count, int fan_in) {
+    const double a = 1.0 / std::sqrt((double)fan_in);
+    for (int i = 0; i < count; ++i) {
+      const double u = (double)(splitmix64(s) >> 11) * 0x1p-53;        // [0, 1)
+      p[(size_t)off + i] = (float)((2.0 * u - 1.0) * a);
+    }
+  };
+  fill(sh.o_w1(), hidden * n_in, n_in);
+  fill(sh.o_w2(), hidden * hidden, hidden);
+  fill(sh.o_w3(), hidden, hidden);
+  return we_mlp_create(n_in, hidden, p.data(), out);
+}
+
+extern "C" we_status we_mlp_coordinate_edges(const we_mlp *M, const int32_t *states, int32_t n, int32_t n_bins,
+                                             double lo_q, float *edges, void *stream) {
+  if (!M || !states || n < 1 || n_bins < 1 || n_bins > 65536 || !edges || !(lo_q >= 0.0) || !(lo_q <= 1.0))
+    return WE_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float *z = nullptr;
+  uint32_t *aux = nullptr;                     // state lo (3), state hi (3), hist (256)
+  float *dedges = nullptr;
+  if (device_alloc((void **)&z, 4 * (size_t)n) || device_alloc((void **)&aux, 4 * (6 + 256)) ||
+      device_alloc((void **)&dedges, 4 * ((size_t)n_bins + 1))) {
+    cudaGetLastError();
+    cudaFree(z); cudaFree(aux); cudaFree(dedges);
+    return WE_ENOMEM;
+  }
+  we_status rc = we_mlp_forward(M, states, n, 1, z, stream);
+  const uint32_t k_lo = (uint32_t)std::floor(lo_q * (double)(n - 1));
+  const uint32_t init[6] = {0u, 0u, k_lo, 0u, 0u, (uint32_t)(n - 1)};
+  cudaError_t e = rc ? cudaSuccess : cudaMemcpyAsync(aux, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  e = e ? e : cudaMemsetAsync(aux + 6, 0, 4 * 256, st);
+  int grid = (n + 255) / 256;
+  if (grid > 152 * 4) grid = 152 * 4;
+  for (int which = 0; which < 2 && !rc && !e; ++which) {
+    uint32_t *state = aux + 3 * which;
+    for (int shift = 24; shift >= 0 && !e; shift -= 8) {
+      k_radix_hist<<<grid, 256, 0, st>>>(z, n, state, shift, aux + 6);
+      k_radix_pick<<<1, 32, 0, st>>>(state, shift, aux + 6);
+      e = cudaGetLastError();
+    }
+  }
+  if (!rc && !e) {
+    k_coordinate_edges<<<(n_bins + 256) / 256, 256, 0, st>>>(aux, aux + 3, n_bins, dedges);
+    e = cudaGetLastError();
+  }
+  e = e ? e : cudaMemcpyAsync(edges, dedges, 4 * ((size_t)n_bins + 1), cudaMemcpyDefault, st);
+  e = e ? e : cudaStreamSynchronize(st);
+  cudaFree(z); cudaFree(aux); cudaFree(dedges);
+  if (rc) return rc;
+  if (e) { cudaGetLastError(); return WE_ECUDA; }
   return WE_OK;
 }
 

@@ -37,8 +37,9 @@ __global__ void __launch_bounds__(kThreads) k_peak_imad(int iters, uint32_t seed
   for (int c = 0; c < kChains; ++c) a[c] = seed + c * 7919u + threadIdx.x;
   const uint32_t m = 0x9E3779B1u, b = 0x7F4A7C15u;
   for (int i = 0; i < iters; ++i) {
+    const uint32_t mi = m ^ (uint32_t)(i << 1);       // a new odd multiplier each step: no closed form
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) a[c] = a[c] * m + b;
+    for (int c = 0; c < kChains; ++c) a[c] = a[c] * mi + b;
   }
   uint32_t s = 0;
 #pragma unroll

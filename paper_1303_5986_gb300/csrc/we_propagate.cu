@@ -189,7 +189,7 @@ __device__ __forceinline__ Smem load_smem(const PropagateParams &prm, unsigned c
 // Epilogue: store the counts, bin the walker, record the interval's observables.
 __device__ __forceinline__ void finish_walker(const PropagateParams &prm, int r, int g, int par,
                                               const int32_t *xme, int B, double t, long long nev,
-                                              int nrec, int status) {
+                                              int nrec, int status, int near) {
   const EnsView &E = prm.ens;
   const int ld = E.R * E.cap;
   int32_t *X = E.x[par];
@@ -209,6 +209,7 @@ __device__ __forceinline__ void finish_walker(const PropagateParams &prm, int r,
     const int o = slot * E.R + r;
     if (nrec) atomicAdd(&E.obs_flux[o], __dmul_rn((double)nrec, wt));
     if (nev) atomicAdd(&E.obs_events[o], (unsigned long long)nev);
+    if (near) atomicAdd(&E.obs_near[o], 1);
     if (E.hist_len > 0) {
       const int v = xme[E.hist_species * B];
       const int idx = v < E.hist_len - 1 ? v : E.hist_len - 1;
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(128) k_propagate_direct(PropagateParams prm) {
   DrawQueue dq;
   dq.init((uint32_t)iter, (uint32_t)w, k0, k1, *sm.logt);
   const bool absorbed = E.feedback == 2 && in_target(E, r, xme, B);
+  double t_stop = 0.0;
   for (; !absorbed;) {
     const double a0 = nd[1];
     if (bits(a0) == 0) break;                        // nothing can fire: idle to tau
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(128) k_propagate_direct(PropagateParams prm) {
     float2 e;
     dq.pop((uint32_t)iter, (uint32_t)w, k0, k1, *sm.logt, m2, e);
     const double tn = advance_clock(t, e, rcp_pos(a0));
-    if (bits(tn) > tau_bits) break;                  // the next event falls after tau
+    if (bits(tn) > tau_bits) { t_stop = tn; break; } // the next event falls after tau
     if (nev >= E.max_steps) { status = kStatusStepCap; break; }
     double target = __dmul_rn(u01_index(m2), a0);
     int k = 1;
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(128) k_propagate_direct(PropagateParams prm) {
     }
     rebuild();
   }
-  finish_walker(prm, r, g, par, xme, B, t, nev, nrec, status);
+  finish_walker(prm, r, g, par, xme, B, t, nev, nrec, status, near_tau_fp64(E.tau, t, t_stop));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -362,13 +364,15 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
   DrawQueue dq;
   dq.init((uint32_t)iter, (uint32_t)w, k0, k1, *sm.logt);
   const bool absorbed = E.feedback == 2 && in_target(E, r, xme, B);
+  unsigned long long stop_u = 0;                    // clock of the first draw past tau (0: none)
   for (; !absorbed;) {
     if (row.idle()) break;                           // nothing can fire: idle to tau
     unsigned long long m2;
     float2 e;
     dq.pop((uint32_t)iter, (uint32_t)w, k0, k1, *sm.logt, m2, e);
     unsigned long long dt;
-    if (!wait_units(e, row.w, dt) || clk + dt > kClockTau) break;   // next event after tau
+    if (!wait_units(e, row.w, dt)) break;            // far beyond the interval
+    if (clk + dt > kClockTau) { stop_u = clk + dt; break; }          // next event after tau
     if (nev >= E.max_steps) { status = kStatusStepCap; break; }
     const int j = row.select(m2, fb);
     const int nx = x + s_dx[j], ny = sy >= 0 ? y + s_dy[j] : 0;
@@ -388,7 +392,7 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
     }
     load_row(x, y);
   }
-  finish_walker(prm, r, g, par, xme, B, clock_time(clk, E.tau), nev, nrec, status);
+  finish_walker(prm, r, g, par, xme, B, clock_time(clk, E.tau), nev, nrec, status, near_tau_units(clk, stop_u));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -455,6 +459,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
   long long nev = 0;
   int nrec = 0, status = 0;
   bool done = !live;
+  double t_stop = 0.0;
   double nd[2 * P];
   auto rebuild = [&]() {
 #pragma unroll
@@ -477,7 +482,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
         const double a0 = nd[1];
         if (bits(a0) == 0) { done = true; break; }
         const double tn = advance_clock(t, e, rcp_pos(a0));
-        if (bits(tn) > tau_bits) { done = true; break; }
+        if (bits(tn) > tau_bits) { t_stop = tn; done = true; break; }
         if (nev >= E.max_steps) { status = kStatusStepCap; done = true; break; }
         double target = __dmul_rn(u01_index(m2), a0);
         int kk = 1;
@@ -515,7 +520,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
     if (!s_more) break;
     __syncthreads();                                      // s_more is rewritten next round
   }
-  if (warp == 0 && live) finish_walker(prm, r, g, par, xme, W, t, nev, nrec, status);
+  if (warp == 0 && live) finish_walker(prm, r, g, par, xme, W, t, nev, nrec, status, near_tau_fp64(E.tau, t, t_stop));
   }
 }
 
@@ -683,6 +688,7 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
   };
   // warp 1: the committed walker
   unsigned long long clk = 0;                           // clock units of tau / 2^62
+  unsigned long long stop_u = 0;                        // clock of the first draw past tau (0: none)
   long long nev = 0;
   int xc = 0, yc = 0, nrec = 0, status = 0;
   bool done = !live || absorbed0, recycled = false;
@@ -833,6 +839,12 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
             done = true;
             const uint32_t bit = 1u << kstop;
             if (!(quiet_m & bit)) status = (cap_m & bit) ? kStatusStepCap : kStatusOverflow;
+            else if ((over_m & bit) && !((idle_m | far_m | absorb_m) & bit)) {
+              unsigned long long ds = 0;                 // the stopping draw's waiting time
+#pragma unroll
+              for (int k = 0; k < K; ++k) ds = (k == kstop) ? dts[k] : ds;
+              stop_u = clk + ds;
+            }
           }
         }
         s_done[sb][lane] = done;
@@ -853,7 +865,8 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
       for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
     xme[TV.species * W] = xc;
     if (D == 2) xme[TV.species2 * W] = yc;
-    finish_walker(prm, r, g, par, xme, W, clock_time(clk, E.tau), (long long)nev, nrec, status);
+    finish_walker(prm, r, g, par, xme, W, clock_time(clk, E.tau), (long long)nev, nrec, status,
+                  near_tau_units(clk, stop_u));
   }
   }
 }

@@ -138,6 +138,17 @@ __device__ __forceinline__ void record_first_passage(const EnsView &E, int r, in
   else if (in_target(E, r, xs, stride)) E.fpt[g] = t0;
 }
 
+// Stop decisions near the end of the interval.  The waiting times carry a relative error of
+// ~1e-14 (float-float logarithm), the oracle's its own rounding, so an event that falls within
+// about that of tau may fire in one and not in the other.  A walker's interval counts as near
+// when its last fired event or its first draw past tau lies within 2^-40 tau (9.1e-13 tau) of
+// tau; such walkers are counted per iteration (WE_OUT_NEAR_TAU) so that a comparison can tell
+// a flip from a fault.
+__device__ __forceinline__ int near_tau_fp64(double tau, double t_last, double t_stop) {
+  const double thr = __dmul_rn(tau, 0x1p-40);
+  return (__dsub_rn(tau, t_last) < thr) || (t_stop > 0.0 && __dsub_rn(t_stop, tau) < thr);
+}
+
 __device__ __forceinline__ int find_run(const int32_t *run_off, int R, int f) {
   int lo = 0, hi = R;
   while (hi - lo > 1) {
@@ -310,6 +321,12 @@ __device__ __forceinline__ bool wait_units(float2 e, float2 w, unsigned long lon
 // Clock units back to time: t = units * tau / 2^62 (one rounding).
 __device__ __forceinline__ double clock_time(unsigned long long units, double tau) {
   return __dmul_rn(__ull2double_rn(units), ldexp(tau, -kClockBits));
+}
+
+// near_tau_fp64 on the fixed-point clock: 2^-40 tau is 2^22 units.
+__device__ __forceinline__ int near_tau_units(unsigned long long clk, unsigned long long stop_u) {
+  constexpr unsigned long long thr = 1ull << (kClockBits - 40);
+  return (kClockTau - clk < thr) || (stop_u > kClockTau && stop_u - kClockTau < thr);
 }
 
 // Draws do not depend on the state, so they are made kDrawBatch at a time: the batch's

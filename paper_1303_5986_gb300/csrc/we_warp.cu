@@ -26,7 +26,7 @@ namespace we {
 
 __device__ __forceinline__ void finish_walker_warp(const PropagateParams &prm, int r, int g, int par,
                                                    const int32_t *xs, double t, long long nev,
-                                                   int nrec, int status, int lane) {
+                                                   int nrec, int status, int near, int lane) {
   const EnsView &E = prm.ens;
   const int ld = E.R * E.cap;
   for (int s = lane; s < E.S; s += 32) E.x[par][(size_t)s * ld + g] = xs[s];
@@ -46,6 +46,7 @@ __device__ __forceinline__ void finish_walker_warp(const PropagateParams &prm, i
     const int o = slot * E.R + r;
     if (nrec) atomicAdd(&E.obs_flux[o], __dmul_rn((double)nrec, wt));
     if (nev) atomicAdd(&E.obs_events[o], (unsigned long long)nev);
+    if (near) atomicAdd(&E.obs_near[o], 1);
     if (E.hist_len > 0) {
       const int v = xs[E.hist_species];
       const int idx = v < E.hist_len - 1 ? v : E.hist_len - 1;
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
   int used = 0;
   // absorbing target: a walker that starts the interval inside it fires nothing
   const bool absorbed = E.feedback == 2 && in_target(E, r, xs, 1);
+  double t_stop = 0.0;
   for (; !absorbed;) {
     const double a0 = nd[1];
     if (bits(a0) == 0) break;
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
     DepRec db = load_dep(dr, lane + 32, N.wrec_dep);
     DepRec dc = load_dep(dr, lane + 64, N.wrec_dep);
     const double tn = advance_clock(t, e, rcp_pos(a0));
-    if (bits(tn) > tau_bits) break;
+    if (bits(tn) > tau_bits) { t_stop = tn; break; }
     if (nev >= E.max_steps) { status = kStatusStepCap; break; }
     if (ps != 0) {                                      // the record holds parameter set 0
       if (da.w.x >= 0) { da.keff = keff[dep_index(da)]; da.Kn = Kn[dep_index(da)]; }
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
     }
   }
   __syncwarp();
-  finish_walker_warp(prm, r, g, par, xs, t, nev, nrec, status, lane);
+  finish_walker_warp(prm, r, g, par, xs, t, nev, nrec, status, near_tau_fp64(E.tau, t, t_stop), lane);
 }
 
 size_t propagate_warp_smem(const NetView &N, int block) {

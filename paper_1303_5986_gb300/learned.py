@@ -6,7 +6,7 @@ moves arrays between the calls.
 """
 import numpy as np
 
-from .api import MLP, first_passage_labels, we_binmap_learned, we_mlp_create
+from .api import MLP, first_passage_labels, we_mlp_coordinate_edges, we_mlp_create_init
 
 
 def harvest_states(ens, n_iters: int, every: int = 1, runs=None) -> np.ndarray:
@@ -21,14 +21,6 @@ def harvest_states(ens, n_iters: int, every: int = 1, runs=None) -> np.ndarray:
             else:
                 out.extend(ens.states(r) for r in runs)
     return np.concatenate(out, axis=0) if out else np.zeros((0, ens.n_species), np.int32)
-
-
-def init_params(n_in: int, hidden: int, seed: int) -> np.ndarray:
-    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and zero biases, FP32."""
-    rng = np.random.default_rng(seed)
-    return np.concatenate([rng.uniform(-1, 1, hidden * n_in) / np.sqrt(n_in), np.zeros(hidden),
-                           rng.uniform(-1, 1, hidden * hidden) / np.sqrt(hidden), np.zeros(hidden),
-                           rng.uniform(-1, 1, hidden) / np.sqrt(hidden), np.zeros(1)]).astype(np.float32)
 
 
 def fit_coordinate(net, states, target, recycle_state, horizon: float, hidden: int = 64,
@@ -51,7 +43,7 @@ def fit_coordinate(net, states, target, recycle_state, horizon: float, hidden: i
     xs = torch.as_tensor(st, device=labels.device)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    mlp = we_mlp_create(st.shape[1], hidden, init_params(st.shape[1], hidden, seed))
+    mlp = we_mlp_create_init(st.shape[1], hidden, seed)
     losses = mlp.train(xs, labels, steps, batch, lr, stream=stream)
     torch.cuda.synchronize()
     if timings is not None:
@@ -60,19 +52,10 @@ def fit_coordinate(net, states, target, recycle_state, horizon: float, hidden: i
     return mlp, xs, labels, losses
 
 
-def coordinate_edges(mlp: MLP, states_dev, n_bins: int, lo_q: float = 0.001, hi_q: float = 1.0,
-                     stream=None) -> np.ndarray:
-    """n_bins equal intervals of z between two quantiles of z over the given states (computed
-    with the BF16 weights that the bin map will use)."""
-    z = mlp.forward(states_dev, bf16=True, stream=stream).cpu().numpy().astype(np.float64)
-    lo, hi = np.quantile(z, lo_q), np.quantile(z, hi_q)
-    if not hi > lo:
-        hi = lo + 1.0
-    return np.linspace(lo, hi, n_bins + 1).astype(np.float32)
+def coordinate_edges(mlp: MLP, states_dev, n_bins: int, lo_q: float = 0.001, stream=None) -> np.ndarray:
+    """n_bins equal intervals of z (with the BF16 weights that the bin map will use) from a low
+    order statistic of z over the given states to its maximum, computed by the library."""
+    return we_mlp_coordinate_edges(mlp, states_dev, n_bins, lo_q, stream=stream)
 
 
-def learned_binmap(mlp: MLP, edges):
-    return we_binmap_learned(mlp, edges)
-
-
-__all__ = ["harvest_states", "init_params", "fit_coordinate", "coordinate_edges", "learned_binmap"]
+__all__ = ["harvest_states", "fit_coordinate", "coordinate_edges"]

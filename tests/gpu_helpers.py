@@ -30,6 +30,7 @@ def gpu_outputs(ens, run, hist=True):
         "flux_weight": ens.per_iter(P.WE_OUT_FLUX, run), "total_weight": ens.per_iter(P.WE_OUT_TOTAL_W, run),
         "n_walkers": ens.per_iter(P.WE_OUT_NWALKERS, run), "events": ens.per_iter(P.WE_OUT_EVENTS, run),
         "status": int(ens.status()[run]),
+        "near_tau": ens.per_iter(P.WE_OUT_NEAR_TAU, run),
     }
     if hist:
         o["hist"] = ens.per_iter(P.WE_OUT_HIST, run)
@@ -40,6 +41,8 @@ def assert_run_parity(g, o, label="", check_parent=True):
     """Bit-exact trajectories (counts, weights, order, parents, event counts); observables
     accumulated by device atomics within 1e-12 relative."""
     assert g["status"] == o["status"], (label, g["status"], o["status"])
+    # no interval ended within 2^-40 tau of an event, where a stop decision could flip
+    assert int(np.sum(g.get("near_tau", 0))) == 0, (label, "near-tau stop decisions")
     assert np.array_equal(g["n_walkers"], o["n_walkers"]), label
     assert np.array_equal(g["events"], o["events"]), label
     assert g["states"].shape == o["states"].shape, (label, g["states"].shape, o["states"].shape)

@@ -273,3 +273,40 @@ def test_learned_bins_on_the_large_network():
     n_occ = len(np.unique(M.bins_of(z, edges)))
     assert ens.get(P.WE_OUT_COUNTS)[0] == 6 * n_occ
     assert abs(ens.weights(0).sum() - 1.0) < 1e-12
+
+
+def test_coordinate_edges_are_order_statistics_of_z():
+    """Bin placement on the learned coordinate runs in the library: the low edge is the
+    floor(lo_q (n-1))-th smallest z of the states (inference form), the top edge the largest,
+    found by radix selection on the device; the edges equal fl32(lo + (hi - lo) i / n_bins)."""
+    import torch
+    rng = np.random.default_rng(8)
+    S, H, n = 3, 64, 50_001
+    mlp = P.we_mlp_create_init(S, H, seed=4)
+    X = rng.integers(0, 400, size=(n, S)).astype(np.int32)
+    X[:10] = X[10]                                        # ties
+    xd = torch.as_tensor(X, device="cuda")
+    z = mlp.forward(xd, bf16=True).cpu().numpy()
+    zs = np.sort(z)
+    for lo_q, nb in ((0.001, 100), (0.0, 7), (0.5, 1)):
+        e = P.we_mlp_coordinate_edges(mlp, xd, nb, lo_q)
+        lo = float(zs[int(np.floor(lo_q * (n - 1)))])
+        hi = float(zs[-1])
+        want = (lo + (hi - lo) * np.arange(nb + 1, dtype=np.float64) / nb).astype(np.float32)
+        assert np.array_equal(e, want), (lo_q, nb)
+
+
+def test_library_initial_weights():
+    """we_mlp_create_init: deterministic for a seed, different across seeds, weights within
+    +-1/sqrt(fan_in) and spread over that range, zero biases."""
+    S, H = 5, 64
+    a = P.we_mlp_create_init(S, H, seed=1).params()
+    b = P.we_mlp_create_init(S, H, seed=1).params()
+    c = P.we_mlp_create_init(S, H, seed=2).params()
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    w1 = a[:H * S]
+    b1 = a[H * S:H * S + H]
+    w2 = a[H * S + H:H * S + H + H * H]
+    assert np.all(b1 == 0) and a[-1] == 0
+    assert np.abs(w1).max() <= 1 / np.sqrt(S) and np.abs(w1).max() > 0.9 / np.sqrt(S)
+    assert np.abs(w2).max() <= 1 / np.sqrt(H) and abs(w2.mean()) < 0.05 / np.sqrt(H)

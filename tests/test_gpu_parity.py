@@ -93,6 +93,31 @@ def test_event_just_before_the_end_of_the_interval(mapping, block):
     assert abs(t[65] - 0.09999999837240271) < 1e-15
 
 
+@pytest.mark.parametrize("mapping,block", [(P.WE_MAP_AUTO, 0), (P.WE_MAP_AUTO, 32), (P.WE_MAP_THREAD, 0),
+                                           (P.WE_MAP_THREAD, 32), (P.WE_MAP_WARP, 0)])
+def test_near_tau_stop_decisions_are_counted(mapping, block):
+    """An interval chosen to end exactly at a walker's first event: the host computes that
+    event's time t1 = -log(u1) / a0 from the same counter-based draw (slot 0, iteration 0) and
+    sets tau = t1.  Whatever the kernel decides for that event, the walker's stop decision is
+    within 2^-40 tau of tau and WE_OUT_NEAR_TAU counts it; the other walkers of the run start
+    elsewhere and are not counted unless they too end that close."""
+    import math
+    cfg = W.birth_death_we(n_iters=1)
+    key = [int(cfg.seed) & 0xffffffff, ((int(cfg.seed) >> 32) + int(cfg.run_ids[0])) & 0xffffffff]
+    r = O.philox([0, 0, 0, 0], key)
+    u1 = O.u01(r[0], r[1])
+    a0 = O.tree_total(O.Network(cfg.network).propensities([100]))
+    cfg.tau = -math.log(u1) / a0
+    ens = gpu_run(cfg, 1, resample=False, mapping=mapping, block_threads=block)
+    ens.sync()
+    near = ens.per_iter(P.WE_OUT_NEAR_TAU, 0)
+    assert near[0] >= 1, (mapping, block, near)
+    assert near[0] <= 3
+    ens2 = gpu_run(W.birth_death_we(n_iters=1), 1, resample=False, mapping=mapping, block_threads=block)
+    ens2.sync()
+    assert ens2.per_iter(P.WE_OUT_NEAR_TAU, 0)[0] == 0
+
+
 @pytest.mark.parametrize("block", [0, 64])
 def test_two_species_table_beyond_its_range(block):
     """A toggle whose counts run past the two-species table (256 x 256 for one parameter set):
