@@ -226,29 +226,43 @@ __global__ void k_mlp_forward(MlpShape sh, const float *p, const int32_t *states
 // ------------------------------------------------------------------------------------------
 // Tensor-core inference.  Dynamic shared memory of a 128-thread block:
 //   [0, 48 KB)     three A tiles (parts 0, 1, 2 of the activations): 128 samples x 64, BF16,
-//                  core-matrix layout, 16 KB each
+//                  core-matrix layout, 16 KB each; reused chunk by chunk for the inputs of the
+//                  first layer when that layer runs on the tensor cores
 //   [48, 56 KB)    B tile: W2 (64 x 64, zero beyond H), BF16, core-matrix layout
 //   [56 KB, +16)   mbarrier, tensor-memory address
-//   [57 KB, ...)   W1 (H x n_in) and w3 (H) as BF16, then b1, b2 (H each) and b3 as FP32
+//   [57 KB, ...)   first layer on the CUDA cores (few inputs): W1 (H x n_in) as BF16;
+//                  on the tensor cores (n_in >= kTcLayer1MinInputs): W1 as ceil(n_in / 64)
+//                  B tiles of 64 x 64 (8 KB each, inputs 64c .. 64c+63, zero-padded);
+//                  then w3 (H) as BF16 and b1, b2 (H each), b3 as FP32
+// Tensor memory: 128 columns; the second layer's accumulator at column 0, the first layer's at
+// column 64.
 // ------------------------------------------------------------------------------------------
 constexpr int kTcTile = 128;
 constexpr size_t kTcWeightsOff = 57 * 1024;
 constexpr int kTcParts = 3;
 constexpr long kTcWaitLimit = 1l << 24;
+constexpr int kTcLayer1MinInputs = 32;     // below this the CUDA-core first layer is cheaper
+
+__host__ __device__ inline bool tc_layer1(int n_in) { return n_in >= kTcLayer1MinInputs; }
+__host__ __device__ inline int tc_chunks(int n_in) { return (n_in + 63) / 64; }
 
 size_t tc_mlp_smem(int n_in, int H) {
-  return kTcWeightsOff + 2 * ((size_t)H * n_in + H) + 8 + 4 * (2 * (size_t)H + 1) + 16;
+  const size_t w1 = tc_layer1(n_in) ? (size_t)tc_chunks(n_in) * 8192 : 2 * (size_t)H * n_in;
+  return kTcWeightsOff + w1 + 2 * (size_t)H + 8 + 4 * (2 * (size_t)H + 1) + 16;
 }
 
 struct TcMlp {
   unsigned char *a, *b;          // A tiles (kTcParts x 16 KB), B tile
+  unsigned char *b1;             // first-layer B tiles (tensor-core first layer), else null
+  int n_chunks;
   uint64_t *mbar;
   uint32_t *slot;
+  uint32_t phase;                // mbarrier phases completed so far
   MlpView m;                     // weights and biases in shared memory
 };
 
 // Carve the shared memory, stage the BF16 weights (w1, w2, w3 given as BF16 bits) and biases,
-// fill the B tile, allocate 64 tensor-memory columns (warp 0) and initialise the mbarrier.
+// fill the B tiles, allocate 128 tensor-memory columns (warp 0) and initialise the mbarrier.
 __device__ TcMlp tc_mlp_setup(unsigned char *sm, int n_in, int H, const uint16_t *w1, const uint16_t *w2,
                               const uint16_t *w3, const float *b1, const float *b2, const float *b3) {
   TcMlp T;
@@ -256,10 +270,23 @@ __device__ TcMlp tc_mlp_setup(unsigned char *sm, int n_in, int H, const uint16_t
   T.b = sm + 49152;
   T.mbar = reinterpret_cast<uint64_t *>(sm + 57344);
   T.slot = reinterpret_cast<uint32_t *>(sm + 57352);
+  T.phase = 0;
+  const bool tc1 = tc_layer1(n_in);
+  T.n_chunks = tc1 ? tc_chunks(n_in) : 0;
   uint16_t *sw1 = reinterpret_cast<uint16_t *>(sm + kTcWeightsOff);
-  uint16_t *sw3 = sw1 + (size_t)H * n_in;
+  T.b1 = tc1 ? sm + kTcWeightsOff : nullptr;
+  uint16_t *sw3 = tc1 ? reinterpret_cast<uint16_t *>(sm + kTcWeightsOff + (size_t)T.n_chunks * 8192)
+                      : sw1 + (size_t)H * n_in;
   float *sb = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(sw3 + H + 3) & ~(uintptr_t)7);
-  for (int i = threadIdx.x; i < H * n_in; i += blockDim.x) sw1[i] = w1[i];
+  if (tc1) {
+    for (int e = threadIdx.x; e < T.n_chunks * 64 * 64; e += blockDim.x) {
+      const int c = e >> 12, n = (e >> 6) & 63, k = e & 63, i = c * 64 + k;
+      *reinterpret_cast<uint16_t *>(T.b1 + (size_t)c * 8192 + tc_tile_offset(n, k)) =
+          (n < H && i < n_in) ? w1[(size_t)n * n_in + i] : (uint16_t)0;
+    }
+  } else {
+    for (int i = threadIdx.x; i < H * n_in; i += blockDim.x) sw1[i] = w1[i];
+  }
   for (int i = threadIdx.x; i < H; i += blockDim.x) { sw3[i] = w3[i]; sb[i] = b1[i]; sb[H + i] = b2[i]; }
   if (threadIdx.x == 0) sb[2 * H] = b3[0];
   for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
@@ -267,14 +294,14 @@ __device__ TcMlp tc_mlp_setup(unsigned char *sm, int n_in, int H, const uint16_t
     *reinterpret_cast<uint16_t *>(T.b + tc_tile_offset(n, k)) = (n < H && k < H) ? w2[n * H + k] : (uint16_t)0;
   }
   if (threadIdx.x == 0) tc_mbar_init(T.mbar, 1);
-  if (threadIdx.x < 32) tc_alloc(T.slot, 64);
+  if (threadIdx.x < 32) tc_alloc(T.slot, 128);
   tc_fence_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   T.m.n_in = n_in;
   T.m.hidden = H;
-  T.m.w1 = sw1;
+  T.m.w1 = tc1 ? nullptr : sw1;
   T.m.w2 = nullptr;
   T.m.w3 = sw3;
   T.m.b1 = sb;
@@ -283,73 +310,123 @@ __device__ TcMlp tc_mlp_setup(unsigned char *sm, int n_in, int H, const uint16_t
   return T;
 }
 
-__device__ __forceinline__ void tc_mlp_teardown(const TcMlp &T) {
+// Free the tensor memory.  After a timed-out wait (ok = false) one more bounded wait lets the
+// MMAs still in flight finish before their accumulator is released.
+__device__ __forceinline__ void tc_mlp_teardown(TcMlp &T, bool ok) {
+  if (!ok) {
+    const bool late = tc_mbar_wait(T.mbar, T.phase & 1u, kTcWaitLimit);
+    __syncthreads_or(late ? 1 : 0);
+  }
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x < 32) tc_dealloc(*T.slot, 64);
+  if (threadIdx.x < 32) tc_dealloc(*T.slot, 128);
 }
 
-// One tile: thread t holds sample t (valid or not).  First layer on the CUDA cores, activations
-// split into three BF16 parts in the A tiles (part p+1 = BF16 of what parts 0..p leave over),
-// thread 0 issues part_p . W2^T for p = 0, 1, 2 (K = 16 per instruction) into one 128 x 64
-// FP32 accumulator, every thread reads its accumulator row
-// and finishes z = b3 + sum_o w3_o silu(acc_o + b2_o).  `tile_no` counts this block's tiles
-// (mbarrier phase).  Returns false (for every thread) if the tensor core did not complete in
-// time; z is then NaN.
-__device__ bool tc_mlp_tile(const TcMlp &T, const int32_t *xs, int stride, bool valid, uint32_t tile_no, float &z) {
+// The next mbarrier phase, every thread waiting at most kTcWaitLimit polls; false (for every
+// thread) if it did not complete.  On success the phase counter advances.
+__device__ __forceinline__ bool tc_wait_phase(TcMlp &T) {
+  const bool done = __syncthreads_and(tc_mbar_wait(T.mbar, T.phase & 1u, kTcWaitLimit) ? 1 : 0) != 0;
+  tc_fence_after();
+  if (done) T.phase += 1;
+  return done;
+}
+
+// Split 8 FP32 values into kTcParts BF16 parts (part q+1 = BF16 of what parts 0..q leave over;
+// their sum equals the value to ~2^-26 relative) and store them as row t, columns col..col+7 of
+// the three A tiles.
+__device__ __forceinline__ void tc_store_parts(unsigned char *a, int t, int col, const float (&v)[8]) {
+  uint32_t pw[kTcParts][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float ra = v[2 * j], rb = v[2 * j + 1];
+#pragma unroll
+    for (int q = 0; q < kTcParts; ++q) {
+      const float pa = bf16_round_dev(ra), pb = bf16_round_dev(rb);
+      pw[q][j] = (__float_as_uint(pa) >> 16) | (__float_as_uint(pb) & 0xffff0000u);
+      ra = __fsub_rn(ra, pa);                                       // exact
+      rb = __fsub_rn(rb, pb);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kTcParts; ++q)
+    *reinterpret_cast<uint4 *>(a + q * 16384 + tc_tile_offset(t, col)) = make_uint4(pw[q][0], pw[q][1], pw[q][2], pw[q][3]);
+}
+
+// thread 0: D (tensor memory at taddr) (+)= sum over the three A parts of part . B^T, K = 64
+__device__ __forceinline__ void tc_issue_parts(const TcMlp &T, uint32_t taddr, const unsigned char *btile, bool acc) {
+  tc_fence_after();
+  constexpr uint32_t idesc = tc_idesc_bf16(kTcTile, 64);
+  const uint32_t aa = tc_smem_addr(T.a), bb = tc_smem_addr(btile);
+#pragma unroll
+  for (int part = 0; part < kTcParts; ++part)
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc)
+      tc_mma_bf16(taddr, tc_desc(aa + 16384 * part + 256 * kc, 128, 1024), tc_desc(bb + 256 * kc, 128, 1024),
+                  idesc, acc || part > 0 || kc > 0);
+  tc_commit(T.mbar);
+}
+
+// One tile: thread t holds sample t (valid or not).  First layer: on the tensor cores for
+// n_in >= kTcLayer1MinInputs (phi = log1p x of 64 inputs at a time split into three BF16 parts
+// in the A tiles, times the W1 chunk, accumulated in tensor memory column 64 on; then
+// h1 = silu(acc + b1)), else on the CUDA cores.  Second layer: the activations split into three
+// BF16 parts in the A tiles, thread 0 issues part_p . W2^T for p = 0, 1, 2 (K = 16 per
+// instruction) into one 128 x 64 FP32 accumulator at column 0; every thread reads its
+// accumulator row and finishes z = b3 + sum_o w3_o silu(acc_o + b2_o).  Returns false (for
+// every thread) if the tensor core did not complete in time; z is then NaN and the caller
+// issues no further tile.
+__device__ bool tc_mlp_tile(TcMlp &T, const int32_t *xs, int stride, bool valid, float &z) {
   const int t = threadIdx.x;
   const int H = T.m.hidden;
+  const uint32_t taddr = *T.slot;
+  z = __int_as_float(0x7fc00000);
   float h1[64];
-  mlp_layer1(T.m, xs, stride, valid, h1);
+  if (T.n_chunks > 0) {
+    const int n_in = T.m.n_in;
+    for (int c = 0; c < T.n_chunks; ++c) {
+#pragma unroll 1
+      for (int kg = 0; kg < 8; ++kg) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = c * 64 + kg * 8 + q;
+          v[q] = (valid && i < n_in) ? log1pf((float)xs[(size_t)i * stride]) : 0.0f;
+        }
+        tc_store_parts(T.a, t, kg * 8, v);
+      }
+      tc_fence_smem();
+      __syncthreads();
+      if (t == 0) tc_issue_parts(T, taddr + 64, T.b1 + (size_t)c * 8192, c > 0);
+      if (!tc_wait_phase(T)) return false;
+    }
+    float acc[64];
+    tc_ld_row64(taddr + 64, acc);
+#pragma unroll
+    for (int o = 0; o < 64; ++o) h1[o] = (o < H) ? silu_f(__fadd_rn(acc[o], T.m.b1[o])) : 0.0f;
+  } else {
+    mlp_layer1(T.m, xs, stride, valid, h1);
+  }
 #pragma unroll
   for (int kg = 0; kg < 8; ++kg) {
-    uint32_t pw[kTcParts][4];
+    float v[8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float ra = h1[kg * 8 + 2 * j], rb = h1[kg * 8 + 2 * j + 1];      // what is left to represent
-#pragma unroll
-      for (int q = 0; q < kTcParts; ++q) {
-        const float pa = bf16_round_dev(ra), pb = bf16_round_dev(rb);
-        pw[q][j] = (__float_as_uint(pa) >> 16) | (__float_as_uint(pb) & 0xffff0000u);
-        ra = __fsub_rn(ra, pa);                                       // exact
-        rb = __fsub_rn(rb, pb);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kTcParts; ++q)
-      *reinterpret_cast<uint4 *>(T.a + q * 16384 + tc_tile_offset(t, kg * 8)) =
-          make_uint4(pw[q][0], pw[q][1], pw[q][2], pw[q][3]);
+    for (int q = 0; q < 8; ++q) v[q] = h1[kg * 8 + q];
+    tc_store_parts(T.a, t, kg * 8, v);
   }
   tc_fence_smem();
   __syncthreads();
-  const uint32_t taddr = *T.slot;
-  if (t == 0) {
-    tc_fence_after();
-    constexpr uint32_t idesc = tc_idesc_bf16(kTcTile, 64);
-    const uint32_t aa = tc_smem_addr(T.a), bb = tc_smem_addr(T.b);
+  if (t == 0) tc_issue_parts(T, taddr, T.b, false);
+  if (!tc_wait_phase(T)) return false;
+  float acc[64];
+  tc_ld_row64(taddr, acc);
+  float zz = T.m.b3[0];
 #pragma unroll
-    for (int part = 0; part < kTcParts; ++part)
-#pragma unroll
-      for (int kc = 0; kc < 4; ++kc)
-        tc_mma_bf16(taddr, tc_desc(aa + 16384 * part + 256 * kc, 128, 1024), tc_desc(bb + 256 * kc, 128, 1024),
-                    idesc, part > 0 || kc > 0);
-    tc_commit(T.mbar);
-  }
-  const bool done = __syncthreads_and(tc_mbar_wait(T.mbar, tile_no & 1u, kTcWaitLimit) ? 1 : 0) != 0;
-  tc_fence_after();
-  z = __int_as_float(0x7fc00000);
-  if (done) {
-    float acc[64];
-    tc_ld_row64(taddr, acc);
-    float zz = T.m.b3[0];
-#pragma unroll
-    for (int o = 0; o < 64; ++o)
-      if (o < H) zz = __fmaf_rn(bf16_to_f32(T.m.w3[o]), silu_f(__fadd_rn(acc[o], T.m.b2[o])), zz);
-    z = zz;
-  }
+  for (int o = 0; o < 64; ++o)
+    if (o < H) zz = __fmaf_rn(bf16_to_f32(T.m.w3[o]), silu_f(__fadd_rn(acc[o], T.m.b2[o])), zz);
+  z = zz;
   tc_fence_before();
-  __syncthreads();                                    // A tiles and the accumulator free again
-  return done;
+  __syncthreads();                                    // A tiles and the accumulators free again
+  return true;
 }
 
 // z of every live walker after the SSA kernel, its bin and the bin counts (learned bin maps):
@@ -363,41 +440,42 @@ __global__ void __launch_bounds__(128) k_learned_bins(PropagateParams prm) {
   const int par = (*E.iter) & 1;
   const int ld = E.R * E.cap;
   const int total = E.run_off[E.R];
-  uint32_t tile_no = 0;
-  for (int base = blockIdx.x * kTcTile; base < total; base += gridDim.x * kTcTile, ++tile_no) {
+  bool ok = true;
+  for (int base = blockIdx.x * kTcTile; base < total && ok; base += gridDim.x * kTcTile) {
     const int f = base + (int)threadIdx.x;
     const bool valid = f < total;
     const int r = !valid ? 0 : (E.R == 1 ? 0 : find_run(E.run_off, E.R, f));
     const int g = r * E.cap + (valid ? f - E.run_off[r] : 0);
     float z;
-    const bool ok = tc_mlp_tile(T, E.x[par] + g, ld, valid, tile_no, z);
+    ok = tc_mlp_tile(T, E.x[par] + g, ld, valid, z);
     if (!valid) continue;
-    if (!ok) atomicCAS(&E.status[r], 0, WE_ETIMEOUT);
+    if (!ok) atomicCAS(&E.status[r], 0, WE_ETIMEOUT);   // this block issues no further tile
     const int b = ok ? z_bin(bv, z) : 0;
     E.bin[g] = b;
     if (bv.zout) bv.zout[g] = z;
     if (prm.resample) atomicAdd(&E.bin_count[r * bv.n_bins + b], 1);
   }
-  tc_mlp_teardown(T);
+  tc_mlp_teardown(T, ok);
 }
 
 // The standalone BF16 forward pass of given states (walker-major, n x n_in) from the FP32 master
 // weights rounded to BF16 here: the same tile computation, so z equals the binning kernel's.
 __global__ void __launch_bounds__(128) k_mlp_forward_tc(MlpShape sh, const float *p, const int32_t *states, int n,
-                                                        uint16_t *wbf, float *z) {
+                                                        uint16_t *wbf, float *z, int32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int H = sh.H, ni = sh.n_in;
   TcMlp T = tc_mlp_setup(smem_raw, ni, H, wbf, wbf + (size_t)H * ni, wbf + (size_t)H * ni + H * H,
                          p + sh.o_b1(), p + sh.o_b2(), p + sh.o_b3());
-  uint32_t tile_no = 0;
-  for (int base = blockIdx.x * kTcTile; base < n; base += gridDim.x * kTcTile, ++tile_no) {
+  bool ok = true;
+  for (int base = blockIdx.x * kTcTile; base < n && ok; base += gridDim.x * kTcTile) {
     const int b = base + (int)threadIdx.x;
     const bool valid = b < n;
     float zz;
-    tc_mlp_tile(T, states + (size_t)(valid ? b : 0) * ni, 1, valid, tile_no, zz);
+    ok = tc_mlp_tile(T, states + (size_t)(valid ? b : 0) * ni, 1, valid, zz);
     if (valid) z[b] = zz;
   }
-  tc_mlp_teardown(T);
+  if (!ok && threadIdx.x == 0) atomicCAS(status, 0, WE_ETIMEOUT);
+  tc_mlp_teardown(T, ok);
 }
 
 // BF16 bits of the weights W1, W2, w3 (round to nearest even), packed in that order.
@@ -485,6 +563,7 @@ struct we_mlp {
   MlpShape sh{};
   float *p = nullptr, *m = nullptr, *v = nullptr;   // device: params, Adam moments
   uint16_t *wbf = nullptr;                          // device: BF16 weights for the forward pass
+  int32_t *status = nullptr;                        // device: WE_ETIMEOUT of the last BF16 forward pass
   int step = 0;
 };
 
@@ -508,12 +587,13 @@ extern "C" we_status we_mlp_create(int32_t n_in, int32_t hidden, const float *pa
   const size_t np = (size_t)M->sh.n_params();
   const size_t nw = (size_t)hidden * n_in + (size_t)hidden * hidden + hidden;
   if (device_alloc((void **)&M->p, 4 * np) || device_alloc((void **)&M->m, 4 * np) ||
-      device_alloc((void **)&M->v, 4 * np) || device_alloc((void **)&M->wbf, 2 * nw)) {
+      device_alloc((void **)&M->v, 4 * np) || device_alloc((void **)&M->wbf, 2 * nw + 16)) {
     cudaGetLastError();
     cudaFree(M->p); cudaFree(M->m); cudaFree(M->v); cudaFree(M->wbf);
     delete M;
     return WE_ENOMEM;
   }
+  M->status = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(M->wbf) + ((2 * nw + 3) & ~(size_t)3));
   cudaError_t e = cudaMemcpy(M->p, params, 4 * np, cudaMemcpyHostToDevice);
   e = e ? e : cudaMemset(M->m, 0, 4 * np);
   e = e ? e : cudaMemset(M->v, 0, 4 * np);
@@ -680,6 +760,7 @@ extern "C" we_status we_mlp_forward(const we_mlp *M, const int32_t *states, int3
   if (n == 0) return WE_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
+  int32_t st_h = 0;
   if (bf16) {
     const size_t smem = tc_mlp_smem(M->sh.n_in, M->sh.H);
     if (smem > 227 * 1024) return WE_ENOTSUPPORTED;
@@ -687,14 +768,17 @@ extern "C" we_status we_mlp_forward(const we_mlp *M, const int32_t *states, int3
     e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int grid = (n + kTcTile - 1) / kTcTile;
     if (grid > 152 * 2) grid = 152 * 2;
-    if (!e) k_mlp_forward_tc<<<grid, kTcTile, smem, st>>>(M->sh, M->p, states, n, M->wbf, z);
+    e = e ? e : cudaMemsetAsync(M->status, 0, 4, st);
+    if (!e) k_mlp_forward_tc<<<grid, kTcTile, smem, st>>>(M->sh, M->p, states, n, M->wbf, z, M->status);
+    e = e ? e : cudaGetLastError();
+    e = e ? e : cudaMemcpyAsync(&st_h, M->status, 4, cudaMemcpyDeviceToHost, st);
   } else {
     k_mlp_forward<<<(n + 127) / 128, 128, 0, st>>>(M->sh, M->p, states, n, z);
   }
   e = e ? e : cudaGetLastError();
   e = e ? e : cudaStreamSynchronize(st);
   if (e) { cudaGetLastError(); return WE_ECUDA; }
-  return WE_OK;
+  return st_h ? st_h : WE_OK;
 }
 
 extern "C" we_status we_mlp_train(we_mlp *M, const int32_t *states, const float *labels, int32_t n,
