@@ -1,6 +1,8 @@
 """GPU path against the CPU oracle at the benchmarks' full sizes, in the launch configurations
-the benchmarks time (collected last: these are the longest GPU tests): the Schloegl MFPT
-workload, the 64-run toggle sweep in full, and sampled walkers of the 354 x 3680 network.
+the benchmarks time (collected late: these are the longest GPU tests): the Schloegl MFPT
+workload, the 64-run toggle sweep in full, the 354 x 3680 network (sampled walkers of its first
+interval, and whole iterations through resampling), the paper-scale Schloegl PDF run and the
+1-D birth-death configuration.
 
 The Schloegl MFPT workload with 10 replicas of 1,600 walker slots each (80 bins x 20 walkers,
 tau = 0.05, recycling at X >= 550 back to X = 85; default mapping and block shape) runs 600
@@ -38,7 +40,7 @@ def test_schlogl_benchmark_configuration_at_full_size():
     recycled, events = 0.0, 0
     for r in range(R):
         g = gpu_outputs(ens, r)
-        for key in ("flux_weight", "total_weight", "n_walkers", "events", "hist"):
+        for key in ("flux_weight", "total_weight", "n_walkers", "events", "hist", "near_tau"):
             g[key] = g[key][k:]
         o = oracle_run(cfg, r, n_iters=m, init_states=states, init_weights=weights, first_iter=k)
         assert_run_parity(g, o, label=f"benchmark configuration, run {r}")
@@ -92,3 +94,50 @@ def test_birth_death_at_full_size(target):
     ens.sync()
     assert_run_parity(gpu_outputs(ens, 0), oracle_run(cfg, 0, n_iters=cfg.n_iters),
                       label=f"birth-death, target {target}")
+
+
+def test_synthetic_354x3680_through_resampling_at_full_size():
+    """The 354 x 3680 network at the benchmark's full size through resampling: 4,096 walkers
+    run 4 iterations on the GPU (the first interval of all 4,096 walkers, then the population
+    the benchmark spends its later iterations in, ~160-250 walkers in the 2-3 occupied bins of
+    82 walkers), then 2 more on the GPU and, from the GPU's own population at iteration 4, on
+    the oracle (its full propensity recomputation per event): walkers, weights, parents, event
+    counts and observables agree."""
+    k, m = 4, 2
+    cfg = W.synthetic_large_we(n_walkers=4096, n_iters=k + m)
+    ens = gpu_run(cfg, k, record_iters=k + m)
+    ens.sync()
+    states = [ens.states(0)]
+    weights = [ens.weights(0)]
+    assert 80 <= len(states[0]) <= 600
+    ens.step(m)
+    ens.sync()
+    g = gpu_outputs(ens, 0)
+    for key in ("flux_weight", "total_weight", "n_walkers", "events", "hist", "near_tau"):
+        g[key] = g[key][k:]
+    o = oracle_run(cfg, 0, n_iters=m, init_states=states, init_weights=weights, first_iter=k)
+    assert_run_parity(g, o, label="354 x 3680 through resampling")
+    assert int(g["events"].sum()) > 500_000
+
+
+def test_schlogl_pdf_paper_scale_at_full_size():
+    """The paper's Schloegl PDF run at its scale (802 unit bins x 100 walkers, tau = 0.05, from
+    X = 82; Sec. III.B.2), two replicas: 99 iterations on the GPU (tens of thousands of walkers
+    per replica spread over hundreds of bins), then the last two iterations (to t = 5) on the GPU
+    and, from the GPU's own populations, on the oracle: the split/merge of every bin at this
+    width, and every walker, weight, parent and histogram entry, agree."""
+    k, m, R = 99, 2, 2
+    cfg = W.schlogl_pdf_we(n_iters=k + m, n_runs=R)
+    ens = gpu_run(cfg, k, record_iters=k + m)
+    ens.sync()
+    states = [ens.states(r) for r in range(R)]
+    weights = [ens.weights(r) for r in range(R)]
+    assert min(len(s) for s in states) > 20_000
+    ens.step(m)
+    ens.sync()
+    for r in range(R):
+        g = gpu_outputs(ens, r)
+        for key in ("flux_weight", "total_weight", "n_walkers", "events", "hist", "near_tau"):
+            g[key] = g[key][k:]
+        o = oracle_run(cfg, r, n_iters=m, init_states=states, init_weights=weights, first_iter=k)
+        assert_run_parity(g, o, label=f"Schloegl PDF at paper scale, run {r}")
