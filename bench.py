@@ -798,8 +798,15 @@ def run_birth_death(a):
     bm = P.we_binmap_grid(base.bins.species, base.bins.edges)
     seeds = rank_seeds(0, a.warmup + a.steps)
 
+    # the library's autotuner picks the SSA mapping and block shape for this configuration (with
+    # ~2 events per walker per interval the plain thread-per-walker table kernel can beat the
+    # pipelined one, whose rounds of 16 draws pay off only for long event chains)
+    c0, keep0 = P.run_config_from(base, record_iters=n_iters)
+    mapping, block = P.we_autotune(net, bm, c0)
+
     def ensemble(seed):
-        c, keep = P.run_config_from(W.birth_death_we(n_iters=n_iters, n_runs=R, seed=seed), record_iters=n_iters)
+        c, keep = P.run_config_from(W.birth_death_we(n_iters=n_iters, n_runs=R, seed=seed), record_iters=n_iters,
+                                    mapping=mapping, block_threads=block)
         return P.we_ensemble_create(net, bm, c, keep)
 
     warm = [ensemble(s) for s in seeds[:a.warmup]]
@@ -840,7 +847,9 @@ def run_birth_death(a):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "1-D birth-death kb=10, kd=0.1, X0=100: 60 bins of width 5 + overflow x 10 "
                                f"walkers, tau=0.1, {n_iters} iterations, 10 replicas per step",
-                   "iterations": n_iters, "l2": "flushed between timed steps (256 MB write)"},
+                   "iterations": n_iters, "l2": "flushed between timed steps (256 MB write)",
+                   "ssa_mapping": {1: "thread", 2: "warp", 3: "thread, state-indexed table"}.get(mapping, mapping),
+                   "ssa_block_threads": block},
         "ssa_events_per_s": events / (total_ms * 1e-3), "status": status,
         "roofline": {"bound": "latency", "achieved": 1.0 / per_iter_ms * 1e3, "peak": 1.0 / floor_ms * 1e3,
                      "unit": "WE iterations/s", "frac": floor_ms / per_iter_ms, "traffic": None,

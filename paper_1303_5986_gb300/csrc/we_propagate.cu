@@ -556,7 +556,7 @@ __device__ __forceinline__ int descend_row(const double *fb, unsigned long long 
 // the same as the serial loop's: the same reaction for each draw, the same waiting time, the
 // same order of clock additions.
 template <int P, int LOG2P, int D>
-__global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) {
+__global__ void __launch_bounds__(128, 3) k_propagate_pipe(PropagateParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Smem sm = load_smem<P>(prm, smem_raw);
   const EnsView &E = prm.ens;
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
 
   auto produce = [&](int buf, uint32_t base, int first, int stride) {
     if (!live) return;
-#pragma unroll 2
+#pragma unroll 1
     for (int k = first; k < K; k += stride) {
       unsigned long long m2;
       float2 e;
@@ -759,7 +759,7 @@ __global__ void __launch_bounds__(128, 4) k_propagate_pipe(PropagateParams prm) 
           int out_at = K;
           int x_out = 0, y_out = 0;
           bool ok_out = false;
-#pragma unroll
+#pragma unroll 4
           for (int kk = 0; kk < K; ++kk) {
             step(kk, true);
             const unsigned off = (unsigned)(x - win_lo);
