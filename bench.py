@@ -56,9 +56,9 @@ FP64_OPS_PER_EVENT_SCHLOGL = 12
 # the species counts): SSA, bin scan, placement, split/merge, finalize
 KERNELS_PER_ITER = 5
 # DRAM bytes (read + write) of one SSA launch on this workload, from an ncu capture of the
-# kernel (dram__bytes_read.sum + dram__bytes_write.sum, mean of two 16,000-walker launches, as
-# in every timed launch)
-SSA_TRAFFIC_BYTES = 397440
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum of the launch of iteration 600, 10,540
+# live walkers in 16,000 slots, as in the timed launches of that stage of the run)
+SSA_TRAFFIC_BYTES = 389632
 
 
 def parse():
