@@ -387,7 +387,7 @@ we_status we_ensemble_get(we_ensemble *ens, int32_t what, int32_t run, void *dst
  *     mu = (sum_i t_i + (N - n) T) / n,    with standard error sigma = mu / sqrt(n)
  * (the printed factor (1 - n/N) on T is read as (N/n - 1): only this form reproduces the
  * paper's own brute-force figures of Sec. III.C).  T <= 0 takes the time simulated so far,
- * (next iteration index) x tau.  Writes runs x 5 doubles (N, n, sum t_i, mu, sigma; mu and
+ * (next iteration index) x tau; a larger T than that is refused (WE_EINVAL).  Writes runs x 5 doubles (N, n, sum t_i, mu, sigma; mu and
  * sigma are +inf when n = 0) to dst (host or device, dst_bytes >= 40 runs); the sums run on
  * the device in slot order; synchronises the stream.  Errors: WE_EINVAL (not an absorbing
  * ensemble, dst too small, between propagate and resample), WE_ECUDA. */

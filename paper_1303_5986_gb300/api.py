@@ -505,13 +505,14 @@ def we_binmap_learned(mlp: MLP, edges) -> BinMap:
     return BinMap(h)
 
 
-def first_passage_labels(net: Network, states, horizon: float, target, recycle_state, seed: int = 0,
+def first_passage_labels(net: Network, states, horizon: float, target, recycle_state=None, seed: int = 0,
                          param_set: int = 0, stream=None):
     """Shooting labels for training a progress coordinate: label 1 where a plain SSA trajectory
     (Sec. II.A) started at a state enters the target set within `horizon` (or starts inside it),
     else 0.  states: (n, S) int; target: (species, ops, thresholds (clauses,)).  Runs one
-    unresampled interval of length `horizon` through the SSA kernel with the target as a
-    recycling set and reads each walker's recycle count.  Returns float32 labels on the device."""
+    unresampled interval of length `horizon` through the SSA kernel with the target as an
+    absorbing set and reads each walker's first-passage time (-1: none; 0: started inside).
+    `recycle_state` is not needed and ignored.  Returns float32 labels on the device."""
     import torch
     st = np.ascontiguousarray(states, dtype=np.int32)
     n, S = st.shape
@@ -519,15 +520,12 @@ def first_passage_labels(net: Network, states, horizon: float, target, recycle_s
     thr = np.asarray(thr, dtype=np.int32).reshape(1, -1)
     c, keep = make_run_config(horizon, 1, st.reshape(1, n, S), np.full((1, n), 1.0 / n), n_runs=1,
                               seed=seed, param_set=[param_set], capacity=n, record_iters=1,
-                              target=(sp, ops, thr), recycle_state=np.asarray(recycle_state).reshape(1, S),
-                              resample=False)
+                              target=(sp, ops, thr), resample=False, absorb=True)
     bm = we_binmap_grid([0], [np.array([0.0, 2.0 ** 31])])
     ens = we_ensemble_create(net, bm, c, keep, stream=stream)
     ens.propagate(stream)
     dev = ens.workspace.device
-    nrec = ens.get(L.WE_OUT_NREC, 0, stream=stream)               # host copy of the recycle counts
+    fpt = torch.empty(n, dtype=torch.float64, device=dev)
+    ens.get(L.WE_OUT_FPT, 0, out=fpt, stream=stream)             # device copy of the passage times
     ens.close()
-    inside = np.ones(n, dtype=bool)
-    for s_, o_, t_ in zip(sp, ops, thr[0]):
-        inside &= (st[:, s_] >= int(t_)) if o_ == L.WE_OP_GE else (st[:, s_] <= int(t_))
-    return torch.as_tensor(((nrec > 0) | inside).astype(np.float32), device=dev)
+    return (fpt >= 0).to(torch.float32)

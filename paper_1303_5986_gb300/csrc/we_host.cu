@@ -1291,6 +1291,10 @@ extern "C" we_status we_ensemble_fpt_mle(we_ensemble *E, double T, void *dst, si
   const int R = E->cfg.n_runs;
   if (!dst || dst_bytes < (size_t)R * 5 * sizeof(double)) return fail(WE_EINVAL, "dst must hold runs x 5 doubles");
   if (std::isnan(T) || std::isinf(T)) return fail(WE_EINVAL, "T must be finite");
+  const double simulated = (double)(E->cfg.first_iter + E->iters_enqueued) * E->cfg.tau;
+  if (T > simulated * (1.0 + 1e-12))
+    return fail(WE_EINVAL, "T = %g is past the %g simulated so far: runs that did not pass were not followed to T",
+                T, simulated);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double *res = at<double>(E->ws, E->off.mle);
   cudaError_t e = launch_fpt_mle(E->prm.ens, T, res, s);

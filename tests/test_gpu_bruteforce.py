@@ -127,3 +127,25 @@ def test_bruteforce_configuration_errors():
     with pytest.raises(P.WEError) as ei:
         bf.checkpoint()
     assert ei.value.status == P.WE_ENOTSUPPORTED
+    with pytest.raises(P.WEError) as ei:
+        bf.fpt_mle(5.0)                                  # past the 1.0 simulated so far
+    assert ei.value.status == P.WE_EINVAL
+
+
+def test_mle_without_transitions_and_with_every_walker_absorbed():
+    """Degenerate campaigns: runs too short for any passage give n = 0 and an infinite estimate
+    (Eq. "mld" has no maximum); walkers that all start inside the target give n = N, times 0,
+    and fire nothing."""
+    cfg = W.birth_death_bruteforce(n_walkers=64, tau=0.01, n_iters=2, threshold=200)
+    ens = gpu_run(cfg, cfg.n_iters, resample=False)
+    ens.sync()
+    N, n, st, mu, sig = ens.fpt_mle()[0]
+    assert N == 64 and n == 0 and st == 0.0 and np.isinf(mu) and np.isinf(sig)
+    assert np.all(ens.first_passage(0) == -1.0)
+    cfg2 = W.birth_death_bruteforce(n_walkers=32, tau=1.0, n_iters=3, threshold=50)
+    ens2 = gpu_run(cfg2, cfg2.n_iters, resample=False)
+    ens2.sync()
+    N, n, st, mu, sig = ens2.fpt_mle()[0]
+    assert N == 32 and n == 32 and st == 0.0 and mu == 0.0
+    assert np.all(ens2.first_passage(0) == 0.0)
+    assert int(ens2.per_iter(P.WE_OUT_EVENTS, 0).sum()) == 0
