@@ -52,13 +52,19 @@ ISSUE_PEAK_GOPS = 152 * 4 * 32 * 2.07
 # four propensity products, three tree additions, the target u2 * a0, two descent subtractions,
 # the division dt = -log(u1) / a0 and the clock addition -- 12, plus one logarithm.
 FP64_OPS_PER_EVENT_SCHLOGL = 12
-# kernels of one WE iteration of networks with at most 8 species (the split/merge kernel copies
-# the species counts): SSA, bin scan, placement, split/merge, finalize
-KERNELS_PER_ITER = 5
 # DRAM bytes (read + write) of one SSA launch on this workload, from an ncu capture of the
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum of the launch of iteration 600, 10,540
 # live walkers in 16,000 slots, as in the timed launches of that stage of the run)
 SSA_TRAFFIC_BYTES = 389632
+
+
+def with_resample_kernel(ens, a):
+    """Apply --resample-kernel / --resample-blocks (the library's automatic choice by default)."""
+    import paper_1303_5986_gb300 as P
+    kinds = {"auto": P.WE_RESAMPLE_AUTO, "chain": P.WE_RESAMPLE_CHAIN, "one_launch": P.WE_RESAMPLE_ONE_LAUNCH}
+    if a.resample_kernel != "auto" or a.resample_blocks:
+        ens.set_resample_kernel(kinds[a.resample_kernel], a.resample_blocks)
+    return ens
 
 
 def parse():
@@ -75,6 +81,10 @@ def parse():
     ap.add_argument("--workload", choices=["schlogl", "toggle_learned", "toggle_batch", "synthetic_large",
                                            "schlogl_flux", "schlogl_e50", "birth_death"],
                     default="schlogl")
+    ap.add_argument("--resample-kernel", choices=["auto", "chain", "one_launch"], default="auto",
+                    help="kernels of the grouping and split/merge step (same results)")
+    ap.add_argument("--resample-blocks", type=int, default=0,
+                    help="one_launch: blocks per run (0: the library's choice)")
     ap.add_argument("--report-iter", type=int, default=-1,
                     help="also report the SSA events of this iteration of the first timed step (for ncu)")
     ap.add_argument("--batch-iters", type=int, default=0,
@@ -515,7 +525,7 @@ def run_batch_workload(a):
 
     def ensemble(seed):
         c, keep = P.run_config_from(mk(seed), record_iters=n_iters)
-        return P.we_ensemble_create(net, bm, c, keep)
+        return with_resample_kernel(P.we_ensemble_create(net, bm, c, keep), a)
 
     warm = [ensemble(s) for s in seeds[:a.warmup]]
     timed = [ensemble(s) for s in seeds[a.warmup:]]
@@ -575,7 +585,7 @@ def run_batch_workload(a):
                      "share_of_step": ssa_ms_est / total_ms, "fp64_ops_per_event": ops,
                      "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz; measured beside it by "
                                     "we_measure_alu_peaks (FP64 FMA lanes/s, this GPU)"},
-        "cpu_baseline": cb, "e2e": None, "gpu_launches": (6 if a.workload == "synthetic_large" else 5) * n_iters * a.steps,
+        "cpu_baseline": cb, "e2e": None, "gpu_launches": timed[0].iteration_kernels() * n_iters * a.steps,
         "clocks": clk,
     }
     print(json.dumps(line))
@@ -807,7 +817,7 @@ def run_birth_death(a):
     def ensemble(seed):
         c, keep = P.run_config_from(W.birth_death_we(n_iters=n_iters, n_runs=R, seed=seed), record_iters=n_iters,
                                     mapping=mapping, block_threads=block)
-        return P.we_ensemble_create(net, bm, c, keep)
+        return with_resample_kernel(P.we_ensemble_create(net, bm, c, keep), a)
 
     warm = [ensemble(s) for s in seeds[:a.warmup]]
     timed = [ensemble(s) for s in seeds[a.warmup:]]
@@ -816,7 +826,8 @@ def run_birth_death(a):
         e.sync()
     for e in timed:                       # capture each timed ensemble's graphs before timing
         e.step_timed(0, every=n_iters)
-    floor_ms = P.measure_graph_floor(KERNELS_PER_ITER, 2000)
+    k_iter = timed[0].iteration_kernels()
+    floor_ms = P.measure_graph_floor(k_iter, 2000)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
@@ -853,11 +864,12 @@ def run_birth_death(a):
         "ssa_events_per_s": events / (total_ms * 1e-3), "status": status,
         "roofline": {"bound": "latency", "achieved": 1.0 / per_iter_ms * 1e3, "peak": 1.0 / floor_ms * 1e3,
                      "unit": "WE iterations/s", "frac": floor_ms / per_iter_ms, "traffic": None,
-                     "kernel": "whole iteration graph (SSA, bin scan, placement, split/merge, finalize)",
+                     "kernel": f"whole iteration graph ({k_iter} kernels: SSA, grouping by bin and split/merge, "
+                               "finalize)",
                      "ms_per_iteration": per_iter_ms, "floor_ms_per_iteration": floor_ms,
-                     "peak_source": f"measured: CUDA graph of {KERNELS_PER_ITER} empty launches of one "
+                     "peak_source": f"measured: CUDA graph of {k_iter} empty launches of one "
                                     "block per SM, replayed 2000 times (we_measure_graph_floor)"},
-        "cpu_baseline": None, "e2e": None, "gpu_launches": KERNELS_PER_ITER * n_iters * a.steps, "clocks": clk,
+        "cpu_baseline": None, "e2e": None, "gpu_launches": k_iter * n_iters * a.steps, "clocks": clk,
     }
     print(json.dumps(line))
 
@@ -957,7 +969,7 @@ def main():
     def ensemble(seed):
         cfg = mk(seed)
         c, keep = P.run_config_from(cfg, record_iters=a.iters, block_threads=a.block)
-        return P.we_ensemble_create(net, bm, c, keep)
+        return with_resample_kernel(P.we_ensemble_create(net, bm, c, keep), a)
 
     seeds = rank_seeds(rank, a.warmup + a.steps + 1)
     # every ensemble of the timed region is uploaded before timing starts (inputs resident)
@@ -1069,7 +1081,7 @@ def main():
             "mfpt_s": mfpt, "mfpt_exact_s": exact, "mfpt_rel_error": rel_err, "mfpt_rel_se": se,
             "mfpt_rel_error_per_gpu_s": rel_err / (total_ms * 1e-3 / a.steps),
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "report_iter": report_iter,
-            "gpu_launches": KERNELS_PER_ITER * a.iters * a.steps, "clocks": clk,
+            "gpu_launches": timed[0].iteration_kernels() * a.iters * a.steps, "clocks": clk,
         }
         print(json.dumps(line))
     if dist is not None:

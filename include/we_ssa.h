@@ -78,6 +78,13 @@ typedef int32_t we_status;
 #define WE_MAP_THREAD_TABLE 3  /* one thread per walker, propensity tree looked up by count
                                   (networks whose propensities all read one species) */
 
+/* Kernels of the grouping-by-bin and split/merge step (we_ensemble_set_resample_kernel). */
+#define WE_RESAMPLE_AUTO 0        /* ONE_LAUNCH for grids of up to 256 bins that fit, else CHAIN */
+#define WE_RESAMPLE_CHAIN 1       /* per-run scan, grid-wide grouping, one warp per occupied bin
+                                     (three launches; any size) */
+#define WE_RESAMPLE_ONE_LAUNCH 2  /* one launch, blocks of 512 threads, the run's walker lists in
+                                     shared memory */
+
 const char *we_status_string(we_status s);
 /* Message of the last failing call on this thread ("" if none).  Valid until the next call. */
 const char *we_last_error(void);
@@ -278,9 +285,24 @@ we_status we_ensemble_propagate(we_ensemble *ens, void *stream);
  * holds m_targ walkers and each bin keeps its total weight.  Advances the iteration counter.
  * Enqueue only. */
 we_status we_ensemble_resample(we_ensemble *ens, void *stream);
+/* Which kernels carry out the grouping by bin and the split/merge of we_ensemble_resample
+ * (Sec. II.B); every choice gives the same walkers, weights, parents and observables.
+ * kind: WE_RESAMPLE_AUTO (default), WE_RESAMPLE_CHAIN, WE_RESAMPLE_ONE_LAUNCH.  blocks_per_run
+ * (0..32, 0: about one occupied bin per warp when every bin is occupied, at most 8) applies to
+ * ONE_LAUNCH: each block of a run groups the run's walkers itself and splits/merges the bins
+ * whose task index is its own modulo blocks_per_run.  ONE_LAUNCH needs 24 n_bins + 16 capacity
+ * bytes of shared memory per block (within the device's opt-in limit) and at most 8 species.
+ * Call between iterations; synchronises the device and drops the captured iteration graphs.
+ * Errors: WE_EINVAL (NULL ensemble, unknown kind, blocks_per_run out of range, ONE_LAUNCH that
+ * does not fit, a propagate without its resample pending). */
+we_status we_ensemble_set_resample_kernel(we_ensemble *ens, int32_t kind, int32_t blocks_per_run);
 /* n_iters full WE iterations (propagate + resample), replayed from a CUDA graph captured on
  * the first call.  Enqueue only.  Errors: WE_EOVERFLOW if record_iters would be exceeded. */
 we_status we_ensemble_step(we_ensemble *ens, int32_t n_iters, void *stream);
+/* Kernel launches of one WE iteration: the kernel nodes of the iteration graph that
+ * we_ensemble_step replays (captured here if it does not exist yet; nothing runs).
+ * Errors: WE_EINVAL (NULL argument, a propagate without its resample pending), WE_ECUDA. */
+we_status we_ensemble_iteration_kernels(we_ensemble *ens, int32_t *n_kernels);
 /* The same n_iters iterations as we_ensemble_step, with the device time of every iteration's
  * SSA kernel measured by CUDA events recorded on `stream` on either side of it; synchronises
  * the stream and writes n_iters durations in milliseconds to propagate_ms (host array).  The

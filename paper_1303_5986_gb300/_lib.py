@@ -27,6 +27,9 @@ WE_MAP_AUTO = 0
 WE_MAP_THREAD = 1
 WE_MAP_WARP = 2
 WE_MAP_THREAD_TABLE = 3
+WE_RESAMPLE_AUTO = 0
+WE_RESAMPLE_CHAIN = 1
+WE_RESAMPLE_ONE_LAUNCH = 2
 WE_OUT_COUNTS = 1
 WE_OUT_STATES = 2
 WE_OUT_WEIGHTS = 3
@@ -89,6 +92,8 @@ SIGNATURES = [
     ("we_ensemble_destroy", C.c_int32, [_VP]),
     ("we_ensemble_propagate", C.c_int32, [_VP, _VP]),
     ("we_ensemble_resample", C.c_int32, [_VP, _VP]),
+    ("we_ensemble_set_resample_kernel", C.c_int32, [_VP, C.c_int32, C.c_int32]),
+    ("we_ensemble_iteration_kernels", C.c_int32, [_VP, C.POINTER(C.c_int32)]),
     ("we_ensemble_step", C.c_int32, [_VP, C.c_int32, _VP]),
     ("we_ensemble_step_timed", C.c_int32, [_VP, C.c_int32, _VP, C.POINTER(C.c_float)]),
     ("we_ensemble_step_timed_every", C.c_int32, [_VP, C.c_int32, C.c_int32, _VP, C.POINTER(C.c_float)]),

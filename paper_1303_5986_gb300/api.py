@@ -214,6 +214,16 @@ class Ensemble:
     def resample(self, stream=None):
         check(lib().we_ensemble_resample(self.h, _stream_handle(stream)))
 
+    def set_resample_kernel(self, kind: int, blocks_per_run: int = 0):
+        """WE_RESAMPLE_AUTO / WE_RESAMPLE_CHAIN / WE_RESAMPLE_ONE_LAUNCH (same results)."""
+        check(lib().we_ensemble_set_resample_kernel(self.h, int(kind), int(blocks_per_run)))
+
+    def iteration_kernels(self) -> int:
+        """Kernel launches of one WE iteration (kernel nodes of the captured iteration graph)."""
+        n = C.c_int32(0)
+        check(lib().we_ensemble_iteration_kernels(self.h, C.byref(n)))
+        return int(n.value)
+
     def step(self, n_iters: int, stream=None):
         check(lib().we_ensemble_step(self.h, int(n_iters), _stream_handle(stream)))
 

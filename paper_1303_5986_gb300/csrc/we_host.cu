@@ -29,6 +29,9 @@ cudaError_t launch_build_table(const NetView &N, const int32_t *base, int specie
 size_t propagate_warp_smem(const NetView &N, int block);
 cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st);
 cudaError_t launch_gather_finalize(const PropagateParams &prm, cudaStream_t st);
+size_t resample_run_smem(const EnsView &E, int n_bins);
+cudaError_t resample_run_prepare();
+cudaError_t launch_resample_run(const PropagateParams &prm, int blocks_per_run, cudaStream_t st);
 cudaError_t launch_fpt_mle(const EnsView &E, double T, double *out, cudaStream_t st);
 cudaError_t launch_pack_states(const EnsView &E, int r, int32_t *out, cudaStream_t st);
 cudaError_t launch_learned_bins(const PropagateParams &prm, cudaStream_t st);
@@ -522,6 +525,8 @@ struct we_ensemble {
   we_run_config cfg{};
   int32_t S = 0, cap = 0, n_bins = 0;
   int32_t mapping = WE_MAP_THREAD, block = 128;
+  int32_t resample_kernel = WE_RESAMPLE_AUTO, resample_blocks = 0;
+  int32_t graph_kernels = 0;        // kernel nodes of the captured iteration graph
   void *ws = nullptr;
   bool owns_ws = false;
   Offsets off{};
@@ -728,6 +733,7 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
     e = e ? e : up(o.lz, lb.zedges.data(), 4 * lb.zedges.size());
   }
   e = e ? e : launch_init_log_tables(at<LogTables>(ws, o.logt), s);
+  e = e ? e : resample_run_prepare();
   if (e) { cudaGetLastError(); return cleanup(cuda_fail(e, "ensemble upload")); }
 
   NetView &N = E->prm.net;
@@ -855,11 +861,22 @@ static cudaError_t enqueue_propagate(we_ensemble *E, cudaStream_t s) {
   return e;
 }
 
+// Grids of up to this many bins whose runs fit in shared memory take the one-launch split/merge.
+constexpr int kOneLaunchAutoMaxBins = 256;
+
+static bool resample_in_one_launch(const we_ensemble *E) {
+  if (E->resample_kernel == WE_RESAMPLE_CHAIN) return false;
+  if (!resample_run_smem(E->prm.ens, E->n_bins)) return false;
+  return E->resample_kernel == WE_RESAMPLE_ONE_LAUNCH || E->n_bins <= kOneLaunchAutoMaxBins;
+}
+
 static cudaError_t enqueue_resample(we_ensemble *E, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   const bool rw = E->prm.resample && E->prm.rw.period > 0;
   if (rw) e = launch_rw_flux(E->prm, s);           // before the split/merge replaces its tasks
-  if (!e && E->prm.resample) e = launch_resample_chain(E->prm, s);
+  if (!e && E->prm.resample)
+    e = resample_in_one_launch(E) ? launch_resample_run(E->prm, E->resample_blocks, s)
+                                  : launch_resample_chain(E->prm, s);
   if (!e) e = launch_gather_finalize(E->prm, s);
   if (!e && rw) e = launch_rw_solve_apply(E->prm, s);
   return e;
@@ -885,6 +902,31 @@ extern "C" we_status we_ensemble_resample(we_ensemble *E, void *stream) {
   return WE_OK;
 }
 
+static void drop_graphs(we_ensemble *E) {
+  if (E->graph) cudaGraphExecDestroy(E->graph);
+  if (E->timed_graph) cudaGraphExecDestroy(E->timed_graph);
+  if (E->timed_graph2) cudaGraphExecDestroy(E->timed_graph2);
+  if (E->timed_graph_src) cudaGraphDestroy(E->timed_graph_src);
+  E->graph = E->timed_graph = E->timed_graph2 = nullptr;
+  E->timed_graph_src = nullptr;
+  E->ev_node_start = E->ev_node_end = nullptr;
+}
+
+extern "C" we_status we_ensemble_set_resample_kernel(we_ensemble *E, int32_t kind, int32_t blocks_per_run) {
+  if (!E) return fail(WE_EINVAL, "ensemble is NULL");
+  if (kind < WE_RESAMPLE_AUTO || kind > WE_RESAMPLE_ONE_LAUNCH) return fail(WE_EINVAL, "unknown resample kernel %d", kind);
+  if (blocks_per_run < 0 || blocks_per_run > 32) return fail(WE_EINVAL, "blocks_per_run must be 0..32");
+  if (kind == WE_RESAMPLE_ONE_LAUNCH && !resample_run_smem(E->prm.ens, E->n_bins))
+    return fail(WE_EINVAL, "the one-launch split/merge needs the runs' walker lists in shared memory "
+                           "(24 n_bins + 16 capacity bytes) and at most 8 species");
+  if (E->phase_propagated) return fail(WE_EINVAL, "set the resample kernel between iterations");
+  WE_CUDA_TRY(cudaDeviceSynchronize());                  // no replay of the old graphs in flight
+  drop_graphs(E);
+  E->resample_kernel = kind;
+  E->resample_blocks = blocks_per_run;
+  return WE_OK;
+}
+
 // The iteration graph (propagate + resample), captured once per ensemble.
 static we_status build_graph(we_ensemble *E) {
   if (!E->cap_stream) WE_CUDA_TRY(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
@@ -894,9 +936,31 @@ static we_status build_graph(we_ensemble *E) {
   cudaGraph_t g = nullptr;
   cudaError_t e3 = cudaStreamEndCapture(E->cap_stream, &g);
   if (e2 || e3) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return cuda_fail(e2 ? e2 : e3, "graph capture"); }
-  cudaError_t e4 = cudaGraphInstantiate(&E->graph, g, 0);
+  size_t n_nodes = 0;
+  cudaError_t e4 = cudaGraphGetNodes(g, nullptr, &n_nodes);
+  std::vector<cudaGraphNode_t> nodes(n_nodes);
+  if (!e4 && n_nodes) e4 = cudaGraphGetNodes(g, nodes.data(), &n_nodes);
+  int32_t n_kernels = 0;
+  for (size_t i = 0; !e4 && i < n_nodes; ++i) {
+    cudaGraphNodeType t;
+    e4 = cudaGraphNodeGetType(nodes[i], &t);
+    if (!e4 && t == cudaGraphNodeTypeKernel) ++n_kernels;
+  }
+  if (!e4) e4 = cudaGraphInstantiate(&E->graph, g, 0);
   cudaGraphDestroy(g);
   if (e4) { E->graph = nullptr; return cuda_fail(e4, "graph instantiate"); }
+  E->graph_kernels = n_kernels;
+  return WE_OK;
+}
+
+extern "C" we_status we_ensemble_iteration_kernels(we_ensemble *E, int32_t *n_kernels) {
+  if (!E || !n_kernels) return fail(WE_EINVAL, "ensemble and n_kernels are required");
+  if (E->phase_propagated) return fail(WE_EINVAL, "a propagate without its resample is pending");
+  if (!E->graph) {
+    we_status st = build_graph(E);
+    if (st) return st;
+  }
+  *n_kernels = E->graph_kernels;
   return WE_OK;
 }
 

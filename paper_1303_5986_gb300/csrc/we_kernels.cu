@@ -5,6 +5,8 @@
 //   k_resample    one warp per occupied bin: merge / split (Sec. II.B)
 //   k_gather      copy species counts of the new ensemble from their parents
 //   k_finalize    per-run counts and offsets, iteration counter
+//   k_resample_run  runs whose walker lists fit in shared memory: the grouping and the
+//                 split/merge of k_scan_bins + k_place + k_resample in one launch
 //
 // Every weight operation is a single IEEE double operation with an explicit round-to-nearest
 // intrinsic; comparisons between non-negative doubles use their bit patterns.
@@ -18,18 +20,20 @@ namespace we {
 // occupied bin, where its walkers go when grouped by bin (in_offset) and where its M_targ
 // resampled walkers go in the new ensemble (out_offset = M_targ * occupied bins before it).
 // ------------------------------------------------------------------------------------------
-__global__ void k_scan_bins(EnsView E, int n_bins) {
-  const int r = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
+// One block: exclusive scans over the bins, in bin order, of the counts c_b and of the
+// occupancy [c_b > 0].  count_of(b) gives c_b; emit(b, c_b, walkers before b, occupied bins
+// before b) is called once per bin by the thread that read it.  Returns (walkers, occupied bins).
+template <typename CountOf, typename Emit>
+__device__ __forceinline__ int2 scan_bins_block(int n_bins, CountOf count_of, Emit emit) {
+  const int tid = threadIdx.x, B = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = B >> 5;
   __shared__ int s_cnt[32], s_occ[32];
   __shared__ int s_base_cnt, s_base_occ;
   if (tid == 0) { s_base_cnt = 0; s_base_occ = 0; }
   __syncthreads();
-  int *bc = E.bin_count + (size_t)r * n_bins;
-  int4 *tasks = E.tasks + (size_t)r * n_bins;
   for (int base = 0; base < n_bins; base += B) {
     const int b = base + tid;
-    const int c = b < n_bins ? bc[b] : 0;
+    const int c = b < n_bins ? count_of(b) : 0;
     const int o = c > 0 ? 1 : 0;
     int ic = c, io = o;                                   // inclusive warp scans
 #pragma unroll
@@ -52,20 +56,31 @@ __global__ void k_scan_bins(EnsView E, int n_bins) {
     }
     __syncthreads();
     const int wc = wid ? s_cnt[wid - 1] : 0, wo = wid ? s_occ[wid - 1] : 0;
-    const int ex_c = s_base_cnt + wc + ic - c;
-    const int ex_o = s_base_occ + wo + io - o;
-    if (o) {
-      tasks[ex_o] = make_int4(b, ex_c, c, ex_o * E.m_targ);
-      E.cursor[(size_t)r * n_bins + b] = ex_c;
-    }
-    if (b < n_bins) bc[b] = 0;                            // ready for the next interval
+    if (b < n_bins) emit(b, c, s_base_cnt + wc + ic - c, s_base_occ + wo + io - o);
     __syncthreads();
     if (tid == 0) { s_base_cnt += s_cnt[nw - 1]; s_base_occ += s_occ[nw - 1]; }
     __syncthreads();
   }
-  if (tid == 0) {
-    E.n_tasks[r] = s_base_occ;
-    if ((long long)s_base_occ * E.m_targ > E.cap) atomicCAS(&E.status[r], 0, kStatusOverflow);
+  return make_int2(s_base_cnt, s_base_occ);
+}
+
+__global__ void k_scan_bins(EnsView E, int n_bins) {
+  const int r = blockIdx.x;
+  int *bc = E.bin_count + (size_t)r * n_bins;
+  int4 *tasks = E.tasks + (size_t)r * n_bins;
+  int *cursor = E.cursor + (size_t)r * n_bins;
+  const int M = E.m_targ;
+  const int2 tot = scan_bins_block(n_bins, [&](int b) { return bc[b]; },
+                                   [&](int b, int c, int ex_c, int ex_o) {
+                                     if (c > 0) {
+                                       tasks[ex_o] = make_int4(b, ex_c, c, ex_o * M);
+                                       cursor[b] = ex_c;
+                                     }
+                                     bc[b] = 0;           // ready for the next interval
+                                   });
+  if (threadIdx.x == 0) {
+    E.n_tasks[r] = tot.y;
+    if ((long long)tot.y * M > E.cap) atomicCAS(&E.status[r], 0, kStatusOverflow);
   }
 }
 
@@ -136,256 +151,353 @@ __device__ __forceinline__ bool key_lt(long long wa, int sa, long long wb, int s
 // The resampled walkers are written in slot order, copies right after their parent, at the
 // bin's output offset.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 4) k_resample(EnsView E, int n_bins, int gather) {
-  const int r = blockIdx.y;
+// Per-run constants of the split/merge.
+struct ResampleCtx {
+  int iter, par, M, slot_obs;
+  size_t base;
+  double *W2;
+  int32_t *P2;
+  uint32_t k0, k1;
+  const unsigned long long *magic;
+};
+
+__device__ __forceinline__ ResampleCtx resample_ctx(const EnsView &E, int r) {
+  ResampleCtx c;
+  c.iter = *E.iter;
+  c.par = c.iter & 1;
+  c.M = E.m_targ;
+  c.slot_obs = c.iter - E.first_iter;
+  c.base = (size_t)r * E.cap;
+  c.W2 = E.w[c.par ^ 1] + c.base;
+  c.P2 = E.parent[c.par ^ 1] + c.base;
+  c.k0 = (uint32_t)E.seed;
+  c.k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
+  c.magic = E.div_magic;
+  return c;
+}
+
+// The split/merge of one occupied bin by one warp: tk = (bin, -, cnt, output offset); lss, lsw,
+// lal hold the bin's cnt walkers (slot, weight, copies) in any order, in global or shared
+// memory, and are overwritten.
+__device__ __forceinline__ void resample_bin(const EnsView &E, int r, const ResampleCtx &cx, int4 tk,
+                                             int32_t *lss, double *lsw, int32_t *lal, int gather) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int n_warps = (gridDim.x * blockDim.x) >> 5;
-  const int nt = E.n_tasks[r];
-  const int iter = *E.iter;
-  const int par = iter & 1;
-  const int M = E.m_targ;
-  const size_t base = (size_t)r * E.cap;
-  double *W2 = E.w[par ^ 1] + base;
-  int32_t *P2 = E.parent[par ^ 1] + base;
-  const uint32_t k0 = (uint32_t)E.seed;
-  const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
-  const int slot_obs = iter - E.first_iter;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const unsigned long long *magic = E.div_magic;
+  const int iter = cx.iter, par = cx.par, M = cx.M, slot_obs = cx.slot_obs;
+  const size_t base = cx.base;
+  double *W2 = cx.W2;
+  int32_t *P2 = cx.P2;
+  const uint32_t k0 = cx.k0, k1 = cx.k1;
+  const unsigned long long *magic = cx.magic;
+  const int b = tk.x, cnt = tk.z, out0 = tk.w;
+  if (out0 + M > E.cap) return;                          // capacity overflow, already flagged
 
-  for (int t = warp; t < nt; t += n_warps) {
-    const int4 tk = E.tasks[(size_t)r * n_bins + t];
-    const int b = tk.x, in0 = tk.y, cnt = tk.z, out0 = tk.w;
-    if (out0 + M > E.cap) continue;                       // capacity overflow, already flagged
-    int32_t *lss = E.sorted_slot + base + in0;
-    double *lsw = E.sorted_w + base + in0;
-    int32_t *lal = E.alive + base + in0;
+  // Register form: up to 128 walkers (entries i = lane + 32 q as index lane * 4 + q), weights
+  // as bits.  The integer split/merge decisions need normal weights (w >= 2^-999 keeps every
+  // quotient normal) and copy counts up to 2048; other bins take the floating-point path.
+  Four<long long> vv;
+  Four<int> sl;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = lane + 32 * q;
+    vv.set(q, i < cnt ? bits(lsw[i]) : -1ll);
+    sl.set(q, i < cnt ? lss[i] : 0x7FFFFFFF);
+  }
+  bool exact = magic != nullptr && cnt <= 128 && M <= 2048;
+  if (exact) {
+    bool small = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) small = small || (vv.get(q) >= 0 && (vv.get(q) >> 52) < 24);
+    exact = !__any_sync(0xffffffffu, small);
+  }
 
-    // Register form: up to 128 walkers (entries i = lane + 32 q as index lane * 4 + q), weights
-    // as bits.  The integer split/merge decisions need normal weights (w >= 2^-999 keeps every
-    // quotient normal) and copy counts up to 2048; other bins take the floating-point path.
-    Four<long long> vv;
-    Four<int> sl;
+  if (cnt > M && exact) {
+    // Merges.  Every merge's uniform is drawn up front (merge k's counter does not depend on
+    // the others); each merge takes the two lightest live entries by (weight, slot) from one
+    // branch-free shuffle reduction; the survivor decision is the integer form of
+    // u < w_p / (w_p + w_q).
+    Four<unsigned long long> ub;
+    const int n_merge = cnt - M;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = lane + 32 * q;
-      vv.set(q, i < cnt ? bits(lsw[i]) : -1ll);
-      sl.set(q, i < cnt ? lss[i] : 0x7FFFFFFF);
+      unsigned long long u = 0;
+      if (i < n_merge) {
+        uint32_t c0 = (uint32_t)i, c1 = (uint32_t)iter, c2 = (uint32_t)b, c3 = 1u;
+        philox4x32_10(c0, c1, c2, c3, k0, k1);
+        u = (unsigned long long)bits(u01(c0, c1));
+      }
+      ub.set(q, u);
     }
-    bool exact = magic != nullptr && cnt <= 128 && M <= 2048;
-    if (exact) {
-      bool small = false;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) small = small || (vv.get(q) >= 0 && (vv.get(q) >> 52) < 24);
-      exact = !__any_sync(0xffffffffu, small);
-    }
-
-    if (cnt > M && exact) {
-      // Merges.  Every merge's uniform is drawn up front (merge k's counter does not depend on
-      // the others); each merge takes the two lightest live entries by (weight, slot) from one
-      // branch-free shuffle reduction; the survivor decision is the integer form of
-      // u < w_p / (w_p + w_q).
-      Four<unsigned long long> ub;
-      const int n_merge = cnt - M;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = lane + 32 * q;
-        unsigned long long u = 0;
-        if (i < n_merge) {
-          uint32_t c0 = (uint32_t)i, c1 = (uint32_t)iter, c2 = (uint32_t)b, c3 = 1u;
-          philox4x32_10(c0, c1, c2, c3, k0, k1);
-          u = (unsigned long long)bits(u01(c0, c1));
-        }
-        ub.set(q, u);
-      }
-      for (int km = 0; km < n_merge; ++km) {
-        long long w1 = 0x7FFFFFFFFFFFFFFFll, w2 = 0x7FFFFFFFFFFFFFFFll;
-        int s1 = 0x7FFFFFFF, s2 = 0x7FFFFFFF, o1 = -1, o2 = -1;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const long long v = vv.get(q);
-          const int sq = sl.get(q), oq = lane * 4 + q;
-          const bool live = v >= 0;
-          const bool lt1 = live && key_lt(v, sq, w1, s1);
-          const bool lt2 = live && key_lt(v, sq, w2, s2);
-          w2 = lt1 ? w1 : (lt2 ? v : w2);
-          s2 = lt1 ? s1 : (lt2 ? sq : s2);
-          o2 = lt1 ? o1 : (lt2 ? oq : o2);
-          w1 = lt1 ? v : w1; s1 = lt1 ? sq : s1; o1 = lt1 ? oq : o1;
-        }
-#pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) {
-          const long long pw1 = __shfl_xor_sync(0xffffffffu, w1, d), pw2 = __shfl_xor_sync(0xffffffffu, w2, d);
-          const int ps1 = __shfl_xor_sync(0xffffffffu, s1, d), ps2 = __shfl_xor_sync(0xffffffffu, s2, d);
-          const int po1 = __shfl_xor_sync(0xffffffffu, o1, d), po2 = __shfl_xor_sync(0xffffffffu, o2, d);
-          // the lighter of the two firsts leads; the second is the lighter of the other first
-          // and the leader's own second
-          const bool plead = key_lt(pw1, ps1, w1, s1);
-          const long long cw = plead ? w1 : pw1, dw = plead ? pw2 : w2;
-          const int cs = plead ? s1 : ps1, ds = plead ? ps2 : s2;
-          const int co = plead ? o1 : po1, dob = plead ? po2 : o2;
-          const bool clt = key_lt(cw, cs, dw, ds);
-          w2 = clt ? cw : dw; s2 = clt ? cs : ds; o2 = clt ? co : dob;
-          w1 = plead ? pw1 : w1; s1 = plead ? ps1 : s1; o1 = plead ? po1 : o1;
-        }
-        const bool a_first = s1 < s2;                        // p: the lower slot of the pair
-        const long long wp = a_first ? w1 : w2, wq = a_first ? w2 : w1;
-        const int op = a_first ? o1 : o2, oq = a_first ? o2 : o1;
-        const unsigned long long u_k = __shfl_sync(0xffffffffu, ub.get(km >> 5), km & 31);
-        const double wsum = __dadd_rn(__longlong_as_double(wp), __longlong_as_double(wq));
-        const bool keep_p = ex_u_below_quotient(u_k, (unsigned long long)wp, (unsigned long long)bits(wsum));
-        const int osurv = keep_p ? op : oq, odead = keep_p ? oq : op;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          long long v = vv.get(q);
-          v = lane * 4 + q == osurv ? bits(wsum) : v;
-          v = lane * 4 + q == odead ? -1ll : v;
-          vv.set(q, v);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = lane + 32 * q;
-        const long long v = vv.get(q);
-        if (i < cnt) { lal[i] = v >= 0 ? 1 : 0; if (v >= 0) lsw[i] = __longlong_as_double(v); }
-      }
-      __syncwarp();
-    } else if (cnt > M) {
-      uint32_t kmerge = 0;
-      for (int live = cnt; live > M; --live) {
-        int ia, ib;
-        warp_argmin(lsw, lss, lal, cnt, -1, ia);
-        warp_argmin(lsw, lss, lal, cnt, ia, ib);
-        if (lane == 0) {
-          const bool a_first = lss[ia] < lss[ib];
-          const int p = a_first ? ia : ib, q = a_first ? ib : ia;
-          uint32_t c0 = kmerge, c1 = (uint32_t)iter, c2 = (uint32_t)b, c3 = 1u;
-          philox4x32_10(c0, c1, c2, c3, k0, k1);
-          const double u = u01(c0, c1);
-          const double wsum = __dadd_rn(lsw[p], lsw[q]);
-          const double prob = __ddiv_rn(lsw[p], wsum);
-          if (bits(u) < bits(prob)) { lsw[p] = wsum; lal[q] = 0; }
-          else { lsw[q] = wsum; lal[p] = 0; }
-        }
-        ++kmerge;
-        __syncwarp();
-      }
-    } else if (cnt == 1 && M > 1) {
-      if (lane == 0) lal[0] = M;                            // every copy goes to the one walker
-      __syncwarp();
-    } else if (cnt < M && exact) {
-      // Splits: the next copy to the largest per-copy weight fl(w_i / c_i) (ties: lower slot);
-      // each entry keeps the value it would have after one more copy (nv), so a round is one
-      // branch-free argmax and one integer division by the lane that holds the receiver.
-      Four<unsigned long long> wo, nv;
-      Four<int> cc;
+    for (int km = 0; km < n_merge; ++km) {
+      long long w1 = 0x7FFFFFFFFFFFFFFFll, w2 = 0x7FFFFFFFFFFFFFFFll;
+      int s1 = 0x7FFFFFFF, s2 = 0x7FFFFFFF, o1 = -1, o2 = -1;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const long long v = vv.get(q);
-        wo.set(q, (unsigned long long)v);
-        cc.set(q, v >= 0 ? 1 : 0);
-        nv.set(q, v >= 0 ? ex_div_small((unsigned long long)v, 2u, magic[2]) : 0ull);
+        const int sq = sl.get(q), oq = lane * 4 + q;
+        const bool live = v >= 0;
+        const bool lt1 = live && key_lt(v, sq, w1, s1);
+        const bool lt2 = live && key_lt(v, sq, w2, s2);
+        w2 = lt1 ? w1 : (lt2 ? v : w2);
+        s2 = lt1 ? s1 : (lt2 ? sq : s2);
+        o2 = lt1 ? o1 : (lt2 ? oq : o2);
+        w1 = lt1 ? v : w1; s1 = lt1 ? sq : s1; o1 = lt1 ? oq : o1;
       }
-      for (int extra = cnt; extra < M; ++extra) {
-        long long bv = -1;
-        int bs = 0x7FFFFFFF, bo = -1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const long long v = vv.get(q);
-          const int sq = sl.get(q);
-          const bool gt = v > bv || (v == bv && sq < bs);
-          bv = gt ? v : bv; bs = gt ? sq : bs; bo = gt ? lane * 4 + q : bo;
-        }
-#pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) {
-          const long long ov = __shfl_xor_sync(0xffffffffu, bv, d);
-          const int os = __shfl_xor_sync(0xffffffffu, bs, d);
-          const int oo = __shfl_xor_sync(0xffffffffu, bo, d);
-          const bool gt = ov > bv || (ov == bv && os < bs);
-          bv = gt ? ov : bv; bs = gt ? os : bs; bo = gt ? oo : bo;
-        }
-        if ((bo >> 2) == lane) {
-          const int q = bo & 3;
-          const int c = cc.get(q) + 1;
-          cc.set(q, c);
-          vv.set(q, (long long)nv.get(q));
-          nv.set(q, c + 1 <= M ? ex_div_small(wo.get(q), (unsigned)(c + 1), magic[c + 1]) : 0ull);
-        }
+      for (int d = 16; d >= 1; d >>= 1) {
+        const long long pw1 = __shfl_xor_sync(0xffffffffu, w1, d), pw2 = __shfl_xor_sync(0xffffffffu, w2, d);
+        const int ps1 = __shfl_xor_sync(0xffffffffu, s1, d), ps2 = __shfl_xor_sync(0xffffffffu, s2, d);
+        const int po1 = __shfl_xor_sync(0xffffffffu, o1, d), po2 = __shfl_xor_sync(0xffffffffu, o2, d);
+        // the lighter of the two firsts leads; the second is the lighter of the other first
+        // and the leader's own second
+        const bool plead = key_lt(pw1, ps1, w1, s1);
+        const long long cw = plead ? w1 : pw1, dw = plead ? pw2 : w2;
+        const int cs = plead ? s1 : ps1, ds = plead ? ps2 : s2;
+        const int co = plead ? o1 : po1, dob = plead ? po2 : o2;
+        const bool clt = key_lt(cw, cs, dw, ds);
+        w2 = clt ? cw : dw; s2 = clt ? cs : ds; o2 = clt ? co : dob;
+        w1 = plead ? pw1 : w1; s1 = plead ? ps1 : s1; o1 = plead ? po1 : o1;
       }
+      const bool a_first = s1 < s2;                        // p: the lower slot of the pair
+      const long long wp = a_first ? w1 : w2, wq = a_first ? w2 : w1;
+      const int op = a_first ? o1 : o2, oq = a_first ? o2 : o1;
+      const unsigned long long u_k = __shfl_sync(0xffffffffu, ub.get(km >> 5), km & 31);
+      const double wsum = __dadd_rn(__longlong_as_double(wp), __longlong_as_double(wq));
+      const bool keep_p = ex_u_below_quotient(u_k, (unsigned long long)wp, (unsigned long long)bits(wsum));
+      const int osurv = keep_p ? op : oq, odead = keep_p ? oq : op;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int i = lane + 32 * q;
-        if (i < cnt) lal[i] = cc.get(q);
+        long long v = vv.get(q);
+        v = lane * 4 + q == osurv ? bits(wsum) : v;
+        v = lane * 4 + q == odead ? -1ll : v;
+        vv.set(q, v);
       }
-      __syncwarp();
-    } else if (cnt < M) {
-      for (int extra = cnt; extra < M; ++extra) {
-        long long bv = -1;
-        int bs = 0x7FFFFFFF, bi = -1;
-        for (int i = lane; i < cnt; i += 32) {
-          const long long v = bits(__ddiv_rn(lsw[i], (double)lal[i]));
-          const int sli = lss[i];
-          if (v > bv || (v == bv && sli < bs)) { bv = v; bs = sli; bi = i; }
-        }
-#pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) {
-          const long long ov = __shfl_xor_sync(0xffffffffu, bv, d);
-          const int os = __shfl_xor_sync(0xffffffffu, bs, d);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, d);
-          if (ov > bv || (ov == bv && os < bs)) { bv = ov; bs = os; bi = oi; }
-        }
-        if (lane == 0) lal[bi] += 1;
-        __syncwarp();
-      }
-    }
-    // Compact the surviving entries (copies > 0) to the front of the list, order kept.
-    int k = 0;
-    for (int i0 = 0; i0 < cnt; i0 += 32) {
-      const int i = i0 + lane;
-      int sli = 0, c = 0;
-      double wv = 0.0;
-      if (i < cnt) { sli = lss[i]; c = lal[i]; wv = lsw[i]; }
-      const unsigned m = __ballot_sync(0xffffffffu, c > 0);
-      __syncwarp();
-      if (c > 0) {
-        const int d = k + __popc(m & lt_mask);
-        lss[d] = sli; lal[d] = c; lsw[d] = wv;
-      }
-      k += __popc(m);
-      __syncwarp();
-    }
-    // Output offset of each survivor: copies of all survivors with a lower slot.
-    double wsum_local = 0.0;
-    for (int i = lane; i < k; i += 32) {
-      const int si = lss[i];
-      int off = 0;
-      for (int j = 0; j < k; ++j) off += (lss[j] < si) ? lal[j] : 0;
-      const int c = lal[i];
-      const double wi = lsw[i];
-      double wc = wi;
-      if (cnt < M && c > 1)
-        wc = exact ? __longlong_as_double((long long)ex_div_small((unsigned long long)bits(wi), (unsigned)c, magic[c]))
-                   : __ddiv_rn(wi, (double)c);
-      for (int q = 0; q < c; ++q) {
-        W2[out0 + off + q] = wc;
-        P2[out0 + off + q] = si;
-      }
-      if (gather) {                                         // the copies' species counts
-        const int ld = E.R * E.cap;
-        for (int sp = 0; sp < E.S; ++sp) {
-          const int32_t v = E.x[par][(size_t)sp * ld + base + si];
-          for (int q = 0; q < c; ++q) E.x[par ^ 1][(size_t)sp * ld + base + out0 + off + q] = v;
-        }
-      }
-      // the c copies' weight, c * wc rounded once (the exact sum of the copies, rounded)
-      wsum_local = __dadd_rn(wsum_local, c == 1 ? wc : __dmul_rn((double)c, wc));
     }
 #pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) wsum_local = __dadd_rn(wsum_local, __shfl_xor_sync(0xffffffffu, wsum_local, d));
-    if (lane == 0 && slot_obs >= 0 && slot_obs < E.record_iters)
-      atomicAdd(&E.obs_totw[slot_obs * E.R + r], wsum_local);
+    for (int q = 0; q < 4; ++q) {
+      const int i = lane + 32 * q;
+      const long long v = vv.get(q);
+      if (i < cnt) { lal[i] = v >= 0 ? 1 : 0; if (v >= 0) lsw[i] = __longlong_as_double(v); }
+    }
     __syncwarp();
+  } else if (cnt > M) {
+    uint32_t kmerge = 0;
+    for (int live = cnt; live > M; --live) {
+      int ia, ib;
+      warp_argmin(lsw, lss, lal, cnt, -1, ia);
+      warp_argmin(lsw, lss, lal, cnt, ia, ib);
+      if (lane == 0) {
+        const bool a_first = lss[ia] < lss[ib];
+        const int p = a_first ? ia : ib, q = a_first ? ib : ia;
+        uint32_t c0 = kmerge, c1 = (uint32_t)iter, c2 = (uint32_t)b, c3 = 1u;
+        philox4x32_10(c0, c1, c2, c3, k0, k1);
+        const double u = u01(c0, c1);
+        const double wsum = __dadd_rn(lsw[p], lsw[q]);
+        const double prob = __ddiv_rn(lsw[p], wsum);
+        if (bits(u) < bits(prob)) { lsw[p] = wsum; lal[q] = 0; }
+        else { lsw[q] = wsum; lal[p] = 0; }
+      }
+      ++kmerge;
+      __syncwarp();
+    }
+  } else if (cnt == 1 && M > 1) {
+    if (lane == 0) lal[0] = M;                            // every copy goes to the one walker
+    __syncwarp();
+  } else if (cnt < M && exact) {
+    // Splits: the next copy to the largest per-copy weight fl(w_i / c_i) (ties: lower slot);
+    // each entry keeps the value it would have after one more copy (nv), so a round is one
+    // branch-free argmax and one integer division by the lane that holds the receiver.
+    Four<unsigned long long> wo, nv;
+    Four<int> cc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long v = vv.get(q);
+      wo.set(q, (unsigned long long)v);
+      cc.set(q, v >= 0 ? 1 : 0);
+      nv.set(q, v >= 0 ? ex_div_small((unsigned long long)v, 2u, magic[2]) : 0ull);
+    }
+    for (int extra = cnt; extra < M; ++extra) {
+      long long bv = -1;
+      int bs = 0x7FFFFFFF, bo = -1;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long v = vv.get(q);
+        const int sq = sl.get(q);
+        const bool gt = v > bv || (v == bv && sq < bs);
+        bv = gt ? v : bv; bs = gt ? sq : bs; bo = gt ? lane * 4 + q : bo;
+      }
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) {
+        const long long ov = __shfl_xor_sync(0xffffffffu, bv, d);
+        const int os = __shfl_xor_sync(0xffffffffu, bs, d);
+        const int oo = __shfl_xor_sync(0xffffffffu, bo, d);
+        const bool gt = ov > bv || (ov == bv && os < bs);
+        bv = gt ? ov : bv; bs = gt ? os : bs; bo = gt ? oo : bo;
+      }
+      if ((bo >> 2) == lane) {
+        const int q = bo & 3;
+        const int c = cc.get(q) + 1;
+        cc.set(q, c);
+        vv.set(q, (long long)nv.get(q));
+        nv.set(q, c + 1 <= M ? ex_div_small(wo.get(q), (unsigned)(c + 1), magic[c + 1]) : 0ull);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = lane + 32 * q;
+      if (i < cnt) lal[i] = cc.get(q);
+    }
+    __syncwarp();
+  } else if (cnt < M) {
+    for (int extra = cnt; extra < M; ++extra) {
+      long long bv = -1;
+      int bs = 0x7FFFFFFF, bi = -1;
+      for (int i = lane; i < cnt; i += 32) {
+        const long long v = bits(__ddiv_rn(lsw[i], (double)lal[i]));
+        const int sli = lss[i];
+        if (v > bv || (v == bv && sli < bs)) { bv = v; bs = sli; bi = i; }
+      }
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) {
+        const long long ov = __shfl_xor_sync(0xffffffffu, bv, d);
+        const int os = __shfl_xor_sync(0xffffffffu, bs, d);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, d);
+        if (ov > bv || (ov == bv && os < bs)) { bv = ov; bs = os; bi = oi; }
+      }
+      if (lane == 0) lal[bi] += 1;
+      __syncwarp();
+    }
+  }
+  // Compact the surviving entries (copies > 0) to the front of the list, order kept.
+  int k = 0;
+  for (int i0 = 0; i0 < cnt; i0 += 32) {
+    const int i = i0 + lane;
+    int sli = 0, c = 0;
+    double wv = 0.0;
+    if (i < cnt) { sli = lss[i]; c = lal[i]; wv = lsw[i]; }
+    const unsigned m = __ballot_sync(0xffffffffu, c > 0);
+    __syncwarp();
+    if (c > 0) {
+      const int d = k + __popc(m & lt_mask);
+      lss[d] = sli; lal[d] = c; lsw[d] = wv;
+    }
+    k += __popc(m);
+    __syncwarp();
+  }
+  // Output offset of each survivor: copies of all survivors with a lower slot.
+  double wsum_local = 0.0;
+  for (int i = lane; i < k; i += 32) {
+    const int si = lss[i];
+    int off = 0;
+    for (int j = 0; j < k; ++j) off += (lss[j] < si) ? lal[j] : 0;
+    const int c = lal[i];
+    const double wi = lsw[i];
+    double wc = wi;
+    if (cnt < M && c > 1)
+      wc = exact ? __longlong_as_double((long long)ex_div_small((unsigned long long)bits(wi), (unsigned)c, magic[c]))
+                 : __ddiv_rn(wi, (double)c);
+    for (int q = 0; q < c; ++q) {
+      W2[out0 + off + q] = wc;
+      P2[out0 + off + q] = si;
+    }
+    if (gather) {                                         // the copies' species counts
+      const int ld = E.R * E.cap;
+      for (int sp = 0; sp < E.S; ++sp) {
+        const int32_t v = E.x[par][(size_t)sp * ld + base + si];
+        for (int q = 0; q < c; ++q) E.x[par ^ 1][(size_t)sp * ld + base + out0 + off + q] = v;
+      }
+    }
+    // the c copies' weight, c * wc rounded once (the exact sum of the copies, rounded)
+    wsum_local = __dadd_rn(wsum_local, c == 1 ? wc : __dmul_rn((double)c, wc));
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) wsum_local = __dadd_rn(wsum_local, __shfl_xor_sync(0xffffffffu, wsum_local, d));
+  if (lane == 0 && slot_obs >= 0 && slot_obs < E.record_iters)
+    atomicAdd(&E.obs_totw[slot_obs * E.R + r], wsum_local);
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(128, 4) k_resample(EnsView E, int n_bins, int gather) {
+  const int r = blockIdx.y;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n_warps = (gridDim.x * blockDim.x) >> 5;
+  const int nt = E.n_tasks[r];
+  const ResampleCtx cx = resample_ctx(E, r);
+  for (int t = warp; t < nt; t += n_warps) {
+    const int4 tk = E.tasks[(size_t)r * n_bins + t];
+    const size_t q = cx.base + tk.y;
+    resample_bin(E, r, cx, tk, E.sorted_slot + q, E.sorted_w + q, E.alive + q, gather);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Runs whose walker lists fit in shared memory: the grouping by bin and the split/merge in one
+// launch.  G blocks serve a run.  Each block counts and scans the run's bins itself (no block
+// waits for another), keeps the occupied bins whose task index is j mod G, groups only their
+// walkers into its shared-memory lists, and splits/merges them, one warp per bin, the warps
+// taking the block's bins in task order.  Decisions and output are those of k_scan_bins +
+// k_place + k_resample: the order of a bin's list is arbitrary in both, and every decision is
+// keyed by (weight, slot).  Block 0 of a run also publishes the run's task list (read by the
+// reweighting), its task count and overflow status, and clears the run's bin counts (which the
+// SSA epilogue accumulates for k_scan_bins).
+// ------------------------------------------------------------------------------------------
+constexpr int kRunThreads = 512;
+
+__global__ void __launch_bounds__(kRunThreads, 1) k_resample_run(EnsView E, int n_bins) {
+  extern __shared__ __align__(16) unsigned char smem_run[];
+  const int r = blockIdx.y, j = blockIdx.x, G = gridDim.x;
+  const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31;
+  const int cap = E.cap, M = E.m_targ;
+  int4 *s_task = reinterpret_cast<int4 *>(smem_run);                  // n_bins
+  double *s_w = reinterpret_cast<double *>(s_task + n_bins);           // cap
+  int32_t *s_slot = reinterpret_cast<int32_t *>(s_w + cap);            // cap
+  int32_t *s_alive = s_slot + cap;                                     // cap
+  int *s_cur = s_alive + cap;                                          // n_bins: counts, then cursors
+  int *s_tob = s_cur + n_bins;                                         // n_bins: task index of each bin
+  __shared__ int s_next;
+  const ResampleCtx cx = resample_ctx(E, r);
+  const int n = E.count[r];
+  const int32_t *bin = E.bin + cx.base;
+  for (int b = tid; b < n_bins; b += B) s_cur[b] = 0;
+  __syncthreads();
+  for (int w = tid; w < n; w += B) atomicAdd(&s_cur[bin[w]], 1);
+  __syncthreads();
+  const int2 tot = scan_bins_block(n_bins, [&](int b) { return s_cur[b]; },
+                                   [&](int b, int c, int ex_c, int ex_o) {
+                                     s_tob[b] = c > 0 ? ex_o : -1;
+                                     if (c > 0) s_task[ex_o] = make_int4(b, ex_c, c, ex_o * M);
+                                     s_cur[b] = ex_c;
+                                   });
+  const int nt = tot.y;
+  if (j == 0) {
+    int4 *tasks = E.tasks + (size_t)r * n_bins;
+    int *bc = E.bin_count + (size_t)r * n_bins;
+    for (int t = tid; t < nt; t += B) tasks[t] = s_task[t];
+    for (int b = tid; b < n_bins; b += B) bc[b] = 0;
+    if (tid == 0) {
+      E.n_tasks[r] = nt;
+      if ((long long)nt * M > cap) atomicCAS(&E.status[r], 0, kStatusOverflow);
+    }
+  }
+  const double *w_in = E.w[cx.par] + cx.base;
+  for (int w = tid; w < n; w += B) {
+    const int b = bin[w];
+    if (s_tob[b] % G != j) continue;
+    const int pos = atomicAdd(&s_cur[b], 1);
+    s_slot[pos] = w;
+    s_w[pos] = w_in[w];
+    s_alive[pos] = 1;
+  }
+  if (tid == 0) s_next = j;
+  __syncthreads();
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(&s_next, G);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= nt) break;
+    const int4 tk = s_task[t];
+    resample_bin(E, r, cx, tk, s_slot + tk.y, s_w + tk.y, s_alive + tk.y, 1);
   }
 }
 
@@ -483,6 +595,52 @@ cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st) {
   if (bx > 64) bx = 64;
   if (bx < 1) bx = 1;
   k_resample<<<dim3(bx, E.R), 128, 0, st>>>(E, nb, gather_in_resample(E) ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// Shared memory of k_resample_run for this ensemble (task list, the three walker lists, bin
+// cursors and task indices), or 0 when its runs do not fit or the split/merge does not gather.
+size_t resample_run_smem(const EnsView &E, int n_bins) {
+  if (!gather_in_resample(E) || n_bins < 1 || E.cap < 1) return 0;
+  const size_t bytes = 24 * (size_t)n_bins + 16 * (size_t)E.cap;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    optin = 48 * 1024;
+  }
+  const size_t static_bytes = 1024;                      // the scan's and the task counter's
+  return bytes + static_bytes <= (size_t)optin ? bytes : 0;
+}
+
+// Let k_resample_run take up to the device's opt-in shared memory per block.  The limit is a
+// per-function setting of the process, so it is set once to the largest value (no ensemble
+// lowers another's); it does not change the occupancy of a launch that asks for less.
+cudaError_t resample_run_prepare() {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  e = e ? e : cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  e = e ? e : cudaFuncGetAttributes(&fa, k_resample_run);
+  e = e ? e : cudaFuncSetAttribute(k_resample_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
+// Blocks per run of k_resample_run: about one occupied bin per warp when every bin is occupied.
+int resample_run_blocks(int n_bins) {
+  const int warps = kRunThreads / 32;
+  const int g = (n_bins + warps - 1) / warps;
+  return g < 1 ? 1 : (g > 8 ? 8 : g);
+}
+
+cudaError_t launch_resample_run(const PropagateParams &prm, int blocks_per_run, cudaStream_t st) {
+  const EnsView &E = prm.ens;
+  const int nb = prm.bins.n_bins;
+  const size_t smem = resample_run_smem(E, nb);
+  if (!smem) return cudaErrorInvalidValue;
+  const int G = blocks_per_run > 0 ? blocks_per_run : resample_run_blocks(nb);
+  k_resample_run<<<dim3(G, E.R), kRunThreads, smem, st>>>(E, nb);
   return cudaGetLastError();
 }
 
