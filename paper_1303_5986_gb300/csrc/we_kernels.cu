@@ -176,11 +176,28 @@ __device__ __forceinline__ ResampleCtx resample_ctx(const EnsView &E, int r) {
   return c;
 }
 
+// Networks of up to kGatherInResample species have their species counts copied by the
+// split/merge warps; larger ones by k_gather, whose loads are coalesced across walkers.
+constexpr int kGatherInResample = 8;
+
+// Per-warp shared scratch of the queue form of the merges (bins of up to 128 walkers): the bin's
+// walkers sorted by (weight, slot), and the merged walkers in the order of their keys.
+constexpr int kQueueMax = 128;
+struct MergeQueues {
+  long long aw[kQueueMax];
+  int32_t as[kQueueMax], ai[kQueueMax];
+  long long qw[kQueueMax];
+  int32_t qs[kQueueMax], qi[kQueueMax];
+};
+
 // The split/merge of one occupied bin by one warp: tk = (bin, -, cnt, output offset); lss, lsw,
 // lal hold the bin's cnt walkers (slot, weight, copies) in any order, in global or shared
-// memory, and are overwritten.
+// memory, and are overwritten.  With kQueue (lists in shared memory, mq the warp's scratch) the
+// merges of bins of up to 128 walkers take the queue form below.
+template <bool kQueue>
 __device__ __forceinline__ void resample_bin(const EnsView &E, int r, const ResampleCtx &cx, int4 tk,
-                                             int32_t *lss, double *lsw, int32_t *lal, int gather) {
+                                             int32_t *lss, double *lsw, int32_t *lal, int gather,
+                                             MergeQueues *mq) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int iter = cx.iter, par = cx.par, M = cx.M, slot_obs = cx.slot_obs;
@@ -211,7 +228,99 @@ __device__ __forceinline__ void resample_bin(const EnsView &E, int r, const Resa
     exact = !__any_sync(0xffffffffu, small);
   }
 
-  if (cnt > M && exact) {
+  if (kQueue && cnt > M && cnt <= kQueueMax) {
+    // Merges, queue form.  The bin's walkers are sorted once by (weight, slot); merged walkers
+    // join a second list that stays in key order, because each merged weight is at least the
+    // previous one (the two lightest are merged, and every other walker weighs at least the
+    // heavier of them, so the next pair sums to at least as much; rounding to nearest keeps the
+    // order), so only a merged walker of equal weight and lower slot moves ahead of another.
+    // The two lightest live walkers are then always among the heads of the two lists: the same
+    // pairs, uniforms, survivor decisions (exact integer test, or the FP64 quotient where the
+    // weights are not all normal) and weights as the forms below.  Every lane runs the loop on
+    // the same values; lane 0 writes.
+    Four<unsigned long long> ub;
+    const int n_merge = cnt - M;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = lane + 32 * q;
+      unsigned long long u = 0;
+      if (i < n_merge) {
+        uint32_t c0 = (uint32_t)i, c1 = (uint32_t)iter, c2 = (uint32_t)b, c3 = 1u;
+        philox4x32_10(c0, c1, c2, c3, k0, k1);
+        u = (unsigned long long)bits(u01(c0, c1));
+      }
+      ub.set(q, u);
+    }
+    Four<int> rk;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) rk.set(q, 0);
+    for (int j = 0; j < cnt; ++j) {                       // ranks by (weight, slot): all distinct
+      const long long vj = bits(lsw[j]);
+      const int sj = lss[j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rk.set(q, rk.get(q) + (key_lt(vj, sj, vv.get(q), sl.get(q)) ? 1 : 0));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = lane + 32 * q;
+      if (i < cnt) { mq->aw[rk.get(q)] = vv.get(q); mq->as[rk.get(q)] = sl.get(q); mq->ai[rk.get(q)] = i; }
+    }
+    __syncwarp();
+    int ia = 0, qh = 0, qt = 0;
+    long long aw = mq->aw[0], qw = 0, tw = 0;               // tw, ts: key of the merged list's tail
+    int as = mq->as[0], ai = mq->ai[0], qs = 0, qi = 0, ts = 0;
+    auto pop = [&](long long &w, int &sl_, int &ix) {
+      const bool from_a = ia < cnt && (qh >= qt || key_lt(aw, as, qw, qs));
+      if (from_a) {
+        w = aw; sl_ = as; ix = ai;
+        if (++ia < cnt) { aw = mq->aw[ia]; as = mq->as[ia]; ai = mq->ai[ia]; }
+      } else {
+        w = qw; sl_ = qs; ix = qi;
+        if (++qh < qt) { qw = mq->qw[qh]; qs = mq->qs[qh]; qi = mq->qi[qh]; }
+      }
+    };
+    for (int km = 0; km < n_merge; ++km) {
+      long long w1, w2;
+      int s1, s2, i1, i2;
+      pop(w1, s1, i1);
+      pop(w2, s2, i2);
+      const bool a_first = s1 < s2;                          // p: the lower slot of the pair
+      const long long wp = a_first ? w1 : w2, wq = a_first ? w2 : w1;
+      const int sp = a_first ? s1 : s2, sq = a_first ? s2 : s1;
+      const int ip = a_first ? i1 : i2, iq = a_first ? i2 : i1;
+      const unsigned long long u_k = __shfl_sync(0xffffffffu, ub.get(km >> 5), km & 31);
+      const double wsum = __dadd_rn(__longlong_as_double(wp), __longlong_as_double(wq));
+      const bool keep_p = exact ? ex_u_below_quotient(u_k, (unsigned long long)wp, (unsigned long long)bits(wsum))
+                                : u_k < (unsigned long long)bits(__ddiv_rn(__longlong_as_double(wp), wsum));
+      const long long nw = bits(wsum);
+      const int ns = keep_p ? sp : sq, ni = keep_p ? ip : iq;
+      int pos = qt;
+      const bool behind = qt > qh && key_lt(nw, ns, tw, ts);  // equal weight, lower slot than the tail
+      if (!behind) { tw = nw; ts = ns; }
+      while (behind && pos > qh && key_lt(nw, ns, mq->qw[pos - 1], mq->qs[pos - 1])) {
+        const long long mw = mq->qw[pos - 1];
+        const int ms_ = mq->qs[pos - 1], mi = mq->qi[pos - 1];
+        __syncwarp();
+        if (lane == 0) { mq->qw[pos] = mw; mq->qs[pos] = ms_; mq->qi[pos] = mi; }
+        __syncwarp();
+        --pos;
+      }
+      if (lane == 0) { mq->qw[pos] = nw; mq->qs[pos] = ns; mq->qi[pos] = ni; }
+      __syncwarp();
+      ++qt;
+      if (pos == qh) { qw = nw; qs = ns; qi = ni; }
+    }
+    // survivors: the rest of the sorted list (weights unchanged) and of the merged list
+    for (int i = lane; i < cnt; i += 32) lal[i] = 0;
+    __syncwarp();
+    for (int t = ia + lane; t < cnt; t += 32) lal[mq->ai[t]] = 1;
+    for (int t = qh + lane; t < qt; t += 32) {
+      const int ix = mq->qi[t];
+      lal[ix] = 1;
+      lsw[ix] = __longlong_as_double(mq->qw[t]);
+    }
+    __syncwarp();
+  } else if (cnt > M && exact) {
     // Merges.  Every merge's uniform is drawn up front (merge k's counter does not depend on
     // the others); each merge takes the two lightest live entries by (weight, slot) from one
     // branch-free shuffle reduction; the survivor decision is the integer form of
@@ -304,6 +413,44 @@ __device__ __forceinline__ void resample_bin(const EnsView &E, int r, const Resa
   } else if (cnt == 1 && M > 1) {
     if (lane == 0) lal[0] = M;                            // every copy goes to the one walker
     __syncwarp();
+  } else if (kQueue && cnt < M && cnt <= 32) {
+    // Splits, sorted form (bins of up to 32 walkers): lane k holds the walker of rank k by
+    // (per-copy weight desc, slot asc); each round gives the next copy to lane 0's walker, whose
+    // per-copy weight becomes fl(w / c) for its new copy count c (exact integer division, or
+    // FP64 division where the weights are not all normal), and moves it down to its new rank
+    // (one ballot, one shift).  The same receivers in the same order as the argmax rounds
+    // below, so the same copy counts.
+    const unsigned full = 0xffffffffu;
+    const bool own = lane < cnt;
+    long long v = vv.get(0);                                // entry i = lane (cnt <= 32)
+    int s_ = sl.get(0), ix = lane, c = own ? 1 : 0;
+    int rank = 0;
+    for (int j = 0; j < cnt; ++j) {
+      const long long vj = __shfl_sync(full, v, j);
+      const int sj = __shfl_sync(full, s_, j);
+      rank += (vj > v || (vj == v && sj < s_)) ? 1 : 0;
+    }
+    if (own) { mq->aw[rank] = v; mq->as[rank] = s_; mq->ai[rank] = ix; }
+    __syncwarp();
+    if (own) { v = mq->aw[lane]; s_ = mq->as[lane]; ix = mq->ai[lane]; }
+    long long wo = v;                                       // every walker starts with one copy
+    __syncwarp();
+    for (int extra = cnt; extra < M; ++extra) {
+      const long long w0 = __shfl_sync(full, wo, 0);
+      const int c0 = __shfl_sync(full, c, 0) + 1;
+      const int s0 = __shfl_sync(full, s_, 0), i0 = __shfl_sync(full, ix, 0);
+      const long long v0 = exact ? (long long)ex_div_small((unsigned long long)w0, (unsigned)c0, magic[c0])
+                                 : bits(__ddiv_rn(__longlong_as_double(w0), (double)c0));
+      const bool above = lane >= 1 && own && (v > v0 || (v == v0 && s_ < s0));
+      const int p = __popc(__ballot_sync(full, above));      // walkers that stay ahead of it
+      const long long vn = __shfl_down_sync(full, v, 1), wn = __shfl_down_sync(full, wo, 1);
+      const int sn = __shfl_down_sync(full, s_, 1), cn = __shfl_down_sync(full, c, 1);
+      const int xn = __shfl_down_sync(full, ix, 1);
+      if (lane < p) { v = vn; wo = wn; s_ = sn; c = cn; ix = xn; }
+      else if (lane == p) { v = v0; wo = w0; s_ = s0; c = c0; ix = i0; }
+    }
+    if (own) lal[ix] = c;
+    __syncwarp();
   } else if (cnt < M && exact) {
     // Splits: the next copy to the largest per-copy weight fl(w_i / c_i) (ties: lower slot);
     // each entry keeps the value it would have after one more copy (nv), so a round is one
@@ -387,8 +534,13 @@ __device__ __forceinline__ void resample_bin(const EnsView &E, int r, const Resa
   }
   // Output offset of each survivor: copies of all survivors with a lower slot.
   double wsum_local = 0.0;
+  const int ld = E.R * E.cap;
   for (int i = lane; i < k; i += 32) {
     const int si = lss[i];
+    int32_t xv[kGatherInResample];                        // the walker's species counts, loaded
+#pragma unroll                                            // ahead of the offset sum
+    for (int sp = 0; sp < kGatherInResample; ++sp)
+      xv[sp] = (gather && sp < E.S) ? E.x[par][(size_t)sp * ld + base + si] : 0;
     int off = 0;
     for (int j = 0; j < k; ++j) off += (lss[j] < si) ? lal[j] : 0;
     const int c = lal[i];
@@ -402,11 +554,10 @@ __device__ __forceinline__ void resample_bin(const EnsView &E, int r, const Resa
       P2[out0 + off + q] = si;
     }
     if (gather) {                                         // the copies' species counts
-      const int ld = E.R * E.cap;
-      for (int sp = 0; sp < E.S; ++sp) {
-        const int32_t v = E.x[par][(size_t)sp * ld + base + si];
-        for (int q = 0; q < c; ++q) E.x[par ^ 1][(size_t)sp * ld + base + out0 + off + q] = v;
-      }
+#pragma unroll
+      for (int sp = 0; sp < kGatherInResample; ++sp)
+        if (sp < E.S)
+          for (int q = 0; q < c; ++q) E.x[par ^ 1][(size_t)sp * ld + base + out0 + off + q] = xv[sp];
     }
     // the c copies' weight, c * wc rounded once (the exact sum of the copies, rounded)
     wsum_local = __dadd_rn(wsum_local, c == 1 ? wc : __dmul_rn((double)c, wc));
@@ -427,7 +578,7 @@ __global__ void __launch_bounds__(128, 4) k_resample(EnsView E, int n_bins, int 
   for (int t = warp; t < nt; t += n_warps) {
     const int4 tk = E.tasks[(size_t)r * n_bins + t];
     const size_t q = cx.base + tk.y;
-    resample_bin(E, r, cx, tk, E.sorted_slot + q, E.sorted_w + q, E.alive + q, gather);
+    resample_bin<false>(E, r, cx, tk, E.sorted_slot + q, E.sorted_w + q, E.alive + q, gather, nullptr);
   }
 }
 
@@ -449,14 +600,21 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_resample_run(EnsView E, int 
   const int r = blockIdx.y, j = blockIdx.x, G = gridDim.x;
   const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31;
   const int cap = E.cap, M = E.m_targ;
-  int4 *s_task = reinterpret_cast<int4 *>(smem_run);                  // n_bins
+  MergeQueues *mq = reinterpret_cast<MergeQueues *>(smem_run);         // one per warp
+  unsigned long long *s_magic = reinterpret_cast<unsigned long long *>(mq + kRunThreads / 32);  // M + 1
+  int4 *s_task = reinterpret_cast<int4 *>(s_magic + ((M + 2) & ~1));   // n_bins
   double *s_w = reinterpret_cast<double *>(s_task + n_bins);           // cap
   int32_t *s_slot = reinterpret_cast<int32_t *>(s_w + cap);            // cap
   int32_t *s_alive = s_slot + cap;                                     // cap
   int *s_cur = s_alive + cap;                                          // n_bins: counts, then cursors
   int *s_tob = s_cur + n_bins;                                         // n_bins: task index of each bin
   __shared__ int s_next;
-  const ResampleCtx cx = resample_ctx(E, r);
+  ResampleCtx cx = resample_ctx(E, r);
+  // the exact division's reciprocals, read once per split round: from shared memory
+  if (cx.magic) {
+    for (int c = tid; c <= M; c += B) s_magic[c] = cx.magic[c];
+    cx.magic = s_magic;
+  }
   const int n = E.count[r];
   const int32_t *bin = E.bin + cx.base;
   for (int b = tid; b < n_bins; b += B) s_cur[b] = 0;
@@ -497,7 +655,7 @@ __global__ void __launch_bounds__(kRunThreads, 1) k_resample_run(EnsView E, int 
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= nt) break;
     const int4 tk = s_task[t];
-    resample_bin(E, r, cx, tk, s_slot + tk.y, s_w + tk.y, s_alive + tk.y, 1);
+    resample_bin<true>(E, r, cx, tk, s_slot + tk.y, s_w + tk.y, s_alive + tk.y, 1, mq + (tid >> 5));
   }
 }
 
@@ -576,10 +734,6 @@ __global__ void k_pack_states(EnsView E, int r, int32_t *out) {
 // ------------------------------------------------------------------------------------------
 // Host-side launch helpers (called from we_host.cu).
 // ------------------------------------------------------------------------------------------
-// Networks of up to kGatherInResample species have their species counts copied by the
-// split/merge warps; larger ones by k_gather, whose loads are coalesced across walkers.
-constexpr int kGatherInResample = 8;
-
 bool gather_in_resample(const EnsView &E) { return E.S <= kGatherInResample && E.x[0] != nullptr; }
 
 cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st) {
@@ -598,11 +752,12 @@ cudaError_t launch_resample_chain(const PropagateParams &prm, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Shared memory of k_resample_run for this ensemble (task list, the three walker lists, bin
-// cursors and task indices), or 0 when its runs do not fit or the split/merge does not gather.
+// Shared memory of k_resample_run for this ensemble (the warps' merge queues, the division
+// reciprocals, task list, the three walker lists, bin cursors and task indices), or 0 when its runs do not fit or the split/merge does not gather.
 size_t resample_run_smem(const EnsView &E, int n_bins) {
   if (!gather_in_resample(E) || n_bins < 1 || E.cap < 1) return 0;
-  const size_t bytes = 24 * (size_t)n_bins + 16 * (size_t)E.cap;
+  const size_t bytes = (kRunThreads / 32) * sizeof(MergeQueues) + 8 * (size_t)((E.m_targ + 2) & ~1) +
+                       24 * (size_t)n_bins + 16 * (size_t)E.cap;
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {

@@ -1,7 +1,7 @@
 """The two kernels of the grouping-by-bin and split/merge step (Sec. II.B) give the same
 ensembles: the three-launch chain (per-run scan, grid-wide grouping, one warp per occupied bin)
 and the one-launch form (each of G blocks per run groups the run's walkers in shared memory and
-splits/merges its share of the bins).  Both are held to the oracle bit for bit: counts, weights,
+splits/merges its share of the bins, merging through two key-ordered lists).  Both are held to the oracle bit for bit: counts, weights,
 order, parents and event counts exact, accumulated observables within 1e-12 relative."""
 import functools
 
@@ -36,6 +36,54 @@ def _many_merges():
                       hist_species=0, hist_len=16, name="merges")
 
 
+def _one_bin(w, m_targ, name):
+    """Walkers of the given weights in one bin of a network that does not move (every interval
+    is a pure split/merge)."""
+    spec = W.birth_death(kb=1e-9, kd=1e-9)
+    n = w.shape[1]
+    init = np.full((1, n, 1), 7, dtype=np.int32)
+    return W.WEConfig(network=spec, bins=W.GridBins([0], [W.uniform_edges(0, 5, 4)]), tau=0.1,
+                      m_targ=m_targ, n_iters=3, x0=[7], init_states=init, init_weights=w,
+                      capacity=max(n, 4 * m_targ), hist_species=0, hist_len=16, name=name)
+
+
+def _equal_weights():
+    """100 walkers of one weight merged to 7: every pair ties on weight, and so do the merged
+    sums (order by slot)."""
+    return _one_bin(np.full((1, 100), 0.01), 7, "equal_weights")
+
+
+def _few_distinct_weights():
+    """90 walkers with weights from {1, 2, 3} / norm merged to 5: merged sums tie with one another
+    and with unmerged walkers."""
+    rng = np.random.default_rng(3)
+    w = rng.integers(1, 4, size=(1, 90)).astype(np.float64)
+    return _one_bin(w / w.sum(), 5, "few_weights")
+
+
+def _tiny_weights():
+    """110 walkers below 2^-999 merged to 4: the survivor decision takes the FP64 quotient."""
+    rng = np.random.default_rng(4)
+    return _one_bin(rng.exponential(size=(1, 110)) * 1e-305, 4, "tiny_weights")
+
+
+def _equal_split():
+    """5 walkers of one weight split to 23 copies: every per-copy weight ties (order by slot)."""
+    return _one_bin(np.full((1, 5), 0.2), 23, "equal_split")
+
+
+def _split_32():
+    """32 walkers of random weight (the most the sorted split form takes) split to 61."""
+    rng = np.random.default_rng(5)
+    w = rng.exponential(size=(1, 32))
+    return _one_bin(w / w.sum(), 61, "split_32")
+
+
+def _tiny_split():
+    """3 walkers below 2^-999 split to 20: the per-copy weights by FP64 division."""
+    return _one_bin(np.array([[3e-306, 1e-305, 7e-306]]), 20, "tiny_split")
+
+
 def _toggle_small_grid():
     """Two-species toggle runs on a 12 x 12 grid (144 bins), four parameter sets."""
     cfg = W.toggle_batch_we(n_runs=4, n_iters=25, m_targ=6)
@@ -51,6 +99,12 @@ CASES = {
     "reweighted": lambda: W.schlogl_flux_we(reweight_period=3, n_iters=15, n_runs=2, m_targ=5),
     "toggle_2d": _toggle_small_grid,
     "many_merges": _many_merges,
+    "equal_weights": _equal_weights,
+    "few_distinct_weights": _few_distinct_weights,
+    "tiny_weights": _tiny_weights,
+    "equal_split": _equal_split,
+    "split_32": _split_32,
+    "tiny_split": _tiny_split,
 }
 
 
