@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
   uint32_t *sfl = reinterpret_cast<uint32_t *>(sy + 2 * K * W);         // [2][3][W] flag masks
   unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(
       (reinterpret_cast<uintptr_t>(sfl + 2 * 3 * W) + 15) & ~(uintptr_t)15);
-  __shared__ int s_more[2], s_win, s_win_n;
+  __shared__ int s_more[2], s_win, s_win_n, s_rwin, s_rwin_n;
   __shared__ int s_done[2][W];
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
     int dx = 0, dy = 0;
@@ -76,33 +76,51 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
   const int ps = live ? E.param_set[r] : 0;
   const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * TV.lenB * P;
 
-  // table rows for a window of counts around this block's walkers, in shared memory
-  int win_lo = 0, win_n = 0;
+  // table rows for a window of counts around this block's walkers, in shared memory, and a
+  // second one around the recycle count: a walker that enters the target mid-interval goes on
+  // from there, and one lane reading its rows from global memory would hold up the whole chain
+  int win_lo = 0, win_n = 0, rec_lo = 0, rec_n = 0;
   if (D == 1 && TV.smem_rows > 0) {
     if (warp == 0) {
-      int lo = 0x7fffffff, hi = -1;
+      int lo = 0x7fffffff, hi = -1, rlo = 0x7fffffff, rhi = -1;
       if (live) lo = hi = E.x[par][(size_t)TV.species * ld + g];
+      if (live && E.feedback == 1) rlo = rhi = E.recycle[r * E.S + TV.species];
       lo = __reduce_min_sync(0xffffffffu, lo);
       hi = __reduce_max_sync(0xffffffffu, hi);
+      rlo = __reduce_min_sync(0xffffffffu, rlo);
+      rhi = __reduce_max_sync(0xffffffffu, rhi);
       const int ps0 = __shfl_sync(0xffffffffu, ps, 0);
       const bool one_set = __all_sync(0xffffffffu, !live || ps == ps0);
       if (lane == 0) {
-        const int n = min(TV.smem_rows, hi - lo + 1 + 2 * kWindowMargin);
+        int n2 = (rhi >= 0 && rlo == rhi) ? min(2 * kWindowMargin + 1, TV.smem_rows / 4) : 0;
+        const int n = min(TV.smem_rows - n2, hi - lo + 1 + 2 * kWindowMargin);
         int start = (lo + hi) / 2 - n / 2;
         start = max(min(start, TV.len - n), 0);
         s_win = (one_set && hi >= 0) ? start : -1;           // no live walker: nothing to stage
         s_win_n = n;
+        if (rhi - kWindowMargin >= start && rhi + kWindowMargin < start + n) n2 = 0;   // in the first
+        s_rwin = max(min(rhi - n2 / 2, TV.len - n2), 0);
+        s_rwin_n = n2;
       }
     }
     __syncthreads();
     if (s_win >= 0) {
       win_lo = s_win;
       win_n = s_win_n;
+      rec_lo = s_rwin;
+      rec_n = s_rwin_n;
       const int ps0 = E.param_set[E.R == 1 ? 0 : find_run(E.run_off, E.R, vb * W)];
       const unsigned long long *src = TV.rows + ((size_t)ps0 * TV.len + win_lo) * P;
       for (int i = threadIdx.x; i < win_n * P; i += blockDim.x) s_tab[i] = src[i];
+      const unsigned long long *src2 = TV.rows + ((size_t)ps0 * TV.len + rec_lo) * P;
+      for (int i = threadIdx.x; i < rec_n * P; i += blockDim.x) s_tab[(size_t)win_n * P + i] = src2[i];
     }
   }
+  // position of count xv's row among the staged rows, or -1
+  auto staged = [&](int xv) {
+    const unsigned o1 = (unsigned)(xv - win_lo), o2 = (unsigned)(xv - rec_lo);
+    return o1 < (unsigned)win_n ? (int)o1 : (o2 < (unsigned)rec_n ? win_n + (int)o2 : -1);
+  };
 
   auto produce = [&](int buf, uint32_t base, int first, int stride) {
     if (!live) return;
@@ -144,9 +162,9 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
   auto in_table = [&](int xv, int yv) { return xv < TV.len && (D == 1 || yv < TV.lenB); };
   auto table_row = [&](int xv, int yv) { return tab + ((size_t)xv * TV.lenB + (D == 2 ? yv : 0)) * P; };
   auto load_row = [&](int xv, int yv) {
-    const unsigned off = (unsigned)(xv - win_lo);
-    if (D == 1 && off < (unsigned)win_n) {
-      row.read(s_tab + (size_t)off * P);
+    const int at = D == 1 ? staged(xv) : -1;
+    if (at >= 0) {
+      row.read(s_tab + (size_t)at * P);
     } else if (in_table(xv, yv)) {
       row.read(table_row(xv, yv));
     } else {
@@ -232,8 +250,8 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
 #pragma unroll 4
           for (int kk = 0; kk < K; ++kk) {
             step(kk, true);
-            const unsigned off = (unsigned)(x - win_lo);
-            if (D == 1 && off < (unsigned)win_n) row.read(s_tab + (size_t)off * P);
+            const int at = D == 1 ? staged(x) : -1;
+            if (at >= 0) row.read(s_tab + (size_t)at * P);
             else if (in_table(x, y)) row.read(table_row(x, y));
             else if (out_at == K) { out_at = kk; x_out = x; y_out = y; ok_out = ok; }
           }
