@@ -44,8 +44,35 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
   uint32_t *sfl = reinterpret_cast<uint32_t *>(sy + 2 * K * W);         // [2][3][W] flag masks
   unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(
       (reinterpret_cast<uintptr_t>(sfl + 2 * 3 * W) + 15) & ~(uintptr_t)15);
-  __shared__ int s_more[2], s_win, s_win_n, s_rwin, s_rwin_n;
+  __shared__ int s_win, s_win_n, s_rwin, s_rwin_n;
   __shared__ int s_done[2][W];
+  // Roles by sub-partition (the 3-blocks build, for launches whose slowest chain sets the time):
+  // the state chain goes to this block's warp on the lowest scheduler index, then the clock,
+  // then the draws, so that in every block the same role lands on the same sub-partition and a
+  // chain warp does not share its scheduler with another block's draw warps (measured: SSA launch
+  // 0.0889 -> 0.0857 ms on the Schloegl MFPT workload; the 4-blocks build, whose launches are
+  // throughput-bound, keeps the roles by warp index: 3 % faster there).  Only performance
+  // depends on this (a warp's slot may change after a preemption); every assignment of the four
+  // roles gives the same results.
+  __shared__ int s_role[4], s_sp[4];
+  if (MINB <= 3) {
+    unsigned wid;
+    asm volatile("mov.u32 %0, %%warpid;" : "=r"(wid));
+    if (lane == 0) s_sp[warp] = (int)(wid & 3u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int taken = 0;
+      for (int k = 0; k < 4; ++k) {                        // role k: the free warp on the lowest index
+        int best = -1;
+        for (int w = 0; w < 4; ++w)
+          if (!((taken >> w) & 1) && (best < 0 || s_sp[w] < s_sp[best])) best = w;
+        s_role[best] = k;
+        taken |= 1 << best;
+      }
+    }
+    __syncthreads();
+  }
+  const int role = MINB <= 3 ? s_role[warp] : warp;
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
     int dx = 0, dy = 0;
     for (int q = sm.meta[j].d_begin; q < sm.meta[j].d_end; ++q) {
@@ -133,10 +160,10 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
       qe[(buf * K + k) * W + lane] = e;
     }
   };
-  produce(0, 0u, warp, 4);                               // round 0: all four warps
+  produce(0, 0u, role, 4);                               // round 0: all four warps
   // absorbing target: a walker that starts the interval inside it fires nothing
   bool absorbed0 = false;
-  if (warp == 1 && live && E.feedback == 2) {
+  if (role == 1 && live && E.feedback == 2) {
     absorbed0 = true;
     for (int c = 0; c < E.n_clauses; ++c) {
       const int v = E.x[par][(size_t)E.tgt_species[c] * ld + g];
@@ -144,10 +171,7 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
       absorbed0 = absorbed0 && (E.tgt_op[c] == 0 ? v >= thr : v <= thr);
     }
   }
-  if (warp == 1) {
-    s_done[1][lane] = !live || absorbed0;
-    if (lane == 0) s_more[1] = 1;
-  }
+  if (role == 1) s_done[1][lane] = !live || absorbed0;
 
   int32_t *xme = sm.xs + lane;
   const double *keff = sm.keff + ps * P;
@@ -180,14 +204,14 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
   long long nev = 0;
   int xc = 0, yc = 0, nrec = 0, status = 0;
   bool done = !live || absorbed0, recycled = false;
-  if (live && warp <= 1) {
-    if (warp == 0)
+  if (live && role <= 1) {
+    if (role == 0)
       for (int s = 0; s < E.S; ++s) xme[s * W] = E.x[par][(size_t)s * ld + g];
     xc = E.x[par][(size_t)TV.species * ld + g];
     if (D == 2) yc = E.x[par][(size_t)TV.species2 * ld + g];
   }
   __syncthreads();
-  if (warp == 0 && live) {
+  if (role == 0 && live) {
 #pragma unroll
     for (int j = 0; j < P; ++j) { dxr[j] = s_dx[j]; dyr[j] = s_dy[j]; }
     x = xc;
@@ -214,8 +238,10 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
     load_row(x, y);
   }
 
-  for (int p = 0;; ++p) {
-    if (warp == 0) {
+  // One loop per role, each ending its phase at the same block barrier, whose OR (from the
+  // clock warp) tells every warp whether any walker goes on.
+  if (role == 0) {
+    for (int p = 0;; ++p) {
       const int qb = p % 3, sb = p & 1;
       if (live && !s_done[sb ^ 1][lane]) {
         uint32_t idle_m = 0u, ovf_m = 0u, rec_m = 0u;
@@ -276,7 +302,11 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
         sfl[(sb * 3 + 1) * W + lane] = ovf_m;
         sfl[(sb * 3 + 2) * W + lane] = rec_m;
       }
-    } else if (warp == 1) {
+      if (!__syncthreads_or(0)) break;
+    }
+  } else if (role == 1) {
+    for (int p = 0;; ++p) {
+      int go = 0;                                        // this walker goes on
       const int sb = p & 1;
       if (p >= 1) {
         const int qb = (p - 1) % 3, pb = sb ^ 1;
@@ -336,19 +366,20 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
           }
         }
         s_done[sb][lane] = done;
-        const int more = __any_sync(0xffffffffu, !done);
-        if (lane == 0) s_more[sb] = more;
+        go = !done;
       } else {
         s_done[0][lane] = done;
-        if (lane == 0) s_more[0] = 1;
+        go = 1;
       }
-    } else {
-      produce((p + 1) % 3, (uint32_t)((p + 1) * K), warp - 2, 2);
+      if (!__syncthreads_or(go)) break;
     }
-    __syncthreads();
-    if (!s_more[p & 1]) break;
+  } else {
+    for (int p = 0;; ++p) {
+      produce((p + 1) % 3, (uint32_t)((p + 1) * K), role - 2, 2);
+      if (!__syncthreads_or(0)) break;
+    }
   }
-  if (warp == 1 && live) {
+  if (role == 1 && live) {
     if (recycled && E.feedback == 1)                     // the other species take the recycle state
       for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
     xme[TV.species * W] = xc;
@@ -364,16 +395,16 @@ template <int MINB>
 static cudaError_t launch_pipe_minb(const PropagateParams &prm, int groups, cudaStream_t st) {
   const bool two = prm.tab.species2 >= 0;
   switch (prm.net.P) {
-    case 1: return two ? launch_pipe(k_propagate_pipe<1, 0, 2, MINB>, prm, groups, st)
-                       : launch_pipe(k_propagate_pipe<1, 0, 1, MINB>, prm, groups, st);
-    case 2: return two ? launch_pipe(k_propagate_pipe<2, 1, 2, MINB>, prm, groups, st)
-                       : launch_pipe(k_propagate_pipe<2, 1, 1, MINB>, prm, groups, st);
-    case 4: return two ? launch_pipe(k_propagate_pipe<4, 2, 2, MINB>, prm, groups, st)
-                       : launch_pipe(k_propagate_pipe<4, 2, 1, MINB>, prm, groups, st);
-    case 8: return two ? launch_pipe(k_propagate_pipe<8, 3, 2, MINB>, prm, groups, st)
-                       : launch_pipe(k_propagate_pipe<8, 3, 1, MINB>, prm, groups, st);
-    case 16: return two ? launch_pipe(k_propagate_pipe<16, 4, 2, MINB>, prm, groups, st)
-                        : launch_pipe(k_propagate_pipe<16, 4, 1, MINB>, prm, groups, st);
+    case 1: return two ? launch_pipe(k_propagate_pipe<1, 0, 2, MINB>, prm, groups, st, MINB)
+                       : launch_pipe(k_propagate_pipe<1, 0, 1, MINB>, prm, groups, st, MINB);
+    case 2: return two ? launch_pipe(k_propagate_pipe<2, 1, 2, MINB>, prm, groups, st, MINB)
+                       : launch_pipe(k_propagate_pipe<2, 1, 1, MINB>, prm, groups, st, MINB);
+    case 4: return two ? launch_pipe(k_propagate_pipe<4, 2, 2, MINB>, prm, groups, st, MINB)
+                       : launch_pipe(k_propagate_pipe<4, 2, 1, MINB>, prm, groups, st, MINB);
+    case 8: return two ? launch_pipe(k_propagate_pipe<8, 3, 2, MINB>, prm, groups, st, MINB)
+                       : launch_pipe(k_propagate_pipe<8, 3, 1, MINB>, prm, groups, st, MINB);
+    case 16: return two ? launch_pipe(k_propagate_pipe<16, 4, 2, MINB>, prm, groups, st, MINB)
+                        : launch_pipe(k_propagate_pipe<16, 4, 1, MINB>, prm, groups, st, MINB);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -212,11 +212,11 @@ static int device_attr(cudaDeviceAttr a, int fallback) {
 static int num_sms() { return std::max(1, device_attr(cudaDevAttrMultiProcessorCount, 1)); }
 
 template <typename K>
-static int pipe_table_rows(K kern, const PropagateParams &prm, int grid) {
+static int pipe_table_rows(K kern, const PropagateParams &prm, int grid, int max_per_sm) {
   if (prm.tab.species < 0 || prm.tab.len <= 0 || prm.tab.species2 >= 0) return 0;   // 1-D window only
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) { cudaGetLastError(); return 0; }
-  const int by_regs = std::max(1, 65536 / std::max(1, fa.numRegs * 128));
+  const int by_regs = std::min(max_per_sm, std::max(1, 65536 / std::max(1, fa.numRegs * 128)));
   const int sms = num_sms();
   const int per_sm = std::min(by_regs, std::max(1, (grid + sms - 1) / sms));
   // an SM's shared memory, shared by per_sm blocks, each of which also holds the reserved
@@ -236,21 +236,24 @@ static int pipe_table_rows(K kern, const PropagateParams &prm, int grid) {
 // Blocks of a persistent launch: enough for every capacity slot, at most the resident ones
 // (the kernels loop over groups of 32 walkers).
 template <typename K>
-static int persistent_grid(K kern, int groups) {
+static int persistent_grid(K kern, int groups, int max_per_sm = 16) {
   cudaFuncAttributes fa;
   int per_sm = 4;
   if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0)
-    per_sm = std::max(1, std::min(16, 65536 / (fa.numRegs * 128)));
+    per_sm = std::max(1, std::min(max_per_sm, 65536 / (fa.numRegs * 128)));
   else
     cudaGetLastError();
   return std::max(1, std::min(groups, per_sm * num_sms()));
 }
 
+// The pipelined kernel built for blocks_per_sm blocks per SM is launched with at most that many
+// per SM (its table window takes the shared memory they leave).
 template <typename K>
-static cudaError_t launch_pipe(K kern, const PropagateParams &prm_in, int groups, cudaStream_t st) {
+static cudaError_t launch_pipe(K kern, const PropagateParams &prm_in, int groups, cudaStream_t st,
+                               int blocks_per_sm) {
   PropagateParams prm = prm_in;
-  const int grid = persistent_grid(kern, groups);
-  prm.tab.smem_rows = pipe_table_rows(kern, prm, grid);
+  const int grid = persistent_grid(kern, groups, blocks_per_sm);
+  prm.tab.smem_rows = pipe_table_rows(kern, prm, grid, blocks_per_sm);
   // the window is sized to fill the SM's shared memory: ask for the largest carveout
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared);
