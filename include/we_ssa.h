@@ -288,7 +288,8 @@ we_status we_ensemble_resample(we_ensemble *ens, void *stream);
 /* Which kernels carry out the grouping by bin and the split/merge of we_ensemble_resample
  * (Sec. II.B); every choice gives the same walkers, weights, parents and observables.
  * kind: WE_RESAMPLE_AUTO (default), WE_RESAMPLE_CHAIN, WE_RESAMPLE_ONE_LAUNCH.  blocks_per_run
- * (0..32, 0: about one occupied bin per warp when every bin is occupied, at most 8) applies to
+ * (0..32, 0: about one bin per two warps, at most 16, and at most two blocks per SM over all
+ * runs) applies to
  * ONE_LAUNCH: each block of a run groups the run's walkers itself and splits/merges the bins
  * whose task index is its own modulo blocks_per_run.  ONE_LAUNCH needs 24 n_bins + 16 capacity
  * bytes of shared memory per block (within the device's opt-in limit) and at most 8 species.

@@ -320,7 +320,7 @@ __device__ __forceinline__ void resample_bin(const EnsView &E, int r, const Resa
       lsw[ix] = __longlong_as_double(mq->qw[t]);
     }
     __syncwarp();
-  } else if (cnt > M && exact) {
+  } else if (!kQueue && cnt > M && exact) {               // (with kQueue the queue form takes these)
     // Merges.  Every merge's uniform is drawn up front (merge k's counter does not depend on
     // the others); each merge takes the two lightest live entries by (weight, slot) from one
     // branch-free shuffle reduction; the survivor decision is the integer form of
@@ -782,11 +782,21 @@ cudaError_t resample_run_prepare() {
   return e;
 }
 
-// Blocks per run of k_resample_run: about one occupied bin per warp when every bin is occupied.
-int resample_run_blocks(int n_bins) {
-  const int warps = kRunThreads / 32;
-  const int g = (n_bins + warps - 1) / warps;
-  return g < 1 ? 1 : (g > 8 ? 8 : g);
+// Blocks per run of k_resample_run: about one bin per two warps (at most 16 blocks), and no more
+// than two blocks per SM over all runs.  Measured on GB300: the Schloegl MFPT grid (80 bins,
+// 10 runs) 111.2 / 110.3 / 110.1 ms per step with 5 / 10 / 16 blocks per run; the birth-death
+// grid (61 bins, 10 runs) 5.08 / 5.03 / 5.84 ms with 4 / 8 / 16.
+int resample_run_blocks(int n_bins, int runs) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  int g = (n_bins + 7) / 8;
+  g = g > 16 ? 16 : g;
+  const int by_sms = (2 * sms) / (runs > 0 ? runs : 1);
+  g = g > by_sms ? by_sms : g;
+  return g < 1 ? 1 : g;
 }
 
 cudaError_t launch_resample_run(const PropagateParams &prm, int blocks_per_run, cudaStream_t st) {
@@ -794,7 +804,7 @@ cudaError_t launch_resample_run(const PropagateParams &prm, int blocks_per_run, 
   const int nb = prm.bins.n_bins;
   const size_t smem = resample_run_smem(E, nb);
   if (!smem) return cudaErrorInvalidValue;
-  const int G = blocks_per_run > 0 ? blocks_per_run : resample_run_blocks(nb);
+  const int G = blocks_per_run > 0 ? blocks_per_run : resample_run_blocks(nb, E.R);
   k_resample_run<<<dim3(G, E.R), kRunThreads, smem, st>>>(E, nb);
   return cudaGetLastError();
 }
