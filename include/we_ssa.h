@@ -65,6 +65,7 @@ typedef int32_t we_status;
 /* Feedback modes of we_run_config.feedback. */
 #define WE_FEEDBACK_RECYCLE 1
 #define WE_FEEDBACK_ABSORB 2
+#define WE_FEEDBACK_ENDPOINT 3
 
 /* Target-set clause operators: x[species] >= threshold, x[species] <= threshold. */
 #define WE_OP_GE 0
@@ -223,7 +224,13 @@ typedef struct {
                                       a walker stops at the event that enters it and stays
                                       there, and the time of that first passage is kept per
                                       walker (WE_OUT_FPT): the brute-force transition-time runs
-                                      of Sec. II.C; needs resample = 0 */
+                                      of Sec. II.C; needs resample = 0.
+                                      WE_FEEDBACK_ENDPOINT (3): the target set is checked at the
+                                      end of each interval only (the protocol of checking at a
+                                      prescribed time step, Sec. IV): a walker found in it is
+                                      put in the recycle state, its weight counted as flux, and
+                                      binned there; a walker that enters and leaves within one
+                                      interval is not counted, which biases the MFPT up */
   int32_t n_clauses;               /* target set B = AND of clauses (1..4 when feedback) */
   int32_t tgt_species[4];
   int32_t tgt_op[4];               /* WE_OP_GE / WE_OP_LE */

@@ -202,7 +202,7 @@ def make_config(cfg, run: int = 0, n_iters: int | None = None, first_iter: int |
         c.bin_nbins[d] = cfg.bins.n_bins_per_dim[d]
     c.bin_edges = _p(keep["edges"], _F64P)
     if cfg.target is not None:
-        c.feedback = 2 if getattr(cfg, "absorb", False) else 1
+        c.feedback = 2 if getattr(cfg, "absorb", False) else (3 if getattr(cfg, "endpoint", False) else 1)
         c.n_clauses = len(cfg.target.species)
         for i in range(c.n_clauses):
             c.tgt_species[i] = cfg.target.species[i]

@@ -263,7 +263,8 @@ static int in_target(const orc_we_config *cfg, const int32_t *x) {
  * running for the rest of the interval (first passage is detected at the event that crosses).
  * With absorbing feedback (the brute-force runs of Sec. II.C, which record the time of the
  * first transition), a walker stops at the event that enters B and stays there; one that starts
- * the interval inside B fires nothing.
+ * the interval inside B fires nothing.  With the end-of-interval check (feedback 3: B checked
+ * at a prescribed time step, Sec. IV), only a walker in B when the interval ends is recycled.
  * ------------------------------------------------------------------------------------------ */
 int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int32_t slot,
                   int32_t *x, int64_t *n_ev, int32_t *n_rec, double *t_last) {
@@ -306,7 +307,7 @@ int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int3
     memcpy(x, xn, sizeof(int32_t) * S);
     ++ev;
     t = tn;
-    if (cfg->feedback && in_target(cfg, x)) {
+    if ((cfg->feedback == 1 || cfg->feedback == 2) && in_target(cfg, x)) {
       ++rec;
       if (cfg->feedback == 2) break;                          /* first passage: stop here */
       memcpy(x, cfg->recycle_state, sizeof(int32_t) * S);
@@ -314,6 +315,10 @@ int orc_propagate(const orc_net *n, const orc_we_config *cfg, int32_t iter, int3
     orc_propensities(n, x, a);
   }
   free(a); free(xn);
+  if (cfg->feedback == 3 && in_target(cfg, x)) {             /* checked at the interval's end */
+    ++rec;
+    memcpy(x, cfg->recycle_state, sizeof(int32_t) * S);
+  }
   *n_ev = ev;
   *n_rec = rec;
   if (t_last) *t_last = t;
@@ -833,7 +838,7 @@ int orc_propagate_dg(const orc_dg *g, const orc_we_config *cfg, int32_t iter, in
     for (int32_t e = n->d_ptr[j]; e < n->d_ptr[j + 1]; ++e) x[n->d_sp[e]] += n->d_val[e];
     ++ev;
     t = tn;
-    if (cfg->feedback && in_target(cfg, x)) {
+    if ((cfg->feedback == 1 || cfg->feedback == 2) && in_target(cfg, x)) {
       ++rec;
       if (cfg->feedback == 2) break;
       memcpy(x, cfg->recycle_state, sizeof(int32_t) * S);
@@ -848,6 +853,10 @@ int orc_propagate_dg(const orc_dg *g, const orc_we_config *cfg, int32_t iter, in
   }
 #undef DG_REBUILD
   free(node);
+  if (cfg->feedback == 3 && in_target(cfg, x)) {             /* checked at the interval's end */
+    ++rec;
+    memcpy(x, cfg->recycle_state, sizeof(int32_t) * S);
+  }
   *n_ev = ev;
   *n_rec = rec;
   if (t_last) *t_last = t;

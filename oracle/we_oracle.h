@@ -72,7 +72,10 @@ typedef struct {
   int32_t feedback;                  /* 0: none; 1: recycle walkers entering the target set
                                         (Sec. II.B.2); 2: absorb them -- a walker stops at its
                                         first entrance and stays there (the brute-force
-                                        transition-time runs of Sec. II.C; resample = 0 only) */
+                                        transition-time runs of Sec. II.C; resample = 0 only);
+                                        3: check the target set at the end of each interval
+                                        only and recycle a walker found in it (B checked at a
+                                        prescribed time step, Sec. IV) */
   int32_t n_clauses;                 /* target set = AND of clauses  x[species] op threshold */
   int32_t tgt_species[4], tgt_op[4], tgt_threshold[4];
   const int32_t *recycle_state;      /* S */

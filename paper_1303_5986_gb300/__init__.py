@@ -8,7 +8,7 @@ from ._lib import (WEError, WE_OK, WE_EINVAL, WE_ENOMEM, WE_ECUDA, WE_EOVERFLOW,
                    WE_MAP_WARP, WE_MAP_THREAD_TABLE, WE_RESAMPLE_AUTO, WE_RESAMPLE_CHAIN, WE_RESAMPLE_ONE_LAUNCH, WE_OP_GE, WE_OP_LE, WE_OUT_COUNTS, WE_OUT_STATES, WE_OUT_WEIGHTS,
                    WE_OUT_PARENT, WE_OUT_FLUX, WE_OUT_TOTAL_W, WE_OUT_NWALKERS, WE_OUT_EVENTS,
                    WE_OUT_HIST, WE_OUT_STATUS, WE_OUT_ITER, WE_OUT_RECORDED, WE_OUT_TLAST,
-                   WE_OUT_Z, WE_OUT_NREC, WE_OUT_RW, WE_OUT_FPT, WE_OUT_NEAR_TAU, WE_FEEDBACK_RECYCLE, WE_FEEDBACK_ABSORB,
+                   WE_OUT_Z, WE_OUT_NREC, WE_OUT_RW, WE_OUT_FPT, WE_OUT_NEAR_TAU, WE_FEEDBACK_RECYCLE, WE_FEEDBACK_ABSORB, WE_FEEDBACK_ENDPOINT,
                    SIGNATURES, lib, status_name)
 from .api import (Network, BinMap, Ensemble, we_network_create, network_from_spec, we_binmap_grid,
                   make_run_config, run_config_from, we_ensemble_workspace_bytes,

@@ -50,6 +50,7 @@ WE_OUT_FPT = 17
 WE_OUT_NEAR_TAU = 18
 WE_FEEDBACK_RECYCLE = 1
 WE_FEEDBACK_ABSORB = 2
+WE_FEEDBACK_ENDPOINT = 3
 
 _I32P = C.POINTER(C.c_int32)
 _U32P = C.POINTER(C.c_uint32)

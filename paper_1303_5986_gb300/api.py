@@ -111,10 +111,12 @@ def we_binmap_grid(species, edges) -> BinMap:
 def make_run_config(tau, m_targ, init_states, init_weights, *, n_runs=None, seed=0, run_ids=None,
                     param_set=None, first_iter=0, capacity=0, record_iters=1, target=None,
                     recycle_state=None, max_steps=0, hist_species=0, hist_len=0, resample=True,
-                    mapping=L.WE_MAP_AUTO, block_threads=0, reweight_period=0, absorb=False):
+                    mapping=L.WE_MAP_AUTO, block_threads=0, reweight_period=0, absorb=False,
+                    endpoint=False):
     """Build a we_run_config.  init_states: (runs, n_init, S); init_weights: (runs, n_init);
     target: None or (species list, op list, thresholds (runs, clauses)); absorb: the target set
-    is absorbing (brute-force first-passage runs, needs resample=False) instead of recycling.  Returns
+    is absorbing (brute-force first-passage runs, needs resample=False) instead of recycling;
+    endpoint: the target set is checked at each interval's end only.  Returns
     (config, keepalive) -- keep the second object alive while the config is used."""
     ist = _i32(init_states)
     iw = _f64(init_weights)
@@ -140,7 +142,8 @@ def make_run_config(tau, m_targ, init_states, init_weights, *, n_runs=None, seed
     if target is not None:
         sp, ops, thr = target
         keep["thr"] = _i32(thr).reshape(R, len(sp))
-        c.feedback = L.WE_FEEDBACK_ABSORB if absorb else L.WE_FEEDBACK_RECYCLE
+        c.feedback = (L.WE_FEEDBACK_ABSORB if absorb else
+                      L.WE_FEEDBACK_ENDPOINT if endpoint else L.WE_FEEDBACK_RECYCLE)
         c.n_clauses = len(sp)
         for k in range(len(sp)):
             c.tgt_species[k] = int(sp[k])
@@ -177,7 +180,7 @@ def run_config_from(cfg, record_iters=None, resample=True, first_iter=None, init
         recycle_state=cfg.recycle_state, max_steps=cfg.max_steps if max_steps is None else max_steps,
         hist_species=cfg.hist_species, hist_len=cfg.hist_len, resample=resample, mapping=mapping,
         block_threads=block_threads, reweight_period=getattr(cfg, "reweight_period", 0) if resample else 0,
-        absorb=bool(getattr(cfg, "absorb", False)))
+        absorb=bool(getattr(cfg, "absorb", False)), endpoint=bool(getattr(cfg, "endpoint", False)))
 
 
 _OUT_DTYPES = {

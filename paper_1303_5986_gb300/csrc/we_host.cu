@@ -559,8 +559,8 @@ static we_status check_config(const we_network *n, const we_binmap *b, const we_
   long long cap = c->capacity > 0 ? c->capacity : std::max<long long>((long long)c->m_targ * b->n_bins, c->n_init);
   if (cap < c->n_init) return fail(WE_EINVAL, "capacity %lld < n_init %d", cap, c->n_init);
   if (cap * c->n_runs > (1ll << 30)) return fail(WE_EINVAL, "runs x capacity too large");
-  if (c->feedback < 0 || c->feedback > WE_FEEDBACK_ABSORB)
-    return fail(WE_EINVAL, "feedback must be 0, WE_FEEDBACK_RECYCLE or WE_FEEDBACK_ABSORB");
+  if (c->feedback < 0 || c->feedback > WE_FEEDBACK_ENDPOINT)
+    return fail(WE_EINVAL, "feedback must be 0, WE_FEEDBACK_RECYCLE, WE_FEEDBACK_ABSORB or WE_FEEDBACK_ENDPOINT");
   if (c->feedback == WE_FEEDBACK_ABSORB && c->resample)
     return fail(WE_EINVAL, "an absorbing target (brute-force runs) needs resample = 0");
   if (c->feedback) {
@@ -659,7 +659,7 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
     for (int sp = 0; sp < S; ++sp)
       rec[(size_t)r * S + sp] = c->recycle_state ? c->recycle_state[(size_t)r * S + sp] : c->init_states[(size_t)r * c->n_init * S + sp];
   }
-  if (c->feedback == WE_FEEDBACK_RECYCLE)
+  if (c->feedback == WE_FEEDBACK_RECYCLE || c->feedback == WE_FEEDBACK_ENDPOINT)
     for (int r = 0; r < R; ++r) {
       bool in = true;
       for (int k = 0; k < c->n_clauses; ++k) {
@@ -770,7 +770,10 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   EnsView &V = E->prm.ens;
   V.R = R; V.cap = cap; V.S = S; V.m_targ = c->m_targ; V.record_iters = c->record_iters;
   V.first_iter = c->first_iter; V.hist_species = c->hist_species; V.hist_len = c->hist_len;
-  V.feedback = c->feedback; V.n_clauses = c->feedback ? c->n_clauses : 0;
+  // the kernels see the end-of-interval check as no feedback inside the interval
+  V.feedback = c->feedback == WE_FEEDBACK_ENDPOINT ? 0 : c->feedback;
+  V.end_check = c->feedback == WE_FEEDBACK_ENDPOINT ? 1 : 0;
+  V.n_clauses = c->feedback ? c->n_clauses : 0;
   for (int k = 0; k < kMaxClauses; ++k) { V.tgt_species[k] = c->tgt_species[k]; V.tgt_op[k] = c->tgt_op[k]; }
   V.max_steps = c->max_steps > 0 ? c->max_steps : WE_DEFAULT_MAX_STEPS;
   V.tau = c->tau; V.seed = c->seed;

@@ -89,7 +89,8 @@ struct EnsView {
   int32_t record_iters;
   int32_t first_iter;
   int32_t hist_species, hist_len;
-  int32_t feedback, n_clauses;  // feedback: 0 none, 1 recycle, 2 absorb
+  int32_t feedback, n_clauses;  // feedback inside the interval: 0 none, 1 recycle, 2 absorb
+  int32_t end_check;           // 1: the target set is checked at the interval's end only
   int32_t tgt_species[kMaxClauses];
   int32_t tgt_op[kMaxClauses];
   int64_t max_steps;

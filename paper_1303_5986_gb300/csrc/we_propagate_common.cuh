@@ -134,11 +134,16 @@ __device__ __forceinline__ Smem load_smem(const PropagateParams &prm, unsigned c
 
 // Epilogue: store the counts, bin the walker, record the interval's observables.
 __device__ __forceinline__ void finish_walker(const PropagateParams &prm, int r, int g, int par,
-                                              const int32_t *xme, int B, double t, long long nev,
+                                              int32_t *xme, int B, double t, long long nev,
                                               int nrec, int status, int near) {
   const EnsView &E = prm.ens;
   const int ld = E.R * E.cap;
   int32_t *X = E.x[par];
+  // target checked at the interval's end only: a walker found in it goes to the recycle state
+  if (E.end_check && in_target(E, r, xme, B)) {
+    for (int s = 0; s < E.S; ++s) xme[s * B] = E.recycle[r * E.S + s];
+    nrec = 1;
+  }
   for (int s = 0; s < E.S; ++s) X[(size_t)s * ld + g] = xme[s * B];
   E.nrec[g] = nrec;
   E.tlast[g] = t;

@@ -25,10 +25,17 @@
 namespace we {
 
 __device__ __forceinline__ void finish_walker_warp(const PropagateParams &prm, int r, int g, int par,
-                                                   const int32_t *xs, double t, long long nev,
+                                                   int32_t *xs, double t, long long nev,
                                                    int nrec, int status, int near, int lane) {
   const EnsView &E = prm.ens;
   const int ld = E.R * E.cap;
+  // target checked at the interval's end only: a walker found in it goes to the recycle state
+  if (E.end_check && in_target(E, r, xs, 1)) {            // every lane reads the same counts
+    __syncwarp();
+    for (int s = lane; s < E.S; s += 32) xs[s] = E.recycle[r * E.S + s];
+    __syncwarp();
+    nrec = 1;
+  }
   for (int s = lane; s < E.S; s += 32) E.x[par][(size_t)s * ld + g] = xs[s];
   if (lane != 0) return;
   E.nrec[g] = nrec;

@@ -854,3 +854,33 @@ def test_stored_golden_values_are_the_oracles():
     assert round(stored["schlogl_mfpt_82_to_563_s"], -4) == 5e4
     assert round(stored["futile_p_s1_gt_90_t100"], 20) == 2.72e-18
     assert round(stored["epigenetic_mfpt_0_30_to_g1_ge_50_s"], -5) == 1.3e6
+
+
+def test_end_of_interval_target_check_renewal_flux():
+    """Target checked at the end of each interval only (B checked at a prescribed time step,
+    Sec. IV), against the renewal closed form: a pure-birth process X -> X + 1 at rate k from 0,
+    recycled to 0, reaches X >= n at the Erlang(n, k) time T and stays there, so a cycle lasts
+    N = ceil(T / tau) intervals and the long-run flux per interval is 1 / E[N], with
+    E[N] = sum_{m >= 0} P(T > m tau) = sum_m P(Poisson(k m tau) <= n - 1).  Checked at the
+    event instead, the flux is tau k / n; the two differ by about 5 % here, many standard errors."""
+    k, n, tau = 1.0, 5, 0.5
+    R, N, iters, burn = 8, 250, 300, 40
+    en = 0.0
+    for m in range(0, 10000):
+        term = stats.poisson.cdf(n - 1, k * m * tau)
+        en += term
+        if term < 1e-16:
+            break
+    net = W.NetworkSpec(species=["X"], reactants=[[]], products=[[(0, 1)]], rate=[[k]])
+    tgt = W.Target(species=[0], op=[W.configs.OP_GE], threshold=np.full((R, 1), n, dtype=np.int32))
+    expect = {True: 1.0 / en, False: tau * k / n}
+    ses = []
+    for endpoint in (True, False):
+        cfg = W.bruteforce_fpt(net, [0], tgt, N, tau, iters, n_runs=R, name="pure_birth")
+        cfg.absorb = False
+        cfg.endpoint = endpoint
+        per_run = [O.we_run(cfg, r, resample=False)["flux_weight"][burn:].mean() for r in range(R)]
+        mean, se = float(np.mean(per_run)), float(np.std(per_run, ddof=1) / math.sqrt(R))
+        assert abs(mean - expect[endpoint]) < 3 * se, (endpoint, mean, expect[endpoint], se)
+        ses.append(se)
+    assert abs(expect[True] - expect[False]) > 10 * max(ses)

@@ -80,6 +80,7 @@ class WEConfig:
     first_iter: int = 0
     reweight_period: int = 0             # >0: steady-state reweighting every this many iterations
     absorb: bool = False                 # with a target: walkers stop at their first entrance
+    endpoint: bool = False               # with a target: checked at each interval's end only
                                          # (brute-force first-passage runs, no resampling)
     name: str = ""
     notes: dict = field(default_factory=dict)
