@@ -86,7 +86,8 @@ def parse():
     ap.add_argument("--resample-blocks", type=int, default=0,
                     help="one_launch: blocks per run (0: the library's choice)")
     ap.add_argument("--report-iter", type=int, default=-1,
-                    help="also report the SSA events of this iteration of the first timed step (for ncu)")
+                    help="also report the SSA events of this iteration of the first timed step (for ncu; "
+                         "default and batch workloads)")
     ap.add_argument("--batch-iters", type=int, default=0,
                     help="toggle_batch / synthetic_large: WE iterations per step (0: 500 / 100)")
     ap.add_argument("--plain-iters", type=int, default=120000, help="toggle_learned: plain-binning iterations")
@@ -586,6 +587,11 @@ def run_batch_workload(a):
                      "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz; measured beside it by "
                                     "we_measure_alu_peaks (FP64 FMA lanes/s, this GPU)"},
         "cpu_baseline": cb, "e2e": None, "gpu_launches": timed[0].iteration_kernels() * n_iters * a.steps,
+        "report_iter": ({"iteration": a.report_iter,
+                         "ssa_events": int(timed[0].per_iter(P.WE_OUT_EVENTS)[a.report_iter].sum()),
+                         "walkers_propagated": int(timed[0].per_iter(P.WE_OUT_NWALKERS)[a.report_iter - 1].sum())
+                         if a.report_iter > 0 else None}
+                        if 0 <= a.report_iter < n_iters else None),
         "clocks": clk,
     }
     print(json.dumps(line))
