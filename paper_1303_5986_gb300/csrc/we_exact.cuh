@@ -10,6 +10,7 @@
 // positive normal doubles; callers route other cases to the plain floating-point path.
 #pragma once
 #include <cstdint>
+#include <cstring>
 
 #if defined(__CUDACC__)
 #define WE_HD __host__ __device__ __forceinline__
@@ -66,6 +67,48 @@ WE_HD bool ex_u_below_quotient(unsigned long long u_bits, unsigned long long w_b
   if (ex_lt(C, A)) return false;
   if (ex_lt(B, C)) return true;
   return ex_eq(C, B) && (mu & 1ull);   // exact midpoint (needs a 54-bit w; kept for completeness)
+}
+
+// A float with the given exponent field whose significand is the first 23 fraction bits of the
+// double `dbits` (truncated: relative error below 2^-23).
+WE_HD float ex_f32_of(int f32_field, unsigned long long dbits) {
+  const unsigned int fb = ((unsigned int)f32_field << 23) | (unsigned int)((dbits >> 29) & 0x7FFFFFull);
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(fb);
+#else
+  float f;
+  std::memcpy(&f, &fb, 4);
+  return f;
+#endif
+}
+
+WE_HD float ex_fmul(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+
+// The same decision u < fl(w / s) screened in FP32 (u < 1, w <= s, all positive doubles):
+// 1 or 0 where FP32 settles it, -1 where it does not (u below 2^-60, w subnormal, or u within
+// about 2^-19 of the quotient; the caller then takes the exact test).  Both sides are divided
+// by 2^(Fs-1023): with d = Fw - Fs, W = w 2^-(Fs-1023) and S = s 2^-(Fs-1023) in [1, 2) as
+// truncated floats, U the truncated float of u, and P = fl(U S), each within 5 2^-24 of its
+// real value relatively.  P < fl(W (1 - 2^-19)) then gives u < q (1 - 26 2^-24) < fl(q), and
+// P > fl(W (1 + 2^-19)) gives u > q (1 + 27 2^-24) > fl(q) (q = w / s).  For d < -100 the
+// quotient is below 2^-99 and u (>= 2^-60) is not below it.
+WE_HD int ex_u_below_quotient_f32(unsigned long long u_bits, unsigned long long w_bits,
+                                  unsigned long long s_bits) {
+  const int fu = ex_field(u_bits), fw = ex_field(w_bits), d = fw - ex_field(s_bits);
+  if (fu < 1023 - 60 || fw == 0 || d > 0) return -1;
+  if (d < -100) return 0;
+  const float U = ex_f32_of(fu - 1023 + 127, u_bits), S = ex_f32_of(127, s_bits),
+              W = ex_f32_of(127 + d, w_bits);
+  const float P = ex_fmul(U, S);
+  if (P < ex_fmul(W, 1.0f - 0x1p-19f)) return 1;
+  if (P > ex_fmul(W, 1.0f + 0x1p-19f)) return 0;
+  return -1;
 }
 
 // floor((2^64 - 1) / c) for 2 <= c: the reciprocal used by ex_div_small (host side).

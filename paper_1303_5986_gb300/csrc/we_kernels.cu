@@ -180,6 +180,18 @@ __device__ __forceinline__ ResampleCtx resample_ctx(const EnsView &E, int r) {
 // split/merge warps; larger ones by k_gather, whose loads are coalesced across walkers.
 constexpr int kGatherInResample = 8;
 
+// u < fl(w_p / s) for the merge's survivor, s = fl(w_p + w_q) (u, w_p, s as bits of positive
+// doubles, u < 1): screened in FP32 first (settles all but the draws within about 2^-19 of the
+// quotient), then the exact integer test, or the FP64 quotient where weights are too small for it.
+__device__ __forceinline__ bool survivor_keeps(unsigned long long u, unsigned long long wp, unsigned long long s,
+                                               bool exact) {
+  const int f = ex_u_below_quotient_f32(u, wp, s);
+  if (f >= 0) return f != 0;
+  return exact ? ex_u_below_quotient(u, wp, s)
+               : u < (unsigned long long)bits(__ddiv_rn(__longlong_as_double((long long)wp),
+                                                        __longlong_as_double((long long)s)));
+}
+
 // Per-warp shared scratch of the queue form of the merges (bins of up to 128 walkers): the bin's
 // walkers sorted by (weight, slot), and the merged walkers in the order of their keys.
 constexpr int kQueueMax = 128;
@@ -290,8 +302,7 @@ __device__ __forceinline__ void resample_bin(const EnsView &E, int r, const Resa
       const int ip = a_first ? i1 : i2, iq = a_first ? i2 : i1;
       const unsigned long long u_k = __shfl_sync(0xffffffffu, ub.get(km >> 5), km & 31);
       const double wsum = __dadd_rn(__longlong_as_double(wp), __longlong_as_double(wq));
-      const bool keep_p = exact ? ex_u_below_quotient(u_k, (unsigned long long)wp, (unsigned long long)bits(wsum))
-                                : u_k < (unsigned long long)bits(__ddiv_rn(__longlong_as_double(wp), wsum));
+      const bool keep_p = survivor_keeps(u_k, (unsigned long long)wp, (unsigned long long)bits(wsum), exact);
       const long long nw = bits(wsum);
       const int ns = keep_p ? sp : sq, ni = keep_p ? ip : iq;
       int pos = qt;
@@ -373,7 +384,7 @@ __device__ __forceinline__ void resample_bin(const EnsView &E, int r, const Resa
       const int op = a_first ? o1 : o2, oq = a_first ? o2 : o1;
       const unsigned long long u_k = __shfl_sync(0xffffffffu, ub.get(km >> 5), km & 31);
       const double wsum = __dadd_rn(__longlong_as_double(wp), __longlong_as_double(wq));
-      const bool keep_p = ex_u_below_quotient(u_k, (unsigned long long)wp, (unsigned long long)bits(wsum));
+      const bool keep_p = survivor_keeps(u_k, (unsigned long long)wp, (unsigned long long)bits(wsum), true);
       const int osurv = keep_p ? op : oq, odead = keep_p ? oq : op;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {

@@ -56,6 +56,36 @@ int main() {
     ++n_cmp;
     if (want != got) { if (fails++ < 10) std::printf("cmp u=%a w=%a s=%a want %d got %d\n", u, w, (double)s, want, got); }
   }
+  // The FP32 screen: where it answers, the answer is the double comparison's; it leaves few
+  // of the generator's uniforms undecided.  Weights over the whole normal range (and subnormal
+  // ones), w <= s, uniforms of the generator and at, just below and just above the quotient.
+  long n_f32 = 0, n_f32_open = 0, n_f32_gen = 0, n_f32_gen_open = 0;
+  for (long k = 0; k < 4000000; ++k) {
+    const int fw = (int)(g() % 2047), dq = (int)(g() % 240) - 120;
+    const unsigned long long wb = ((unsigned long long)fw << 52) | (g() & 0xFFFFFFFFFFFFFull);
+    const int fq0 = fw + dq, fq = fq0 < 0 ? 0 : (fq0 > 2000 ? 2000 : fq0);
+    const unsigned long long qb = ((unsigned long long)fq << 52) | (g() & 0xFFFFFFFFFFFFFull);
+    const double w = D(wb), q = D(qb);
+    const volatile double s = w + q;
+    if (!(s < INFINITY) || !(s > 0.0) || !(w > 0.0)) continue;
+    const volatile double prob = w / s;
+    double u;
+    switch (k % 5) {
+      case 0: u = (double)(2 * (g() >> 12) + 1) * 0x1p-53; break;
+      case 1: u = prob; break;
+      case 2: u = std::nextafter((double)prob, 0.0); break;
+      case 3: u = std::nextafter((double)prob, 1.0); break;
+      default: u = (double)prob * (1.0 + std::ldexp((double)(g() % 64) - 32.0, -24)); break;
+    }
+    if (!(u > 0.0 && u < 1.0)) continue;
+    const int got = we::ex_u_below_quotient_f32(B(u), wb, B((double)s));
+    ++n_f32;
+    if (k % 5 == 0) ++n_f32_gen;
+    if (got < 0) { ++n_f32_open; if (k % 5 == 0) ++n_f32_gen_open; continue; }
+    const bool want = u < prob;
+    if (want != (got == 1)) { if (fails++ < 10) std::printf("f32 u=%a w=%a s=%a want %d got %d\n", u, w, (double)s, want, got); }
+  }
+  if (n_f32_gen_open * 1000 > n_f32_gen) { ++fails; std::printf("f32 screen leaves %ld of %ld uniforms open\n", n_f32_gen_open, n_f32_gen); }
   // quotients exactly equal to u (s a power of two, w = u s exact).  An exact midpoint
   // w/s = u + ulp(u)/2 cannot occur: it needs the 54-bit odd significand 2 mu + 1 in w.
   for (long k = 0; k < 200000; ++k) {
@@ -69,6 +99,7 @@ int main() {
     ++n_tie;
     if (want != got) { if (fails++ < 10) std::printf("eq u=%a w=%a s=%a\n", u, w, s); }
   }
-  std::printf("%s div=%ld cmp=%ld eq=%ld fails=%ld\n", fails ? "FAIL" : "ok", n_div, n_cmp, n_tie, fails);
+  std::printf("%s div=%ld cmp=%ld eq=%ld f32=%ld (open %ld; uniforms %ld open %ld) fails=%ld\n", fails ? "FAIL" : "ok",
+              n_div, n_cmp, n_tie, n_f32, n_f32_open, n_f32_gen, n_f32_gen_open, fails);
   return fails ? 1 : 0;
 }
