@@ -336,6 +336,29 @@ extern "C" we_status we_binmap_grid(int32_t ndim, const int32_t *species, const 
   return WE_OK;
 }
 
+// Inner edges e_1 .. e_{nb-1} of one grid dimension that are integers in arithmetic progression
+// (e_k = e_1 + (k - 1) h, h a positive integer; any h for nb = 2): first = e_1, step = h, and
+// the device bins a count by division.  Otherwise step = 0 (the device searches the edges).
+// Limits keep count - e_1 within 32 bits for every count.
+static void uniform_inner_edges(const double *e, int nb, int32_t *first, int32_t *step) {
+  *first = 0;
+  *step = 0;
+  if (nb < 2) return;
+  const double lim = 1073741824.0;                         // 2^30
+  auto is_int = [&](double v) { return std::isfinite(v) && std::fabs(v) <= lim && v == std::floor(v); };
+  if (!is_int(e[1])) return;
+  long long h = 1;
+  if (nb >= 3) {
+    if (!is_int(e[2])) return;
+    h = (long long)e[2] - (long long)e[1];
+    if (h < 1 || h > (long long)lim) return;
+  }
+  for (int k = 1; k <= nb - 1; ++k)
+    if (!is_int(e[k]) || (long long)e[k] != (long long)e[1] + (long long)(k - 1) * h) return;
+  *first = (int32_t)e[1];
+  *step = (int32_t)h;
+}
+
 extern "C" void we_binmap_destroy(we_binmap *b) { delete b; }
 extern "C" int32_t we_binmap_n_bins(const we_binmap *b) { return b ? b->n_bins : 0; }
 
@@ -752,7 +775,11 @@ extern "C" we_status we_ensemble_create(const we_network *n, const we_binmap *b,
   }
   BinView &Bv = E->prm.bins;
   Bv.ndim = b->ndim; Bv.n_bins = b->n_bins;
-  for (int d = 0; d < kMaxBinDims; ++d) { Bv.species[d] = b->species[d]; Bv.nb[d] = b->nb[d]; Bv.edge_off[d] = b->edge_off[d]; }
+  for (int d = 0; d < kMaxBinDims; ++d) {
+    Bv.species[d] = b->species[d]; Bv.nb[d] = b->nb[d]; Bv.edge_off[d] = b->edge_off[d];
+    Bv.ufirst[d] = 0; Bv.ustep[d] = 0;
+    if (d < b->ndim) uniform_inner_edges(b->edges.data() + b->edge_off[d], b->nb[d], &Bv.ufirst[d], &Bv.ustep[d]);
+  }
   Bv.edges = at<double>(ws, o.edges);
   Bv.learned = b->learned ? 1 : 0;
   if (b->learned) {

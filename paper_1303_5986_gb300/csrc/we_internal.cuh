@@ -75,6 +75,9 @@ struct BinView {
   int32_t species[kMaxBinDims];
   int32_t nb[kMaxBinDims];
   int32_t edge_off[kMaxBinDims];
+  // Dimensions whose inner edges e_1 .. e_{nb-1} are integers e_1 + (k - 1) h (ustep = h > 0):
+  // the bin of a count comes from one division instead of a search of the edges in memory.
+  int32_t ufirst[kMaxBinDims], ustep[kMaxBinDims];
   const double *edges;
   int32_t learned;             // 1: bins are intervals of the learned coordinate z
   MlpView mlp;

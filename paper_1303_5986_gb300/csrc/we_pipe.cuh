@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
   const int total = E.run_off[E.R];
   const int f = vb * W + lane;
   const bool live = f < total;
-  const int r = !live ? 0 : (E.R == 1 ? 0 : find_run(E.run_off, E.R, f));
-  const int w = live ? f - E.run_off[r] : 0;
+  int r_start = 0;
+  const int r = (!live || E.R == 1) ? 0 : find_run_start(E.run_off, E.R, f, r_start);
+  const int w = live ? f - r_start : 0;
   const uint32_t k0 = (uint32_t)E.seed;
   const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
   const LogTables &LT = *sm.logt;

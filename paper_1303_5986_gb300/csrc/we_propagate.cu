@@ -76,25 +76,28 @@ __global__ void k_build_table(NetView N, const int32_t *base, int species, int s
 template <int P, int LOG2P>
 __global__ void __launch_bounds__(128) k_propagate_direct(PropagateParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Smem sm = load_smem<P>(prm, smem_raw);
   const EnsView &E = prm.ens;
   const int B = blockDim.x, tid = threadIdx.x;
+  // the walker's run, slot and parameters first, so that their loads overlap the prologue
   const int iter = *E.iter;
   const int total = E.run_off[E.R];
   const int f = blockIdx.x * B + tid;
-  if (f >= total) return;
-  const int r = E.R == 1 ? 0 : find_run(E.run_off, E.R, f);
-  const int w = f - E.run_off[r];
+  const bool live = f < total;
+  int r_start = 0;
+  const int r = (!live || E.R == 1) ? 0 : find_run_start(E.run_off, E.R, f, r_start);
+  const int ps = E.param_set[r];
+  const uint32_t k0 = (uint32_t)E.seed;
+  const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
+  const Smem sm = load_smem<P>(prm, smem_raw);
+  if (!live) return;
+  const int w = f - r_start;
   const int g = r * E.cap + w;
   const int par = iter & 1;
   const int ld = E.R * E.cap;
   int32_t *xme = sm.xs + tid;
   for (int s = 0; s < E.S; ++s) xme[s * B] = E.x[par][(size_t)s * ld + g];
-  const int ps = E.param_set[r];
   const double *keff = sm.keff + ps * P;
   const double *Kn = sm.Kn + ps * P;
-  const uint32_t k0 = (uint32_t)E.seed;
-  const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
 
   double nd[2 * P];
   auto rebuild = [&]() {
@@ -162,10 +165,20 @@ __global__ void __launch_bounds__(128) k_propagate_direct(PropagateParams prm) {
 template <int P, int LOG2P>
 __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Smem sm = load_smem<P>(prm, smem_raw);
   const EnsView &E = prm.ens;
   const TableView &TV = prm.tab;
   const int B = blockDim.x, tid = threadIdx.x;
+  // the walker's run, slot and parameters first, so that their loads overlap the prologue
+  const int iter = *E.iter;
+  const int total = E.run_off[E.R];
+  const int f = blockIdx.x * B + tid;
+  const bool live = f < total;
+  int r_start = 0;
+  const int r = (!live || E.R == 1) ? 0 : find_run_start(E.run_off, E.R, f, r_start);
+  const int ps = E.param_set[r];
+  const uint32_t k0 = (uint32_t)E.seed;
+  const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
+  const Smem sm = load_smem<P>(prm, smem_raw);
   int32_t *s_dx = sm.xs + E.S * B;                   // net change of the table species, per reaction
   int32_t *s_dy = s_dx + P;                           // ... and of the second one
   for (int j = tid; j < P; j += B) {
@@ -178,23 +191,16 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
     s_dy[j] = dy;
   }
   __syncthreads();
-  const int iter = *E.iter;
-  const int total = E.run_off[E.R];
-  const int f = blockIdx.x * B + tid;
-  if (f >= total) return;
-  const int r = E.R == 1 ? 0 : find_run(E.run_off, E.R, f);
-  const int w = f - E.run_off[r];
+  if (!live) return;
+  const int w = f - r_start;
   const int g = r * E.cap + w;
   const int par = iter & 1;
   const int ld = E.R * E.cap;
   int32_t *xme = sm.xs + tid;
   for (int s = 0; s < E.S; ++s) xme[s * B] = E.x[par][(size_t)s * ld + g];
-  const int ps = E.param_set[r];
   const double *keff = sm.keff + ps * P;
   const double *Kn = sm.Kn + ps * P;
   const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * TV.lenB * P;
-  const uint32_t k0 = (uint32_t)E.seed;
-  const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
   const int sx = TV.species, sy = TV.species2;
 
   TableRow<P, LOG2P> row;
@@ -273,8 +279,9 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
   const int total = E.run_off[E.R];
   const int f = vb * W + lane;
   const bool live = f < total;
-  const int r = !live ? 0 : (E.R == 1 ? 0 : find_run(E.run_off, E.R, f));
-  const int w = live ? f - E.run_off[r] : 0;
+  int r_start = 0;
+  const int r = (!live || E.R == 1) ? 0 : find_run_start(E.run_off, E.R, f, r_start);
+  const int w = live ? f - r_start : 0;
   const uint32_t k0 = (uint32_t)E.seed;
   const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
   const LogTables &LT = *sm.logt;

@@ -103,12 +103,22 @@ __device__ __forceinline__ int bin_of(const BinView &bv, const int32_t *xs, int 
   int flat = 0;
 #pragma unroll 1
   for (int d = 0; d < bv.ndim; ++d) {
-    const double v = (double)xs[bv.species[d] * stride];
-    const double *e = bv.edges + bv.edge_off[d];
-    int lo = 0, hi = bv.nb[d] - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (e[mid] <= v) lo = mid; else hi = mid - 1;
+    const int xv = xs[bv.species[d] * stride];
+    int lo = 0;
+    if (bv.ustep[d] > 0) {
+      // the last k in 1..nb-1 with e_k = e_1 + (k - 1) h <= x, else 0 (the search below, exactly)
+      if (xv >= bv.ufirst[d]) {
+        const unsigned q = ((unsigned)xv - (unsigned)bv.ufirst[d]) / (unsigned)bv.ustep[d];
+        lo = q >= (unsigned)(bv.nb[d] - 2) ? bv.nb[d] - 1 : (int)q + 1;
+      }
+    } else {
+      const double v = (double)xv;
+      const double *e = bv.edges + bv.edge_off[d];
+      int hi = bv.nb[d] - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (e[mid] <= v) lo = mid; else hi = mid - 1;
+      }
     }
     flat = flat * bv.nb[d] + lo;
   }
@@ -156,6 +166,25 @@ __device__ __forceinline__ int find_run(const int32_t *run_off, int R, int f) {
     if (run_off[mid] <= f) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// The run holding flat walker index f and the run's first index (run_off ascending from
+// run_off[0] = 0).  Up to 16 runs: every offset loaded at once and counted (the last one at or
+// below f is the start), one memory latency instead of a chain of log2(R) dependent loads.
+__device__ __forceinline__ int find_run_start(const int32_t *run_off, int R, int f, int &start) {
+  if (R <= 16) {
+    int r = 0, s = 0;
+#pragma unroll
+    for (int k = 1; k < 16; ++k) {
+      const int v = k < R ? run_off[k] : 0x7FFFFFFF;
+      if (v <= f) { ++r; s = v; }
+    }
+    start = s;
+    return r;
+  }
+  const int r = find_run(run_off, R, f);
+  start = run_off[r];
+  return r;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -143,8 +143,9 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
   const int total = E.run_off[E.R];
   const int f = blockIdx.x;
   if (f >= total) return;
-  const int r = E.R == 1 ? 0 : find_run(E.run_off, E.R, f);
-  const int w = f - E.run_off[r];
+  int r_start = 0;
+  const int r = E.R == 1 ? 0 : find_run_start(E.run_off, E.R, f, r_start);
+  const int w = f - r_start;
   const int g = r * E.cap + w;
   const int par = iter & 1;
   const int ld = E.R * E.cap;

@@ -46,6 +46,22 @@ def test_birth_death_we_with_recycling(mapping):
     _parity(W.birth_death_we(n_iters=60, target=130), 60, mapping=mapping)
 
 
+@pytest.mark.parametrize("edges", [
+    W.uniform_edges(93, 4, 9),                        # integer inner edges 97..125 with an offset
+    np.array([0.0, 103.0, np.inf]),                   # two bins
+    W.uniform_edges(90.5, 3, 8, overflow=True),       # uniform but not integers: searched
+    np.array([0.0, 95, 99, 100, 104, 120, np.inf]),   # integers, not uniform: searched
+], ids=["uniform_offset", "two_bins", "non_integer", "non_uniform"])
+@pytest.mark.parametrize("mapping", [P.WE_MAP_AUTO, P.WE_MAP_THREAD, P.WE_MAP_WARP])
+def test_grid_bin_forms(edges, mapping):
+    """A count's bin by division (integer inner edges in arithmetic progression) or by searching
+    the edges (any other grid) equals the oracle's search, counts below the first inner edge and
+    above the last included (birth-death around X = 100)."""
+    cfg = W.birth_death_we(n_iters=30)
+    cfg.bins = W.GridBins([0], [np.asarray(edges, dtype=np.float64)])
+    _parity(cfg, 30, mapping=mapping)
+
+
 @pytest.mark.parametrize("mapping", MAPPINGS)
 @pytest.mark.parametrize("block", [0, 32])
 def test_schlogl_mfpt_batched_replicas(mapping, block):
