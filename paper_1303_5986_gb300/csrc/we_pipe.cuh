@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
       for (int s = 0; s < E.S; ++s) xme[s * W] = E.recycle[r * E.S + s];
     xme[TV.species * W] = xc;
     if (D == 2) xme[TV.species2 * W] = yc;
-    finish_walker(prm, r, g, par, xme, W, clock_time(clk, E.tau), (long long)nev, nrec, status,
+    finish_walker(prm, r, g, par, iter, xme, W, clock_time(clk, E.tau), (long long)nev, nrec, status,
                   near_tau_units(clk, stop_u));
   }
   }

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(128) k_propagate_direct(PropagateParams prm) {
     }
     rebuild();
   }
-  finish_walker(prm, r, g, par, xme, B, t, nev, nrec, status, near_tau_fp64(E.tau, t, t_stop));
+  finish_walker(prm, r, g, par, iter, xme, B, t, nev, nrec, status, near_tau_fp64(E.tau, t, t_stop));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -178,6 +178,18 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
   const int ps = E.param_set[r];
   const uint32_t k0 = (uint32_t)E.seed;
   const uint32_t k1 = (uint32_t)(E.seed >> 32) + E.run_id[r];
+  const int par = iter & 1;
+  const int ld = E.R * E.cap;
+  const int w = f - r_start;
+  const int g = r * E.cap + w;
+  const int sx = TV.species, sy = TV.species2;
+  // ... and the table species' counts and their row (a count past the table is evaluated below)
+  const int x0 = live ? E.x[par][(size_t)sx * ld + g] : 0;
+  const int y0 = (live && sy >= 0) ? E.x[par][(size_t)sy * ld + g] : 0;
+  const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * TV.lenB * P;
+  const bool in_table = x0 < TV.len && y0 < TV.lenB;
+  TableRow<P, LOG2P> row;
+  if (live && in_table) row.read(tab + ((size_t)x0 * TV.lenB + y0) * P);
   const Smem sm = load_smem<P>(prm, smem_raw);
   int32_t *s_dx = sm.xs + E.S * B;                   // net change of the table species, per reaction
   int32_t *s_dy = s_dx + P;                           // ... and of the second one
@@ -192,25 +204,18 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
   }
   __syncthreads();
   if (!live) return;
-  const int w = f - r_start;
-  const int g = r * E.cap + w;
-  const int par = iter & 1;
-  const int ld = E.R * E.cap;
   int32_t *xme = sm.xs + tid;
   for (int s = 0; s < E.S; ++s) xme[s * B] = E.x[par][(size_t)s * ld + g];
   const double *keff = sm.keff + ps * P;
   const double *Kn = sm.Kn + ps * P;
-  const unsigned long long *tab = TV.rows + (size_t)ps * TV.len * TV.lenB * P;
-  const int sx = TV.species, sy = TV.species2;
 
-  TableRow<P, LOG2P> row;
   double fb[2 * P];
   auto load_row = [&](int xv, int yv) {           // xme holds the current counts
     if (xv < TV.len && yv < TV.lenB) row.read(tab + ((size_t)xv * TV.lenB + yv) * P);
     else row.evaluate(fb, sm.meta, keff, Kn, xme, B, TV.clock_scale);
   };
-  int x = xme[sx * B], y = sy >= 0 ? xme[sy * B] : 0;
-  load_row(x, y);
+  int x = x0, y = y0;
+  if (!in_table) load_row(x, y);
 
   unsigned long long clk = 0;                       // clock units of tau / 2^62
   long long nev = 0;
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(128) k_propagate_table(PropagateParams prm) {
     }
     load_row(x, y);
   }
-  finish_walker(prm, r, g, par, xme, B, clock_time(clk, E.tau), nev, nrec, status, near_tau_units(clk, stop_u));
+  finish_walker(prm, r, g, par, iter, xme, B, clock_time(clk, E.tau), nev, nrec, status, near_tau_units(clk, stop_u));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(128) k_propagate_ws(PropagateParams prm) {
     if (!s_more) break;
     __syncthreads();                                      // s_more is rewritten next round
   }
-  if (warp == 0 && live) finish_walker(prm, r, g, par, xme, W, t, nev, nrec, status, near_tau_fp64(E.tau, t, t_stop));
+  if (warp == 0 && live) finish_walker(prm, r, g, par, iter, xme, W, t, nev, nrec, status, near_tau_fp64(E.tau, t, t_stop));
   }
 }
 

@@ -133,11 +133,15 @@ __device__ __forceinline__ Smem load_smem(const PropagateParams &prm, unsigned c
 }
 
 // Epilogue: store the counts, bin the walker, record the interval's observables.
-__device__ __forceinline__ void finish_walker(const PropagateParams &prm, int r, int g, int par,
+__device__ __forceinline__ void finish_walker(const PropagateParams &prm, int r, int g, int par, int iter,
                                               int32_t *xme, int B, double t, long long nev,
                                               int nrec, int status, int near) {
   const EnsView &E = prm.ens;
   const int ld = E.R * E.cap;
+  // the walker's weight is loaded first, so that the load overlaps the stores and the binning
+  const int slot = iter - E.first_iter;
+  const bool rec = slot >= 0 && slot < E.record_iters;
+  const double wt = rec ? E.w[par][g] : 0.0;
   int32_t *X = E.x[par];
   // target checked at the interval's end only: a walker found in it goes to the recycle state
   if (E.end_check && in_target(E, r, xme, B)) {
@@ -154,9 +158,7 @@ __device__ __forceinline__ void finish_walker(const PropagateParams &prm, int r,
     E.bin[g] = b;
     if (prm.resample) atomicAdd(&E.bin_count[r * prm.bins.n_bins + b], 1);
   }
-  const int slot = *E.iter - E.first_iter;
-  if (slot >= 0 && slot < E.record_iters) {
-    const double wt = E.w[par][g];
+  if (rec) {
     const int o = slot * E.R + r;
     if (nrec) atomicAdd(&E.obs_flux[o], __dmul_rn((double)nrec, wt));
     if (nev) atomicAdd(&E.obs_events[o], (unsigned long long)nev);

@@ -24,11 +24,15 @@
 
 namespace we {
 
-__device__ __forceinline__ void finish_walker_warp(const PropagateParams &prm, int r, int g, int par,
+__device__ __forceinline__ void finish_walker_warp(const PropagateParams &prm, int r, int g, int par, int iter,
                                                    int32_t *xs, double t, long long nev,
                                                    int nrec, int status, int near, int lane) {
   const EnsView &E = prm.ens;
   const int ld = E.R * E.cap;
+  // the walker's weight is loaded first, so that the load overlaps the stores and the binning
+  const int slot = iter - E.first_iter;
+  const bool rec = lane == 0 && slot >= 0 && slot < E.record_iters;
+  const double wt = rec ? E.w[par][g] : 0.0;
   // target checked at the interval's end only: a walker found in it goes to the recycle state
   if (E.end_check && in_target(E, r, xs, 1)) {            // every lane reads the same counts
     __syncwarp();
@@ -47,9 +51,7 @@ __device__ __forceinline__ void finish_walker_warp(const PropagateParams &prm, i
     E.bin[g] = b;
     if (prm.resample) atomicAdd(&E.bin_count[r * prm.bins.n_bins + b], 1);
   }
-  const int slot = *E.iter - E.first_iter;
-  if (slot >= 0 && slot < E.record_iters) {
-    const double wt = E.w[par][g];
+  if (rec) {
     const int o = slot * E.R + r;
     if (nrec) atomicAdd(&E.obs_flux[o], __dmul_rn((double)nrec, wt));
     if (nev) atomicAdd(&E.obs_events[o], (unsigned long long)nev);
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(32) k_propagate_warp(PropagateParams prm) {
     }
   }
   __syncwarp();
-  finish_walker_warp(prm, r, g, par, xs, t, nev, nrec, status, near_tau_fp64(E.tau, t, t_stop), lane);
+  finish_walker_warp(prm, r, g, par, iter, xs, t, nev, nrec, status, near_tau_fp64(E.tau, t, t_stop), lane);
 }
 
 size_t propagate_warp_smem(const NetView &N, int block) {
