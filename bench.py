@@ -55,7 +55,7 @@ FP64_OPS_PER_EVENT_SCHLOGL = 12
 # DRAM bytes (read + write) of one SSA launch on this workload, from an ncu capture of the
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum of the launch of iteration 600, 10,540
 # live walkers in 16,000 slots, as in the timed launches of that stage of the run)
-SSA_TRAFFIC_BYTES = 391936
+SSA_TRAFFIC_BYTES = 393472
 
 
 def with_resample_kernel(ens, a):
