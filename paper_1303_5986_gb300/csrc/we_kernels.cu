@@ -696,12 +696,12 @@ __global__ void k_gather(EnsView E, int resample) {
 
 // One block: counts, run offsets and the walker-count observable; advance the iteration.
 __global__ void k_finalize(EnsView E, int resample) {
-  __shared__ int s_new[1024];
+  __shared__ int s_new[1024], s_old[1024];
   const int iter = *E.iter;
   const int slot = iter - E.first_iter;
   for (int r = threadIdx.x; r < E.R; r += blockDim.x) {
     const int c = new_count(E, r, resample);
-    if (r < 1024) s_new[r] = c;
+    if (r < 1024) { s_new[r] = c; s_old[r] = E.count[r]; }   // both loads in one round trip
     if (slot >= 0 && slot < E.record_iters) E.obs_nw[slot * E.R + r] = c;
   }
   __syncthreads();
@@ -717,7 +717,7 @@ __global__ void k_finalize(EnsView E, int resample) {
   __syncthreads();
   for (int r = threadIdx.x; r < E.R; r += blockDim.x) {
     const int c = r < 1024 ? s_new[r] : new_count(E, r, resample);
-    E.prev_count[r] = E.count[r];
+    E.prev_count[r] = r < 1024 ? s_old[r] : E.count[r];
     E.count[r] = c;
   }
   __syncthreads();
