@@ -7,7 +7,9 @@
 //
 // Both give the same bits as IEEE round-to-nearest-even double arithmetic (checked on the
 // host against the C library's double division in tests/test_exact_arith.py).  Inputs are
-// positive normal doubles; callers route other cases to the plain floating-point path.
+// positive normal doubles; callers route other cases to the plain floating-point path.  The
+// merge decision also has an FP32 screen that answers only where its error bound allows and
+// otherwise defers to the exact test (checked the same way).
 #pragma once
 #include <cstdint>
 #include <cstring>
