@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
   uint32_t *sfl = reinterpret_cast<uint32_t *>(sy + 2 * K * W);         // [2][3][W] flag masks
   unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(
       (reinterpret_cast<uintptr_t>(sfl + 2 * 3 * W) + 15) & ~(uintptr_t)15);
-  __shared__ int s_win, s_win_n, s_rwin, s_rwin_n, s_ps0;
+  __shared__ int s_win, s_win_n, s_rwin, s_rwin_n;
   __shared__ int s_done[2][W];
   // Roles by sub-partition (the 3-blocks build, for launches whose slowest chain sets the time):
   // the state chain goes to this block's warp on the lowest scheduler index, then the clock,
@@ -129,7 +129,6 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
         if (rhi - kWindowMargin >= start && rhi + kWindowMargin < start + n) n2 = 0;   // in the first
         s_rwin = max(min(rhi - n2 / 2, TV.len - n2), 0);
         s_rwin_n = n2;
-        s_ps0 = ps0;                                         // the group's one parameter set
       }
     }
     __syncthreads();
@@ -138,7 +137,7 @@ __global__ void __launch_bounds__(128, MINB) k_propagate_pipe(PropagateParams pr
       win_n = s_win_n;
       rec_lo = s_rwin;
       rec_n = s_rwin_n;
-      const int ps0 = s_ps0;
+      const int ps0 = E.param_set[E.R == 1 ? 0 : find_run(E.run_off, E.R, vb * W)];
       const unsigned long long *src = TV.rows + ((size_t)ps0 * TV.len + win_lo) * P;
       for (int i = threadIdx.x; i < win_n * P; i += blockDim.x) s_tab[i] = src[i];
       const unsigned long long *src2 = TV.rows + ((size_t)ps0 * TV.len + rec_lo) * P;
